@@ -1,0 +1,72 @@
+"""Seeded synthetic inputs shared by the engine's callers, the tests and the
+oracle: connectomes and the parameter-axis specifications of the standard
+workloads. This module holds none of the method's arithmetic (no transfer
+function, no integration, no delay rounding, no grid expansion); both the
+engine and the oracle consume the arrays it returns.
+
+The paper runs on a 68-region connectome shipped as a zip file that is not
+available here (Section 2 "Output", -cf flag); these generators stand in for
+it with the same shape and sparsity class:
+  * weights: symmetric log-normal (sigma = 1) on a Bernoulli(0.3) mask of the
+    upper triangle, mirrored, zero diagonal, normalised to a maximum of 1;
+  * tract lengths: Euclidean distances (mm) between points drawn uniformly in
+    a +-70 mm cube.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Fixed seed per connectome size.
+CONNECTOME_SEEDS = {68: 1, 84: 2, 192: 3, 360: 4}
+
+
+def connectome(n_regions: int, seed: int | None = None, density: float = 0.3,
+               box_mm: float = 70.0) -> tuple[np.ndarray, np.ndarray]:
+    """Return (weights, tract_lengths_mm), both float64 [n][n] row-major."""
+    if seed is None:
+        seed = CONNECTOME_SEEDS.get(n_regions, n_regions)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(n_regions)
+    a = rng.lognormal(mean=0.0, sigma=1.0, size=(n, n))
+    mask = rng.random((n, n)) < density
+    upper = np.triu(a * mask, k=1)
+    w = upper + upper.T
+    mx = w.max()
+    if mx > 0:
+        w = w / mx
+    pts = rng.uniform(-box_mm, box_mm, size=(n, 3))
+    diff = pts[:, None, :] - pts[None, :, :]
+    lengths = np.sqrt((diff * diff).sum(axis=-1))
+    np.fill_diagonal(lengths, 0.0)
+    return np.ascontiguousarray(w), np.ascontiguousarray(lengths)
+
+
+# Parameter axes of the standard workloads: (axis name, (lo, hi, n)) or
+# (axis name, explicit values). Axis names follow the paper's notation.
+SMALL_SWEEP_AXES = [("g", [0.0, 0.1, 0.2, 0.3]), ("b_e", [0.0, 30.0, 60.0, 120.0])]
+PAPER_SCALE_AXES = [("g", (0.0, 0.9, 16)), ("b_e", (0.0, 120.0, 16)),
+                    ("E_L_i", (-80.0, -60.0, 16)), ("tau_w_e", (100.0, 1000.0, 8))]
+SMALL_SWEEP = dict(n_regions=68, axes=SMALL_SWEEP_AXES, speed=4.0, dt=0.1, n_steps=10_000,
+                   tavg_steps=10, seed=1)
+PAPER_SCALE_SWEEP = dict(n_regions=68, axes=PAPER_SCALE_AXES, speed=4.0, dt=0.1,
+                         n_steps=50_000, tavg_steps=10, seed=1)
+
+
+def correlated_series(n_sets: int, n_regions: int, n_samples: int, seed: int,
+                      rho_scale: float = 0.6) -> tuple[np.ndarray, np.ndarray]:
+    """Gaussian series [P][N][T] with a prescribed correlation matrix per set,
+    made by Cholesky mixing of white noise; returns (series, correlations).
+    Used to check FC kernels against a known answer."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xs = np.empty((n_sets, n_regions, n_samples))
+    cs = np.empty((n_sets, n_regions, n_regions))
+    for p in range(n_sets):
+        b = rng.standard_normal((n_regions, n_regions)) * rho_scale / np.sqrt(n_regions)
+        cov = b @ b.T + np.eye(n_regions)
+        d = np.sqrt(np.diag(cov))
+        corr = cov / np.outer(d, d)
+        lo = np.linalg.cholesky(corr)
+        z = rng.standard_normal((n_regions, n_samples))
+        xs[p] = lo @ z * rng.uniform(0.5, 2.0, size=(n_regions, 1)) + rng.uniform(-1, 1, size=(n_regions, 1))
+        cs[p] = corr
+    return xs, cs
