@@ -1,0 +1,236 @@
+/*
+ * tvbx — GB300 (sm_103a) engine for the data-parallel hot path of the
+ * TVB-AdEx parameter-space exploration of arXiv 2311.13337 ("Vast TVB
+ * parameter space exploration"): lock-step time integration of many
+ * independent whole-brain AdEx mean-field simulations, one per parameter
+ * point, and the reduction of their excitatory-rate series to functional
+ * connectivity (FC), FC dynamics (FCD) and per-set summaries.
+ *
+ * Conventions for every entry point:
+ *   - Return value: TVBX_OK (0) or a negative tvbx_status. The message of the
+ *     last failure on the calling thread is returned by tvbx_last_error().
+ *   - Units: time ms, rates kHz inside the model (Hz where a name says _hz),
+ *     voltages mV, conductances nS, capacitance pF, currents pA, tract
+ *     lengths mm, conduction speed m/s (= mm/ms).
+ *   - Inputs passed by pointer are copied before the call returns; the caller
+ *     keeps ownership. Outputs go to caller-owned buffers whose memory kind is
+ *     given by a `mem` argument (TVBX_MEM_HOST or TVBX_MEM_DEVICE). Host output
+ *     calls synchronise the handle's stream before returning.
+ *   - Set order: parameter sets are numbered in grid order (Cartesian product,
+ *     last axis fastest) or in the order of an explicit point list. All per-set
+ *     outputs use that order.
+ *   - A handle is used by one host thread at a time; device work is enqueued
+ *     on the stream passed to tvbx_run (or the default stream when NULL).
+ *   - No entry point falls back to a CPU path: without a usable CUDA device
+ *     they return TVBX_E_CUDA.
+ */
+#ifndef TVBX_H
+#define TVBX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tvbx_status;
+#define TVBX_OK             0
+#define TVBX_E_INVALID_ARG (-1) /* bad pointer, size, range or combination */
+#define TVBX_E_OOM         (-2) /* device allocation failed (P x H x N too large) */
+#define TVBX_E_CUDA        (-3) /* CUDA runtime or launch error, or no device */
+#define TVBX_E_NUMERIC     (-4) /* every set became non-finite */
+#define TVBX_E_TIMEOUT     (-5) /* a bounded device-side wait gave up */
+#define TVBX_E_BAD_STATE   (-6) /* call out of order (e.g. tvbx_fc before tvbx_run) */
+#define TVBX_E_UNSUPPORTED (-7) /* valid request this build does not implement */
+
+#define TVBX_MEM_HOST   0
+#define TVBX_MEM_DEVICE 1
+
+/* Per-set status bits (tvbx_summary). */
+#define TVBX_SET_NONFINITE 1u /* a state variable became NaN or Inf */
+#define TVBX_SET_CLAMP_HI  2u /* E or I was clamped at the upper bound */
+#define TVBX_SET_CLAMP_LO  4u /* E or I was clamped at the lower bound */
+#define TVBX_SET_ZERO_VAR  8u /* a region's E series had zero variance (FC row 0) */
+
+/* Sweepable axes: the per-set parameters of the sweep (Sec. "Vast parameter
+ * space exploration and analysis", Table 4, plus the leak reversals of
+ * Table 3). */
+enum tvbx_axis {
+    TVBX_AXIS_G = 0,     /* global coupling g (Eq. 5), dimensionless */
+    TVBX_AXIS_B_E,       /* spike-frequency adaptation b_e (Eq. 3), pA */
+    TVBX_AXIS_TAU_W_E,   /* adaptation time constant tau_w,e (Eq. 3), ms */
+    TVBX_AXIS_E_L_E,     /* leak reversal of the excitatory population, mV */
+    TVBX_AXIS_E_L_I,     /* leak reversal of the inhibitory population, mV */
+    TVBX_AXIS_SPEED,     /* conduction speed (delays = length / speed), m/s */
+    TVBX_AXIS_A_E,       /* subthreshold adaptation a_e (Eq. 3), nS */
+    TVBX_AXIS_W_NOISE,   /* weight of the OU noise in the excitatory input (Eq. 5) */
+    TVBX_AXIS_CF_EE,     /* constant input c_F{e,e} (Eq. 5), kHz */
+    TVBX_AXIS_CF_EI,     /* c_F{e,i}, kHz */
+    TVBX_AXIS_CF_IE,     /* c_F{i,e}, kHz */
+    TVBX_AXIS_CF_II,     /* c_F{i,i}, kHz */
+    TVBX_N_AXES
+};
+
+/* Model constants shared by all sets of a sweep. The transfer function is
+ * the semi-analytic template the paper cites (Sec. "Transfer Function",
+ * Eq. 5) with the threshold polynomial of Table 1; the rate, covariance and
+ * adaptation equations are Eq. 1-3 and the noise is Eq. 4. */
+typedef struct {
+    double g_L, C_m, E_e, E_i, Q_e, Q_i, tau_e, tau_i;
+    double K_e, K_i;          /* synaptic inputs per cell from the e / i pools */
+    double N_e, N_i;          /* population sizes in the finite-size term of Eq. 2 */
+    double T;                 /* time constant of Eq. 1-2, ms */
+    double P_e[10], P_i[10];  /* Table 1 rows (RS for e, FS for i), mV, in the
+                                 table's column order */
+    double mu0, dmu0, sig0, dsig0, tau0, dtau0; /* normalisation of mu_V, sigma_V, tau_V^N */
+    double rate_floor;        /* added to K*nu so that sigma_V > 0, kHz */
+    double tau_OU, mu_OU, sigma_OU; /* Eq. 4 */
+    double b_i, a_i, tau_w_i; /* inhibitory adaptation */
+    double E_min, E_max;      /* E and I are clamped to [E_min, E_max] after each step, kHz */
+    double E0, I0;            /* initial rates, kHz; also the constant prehistory of E */
+    double defaults[TVBX_N_AXES]; /* value of each axis when it is not swept */
+} tvbx_model;
+
+/* One swept axis: n values, either values[0..n-1] or, when values is NULL,
+ * n equally spaced values in [lo, hi] with both ends included (Sec. "TVB-AdEx
+ * to GPU": "-s0 6 generates six values equally spaced within the defined
+ * range"). */
+typedef struct {
+    int32_t axis;             /* enum tvbx_axis */
+    int32_t n;                /* >= 1 */
+    double lo, hi;
+    const double* values;     /* nullable, host memory, n entries */
+} tvbx_axis_spec;
+
+/* Cartesian product of the axes, last axis fastest: the work items. */
+typedef struct {
+    int32_t n_axes;
+    const tvbx_axis_spec* axes;
+} tvbx_grid;
+
+typedef struct tvbx_sweep tvbx_sweep;
+
+/* Integration settings (Sec. "TVB-AdEx to GPU" and "MPI", last paragraph:
+ * forward Euler; Sec. "Output": the observable is the mean of the inner
+ * steps). */
+typedef struct {
+    double dt_ms;             /* Euler step, ms (> 0) */
+    int64_t n_steps;          /* steps to integrate from the initial state (>= 0) */
+    int32_t tavg_steps;       /* steps per temporal-average sample (>= 1) */
+    int32_t noise_per_set;    /* 0: one OU process per region, shared by all
+                                 sets (the paper's precomputed noise);
+                                 1: an independent process per set and region */
+    uint64_t seed;            /* Philox4x32-10 key */
+    int64_t p_offset;         /* global index of set 0; keys per-set noise so
+                                 that shards of a sweep reproduce it exactly */
+    int32_t transient_samples;/* samples excluded from means, FC, chi */
+    int32_t chunk_steps;      /* steps per kernel launch; 0 = automatic. Must be
+                                 a multiple of tavg_steps when given. */
+} tvbx_run_cfg;
+
+/* FC settings (Sec. "Output": FC from the covariance of the series,
+ * Eq. 6 Pearson; FCD over sliding windows). */
+typedef struct {
+    int32_t precision;        /* TVBX_FC_FP32 (SIMT, FP32 accumulation) */
+    int32_t fcd_window;       /* samples per FCD window; 0 = no FCD */
+    int32_t fcd_step;         /* samples between window starts; fcd_window must
+                                 be a multiple of fcd_step */
+} tvbx_fc_cfg;
+#define TVBX_FC_FP32 0
+
+/* Library version string. */
+const char* tvbx_version(void);
+
+/* Message of the last failed call on this thread ("" if none). Valid until
+ * the next failing call on the same thread. */
+const char* tvbx_last_error(void);
+
+/* Fill *out with the engine's default model constants and axis defaults.
+ * Needs no GPU. */
+tvbx_status tvbx_model_defaults(tvbx_model* out);
+
+/* Create a sweep over a grid of parameter sets.
+ *   weights    [n_regions][n_regions] row-major connectome weights u_kj
+ *              (Eq. 5: region k receives sum_j u_kj nu_e,j(t - tau_kj)); host.
+ *   tract_mm   [n_regions][n_regions] tract lengths in mm (delays tau_kj =
+ *              length / speed, Eq. 5); host, >= 0.
+ *   grid       the swept axes; an empty grid gives one set at the defaults.
+ *   model      constants; NULL = tvbx_model_defaults().
+ *   out        receives the handle (release with tvbx_sweep_destroy).
+ * Errors: TVBX_E_INVALID_ARG for NULL pointers, n_regions < 1, non-finite or
+ * negative lengths, unknown or repeated axes, n < 1; TVBX_E_CUDA without a
+ * device. Device memory is allocated by tvbx_run, not here. */
+tvbx_status tvbx_sweep_create(const double* weights, const double* tract_mm, int32_t n_regions,
+                              const tvbx_grid* grid, const tvbx_model* model, tvbx_sweep** out);
+
+/* Create a sweep over explicit points: params[n_sets][TVBX_N_AXES] (host),
+ * one row per set in enum tvbx_axis order. Otherwise as tvbx_sweep_create. */
+tvbx_status tvbx_sweep_create_points(const double* weights, const double* tract_mm,
+                                     int32_t n_regions, int64_t n_sets, const double* params,
+                                     const tvbx_model* model, tvbx_sweep** out);
+
+/* Number of sets, regions and (after tvbx_run) samples per region. */
+tvbx_status tvbx_sweep_info(const tvbx_sweep* h, int64_t* n_sets, int32_t* n_regions,
+                            int64_t* n_samples);
+
+/* Integrate every set for cfg->n_steps steps from the initial state
+ * (Eq. 1-5, forward Euler; delays rint(length / (speed dt)), ties to even;
+ * constant prehistory E0). Each step, for every (set, region): gather the
+ * delayed coupling from the set's ring buffer, evaluate both transfer
+ * functions with their gradients and Hessians, advance E, I, C_ee, C_ei,
+ * C_ii, W_e, W_i and OU, clamp E and I, write E to the ring, and accumulate
+ * the temporal average. The work is enqueued on `cuda_stream` (a
+ * cudaStream_t; NULL = default stream) and the call returns without waiting.
+ * Allocates (or reuses) the ring buffers [H][N][P_group], the state, and the
+ * E series [P][N][T] (T = n_steps / tavg_steps).
+ * Errors: TVBX_E_INVALID_ARG (dt <= 0, tavg_steps < 1, bad chunk_steps,
+ * transient_samples >= T), TVBX_E_OOM, TVBX_E_CUDA. */
+tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream);
+
+/* Per-set summary of the last run, each output [n_sets] (any may be NULL):
+ * mean E and I rates (Hz) over samples after the transient and regions,
+ * the synchrony index chi = sqrt(Var_t(mean_k E_k) / mean_k Var_t(E_k)),
+ * mean off-diagonal FC (Table 2 "mean_FC"), and the status bits.
+ * chi and mean_fc need the FC pass: they are computed here if tvbx_fc has not
+ * run since the last tvbx_run. Errors: TVBX_E_BAD_STATE before tvbx_run. */
+tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* mean_i_hz,
+                         float* chi, float* mean_fc, uint32_t* status);
+
+/* Copy the E series [n_sets][n_regions][n_samples] (kHz) of the last run. */
+tvbx_status tvbx_series(const tvbx_sweep* h, int32_t mem, float* out);
+
+/* Copy the final state [n_sets][8][n_regions] of the last run, variables in
+ * the order E, I, C_ee, C_ei, C_ii, W_e, W_i, OU (OU is the shared process of
+ * each region when noise is shared). */
+tvbx_status tvbx_state(const tvbx_sweep* h, int32_t mem, float* out);
+
+/* Pearson FC (Eq. 6) of every set's E series after the transient:
+ * fc_out [n_sets][n_regions][n_regions] (nullable), and, when
+ * cfg->fcd_window > 0, FCD fcd_out [n_sets][n_windows][n_windows] with
+ * n_windows = (T' - fcd_window) / fcd_step + 1 over T' = samples after the
+ * transient (nullable). A region with zero variance has a zero FC row and
+ * column and a unit diagonal, and sets TVBX_SET_ZERO_VAR.
+ * Errors: TVBX_E_BAD_STATE before tvbx_run; TVBX_E_INVALID_ARG for a bad
+ * window; TVBX_E_UNSUPPORTED for an unknown precision. */
+tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* fc_out,
+                    float* fcd_out, int32_t* n_windows);
+
+/* The transfer function of one population (Sec. "Transfer Function", Eq. 5
+ * with Table 1) and its derivatives, evaluated on the GPU at n points, with
+ * the same device code the integration uses. pop: 0 = excitatory (RS row,
+ * W = W_e), 1 = inhibitory (FS row). Inputs x_e, x_i (total input rates,
+ * kHz), W (pA), E_L (mV), each [n]; out [n][7] = F, dF/dx_e, dF/dx_i,
+ * d2F/dx_e2, d2F/dx_e dx_i, d2F/dx_i2 (kHz-based units), mu_V (mV). All
+ * arrays live in memory of kind `mem`. model NULL = defaults. Synchronous. */
+tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t n, int32_t mem,
+                                   const float* x_e, const float* x_i, const float* W,
+                                   const float* E_L, float* out);
+
+/* Release the handle and its device memory. NULL is accepted. */
+tvbx_status tvbx_sweep_destroy(tvbx_sweep* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TVBX_H */

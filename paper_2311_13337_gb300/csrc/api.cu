@@ -1,0 +1,775 @@
+// Host side of the tvbx C-ABI (include/tvbx.h): argument checks, grid
+// expansion, delay groups, device memory, chunked launches and exports.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "tvbx.h"
+
+using namespace tvbx;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tvbx_status fail(tvbx_status code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+tvbx_status cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(TVBX_E_OOM, "%s: device allocation failed (%s)", what, cudaGetErrorString(e));
+    return fail(TVBX_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                       \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+    } while (0)
+
+// A device allocation owned by a sweep handle; grows on demand.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t n)
+    {
+        if (n <= bytes && ptr) return cudaSuccess;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        if (n == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&ptr, n);
+        if (e == cudaSuccess) bytes = n;
+        else (void)cudaGetLastError();
+        return e;
+    }
+    void release()
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+void engine_defaults(tvbx_model* m)
+{
+    // Table 1 rows as printed (mV), except the RS entry P_sigmaV.tauN, read
+    // as -40.7 (with the printed +40.7 the second-order system diverges for
+    // every set of the 16-set sweep). Cell, synapse and network constants
+    // follow the AdEx mean-field works the paper cites for the model.
+    static const double Pe[10] = {-48.9, 5.1, -25.0, 1.4, -0.41, 10.5, -36.0, 7.4, 1.2, -40.7};
+    static const double Pi[10] = {-51.4, 0.4, -8.3, 0.2, -0.5, 1.4, -14.6, 4.5, 2.8, 15.3};
+    memset(m, 0, sizeof *m);
+    const double n_tot = 10000.0, p_conn = 0.05, g_inh = 0.2;
+    m->g_L = 10.0; m->C_m = 200.0; m->E_e = 0.0; m->E_i = -80.0;
+    m->Q_e = 1.5; m->Q_i = 5.0; m->tau_e = 5.0; m->tau_i = 5.0;
+    m->K_e = n_tot * p_conn * (1.0 - g_inh);
+    m->K_i = n_tot * p_conn * g_inh;
+    m->N_e = n_tot * (1.0 - g_inh);
+    m->N_i = n_tot * g_inh;
+    m->T = 20.0;
+    memcpy(m->P_e, Pe, sizeof Pe);
+    memcpy(m->P_i, Pi, sizeof Pi);
+    m->mu0 = -60.0; m->dmu0 = 10.0; m->sig0 = 4.0; m->dsig0 = 6.0; m->tau0 = 0.5; m->dtau0 = 1.0;
+    m->rate_floor = 1e-9;
+    m->tau_OU = 5.0; m->mu_OU = 0.0; m->sigma_OU = 1.0;
+    m->b_i = 0.0; m->a_i = 0.0; m->tau_w_i = 1.0;
+    m->E_min = 0.0; m->E_max = 0.2;
+    m->E0 = 1e-3; m->I0 = 1e-3;
+    double* d = m->defaults;
+    d[TVBX_AXIS_G] = 0.0; d[TVBX_AXIS_B_E] = 0.0; d[TVBX_AXIS_TAU_W_E] = 417.0;
+    d[TVBX_AXIS_E_L_E] = -64.0; d[TVBX_AXIS_E_L_I] = -64.0; d[TVBX_AXIS_SPEED] = 4.0;
+    d[TVBX_AXIS_A_E] = 0.0; d[TVBX_AXIS_W_NOISE] = 1e-6;
+    d[TVBX_AXIS_CF_EE] = 0.3e-3; d[TVBX_AXIS_CF_EI] = 0.0; d[TVBX_AXIS_CF_IE] = 0.3e-3;
+    d[TVBX_AXIS_CF_II] = 0.0;
+}
+
+DevModel to_device_model(const tvbx_model& m, double dt)
+{
+    DevModel d;
+    memset(&d, 0, sizeof d);
+    d.g_L = (float)m.g_L; d.C_m = (float)m.C_m; d.E_e = (float)m.E_e; d.E_i = (float)m.E_i;
+    d.qe = (float)(m.Q_e * m.tau_e); d.qi = (float)(m.Q_i * m.tau_i);
+    d.tau_e = (float)m.tau_e; d.tau_i = (float)m.tau_i;
+    d.K_e = (float)m.K_e; d.K_i = (float)m.K_i;
+    d.inv_Ne = (float)(1.0 / m.N_e); d.inv_Ni = (float)(1.0 / m.N_i); d.inv_T = (float)(1.0 / m.T);
+    for (int i = 0; i < 10; ++i) { d.P_e[i] = (float)m.P_e[i]; d.P_i[i] = (float)m.P_i[i]; }
+    d.mu0 = (float)m.mu0; d.inv_dmu0 = (float)(1.0 / m.dmu0);
+    d.sig0 = (float)m.sig0; d.inv_dsig0 = (float)(1.0 / m.dsig0);
+    d.tau0 = (float)m.tau0; d.inv_dtau0 = (float)(1.0 / m.dtau0);
+    d.gL_over_Cm = (float)(m.g_L / m.C_m);
+    d.rate_floor = (float)m.rate_floor;
+    d.b_i = (float)m.b_i; d.a_i = (float)m.a_i; d.inv_tau_w_i = (float)(1.0 / m.tau_w_i);
+    d.E_min = (float)m.E_min; d.E_max = (float)m.E_max;
+    d.E0 = (float)m.E0; d.I0 = (float)m.I0;
+    d.ou_a = (float)(dt / m.tau_OU);
+    d.ou_b = (float)(m.sigma_OU * sqrt(dt) / m.tau_OU);
+    d.ou_mu = (float)m.mu_OU;
+    d.dt = (float)dt;
+    return d;
+}
+
+bool model_ok(const tvbx_model& m)
+{
+    const double pos[] = {m.g_L, m.C_m, m.Q_e, m.Q_i, m.tau_e, m.tau_i, m.K_e, m.K_i, m.N_e, m.N_i,
+                          m.T, m.dmu0, m.dsig0, m.dtau0, m.tau_OU, m.tau_w_i};
+    for (double v : pos)
+        if (!(v > 0.0) || !isfinite(v)) return false;
+    return m.E_max > m.E_min;
+}
+
+int device_ready()
+{
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return 1;
+}
+
+struct Group {
+    double speed;
+    std::vector<int64_t> sets;      // external indices
+    int32_t H = 0;
+    std::vector<int32_t> row_ptr;
+    std::vector<uint32_t> col_dly;
+    std::vector<float> w;
+    int64_t ring_offset = 0;        // floats into the ring allocation
+    int32_t p_base = 0;
+};
+
+}  // namespace
+
+struct tvbx_sweep {
+    int32_t N = 0;
+    int64_t P = 0;
+    std::vector<double> W, L;       // [N][N]
+    std::vector<double> prm;        // [P][TVBX_N_AXES], external order
+    tvbx_model model;
+
+    // products of the last run
+    bool ran = false;
+    bool fc_valid = false;
+    tvbx_run_cfg cfg{};
+    int64_t T = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<int64_t> perm;      // internal -> external
+    bool identity = true;
+    int32_t pb = 16;
+
+    DevBuf d_prm, d_ext, d_state, d_status, d_ring, d_series, d_ou_table, d_ou_state;
+    DevBuf d_csr_row, d_csr_cd, d_csr_w, d_groups, d_tiles;
+    DevBuf d_blocks, d_fc, d_chi, d_meanfc, d_vec, d_fcd, d_tmp, d_perm, d_mean_e, d_mean_i;
+
+    ~tvbx_sweep()
+    {
+        DevBuf* all[] = {&d_prm, &d_ext, &d_state, &d_status, &d_ring, &d_series, &d_ou_table,
+                         &d_ou_state, &d_csr_row, &d_csr_cd, &d_csr_w, &d_groups, &d_tiles,
+                         &d_blocks, &d_fc, &d_chi, &d_meanfc, &d_vec, &d_fcd, &d_tmp, &d_perm,
+                         &d_mean_e, &d_mean_i};
+        for (DevBuf* b : all) b->release();
+    }
+};
+
+// ---------------------------------------------------------------------------
+// permutation / transposition kernels for exports (internal -> external order)
+// ---------------------------------------------------------------------------
+__global__ void gather_rows_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                   const int64_t* __restrict__ perm, int64_t rows, int64_t len)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * len;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / len, c = i - r * len;
+        out[perm[r] * len + c] = in[i];
+    }
+}
+__global__ void gather_u32_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                  const int64_t* __restrict__ perm, int64_t rows)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[perm[i]] = in[i];
+}
+// series [T][N][P] (internal) -> out [P][N][T] (external)
+__global__ void series_export_kernel(const float* __restrict__ X, float* __restrict__ out,
+                                     const int64_t* __restrict__ perm, int64_t T, int32_t N, int64_t P)
+{
+    const int64_t total = T * N * P;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i % P, rest = i / P, k = rest % N, t = rest / N;
+        out[(perm[p] * N + k) * T + t] = X[i];
+    }
+}
+// state [SV][N][P] -> out [P][8][N]; shared OU from ou_state[k]
+__global__ void state_export_kernel(const float* __restrict__ S, const float* __restrict__ ou_state,
+                                    float* __restrict__ out, const int64_t* __restrict__ perm, int32_t N,
+                                    int64_t P)
+{
+    const int64_t total = (int64_t)8 * N * P;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i % P, rest = i / P, k = rest % N, v = rest / N;
+        float x = S[i];
+        if (v == SV_OU && ou_state) x = ou_state[k];
+        out[(perm[p] * 8 + v) * N + k] = x;
+    }
+}
+
+namespace {
+
+int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 8192); }
+
+tvbx_status copy_out(void* dst, const void* src, size_t bytes, int32_t mem, cudaStream_t s)
+{
+    if (bytes == 0) return TVBX_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, mem == TVBX_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s),
+       "copy out");
+    if (mem == TVBX_MEM_HOST) CK(cudaStreamSynchronize(s), "synchronize");
+    return TVBX_OK;
+}
+
+// Copy per-set rows (internal order, device) to `dst` in external order.
+tvbx_status export_rows(tvbx_sweep* h, const float* src, int64_t len, int32_t mem, float* dst)
+{
+    const size_t bytes = sizeof(float) * (size_t)h->P * len;
+    if (h->identity) return copy_out(dst, src, bytes, mem, h->stream);
+    float* target = dst;
+    if (mem == TVBX_MEM_HOST) {
+        CK(h->d_tmp.ensure(bytes), "export buffer");
+        target = h->d_tmp.as<float>();
+    }
+    gather_rows_kernel<<<grid_for(h->P * len), 256, 0, h->stream>>>(src, target, h->d_perm.as<int64_t>(), h->P,
+                                                                       len);
+    CK(cudaGetLastError(), "gather rows");
+    if (mem == TVBX_MEM_HOST) return copy_out(dst, target, bytes, mem, h->stream);
+    return TVBX_OK;
+}
+
+tvbx_status check_mem(int32_t mem)
+{
+    if (mem != TVBX_MEM_HOST && mem != TVBX_MEM_DEVICE)
+        return fail(TVBX_E_INVALID_ARG, "mem must be TVBX_MEM_HOST or TVBX_MEM_DEVICE");
+    return TVBX_OK;
+}
+
+tvbx_status create_common(const double* weights, const double* tract_mm, int32_t n_regions,
+                          const tvbx_model* model, tvbx_sweep** out, tvbx_sweep** made)
+{
+    if (!weights || !tract_mm || !out) return fail(TVBX_E_INVALID_ARG, "NULL weights, tract_mm or out");
+    if (n_regions < 1 || n_regions > 65535) return fail(TVBX_E_INVALID_ARG, "n_regions must be in [1, 65535]");
+    const size_t nn = (size_t)n_regions * n_regions;
+    for (size_t i = 0; i < nn; ++i) {
+        if (!isfinite(weights[i])) return fail(TVBX_E_INVALID_ARG, "non-finite weight at %zu", i);
+        if (!isfinite(tract_mm[i]) || tract_mm[i] < 0.0)
+            return fail(TVBX_E_INVALID_ARG, "tract length at %zu must be finite and >= 0", i);
+    }
+    if (!device_ready()) return fail(TVBX_E_CUDA, "no CUDA device available");
+    tvbx_sweep* h = new tvbx_sweep();
+    h->N = n_regions;
+    h->W.assign(weights, weights + nn);
+    h->L.assign(tract_mm, tract_mm + nn);
+    if (model) h->model = *model;
+    else engine_defaults(&h->model);
+    if (!model_ok(h->model)) {
+        delete h;
+        return fail(TVBX_E_INVALID_ARG, "model constants must be positive where they divide");
+    }
+    *made = h;
+    return TVBX_OK;
+}
+
+// Build the speed groups for dt: delays, CSR and ring depth per distinct speed.
+tvbx_status build_groups(tvbx_sweep* h, double dt, std::vector<Group>& groups)
+{
+    std::map<double, int> index;
+    for (int64_t p = 0; p < h->P; ++p) {
+        const double v = h->prm[p * TVBX_N_AXES + TVBX_AXIS_SPEED];
+        if (!(v > 0.0) || !isfinite(v)) return fail(TVBX_E_INVALID_ARG, "set %lld: speed must be > 0", (long long)p);
+        auto it = index.find(v);
+        if (it == index.end()) {
+            index[v] = (int)groups.size();
+            groups.push_back(Group{});
+            groups.back().speed = v;
+            it = index.find(v);
+        }
+        groups[it->second].sets.push_back(p);
+    }
+    const int N = h->N;
+    for (Group& g : groups) {
+        g.row_ptr.assign(N + 1, 0);
+        int64_t dmax = 0;
+        for (int k = 0; k < N; ++k) {
+            for (int j = 0; j < N; ++j) {
+                const double w = h->W[(size_t)k * N + j];
+                if (w == 0.0) continue;
+                // delay in steps: rint (ties to even) of length / (speed dt), in FP64
+                const double steps = rint(h->L[(size_t)k * N + j] / (g.speed * dt));
+                if (steps > 65535.0) return fail(TVBX_E_UNSUPPORTED, "delay of %g steps exceeds 65535", steps);
+                const int64_t d = steps < 0 ? 0 : (int64_t)steps;
+                dmax = std::max(dmax, d);
+                g.col_dly.push_back(((uint32_t)d << 16) | (uint32_t)j);
+                g.w.push_back((float)w);
+            }
+            g.row_ptr[k + 1] = (int32_t)g.col_dly.size();
+        }
+        g.H = (int32_t)(dmax + 2);
+    }
+    return TVBX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tvbx_version(void) { return "tvbx 0.1 (sm_103a)"; }
+
+const char* tvbx_last_error(void) { return g_last_error.c_str(); }
+
+tvbx_status tvbx_model_defaults(tvbx_model* out)
+{
+    if (!out) return fail(TVBX_E_INVALID_ARG, "NULL out");
+    engine_defaults(out);
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_sweep_create_points(const double* weights, const double* tract_mm, int32_t n_regions,
+                                     int64_t n_sets, const double* params, const tvbx_model* model,
+                                     tvbx_sweep** out)
+{
+    if (n_sets < 1 || n_sets > (int64_t)INT32_MAX) return fail(TVBX_E_INVALID_ARG, "n_sets must be in [1, 2^31)");
+    if (!params) return fail(TVBX_E_INVALID_ARG, "NULL params");
+    for (int64_t i = 0; i < n_sets * TVBX_N_AXES; ++i)
+        if (isinf(params[i])) return fail(TVBX_E_INVALID_ARG, "infinite parameter at %lld", (long long)i);
+    tvbx_sweep* h = nullptr;
+    tvbx_status st = create_common(weights, tract_mm, n_regions, model, out, &h);
+    if (st != TVBX_OK) return st;
+    h->P = n_sets;
+    h->prm.assign(params, params + n_sets * TVBX_N_AXES);
+    *out = h;
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_sweep_create(const double* weights, const double* tract_mm, int32_t n_regions,
+                              const tvbx_grid* grid, const tvbx_model* model, tvbx_sweep** out)
+{
+    tvbx_model m;
+    if (model) m = *model;
+    else engine_defaults(&m);
+    std::vector<std::vector<double>> vals;
+    std::vector<int> axes;
+    int64_t P = 1;
+    if (grid && grid->n_axes > 0) {
+        if (!grid->axes) return fail(TVBX_E_INVALID_ARG, "grid->axes is NULL");
+        for (int a = 0; a < grid->n_axes; ++a) {
+            const tvbx_axis_spec& s = grid->axes[a];
+            if (s.axis < 0 || s.axis >= TVBX_N_AXES) return fail(TVBX_E_INVALID_ARG, "unknown axis %d", s.axis);
+            if (std::find(axes.begin(), axes.end(), s.axis) != axes.end())
+                return fail(TVBX_E_INVALID_ARG, "axis %d repeated", s.axis);
+            if (s.n < 1) return fail(TVBX_E_INVALID_ARG, "axis %d: n must be >= 1", s.axis);
+            std::vector<double> v((size_t)s.n);
+            for (int i = 0; i < s.n; ++i) {
+                if (s.values) v[i] = s.values[i];
+                else v[i] = s.n > 1 ? s.lo + (s.hi - s.lo) * (double)i / (double)(s.n - 1) : s.lo;
+            }
+            axes.push_back(s.axis);
+            vals.push_back(v);
+            P *= s.n;
+            if (P > (int64_t)INT32_MAX) return fail(TVBX_E_INVALID_ARG, "grid has more than 2^31 sets");
+        }
+    }
+    std::vector<double> prm((size_t)P * TVBX_N_AXES);
+    for (int64_t p = 0; p < P; ++p) {
+        double* row = prm.data() + p * TVBX_N_AXES;
+        for (int a = 0; a < TVBX_N_AXES; ++a) row[a] = m.defaults[a];
+        int64_t rem = p;
+        for (int a = (int)axes.size() - 1; a >= 0; --a) {   // last axis fastest
+            const int64_t n = (int64_t)vals[a].size();
+            row[axes[a]] = vals[a][rem % n];
+            rem /= n;
+        }
+    }
+    return tvbx_sweep_create_points(weights, tract_mm, n_regions, P, prm.data(), &m, out);
+}
+
+tvbx_status tvbx_sweep_info(const tvbx_sweep* h, int64_t* n_sets, int32_t* n_regions, int64_t* n_samples)
+{
+    if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
+    if (n_sets) *n_sets = h->P;
+    if (n_regions) *n_regions = h->N;
+    if (n_samples) *n_samples = h->ran ? h->T : 0;
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
+{
+    if (!h || !cfg) return fail(TVBX_E_INVALID_ARG, "NULL handle or cfg");
+    const tvbx_run_cfg c = *cfg;
+    if (!(c.dt_ms > 0.0) || !isfinite(c.dt_ms)) return fail(TVBX_E_INVALID_ARG, "dt_ms must be > 0");
+    if (c.n_steps < 0 || c.n_steps > ((int64_t)1 << 32) - 2)
+        return fail(TVBX_E_INVALID_ARG, "n_steps must be in [0, 2^32 - 1)");
+    if (c.tavg_steps < 1) return fail(TVBX_E_INVALID_ARG, "tavg_steps must be >= 1");
+    if (c.chunk_steps < 0 || (c.chunk_steps > 0 && c.chunk_steps % c.tavg_steps != 0))
+        return fail(TVBX_E_INVALID_ARG, "chunk_steps must be 0 or a positive multiple of tavg_steps");
+    const int64_t T = c.n_steps / c.tavg_steps;
+    if (c.transient_samples < 0 || (T > 0 && c.transient_samples >= T))
+        return fail(TVBX_E_INVALID_ARG, "transient_samples must be in [0, n_samples)");
+    if (c.p_offset < 0) return fail(TVBX_E_INVALID_ARG, "p_offset must be >= 0");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    h->stream = s;
+    h->ran = false;
+    h->fc_valid = false;
+
+    std::vector<Group> groups;
+    tvbx_status st = build_groups(h, c.dt_ms, groups);
+    if (st != TVBX_OK) return st;
+    const int N = h->N;
+    const int64_t P = h->P;
+
+    // internal order: sets grouped by speed
+    h->perm.clear();
+    int64_t ring_floats = 0;
+    for (Group& g : groups) {
+        g.p_base = (int32_t)h->perm.size();
+        g.ring_offset = ring_floats;
+        ring_floats += (int64_t)g.H * N * (int64_t)g.sets.size();
+        for (int64_t e : g.sets) h->perm.push_back(e);
+    }
+    h->identity = true;
+    for (int64_t i = 0; i < P; ++i)
+        if (h->perm[i] != i) { h->identity = false; break; }
+
+    // per-set parameters in internal order, SoA
+    std::vector<float> prm_soa((size_t)TVBX_N_AXES * P);
+    for (int64_t i = 0; i < P; ++i)
+        for (int a = 0; a < TVBX_N_AXES; ++a)
+            prm_soa[(size_t)a * P + i] = (float)h->prm[h->perm[i] * TVBX_N_AXES + a];
+
+    // tiles of pb sets; pb from the smem budget
+    int pb = 16;
+    while (pb > 8 && sim_smem_bytes(N, pb) > 200 * 1024) pb /= 2;
+    if (sim_smem_bytes(N, pb) > 200 * 1024) return fail(TVBX_E_UNSUPPORTED, "n_regions %d too large", N);
+    h->pb = pb;
+    std::vector<TileDev> tiles;
+    std::vector<GroupDev> gdev(groups.size());
+    std::vector<int32_t> all_row;
+    std::vector<uint32_t> all_cd;
+    std::vector<float> all_w;
+    std::vector<int64_t> row_off(groups.size()), nz_off(groups.size());
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        Group& g = groups[gi];
+        row_off[gi] = (int64_t)all_row.size();
+        nz_off[gi] = (int64_t)all_cd.size();
+        all_row.insert(all_row.end(), g.row_ptr.begin(), g.row_ptr.end());
+        all_cd.insert(all_cd.end(), g.col_dly.begin(), g.col_dly.end());
+        all_w.insert(all_w.end(), g.w.begin(), g.w.end());
+        const int32_t Pg = (int32_t)g.sets.size();
+        for (int32_t q0 = 0; q0 < Pg; q0 += pb) tiles.push_back(TileDev{(int32_t)gi, q0, std::min(pb, Pg - q0), 0});
+    }
+    if (all_cd.empty()) { all_cd.push_back(0); all_w.push_back(0.f); }
+
+    // device memory
+    CK(h->d_prm.ensure(sizeof(float) * prm_soa.size()), "parameters");
+    CK(h->d_ext.ensure(sizeof(int64_t) * P), "set index");
+    CK(h->d_perm.ensure(sizeof(int64_t) * P), "set index");
+    CK(h->d_state.ensure(sizeof(float) * (size_t)SV_COUNT * N * P), "state");
+    CK(h->d_status.ensure(sizeof(uint32_t) * P), "status");
+    CK(h->d_ring.ensure(sizeof(float) * (size_t)std::max<int64_t>(ring_floats, 1)), "ring buffers");
+    CK(h->d_series.ensure(sizeof(float) * (size_t)std::max<int64_t>(T * N * P, 1)), "series");
+    CK(h->d_ou_state.ensure(sizeof(float) * N), "OU state");
+    CK(h->d_csr_row.ensure(sizeof(int32_t) * all_row.size()), "CSR");
+    CK(h->d_csr_cd.ensure(sizeof(uint32_t) * all_cd.size()), "CSR");
+    CK(h->d_csr_w.ensure(sizeof(float) * all_w.size()), "CSR");
+    CK(h->d_groups.ensure(sizeof(GroupDev) * gdev.size()), "groups");
+    CK(h->d_tiles.ensure(sizeof(TileDev) * std::max<size_t>(tiles.size(), 1)), "tiles");
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        GroupDev& d = gdev[gi];
+        d.ring = h->d_ring.as<float>() + groups[gi].ring_offset;
+        d.row_ptr = h->d_csr_row.as<int32_t>() + row_off[gi];
+        d.col_dly = h->d_csr_cd.as<uint32_t>() + nz_off[gi];
+        d.w = h->d_csr_w.as<float>() + nz_off[gi];
+        d.H = groups[gi].H;
+        d.P_g = (int32_t)groups[gi].sets.size();
+        d.p_base = groups[gi].p_base;
+        d.pad = 0;
+    }
+    CK(cudaMemcpyAsync(h->d_prm.ptr, prm_soa.data(), sizeof(float) * prm_soa.size(), cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaMemcpyAsync(h->d_ext.ptr, h->perm.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaMemcpyAsync(h->d_perm.ptr, h->perm.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaMemcpyAsync(h->d_csr_row.ptr, all_row.data(), sizeof(int32_t) * all_row.size(), cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaMemcpyAsync(h->d_csr_cd.ptr, all_cd.data(), sizeof(uint32_t) * all_cd.size(), cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaMemcpyAsync(h->d_csr_w.ptr, all_w.data(), sizeof(float) * all_w.size(), cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaMemcpyAsync(h->d_groups.ptr, gdev.data(), sizeof(GroupDev) * gdev.size(), cudaMemcpyHostToDevice, s), "upload");
+    if (!tiles.empty())
+        CK(cudaMemcpyAsync(h->d_tiles.ptr, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice, s), "upload");
+    CK(cudaMemsetAsync(h->d_ou_state.ptr, 0, sizeof(float) * N, s), "OU state");
+
+    // chunking: keep each launch around 4-8 thousand steps
+    int64_t chunk = c.chunk_steps > 0 ? c.chunk_steps : 0;
+    if (chunk == 0) {
+        chunk = (int64_t)c.tavg_steps * std::max<int64_t>(1, 5000 / c.tavg_steps);
+        if (chunk <= 0) chunk = c.tavg_steps;
+    }
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(c.n_steps, 1));
+    if (!c.noise_per_set) CK(h->d_ou_table.ensure(sizeof(float) * (size_t)chunk * N), "OU table");
+
+    SimArgs a;
+    memset(&a, 0, sizeof a);
+    a.m = to_device_model(h->model, c.dt_ms);
+    a.groups = h->d_groups.as<GroupDev>();
+    a.tiles = h->d_tiles.as<TileDev>();
+    a.prm = h->d_prm.as<float>();
+    a.ext_index = h->d_ext.as<int64_t>();
+    a.state = h->d_state.as<float>();
+    a.series = h->d_series.as<float>();
+    a.ou_table = c.noise_per_set ? nullptr : h->d_ou_table.as<float>();
+    a.status = h->d_status.as<uint32_t>();
+    a.N = N;
+    a.P = (int32_t)P;
+    a.ts = c.tavg_steps;
+    a.T = T;
+    a.transient = c.transient_samples;
+    a.noise_per_set = c.noise_per_set ? 1 : 0;
+    a.seed = c.seed;
+    a.p_offset = c.p_offset;
+
+    CK(launch_init_state(a, s), "init state");
+    for (size_t gi = 0; gi < groups.size(); ++gi)
+        CK(launch_init_ring(gdev[gi].ring, (int64_t)gdev[gi].H * N * gdev[gi].P_g, a.m.E0, s), "init ring");
+    for (int64_t n0 = 0; n0 < c.n_steps; n0 += chunk) {
+        a.n0 = n0;
+        a.n_chunk = (int32_t)std::min<int64_t>(chunk, c.n_steps - n0);
+        if (!c.noise_per_set)
+            CK(launch_ou_table(a.m, h->d_ou_table.as<float>(), h->d_ou_state.as<float>(), N, n0, a.n_chunk, c.seed, s),
+               "OU table");
+        CK(launch_sim_chunk(a, (int32_t)tiles.size(), pb, s), "simulation chunk");
+    }
+    h->cfg = c;
+    h->T = T;
+    h->ran = true;
+    return TVBX_OK;
+}
+
+static tvbx_status run_fc(tvbx_sweep* h, int32_t fcd_window, int32_t fcd_step, int32_t* nw_out)
+{
+    const int N = h->N;
+    const int64_t P = h->P;
+    const int64_t t0 = h->cfg.transient_samples, t1 = h->T;
+    const int64_t Tn = t1 - t0;
+    if (Tn < 1) return fail(TVBX_E_BAD_STATE, "the last run produced no samples");
+    int32_t blk = 0, n_blocks = 1, m = 0, nw = 0;
+    if (fcd_window > 0) {
+        if (fcd_step < 1 || fcd_window % fcd_step != 0)
+            return fail(TVBX_E_INVALID_ARG, "fcd_window must be a positive multiple of fcd_step");
+        if (fcd_window > Tn) return fail(TVBX_E_INVALID_ARG, "fcd_window exceeds the samples after the transient");
+        if (N < 3) return fail(TVBX_E_INVALID_ARG, "FCD needs at least 3 regions");
+        blk = fcd_step;
+        n_blocks = (int32_t)((Tn + blk - 1) / blk);
+        m = fcd_window / fcd_step;
+        nw = (int32_t)((Tn - fcd_window) / fcd_step + 1);
+    }
+    const size_t stride_b = (size_t)N * N + N;
+    CK(h->d_blocks.ensure(sizeof(float) * (size_t)P * n_blocks * stride_b), "FC block moments");
+    CK(h->d_fc.ensure(sizeof(float) * (size_t)P * N * N), "FC");
+    CK(h->d_chi.ensure(sizeof(float) * P), "chi");
+    CK(h->d_meanfc.ensure(sizeof(float) * P), "mean FC");
+    FcArgs f;
+    memset(&f, 0, sizeof f);
+    f.series = h->d_series.as<float>();
+    f.state = h->d_state.as<float>();
+    f.N = N;
+    f.P = (int32_t)P;
+    f.t_begin = t0;
+    f.t_end = t1;
+    f.blk = blk;
+    f.n_blocks = n_blocks;
+    f.blocks = h->d_blocks.as<float>();
+    f.fc = h->d_fc.as<float>();
+    f.chi = h->d_chi.as<float>();
+    f.mean_fc = h->d_meanfc.as<float>();
+    f.status = h->d_status.as<uint32_t>();
+    CK(launch_fc(f, h->stream), "FC");
+    if (fcd_window > 0) {
+        const size_t M = (size_t)N * (N - 1) / 2;
+        CK(h->d_vec.ensure(sizeof(float) * (size_t)P * nw * M), "FCD vectors");
+        CK(h->d_fcd.ensure(sizeof(float) * (size_t)P * nw * nw), "FCD");
+        CK(launch_fcd(f.blocks, (int32_t)P, N, n_blocks, m, nw, fcd_window, h->d_vec.as<float>(), h->d_fcd.as<float>(),
+                      h->stream),
+           "FCD");
+    }
+    if (nw_out) *nw_out = nw;
+    h->fc_valid = true;
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* fc_out, float* fcd_out,
+                    int32_t* n_windows)
+{
+    if (!h || !cfg) return fail(TVBX_E_INVALID_ARG, "NULL handle or cfg");
+    if (check_mem(mem)) return TVBX_E_INVALID_ARG;
+    if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_fc before tvbx_run");
+    if (cfg->precision != TVBX_FC_FP32) return fail(TVBX_E_UNSUPPORTED, "FC precision %d", cfg->precision);
+    if (cfg->fcd_window < 0) return fail(TVBX_E_INVALID_ARG, "fcd_window must be >= 0");
+    int32_t nw = 0;
+    tvbx_status st = run_fc(h, cfg->fcd_window, cfg->fcd_step, &nw);
+    if (st != TVBX_OK) return st;
+    if (n_windows) *n_windows = nw;
+    if (fc_out) {
+        st = export_rows(h, h->d_fc.as<float>(), (int64_t)h->N * h->N, mem, fc_out);
+        if (st != TVBX_OK) return st;
+    }
+    if (fcd_out && cfg->fcd_window > 0) {
+        st = export_rows(h, h->d_fcd.as<float>(), (int64_t)nw * nw, mem, fcd_out);
+        if (st != TVBX_OK) return st;
+    }
+    if (mem == TVBX_MEM_HOST) CK(cudaStreamSynchronize(h->stream), "synchronize");
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* mean_i_hz, float* chi,
+                         float* mean_fc, uint32_t* status)
+{
+    if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
+    if (check_mem(mem)) return TVBX_E_INVALID_ARG;
+    if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_summary before tvbx_run");
+    const int64_t P = h->P;
+    if ((chi || mean_fc || status) && !h->fc_valid) {
+        tvbx_status st = run_fc(h, 0, 0, nullptr);
+        if (st != TVBX_OK) return st;
+    }
+    tvbx_status st = TVBX_OK;
+    if (mean_e_hz || mean_i_hz) {
+        CK(h->d_mean_e.ensure(sizeof(float) * P), "summary");
+        CK(h->d_mean_i.ensure(sizeof(float) * P), "summary");
+        CK(launch_summary(h->d_state.as<float>(), h->N, (int32_t)P, h->T - h->cfg.transient_samples,
+                          h->d_mean_e.as<float>(), h->d_mean_i.as<float>(), h->stream),
+           "summary");
+        if (mean_e_hz && (st = export_rows(h, h->d_mean_e.as<float>(), 1, mem, mean_e_hz))) return st;
+        if (mean_i_hz && (st = export_rows(h, h->d_mean_i.as<float>(), 1, mem, mean_i_hz))) return st;
+    }
+    if (chi && (st = export_rows(h, h->d_chi.as<float>(), 1, mem, chi))) return st;
+    if (mean_fc && (st = export_rows(h, h->d_meanfc.as<float>(), 1, mem, mean_fc))) return st;
+    if (status) {
+        uint32_t* target = status;
+        if (!h->identity) {
+            CK(h->d_tmp.ensure(sizeof(uint32_t) * P), "export buffer");
+            target = mem == TVBX_MEM_HOST ? h->d_tmp.as<uint32_t>() : status;
+            gather_u32_kernel<<<grid_for(P), 256, 0, h->stream>>>(h->d_status.as<uint32_t>(), target,
+                                                                   h->d_perm.as<int64_t>(), P);
+            CK(cudaGetLastError(), "gather status");
+            if (mem == TVBX_MEM_HOST && (st = copy_out(status, target, sizeof(uint32_t) * P, mem, h->stream))) return st;
+        } else if ((st = copy_out(status, h->d_status.ptr, sizeof(uint32_t) * P, mem, h->stream))) {
+            return st;
+        }
+    }
+    if (mem == TVBX_MEM_HOST) CK(cudaStreamSynchronize(h->stream), "synchronize");
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_series(const tvbx_sweep* hc, int32_t mem, float* out)
+{
+    tvbx_sweep* h = const_cast<tvbx_sweep*>(hc);
+    if (!h || !out) return fail(TVBX_E_INVALID_ARG, "NULL handle or out");
+    if (check_mem(mem)) return TVBX_E_INVALID_ARG;
+    if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_series before tvbx_run");
+    const size_t total = (size_t)h->T * h->N * h->P;
+    if (total == 0) return TVBX_OK;
+    float* target = out;
+    if (mem == TVBX_MEM_HOST) {
+        CK(h->d_tmp.ensure(sizeof(float) * total), "export buffer");
+        target = h->d_tmp.as<float>();
+    }
+    series_export_kernel<<<grid_for((int64_t)total), 256, 0, h->stream>>>(h->d_series.as<float>(), target,
+                                                                          h->d_perm.as<int64_t>(), h->T, h->N, h->P);
+    CK(cudaGetLastError(), "series export");
+    if (mem == TVBX_MEM_HOST) return copy_out(out, target, sizeof(float) * total, mem, h->stream);
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_state(const tvbx_sweep* hc, int32_t mem, float* out)
+{
+    tvbx_sweep* h = const_cast<tvbx_sweep*>(hc);
+    if (!h || !out) return fail(TVBX_E_INVALID_ARG, "NULL handle or out");
+    if (check_mem(mem)) return TVBX_E_INVALID_ARG;
+    if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_state before tvbx_run");
+    const size_t total = (size_t)8 * h->N * h->P;
+    float* target = out;
+    if (mem == TVBX_MEM_HOST) {
+        CK(h->d_tmp.ensure(sizeof(float) * total), "export buffer");
+        target = h->d_tmp.as<float>();
+    }
+    state_export_kernel<<<grid_for((int64_t)total), 256, 0, h->stream>>>(
+        h->d_state.as<float>(), h->cfg.noise_per_set ? nullptr : h->d_ou_state.as<float>(), target,
+        h->d_perm.as<int64_t>(), h->N, h->P);
+    CK(cudaGetLastError(), "state export");
+    if (mem == TVBX_MEM_HOST) return copy_out(out, target, sizeof(float) * total, mem, h->stream);
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t n, int32_t mem,
+                                   const float* x_e, const float* x_i, const float* W, const float* E_L,
+                                   float* out)
+{
+    if (pop != 0 && pop != 1) return fail(TVBX_E_INVALID_ARG, "pop must be 0 or 1");
+    if (n < 0) return fail(TVBX_E_INVALID_ARG, "n must be >= 0");
+    if (check_mem(mem)) return TVBX_E_INVALID_ARG;
+    if (n == 0) return TVBX_OK;
+    if (!x_e || !x_i || !W || !E_L || !out) return fail(TVBX_E_INVALID_ARG, "NULL array");
+    if (!device_ready()) return fail(TVBX_E_CUDA, "no CUDA device available");
+    tvbx_model m;
+    if (model) m = *model;
+    else engine_defaults(&m);
+    if (!model_ok(m)) return fail(TVBX_E_INVALID_ARG, "model constants must be positive where they divide");
+    const DevModel dm = to_device_model(m, 0.1);
+    DevBuf in, res;
+    const float *dxe = x_e, *dxi = x_i, *dW = W, *dEL = E_L;
+    float* dout = out;
+    if (mem == TVBX_MEM_HOST) {
+        CK(in.ensure(sizeof(float) * 4 * n), "inputs");
+        CK(res.ensure(sizeof(float) * 7 * n), "outputs");
+        float* b = in.as<float>();
+        CK(cudaMemcpy(b, x_e, sizeof(float) * n, cudaMemcpyHostToDevice), "upload");
+        CK(cudaMemcpy(b + n, x_i, sizeof(float) * n, cudaMemcpyHostToDevice), "upload");
+        CK(cudaMemcpy(b + 2 * n, W, sizeof(float) * n, cudaMemcpyHostToDevice), "upload");
+        CK(cudaMemcpy(b + 3 * n, E_L, sizeof(float) * n, cudaMemcpyHostToDevice), "upload");
+        dxe = b; dxi = b + n; dW = b + 2 * n; dEL = b + 3 * n;
+        dout = res.as<float>();
+    }
+    CK(launch_tf_eval(dm, pop, n, dxe, dxi, dW, dEL, dout, 0), "transfer function");
+    if (mem == TVBX_MEM_HOST) CK(cudaMemcpy(out, dout, sizeof(float) * 7 * n, cudaMemcpyDeviceToHost), "download");
+    CK(cudaDeviceSynchronize(), "synchronize");
+    in.release();
+    res.release();
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_sweep_destroy(tvbx_sweep* h)
+{
+    if (!h) return TVBX_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+    return TVBX_OK;
+}
+
+}  // extern "C"

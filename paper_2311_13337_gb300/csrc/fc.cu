@@ -1,0 +1,358 @@
+// Functional-connectivity kernels of the tvbx engine (arXiv 2311.13337,
+// Sec. "Output": the FC is obtained from the covariance of the simulated
+// series; Eq. 6: Pearson correlation; Table 2 "mean_FC").
+//
+// The E series is stored [T][N][P] (sets fastest). For each set the kernels
+// form block moments over the samples [t_begin, t_end):
+//   G_b[k][j] = sum_{t in block b} (x_k(t) - m_k)(x_j(t) - m_j),
+//   s_b[k]    = sum_{t in block b} (x_k(t) - m_k),
+// with the shift m_k = the running mean kept by the simulation (any shift is
+// exact; a close one avoids cancellation). The covariance over a union of
+// blocks of length L is sum G_b - (sum s_b)(sum s_b)^T / L.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace tvbx {
+
+constexpr int FC_SETS = 8;        // sets per CTA (one 32-byte sector per (t, k) row)
+constexpr int FC_THREADS = 256;
+constexpr int FC_TASKS_PER_THREAD = 5;
+
+// Gram block moments. grid = (P / FC_SETS, task chunks). Each thread owns up to
+// FC_TASKS_PER_THREAD 4x4 tiles (set q, row tile kb <= column tile jb).
+__global__ void __launch_bounds__(FC_THREADS)
+fc_moments_kernel(const __grid_constant__ FcArgs a, int32_t Npad, int32_t Tt, int32_t tasks_per_set,
+                  int32_t tasks_per_chunk)
+{
+    extern __shared__ float xs[];             // [FC_SETS][Tt][Npad]
+    __shared__ float shift[FC_SETS * 384];    // N <= 384
+    const int N = a.N;
+    const int p0 = blockIdx.x * FC_SETS;
+    const int nsets = min(FC_SETS, a.P - p0);
+    const int64_t Tn = a.t_end - a.t_begin;
+    const int nb = Npad / 4;
+
+    for (int i = threadIdx.x; i < FC_SETS * N; i += blockDim.x) {
+        const int q = i / N, k = i - q * N;
+        float mval = 0.0f;
+        if (q < nsets && Tn > 0) {
+            const int64_t p = p0 + q;
+            mval = a.state[(int64_t)SV_SUM_E * N * a.P + (int64_t)k * a.P + p] / (float)Tn;
+        }
+        shift[q * N + k] = mval;
+    }
+
+    // this thread's tasks
+    int tq[FC_TASKS_PER_THREAD], tk[FC_TASKS_PER_THREAD], tj[FC_TASKS_PER_THREAD];
+    int ntask = 0;
+    const int chunk0 = blockIdx.y * tasks_per_chunk;
+    for (int i = 0; i < FC_TASKS_PER_THREAD; ++i) {
+        const int task = chunk0 + threadIdx.x + i * FC_THREADS;
+        tq[i] = -1;
+        if (task < chunk0 + tasks_per_chunk && task < tasks_per_set * FC_SETS) {
+            const int q = task / tasks_per_set;
+            int r = task - q * tasks_per_set;
+            int kb = 0;
+            while (r >= nb - kb) { r -= nb - kb; ++kb; }
+            if (q < nsets) { tq[i] = q; tk[i] = kb; tj[i] = kb + r; ntask = i + 1; }
+        }
+    }
+    float acc[FC_TASKS_PER_THREAD][16];
+    float rs[FC_TASKS_PER_THREAD][4];
+#pragma unroll
+    for (int i = 0; i < FC_TASKS_PER_THREAD; ++i) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[i][c] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) rs[i][c] = 0.0f;
+    }
+    const int64_t blk = a.blk > 0 ? a.blk : Tn;
+    const int64_t NP = (int64_t)N * a.P;
+    const int64_t stride_b = (int64_t)N * N + N;
+    __syncthreads();
+
+    for (int64_t t0 = 0; t0 < Tn; t0 += Tt) {
+        const int len = (int)(Tn - t0 < (int64_t)Tt ? Tn - t0 : (int64_t)Tt);
+        // stage rows x[t][k][p0 .. p0 + FC_SETS) minus the shift, transposed to [q][t][k]
+        for (int i = threadIdx.x; i < len * Npad * FC_SETS; i += blockDim.x) {
+            const int q = i % FC_SETS;
+            const int rem = i / FC_SETS;
+            const int k = rem % Npad;
+            const int tt = rem / Npad;
+            float v = 0.0f;
+            if (k < N && q < nsets)
+                v = a.series[(a.t_begin + t0 + tt) * NP + (int64_t)k * a.P + p0 + q] - shift[q * N + k];
+            xs[((int64_t)q * Tt + tt) * Npad + k] = v;
+        }
+        __syncthreads();
+        for (int tt = 0; tt < len; ++tt) {
+#pragma unroll
+            for (int i = 0; i < FC_TASKS_PER_THREAD; ++i) {
+                if (i < ntask && tq[i] >= 0) {
+                    const float4 xk = *reinterpret_cast<const float4*>(xs + ((int64_t)tq[i] * Tt + tt) * Npad + 4 * tk[i]);
+                    const float4 xj = *reinterpret_cast<const float4*>(xs + ((int64_t)tq[i] * Tt + tt) * Npad + 4 * tj[i]);
+                    const float kv[4] = {xk.x, xk.y, xk.z, xk.w};
+                    const float jv[4] = {xj.x, xj.y, xj.z, xj.w};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[i][r * 4 + c] = fmaf(kv[r], jv[c], acc[i][r * 4 + c]);
+                        rs[i][r] += kv[r];
+                    }
+                }
+            }
+            // end of a moment block: write it out and restart
+            const int64_t tg = t0 + tt + 1;
+            if (tg % blk == 0 || tg == Tn) {
+                const int64_t b = (tg - 1) / blk;
+#pragma unroll
+                for (int i = 0; i < FC_TASKS_PER_THREAD; ++i) {
+                    if (i < ntask && tq[i] >= 0) {
+                        float* G = a.blocks + ((int64_t)(p0 + tq[i]) * a.n_blocks + b) * stride_b;
+                        for (int r = 0; r < 4; ++r) {
+                            const int k = 4 * tk[i] + r;
+                            if (k >= N) continue;
+                            for (int c = 0; c < 4; ++c) {
+                                const int j = 4 * tj[i] + c;
+                                if (j >= N) continue;
+                                G[(int64_t)k * N + j] = acc[i][r * 4 + c];
+                                G[(int64_t)j * N + k] = acc[i][r * 4 + c];
+                            }
+                            if (tk[i] == tj[i]) G[(int64_t)N * N + k] = rs[i][r];
+                        }
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) acc[i][c] = 0.0f;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) rs[i][c] = 0.0f;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Per set: covariance over all blocks, Pearson FC, chi and mean off-diagonal FC.
+__global__ void fc_finalize_kernel(const __grid_constant__ FcArgs a)
+{
+    extern __shared__ float sm[];   // cov [N][N] + sdev [N] + red[64]
+    const int N = a.N;
+    const int p = blockIdx.x;
+    const int64_t Tn = a.t_end - a.t_begin;
+    float* cov = sm;
+    float* sd = sm + N * N;
+    float* red = sd + N;
+    const int64_t stride_b = (int64_t)N * N + N;
+    const float* B = a.blocks + (int64_t)p * a.n_blocks * stride_b;
+    const float invT = Tn > 0 ? 1.0f / (float)Tn : 0.0f;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        const int k = i / N, j = i - k * N;
+        float g = 0.0f, sk = 0.0f, sj = 0.0f;
+        for (int b = 0; b < a.n_blocks; ++b) {
+            g += B[b * stride_b + i];
+            sk += B[b * stride_b + (int64_t)N * N + k];
+            sj += B[b * stride_b + (int64_t)N * N + j];
+        }
+        cov[i] = g - sk * sj * invT;
+    }
+    __syncthreads();
+    bool zero = false;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const float v = cov[k * N + k];
+        sd[k] = v > 0.0f ? sqrtf(v) : 0.0f;
+    }
+    __syncthreads();
+    // chi^2 = (sum_kj cov / N^2) / (sum_k cov_kk / N); mean off-diagonal FC
+    float s_all = 0.0f, s_diag = 0.0f, s_fc = 0.0f;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        const int k = i / N, j = i - k * N;
+        s_all += cov[i];
+        float f;
+        if (k == j) {
+            s_diag += cov[i];
+            f = 1.0f;
+            if (!(sd[k] > 0.0f)) zero = true;
+        } else {
+            const float d = sd[k] * sd[j];
+            f = d > 0.0f ? cov[i] / d : 0.0f;
+            s_fc += f;
+        }
+        if (a.fc) a.fc[(int64_t)p * N * N + i] = f;
+    }
+    // block reduction of the three sums
+    for (int o = 16; o > 0; o >>= 1) {
+        s_all += __shfl_xor_sync(0xffffffffu, s_all, o);
+        s_diag += __shfl_xor_sync(0xffffffffu, s_diag, o);
+        s_fc += __shfl_xor_sync(0xffffffffu, s_fc, o);
+    }
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0) { red[warp] = s_all; red[16 + warp] = s_diag; red[32 + warp] = s_fc; }
+    if (zero) atomicOr(a.status + p, TVBX_SET_ZERO_VAR);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float A = 0.0f, D = 0.0f, Fs = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) { A += red[w]; D += red[16 + w]; Fs += red[32 + w]; }
+        const float num = A / ((float)N * (float)N), den = D / (float)N;
+        a.chi[p] = den > 0.0f ? sqrtf(fmaxf(num / den, 0.0f)) : 0.0f;
+        a.mean_fc[p] = N > 1 ? Fs / ((float)N * (float)(N - 1)) : 0.0f;
+    }
+}
+
+// Per set: FC of each window (blocks [w, w + m)), upper-triangle vectors, and
+// the Pearson correlation between every pair of window vectors.
+__global__ void fcd_kernel(const float* __restrict__ blocks, int32_t N, int32_t n_blocks,
+                           int32_t m, int32_t nw, int64_t Lw, float* __restrict__ vec,
+                           float* __restrict__ fcd)
+{
+    extern __shared__ float sm[];   // diag [N] + mom [nw] + red
+    const int p = blockIdx.x;
+    const int M = N * (N - 1) / 2;
+    const int64_t stride_b = (int64_t)N * N + N;
+    const float* B = blocks + (int64_t)p * n_blocks * stride_b;
+    float* V = vec + (int64_t)p * nw * M;
+    float* dg = sm;
+    float* mom = sm + N;         // [nw] means then inverse norms
+    float* red = mom + 2 * nw;
+    const float invL = 1.0f / (float)Lw;
+    for (int w = 0; w < nw; ++w) {
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            float g = 0.0f, s = 0.0f;
+            for (int b = w; b < w + m; ++b) {
+                g += B[b * stride_b + (int64_t)k * N + k];
+                s += B[b * stride_b + (int64_t)N * N + k];
+            }
+            const float v = g - s * s * invL;
+            dg[k] = v > 0.0f ? sqrtf(v) : 0.0f;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < M; idx += blockDim.x) {
+            // idx -> (k, j), k < j, row by row
+            int k = 0, r = idx;
+            while (r >= N - 1 - k) { r -= N - 1 - k; ++k; }
+            const int j = k + 1 + r;
+            float g = 0.0f, sk = 0.0f, sj = 0.0f;
+            for (int b = w; b < w + m; ++b) {
+                g += B[b * stride_b + (int64_t)k * N + j];
+                sk += B[b * stride_b + (int64_t)N * N + k];
+                sj += B[b * stride_b + (int64_t)N * N + j];
+            }
+            const float c = g - sk * sj * invL;
+            const float d = dg[k] * dg[j];
+            V[(int64_t)w * M + idx] = d > 0.0f ? c / d : 0.0f;
+        }
+        __syncthreads();
+    }
+    // centre each window vector and normalise it
+    for (int w = 0; w < nw; ++w) {
+        float s = 0.0f;
+        for (int i = threadIdx.x; i < M; i += blockDim.x) s += V[(int64_t)w * M + i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += red[q];
+            mom[w] = t / (float)M;
+        }
+        __syncthreads();
+        const float mu = mom[w];
+        float ss = 0.0f;
+        for (int i = threadIdx.x; i < M; i += blockDim.x) {
+            const float v = V[(int64_t)w * M + i] - mu;
+            V[(int64_t)w * M + i] = v;
+            ss += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        __syncthreads();
+        if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = ss;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += red[q];
+            mom[nw + w] = t > 0.0f ? rsqrtf(t) : 0.0f;
+        }
+        __syncthreads();
+    }
+    for (int pair = 0; pair < nw * nw; ++pair) {
+        const int u = pair / nw, v = pair - u * nw;
+        if (v < u) continue;
+        float s = 0.0f;
+        for (int i = threadIdx.x; i < M; i += blockDim.x) s += V[(int64_t)u * M + i] * V[(int64_t)v * M + i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += red[q];
+            float r = t * mom[nw + u] * mom[nw + v];
+            if (u == v) r = 1.0f;
+            fcd[((int64_t)p * nw + u) * nw + v] = r;
+            fcd[((int64_t)p * nw + v) * nw + u] = r;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void summary_kernel(const float* __restrict__ state, int32_t N, int32_t P, int64_t n_samples,
+                               float* __restrict__ mean_e_hz, float* __restrict__ mean_i_hz)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float se = 0.0f, si = 0.0f;
+    for (int k = 0; k < N; ++k) {
+        se += state[(int64_t)SV_SUM_E * N * P + (int64_t)k * P + p];
+        si += state[(int64_t)SV_SUM_I * N * P + (int64_t)k * P + p];
+    }
+    const float scale = n_samples > 0 ? 1000.0f / ((float)N * (float)n_samples) : 0.0f;
+    mean_e_hz[p] = se * scale;
+    mean_i_hz[p] = si * scale;
+}
+
+cudaError_t launch_fc(const FcArgs& a, cudaStream_t s)
+{
+    if (a.N > 384) return cudaErrorInvalidValue;
+    const int Npad = (a.N + 3) / 4 * 4;
+    const int nb = Npad / 4;
+    const int tasks_per_set = nb * (nb + 1) / 2;
+    const int total = tasks_per_set * FC_SETS;
+    const int per_chunk = FC_THREADS * FC_TASKS_PER_THREAD;
+    const int chunks = (total + per_chunk - 1) / per_chunk;
+    int Tt = 16384 / (FC_SETS * Npad);
+    Tt = Tt < 4 ? 4 : (Tt > 32 ? 32 : Tt);
+    const size_t smem = sizeof(float) * (size_t)FC_SETS * Tt * Npad;
+    cudaError_t e = cudaFuncSetAttribute(fc_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.P + FC_SETS - 1) / FC_SETS, chunks);
+    fc_moments_kernel<<<grid, FC_THREADS, smem, s>>>(a, Npad, Tt, tasks_per_set, per_chunk);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem2 = sizeof(float) * ((size_t)a.N * a.N + a.N + 64);
+    e = cudaFuncSetAttribute(fc_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
+    fc_finalize_kernel<<<a.P, 512, smem2, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fcd(const float* blocks, int32_t P, int32_t N, int32_t n_blocks,
+                       int32_t blocks_per_window, int32_t n_windows, int64_t window_samples,
+                       float* vec_scratch, float* fcd, cudaStream_t s)
+{
+    const size_t smem = sizeof(float) * ((size_t)N + 2 * n_windows + 64);
+    fcd_kernel<<<P, 256, smem, s>>>(blocks, N, n_blocks, blocks_per_window, n_windows, window_samples,
+                                    vec_scratch, fcd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_summary(const float* state, int32_t N, int32_t P, int64_t n_samples,
+                           float* mean_e_hz, float* mean_i_hz, cudaStream_t s)
+{
+    summary_kernel<<<(P + 255) / 256, 256, 0, s>>>(state, N, P, n_samples, mean_e_hz, mean_i_hz);
+    return cudaGetLastError();
+}
+
+}  // namespace tvbx

@@ -1,0 +1,113 @@
+// Engine-internal declarations shared by the tvbx CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tvbx.h"
+
+namespace tvbx {
+
+// Number of per-(set, region) state words kept across steps and chunks:
+// E, I, C_ee, C_ei, C_ii, W_e, W_i, OU, then the temporal-average accumulators
+// of E and I, then compensated running sums (sum, carry) of the E and I samples.
+enum {
+    SV_E = 0, SV_I, SV_CEE, SV_CEI, SV_CII, SV_WE, SV_WI, SV_OU,
+    SV_ACC_E, SV_ACC_I, SV_SUM_E, SV_CMP_E, SV_SUM_I, SV_CMP_I, SV_COUNT
+};
+
+// Model constants prepared for the device (FP32, with derived quantities).
+struct DevModel {
+    float g_L, C_m, E_e, E_i;
+    float qe, qi;            // Q_e tau_e, Q_i tau_i (nS ms)
+    float tau_e, tau_i;
+    float K_e, K_i;
+    float inv_Ne, inv_Ni, inv_T;
+    float P_e[10], P_i[10];
+    float mu0, inv_dmu0, sig0, inv_dsig0, tau0, inv_dtau0;
+    float gL_over_Cm;
+    float rate_floor;
+    float b_i, a_i, inv_tau_w_i;
+    float E_min, E_max;
+    float E0, I0;
+    // OU (Eq. 4) by Euler-Maruyama: OU' = OU + ou_a (mu - OU) + ou_b xi
+    float ou_a, ou_b, ou_mu;
+    float dt;
+};
+
+// One speed group: sets sharing a delay matrix and a ring buffer.
+struct GroupDev {
+    float* ring;               // [H][N][P_g], E of the group's sets
+    const int32_t* row_ptr;    // [N + 1] CSR rows of the nonzero weights u_kj
+    const uint32_t* col_dly;   // [nnz] (delay << 16) | j
+    const float* w;            // [nnz] u_kj
+    int32_t H;                 // ring depth (max delay + 2)
+    int32_t P_g;               // sets in the group (ring stride)
+    int32_t p_base;            // first internal set index of the group
+    int32_t pad;
+};
+
+// One CTA's work: sets [q0, q0 + nq) of group g (q relative to the group).
+struct TileDev {
+    int32_t group;
+    int32_t q0;
+    int32_t nq;
+    int32_t pad;
+};
+
+// Arguments of one simulation chunk launch.
+struct SimArgs {
+    DevModel m;
+    const GroupDev* groups;
+    const TileDev* tiles;
+    const float* prm;          // [TVBX_N_AXES][P] per-set parameters (internal order)
+    const int64_t* ext_index;  // [P] external set index (keys per-set noise)
+    float* state;              // [SV_COUNT][N][P]
+    float* series;             // [T][N][P] E samples (sets fastest)
+    const float* ou_table;     // [n_chunk][N] shared OU values, or null
+    uint32_t* status;          // [P]
+    int64_t n0;                // global index of the chunk's first step
+    int32_t n_chunk;           // steps in this chunk
+    int32_t N;                 // regions
+    int32_t P;                 // sets (internal)
+    int32_t ts;                // steps per sample
+    int64_t T;                 // samples in the run
+    int32_t transient;         // samples excluded from the running sums
+    int32_t noise_per_set;
+    uint64_t seed;
+    int64_t p_offset;
+};
+
+// Kernels / launchers (sim.cu).
+cudaError_t launch_init_state(const SimArgs& a, cudaStream_t s);
+cudaError_t launch_init_ring(float* ring, int64_t count, float value, cudaStream_t s);
+cudaError_t launch_ou_table(const DevModel& m, float* table, float* ou_state, int32_t N,
+                            int64_t n0, int32_t n_chunk, uint64_t seed, cudaStream_t s);
+cudaError_t launch_sim_chunk(const SimArgs& a, int32_t n_tiles, int32_t pb, cudaStream_t s);
+cudaError_t launch_tf_eval(const DevModel& m, int pop, int64_t n, const float* x_e, const float* x_i,
+                           const float* W, const float* E_L, float* out, cudaStream_t s);
+int sim_threads(int N, int pb);
+size_t sim_smem_bytes(int N, int pb);
+
+// FC (fc.cu).
+struct FcArgs {
+    const float* series;       // [T][N][P]
+    const float* state;        // [SV_COUNT][N][P] (running sums give the shift)
+    int32_t N, P;
+    int64_t t_begin, t_end;    // samples used: [t_begin, t_end)
+    int32_t blk;               // samples per FCD block (0: one block)
+    int32_t n_blocks;
+    float* blocks;             // [P][n_blocks][N*N + N] block moments (nullable)
+    float* fc;                 // [P][N][N] internal order (nullable)
+    float* chi;                // [P]
+    float* mean_fc;            // [P]
+    uint32_t* status;          // [P]
+};
+cudaError_t launch_fc(const FcArgs& a, cudaStream_t s);
+cudaError_t launch_fcd(const float* blocks, int32_t P, int32_t N, int32_t n_blocks,
+                       int32_t blocks_per_window, int32_t n_windows, int64_t window_samples,
+                       float* vec_scratch, float* fcd, cudaStream_t s);
+cudaError_t launch_summary(const float* state, int32_t N, int32_t P, int64_t n_samples,
+                           float* mean_e_hz, float* mean_i_hz, cudaStream_t s);
+
+}  // namespace tvbx

@@ -1,0 +1,333 @@
+"""Python binding of the tvbx C-ABI (include/tvbx.h).
+
+Argument marshalling only: every step of the sweep runs in the CUDA library
+``lib/libtvbx.so``. Host arrays are numpy arrays; device arrays are CUDA
+torch tensors (PyTorch supplies device memory and streams). There is no CPU
+fallback: if the library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AXES = ("g", "b_e", "tau_w_e", "E_L_e", "E_L_i", "speed", "a_e", "w_noise",
+        "cF_ee", "cF_ei", "cF_ie", "cF_ii")
+N_AXES = len(AXES)
+MEM_HOST, MEM_DEVICE = 0, 1
+SET_NONFINITE, SET_CLAMP_HI, SET_CLAMP_LO, SET_ZERO_VAR = 1, 2, 4, 8
+FC_FP32 = 0
+STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NUMERIC", -5: "TIMEOUT",
+                -6: "BAD_STATE", -7: "UNSUPPORTED"}
+STATE_VARS = ("E", "I", "C_ee", "C_ei", "C_ii", "W_e", "W_i", "OU")
+
+
+class TvbxError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} ({code}): {msg}")
+        self.code = code
+
+
+class Model(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("g_L", "C_m", "E_e", "E_i", "Q_e", "Q_i", "tau_e", "tau_i",
+                 "K_e", "K_i", "N_e", "N_i", "T")] + \
+               [("P_e", ctypes.c_double * 10), ("P_i", ctypes.c_double * 10)] + \
+               [(n, ctypes.c_double) for n in
+                ("mu0", "dmu0", "sig0", "dsig0", "tau0", "dtau0", "rate_floor",
+                 "tau_OU", "mu_OU", "sigma_OU", "b_i", "a_i", "tau_w_i",
+                 "E_min", "E_max", "E0", "I0")] + \
+               [("defaults", ctypes.c_double * N_AXES)]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if name in ("P_e", "P_i", "defaults") else float(v)
+        return d
+
+
+class AxisSpec(ctypes.Structure):
+    _fields_ = [("axis", ctypes.c_int32), ("n", ctypes.c_int32), ("lo", ctypes.c_double),
+                ("hi", ctypes.c_double), ("values", ctypes.POINTER(ctypes.c_double))]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n_axes", ctypes.c_int32), ("axes", ctypes.POINTER(AxisSpec))]
+
+
+class RunCfg(ctypes.Structure):
+    _fields_ = [("dt_ms", ctypes.c_double), ("n_steps", ctypes.c_int64), ("tavg_steps", ctypes.c_int32),
+                ("noise_per_set", ctypes.c_int32), ("seed", ctypes.c_uint64), ("p_offset", ctypes.c_int64),
+                ("transient_samples", ctypes.c_int32), ("chunk_steps", ctypes.c_int32)]
+
+
+class FcCfg(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("fcd_window", ctypes.c_int32), ("fcd_step", ctypes.c_int32)]
+
+
+_lib = None
+EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep_create",
+           "tvbx_sweep_create_points", "tvbx_sweep_info", "tvbx_run", "tvbx_summary", "tvbx_series",
+           "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_sweep_destroy")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load lib/libtvbx.so (optionally building it first). Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"tvbx CUDA library not built: {path} (run paper_2311_13337_gb300/build.py)")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dp, fp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+    L.tvbx_version.restype = ctypes.c_char_p
+    L.tvbx_last_error.restype = ctypes.c_char_p
+    L.tvbx_model_defaults.argtypes = [ctypes.POINTER(Model)]
+    L.tvbx_sweep_create.argtypes = [dp, dp, i32, ctypes.POINTER(Grid), ctypes.POINTER(Model), ctypes.POINTER(vp)]
+    L.tvbx_sweep_create_points.argtypes = [dp, dp, i32, i64, dp, ctypes.POINTER(Model), ctypes.POINTER(vp)]
+    L.tvbx_sweep_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)]
+    L.tvbx_run.argtypes = [vp, ctypes.POINTER(RunCfg), vp]
+    L.tvbx_summary.argtypes = [vp, i32, fp, fp, fp, fp, fp]
+    L.tvbx_series.argtypes = [vp, i32, fp]
+    L.tvbx_state.argtypes = [vp, i32, fp]
+    L.tvbx_fc.argtypes = [vp, ctypes.POINTER(FcCfg), i32, fp, fp, ctypes.POINTER(i32)]
+    L.tvbx_transfer_function.argtypes = [ctypes.POINTER(Model), i32, i64, i32, fp, fp, fp, fp, fp]
+    L.tvbx_sweep_destroy.argtypes = [vp]
+    for name in EXPORTS:
+        if name not in ("tvbx_version", "tvbx_last_error"):
+            getattr(L, name).restype = ctypes.c_int32
+    _lib = L
+    return L
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise TvbxError(code, where, load().tvbx_last_error().decode())
+
+
+def version() -> str:
+    return load().tvbx_version().decode()
+
+
+def last_error() -> str:
+    return load().tvbx_last_error().decode()
+
+
+def model_defaults() -> Model:
+    m = Model()
+    _check(load().tvbx_model_defaults(ctypes.byref(m)), "tvbx_model_defaults")
+    return m
+
+
+def make_model(overrides: dict | None = None) -> Model:
+    m = model_defaults()
+    for k, v in (overrides or {}).items():
+        if k in ("P_e", "P_i"):
+            arr = getattr(m, k)
+            for i in range(10):
+                arr[i] = float(v[i])
+        elif k in AXES:
+            m.defaults[AXES.index(k)] = float(v)
+        else:
+            setattr(m, k, float(v))
+    return m
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _out_ptr(x):
+    """(pointer, mem kind) for a numpy array or a CUDA torch tensor."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("output arrays must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data), MEM_HOST
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("output tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), MEM_DEVICE if x.is_cuda else MEM_HOST
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def sweep_create(weights, tract_mm, axes: list, model: Model | None = None):
+    """Handle for the Cartesian grid of `axes`: list of (axis name, values) or
+    (axis name, (lo, hi, n)); last axis fastest."""
+    W, L = _f64(weights), _f64(tract_mm)
+    n = W.shape[0]
+    specs = (AxisSpec * max(len(axes), 1))()
+    keep = []
+    for i, (name, vals) in enumerate(axes):
+        s = specs[i]
+        s.axis = AXES.index(name)
+        if isinstance(vals, tuple) and len(vals) == 3 and isinstance(vals[2], int):
+            s.lo, s.hi, s.n = float(vals[0]), float(vals[1]), int(vals[2])
+            s.values = None
+        else:
+            arr = _f64(vals)
+            keep.append(arr)
+            s.n = len(arr)
+            s.values = _dptr(arr)
+    grid = Grid(len(axes), specs)
+    h = ctypes.c_void_p()
+    _check(load().tvbx_sweep_create(_dptr(W), _dptr(L), n, ctypes.byref(grid),
+                                    ctypes.byref(model) if model is not None else None, ctypes.byref(h)),
+           "tvbx_sweep_create")
+    return h
+
+
+def sweep_create_points(weights, tract_mm, params, model: Model | None = None):
+    """Handle for explicit points params[n_sets][N_AXES] (axis order AXES)."""
+    W, L, P = _f64(weights), _f64(tract_mm), _f64(params).reshape(-1, N_AXES)
+    h = ctypes.c_void_p()
+    _check(load().tvbx_sweep_create_points(_dptr(W), _dptr(L), W.shape[0], P.shape[0], _dptr(P),
+                                           ctypes.byref(model) if model is not None else None, ctypes.byref(h)),
+           "tvbx_sweep_create_points")
+    return h
+
+
+def sweep_info(h) -> tuple[int, int, int]:
+    p, n, t = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().tvbx_sweep_info(h, ctypes.byref(p), ctypes.byref(n), ctypes.byref(t)), "tvbx_sweep_info")
+    return p.value, n.value, t.value
+
+
+def run(h, dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
+        transient_samples=0, chunk_steps=0, stream=None):
+    """Enqueue the integration on `stream` (a torch.cuda.Stream, a raw handle
+    or None for the default stream)."""
+    cfg = RunCfg(float(dt_ms), int(n_steps), int(tavg_steps), int(bool(noise_per_set)), int(seed),
+                 int(p_offset), int(transient_samples), int(chunk_steps))
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(load().tvbx_run(h, ctypes.byref(cfg), sp), "tvbx_run")
+
+
+def summary(h, mean_e_hz=None, mean_i_hz=None, chi=None, mean_fc=None, status=None):
+    outs = [mean_e_hz, mean_i_hz, chi, mean_fc, status]
+    kinds = {k for _, k in (_out_ptr(o) for o in outs) if k is not None}
+    if len(kinds) > 1:
+        raise ValueError("summary outputs must all be host or all be device")
+    mem = kinds.pop() if kinds else MEM_HOST
+    ptrs = [_out_ptr(o)[0] for o in outs]
+    _check(load().tvbx_summary(h, mem, *ptrs), "tvbx_summary")
+
+
+def series(h, out):
+    ptr, mem = _out_ptr(out)
+    _check(load().tvbx_series(h, mem, ptr), "tvbx_series")
+
+
+def state(h, out):
+    ptr, mem = _out_ptr(out)
+    _check(load().tvbx_state(h, mem, ptr), "tvbx_state")
+
+
+def fc(h, fc_out=None, fcd_out=None, fcd_window=0, fcd_step=0, precision=FC_FP32) -> int:
+    kinds = {k for _, k in (_out_ptr(o) for o in (fc_out, fcd_out)) if k is not None}
+    if len(kinds) > 1:
+        raise ValueError("fc outputs must both be host or both be device")
+    mem = kinds.pop() if kinds else MEM_HOST
+    cfg = FcCfg(int(precision), int(fcd_window), int(fcd_step))
+    nw = ctypes.c_int32()
+    _check(load().tvbx_fc(h, ctypes.byref(cfg), mem, _out_ptr(fc_out)[0], _out_ptr(fcd_out)[0],
+                          ctypes.byref(nw)), "tvbx_fc")
+    return nw.value
+
+
+def transfer_function(pop: int, x_e, x_i, W, E_L, model: Model | None = None) -> np.ndarray:
+    """[n][7] = F, F_e, F_i, F_ee, F_ei, F_ii, mu_V from the device code."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (x_e, x_i, W, E_L)]
+    n = arrs[0].shape[0]
+    out = np.zeros((n, 7), dtype=np.float32)
+    fptr = [ctypes.c_void_p(a.ctypes.data) for a in arrs]
+    _check(load().tvbx_transfer_function(ctypes.byref(model) if model is not None else None, int(pop), n,
+                                         MEM_HOST, *fptr, ctypes.c_void_p(out.ctypes.data)),
+           "tvbx_transfer_function")
+    return out
+
+
+def sweep_destroy(h):
+    if h is not None and h.value:
+        _check(load().tvbx_sweep_destroy(h), "tvbx_sweep_destroy")
+
+
+class Sweep:
+    """Owning wrapper: one handle, host-side convenience readers."""
+
+    def __init__(self, weights, tract_mm, axes=None, points=None, model: Model | None = None):
+        if points is not None:
+            self.h = sweep_create_points(weights, tract_mm, points, model)
+        else:
+            self.h = sweep_create(weights, tract_mm, axes or [], model)
+        self.n_sets, self.n_regions, _ = sweep_info(self.h)
+
+    def run(self, **kw):
+        run(self.h, **kw)
+        self._transient = int(kw.get("transient_samples", 0))
+        return self
+
+    @property
+    def n_samples(self) -> int:
+        return sweep_info(self.h)[2]
+
+    def summary(self) -> dict:
+        P = self.n_sets
+        out = {k: np.zeros(P, dtype=np.float32) for k in ("mean_e_hz", "mean_i_hz", "chi", "mean_fc")}
+        st = np.zeros(P, dtype=np.uint32)
+        summary(self.h, out["mean_e_hz"], out["mean_i_hz"], out["chi"], out["mean_fc"], st)
+        out["status"] = st
+        return out
+
+    def series(self) -> np.ndarray:
+        x = np.zeros((self.n_sets, self.n_regions, self.n_samples), dtype=np.float32)
+        series(self.h, x)
+        return x
+
+    def state(self) -> np.ndarray:
+        x = np.zeros((self.n_sets, 8, self.n_regions), dtype=np.float32)
+        state(self.h, x)
+        return x
+
+    def fc(self, fcd_window=0, fcd_step=0):
+        P, N = self.n_sets, self.n_regions
+        out = np.zeros((P, N, N), dtype=np.float32)
+        if fcd_window > 0:
+            T = self.n_samples - getattr(self, "_transient", 0)
+            nw = (T - fcd_window) // fcd_step + 1 if fcd_step > 0 and T >= fcd_window else 1
+            fcd_out = np.zeros((P, nw, nw), dtype=np.float32)
+            got = fc(self.h, out, fcd_out, fcd_window, fcd_step)
+            assert got == nw
+            return out, fcd_out
+        fc(self.h, out)
+        return out
+
+    def close(self):
+        sweep_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None:
+                self.close()
+        except Exception:
+            pass

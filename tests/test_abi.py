@@ -1,0 +1,89 @@
+"""CPU checks of the C-ABI boundary: the library builds for sm_103a, loads,
+exports every function include/tvbx.h declares, reports its defaults, and
+rejects bad arguments before touching a device. No compute call needs a GPU
+here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_13337_gb300 import build, tvbx
+    try:
+        build.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    build.build()
+    return tvbx
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(tvbx_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L = lib.load()
+    declared = _declared_functions()
+    assert "tvbx_run" in declared and "tvbx_fc" in declared
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(declared) == set(lib.EXPORTS)
+
+
+def test_defaults_match_the_oracle(lib, oracle):
+    eng = lib.model_defaults().as_dict()
+    orc = oracle.default_constants()
+    for k, v in orc.items():
+        if isinstance(v, list):
+            assert np.array_equal(eng[k], v), k
+        else:
+            assert eng[k] == v, k
+    prm = oracle.default_params()
+    assert [eng["defaults"][i] for i in range(lib.N_AXES)] == [prm[a] for a in lib.AXES]
+    assert tuple(lib.AXES) == tuple(oracle.AXES)
+
+
+def test_version_and_error_reporting(lib):
+    assert "sm_103a" in lib.version()
+    L = lib.load()
+    h = ctypes.c_void_p()
+    # argument errors come back before any device use
+    rc = L.tvbx_sweep_create(None, None, 4, None, None, ctypes.byref(h))
+    assert rc == -1 and "NULL" in lib.last_error()
+    w = np.zeros((3, 3))
+    bad = np.full((3, 3), -1.0)
+    rc = L.tvbx_sweep_create(w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 3, None, None,
+                             ctypes.byref(h))
+    assert rc == -1 and "tract length" in lib.last_error()
+    with pytest.raises(lib.TvbxError) as e:
+        lib.sweep_create(w, w, [("g", [0.1]), ("g", [0.2])])
+    assert e.value.code == -1 and "repeated" in str(e.value)
+    with pytest.raises(lib.TvbxError):
+        lib.sweep_create(w, w, [("g", (0.0, 1.0, 0))])
+    assert L.tvbx_sweep_destroy(None) == 0
+
+
+def test_no_cpu_fallback_without_a_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    w = np.zeros((4, 4))
+    with pytest.raises(lib.TvbxError) as e:
+        lib.sweep_create(w, w, [("g", [0.1])])
+    assert e.value.code == -3
+    with pytest.raises(lib.TvbxError) as e:
+        lib.transfer_function(0, [0.01], [0.01], [0.0], [-64.0])
+    assert e.value.code == -3
