@@ -452,6 +452,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     int64_t ring_floats = 0;
     for (Group& g : groups) {
         g.p_base = (int32_t)h->perm.size();
+        ring_floats = (ring_floats + 63) / 64 * 64;   // 256-byte aligned ring per group
         g.ring_offset = ring_floats;
         ring_floats += (int64_t)g.H * N * (int64_t)g.sets.size();
         for (int64_t e : g.sets) h->perm.push_back(e);
