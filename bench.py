@@ -1,0 +1,354 @@
+"""Benchmark of the TVB-AdEx sweep engine on GB300.
+
+One step = the whole hot path over the paper-scale workload: integrate
+32,768 parameter sets (g16 x b_e16 x E_L_i16 x tau_w_e8) of the 68-region
+synthetic connectome for 50,000 steps (5 s at dt = 0.1 ms, v = 4 m/s), then
+FC, FCD (1,000-sample windows, 500-sample step) and the per-set summary.
+
+Prints one JSON line (rank 0). Metric: region-steps/s, whole job.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+Under torchrun each rank integrates its own 32,768-set slice of an
+N x 32,768-set sweep (tau_w_e resolution 8N): weak scaling, no collective on
+the data path; a barrier and a max-reduce of the elapsed time only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "region-steps/s on 1 GB300 (plain vs batched/surrogate, at stated FC error)"
+UNIT = "region-steps/s"
+FCD_WINDOW, FCD_STEP = 1000, 500
+
+
+def workload(n_ranks: int, rank: int):
+    from paper_2311_13337_gb300 import synth
+    cfg = dict(synth.PAPER_SCALE_SWEEP)
+    axes = [("g", (0.0, 0.9, 16)), ("b_e", (0.0, 120.0, 16)), ("E_L_i", (-80.0, -60.0, 16)),
+            ("tau_w_e", (100.0, 1000.0, 8 * n_ranks))]
+    cfg["axes"] = axes
+    return cfg
+
+
+def points_for_rank(axes, n_ranks, rank, per_rank=32768):
+    """Explicit parameter rows of this rank's contiguous slice (last axis fastest)."""
+    from paper_2311_13337_gb300.tvbx import AXES, make_model
+    m = make_model()
+    vals = []
+    for name, (lo, hi, n) in axes:
+        vals.append((AXES.index(name), [lo + (hi - lo) * i / (n - 1) for i in range(n)]))
+    total = int(np.prod([len(v) for _, v in vals]))
+    assert total == per_rank * n_ranks
+    idx = np.arange(rank * per_rank, (rank + 1) * per_rank)
+    pts = np.tile(np.array([m.defaults[i] for i in range(len(AXES))]), (per_rank, 1))
+    rem = idx.copy()
+    for ax, v in reversed(vals):
+        pts[:, ax] = np.asarray(v)[rem % len(v)]
+        rem //= len(v)
+    return pts
+
+
+# ---------------------------------------------------------------------------
+def start_clock_sampler(device_index: int):
+    cmd = ["nvidia-smi", f"--id={device_index}",
+           "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        return subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except (OSError, FileNotFoundError):
+        return None
+
+
+def stop_clock_sampler(proc):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for name, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(name)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("sim.cu", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2311_13337_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_region_step():
+    """DRAM bytes per (set, region, step) of the simulation kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sim_chunk_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_region_step")
+
+
+def algorithmic_bytes_per_region_step(W, tavg_steps):
+    """Coupling gather (4 B per nonzero weight of the row) + ring write (4 B)
+    + series write (4 B per tavg_steps steps)."""
+    N = W.shape[0]
+    nnz = int(np.count_nonzero(W))
+    return 4.0 * nnz / N + 4.0 + 4.0 / tavg_steps
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(target_seconds=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    the first S sets of the paper-scale grid for 5,000 steps (0.5 s), plus
+    their FC; S is sized so the sample takes about target_seconds."""
+    from oracle import oracle as O
+    from paper_2311_13337_gb300 import synth
+    W, L = synth.connectome(68)
+    grid = O.expand_grid(synth.PAPER_SCALE_AXES)
+    m = O.make_model()
+    cores = O.max_threads()
+    steps = 5000
+    n_cal = max(cores, 16)
+    t0 = time.time()
+    O.simulate(m, W, L, grid[:n_cal], 0.1, 1000, 10, 1, want_I=True, want_state=False)
+    cal = time.time() - t0
+    per_set_step = cal / (n_cal * 1000)
+    n_sets = int(max(cores, min(4096, target_seconds / max(per_set_step * steps, 1e-9))))
+    n_sets = max(cores, (n_sets // cores) * cores)
+    t0 = time.time()
+    r = O.simulate(m, W, L, grid[:n_sets], 0.1, steps, 10, 1, want_state=False)
+    O.summary(r["E"], r["I"])
+    el = time.time() - t0
+    rs = n_sets * 68 * steps
+    return {"value": rs / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_sets} sets of the 32,768-set grid, 68 regions, {steps} steps (0.5 s) "
+                      f"+ FC, FP64, OpenMP over sets; {el:.1f} s"}, n_sets
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    base, n_sets = cpu_baseline(target_seconds=max(5.0, 60.0 / max(args.steps + args.warmup, 1)))
+    from oracle import oracle as O
+    from paper_2311_13337_gb300 import synth
+    W, L = synth.connectome(68)
+    grid = O.expand_grid(synth.PAPER_SCALE_AXES)
+    m = O.make_model()
+    steps = 5000
+
+    def one():
+        r = O.simulate(m, W, L, grid[:n_sets], 0.1, steps, 10, 1, want_state=False)
+        O.summary(r["E"], r["I"])
+    for _ in range(args.warmup):
+        one()
+    t0 = time.time()
+    for _ in range(args.steps):
+        one()
+    el = time.time() - t0
+    value = args.steps * n_sets * 68 * steps / el
+    base = dict(base, value=value, sample=base["sample"].rsplit(";", 1)[0] + f"; {args.steps} timed steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "paper-scale plain sweep, bounded sample on host cores (FP64 oracle)",
+                       "n_sets": n_sets, "n_regions": 68, "n_steps": steps, "dt_ms": 0.1, "speed_m_s": 4.0},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_engine(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2311_13337_gb300 import synth, tvbx
+
+    cfg = workload(world, rank)
+    W, L = synth.connectome(68)
+    pts = points_for_rank(cfg["axes"], world, rank)
+    P, N, S, ts = pts.shape[0], 68, cfg["n_steps"], cfg["tavg_steps"]
+    region_steps = float(P) * N * S
+    stream = torch.cuda.Stream(device=dev)
+
+    sw = tvbx.Sweep(W, L, points=pts)
+    fc_dev = torch.empty((P, N, N), dtype=torch.float32, device=dev)
+    nw = (S // ts - FCD_WINDOW) // FCD_STEP + 1
+    fcd_dev = torch.empty((P, nw, nw), dtype=torch.float32, device=dev)
+    summ = {k: torch.empty(P, dtype=torch.float32, device=dev) for k in ("e", "i", "chi", "mfc")}
+    status = torch.empty(P, dtype=torch.int32, device=dev)
+
+    def step():
+        tvbx.run(sw.h, dt_ms=cfg["dt"], n_steps=S, tavg_steps=ts, seed=cfg["seed"], p_offset=rank * P,
+                 stream=stream)
+        tvbx.fc(sw.h, fc_dev, fcd_dev, FCD_WINDOW, FCD_STEP)
+        tvbx.summary(sw.h, summ["e"], summ["i"], summ["chi"], summ["mfc"], status)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    tvbx.profile_enable(sw.h, True)
+    launches0 = tvbx.launch_count()
+    sampler = start_clock_sampler(local) if rank == 0 else None
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    barrier()
+    clocks = stop_clock_sampler(sampler)
+    launches = tvbx.launch_count() - launches0
+    sim_ms, sim_launches, sim_rs = tvbx.profile_read(sw.h)
+    tvbx.profile_enable(sw.h, False)
+    t = torch.tensor([el], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    el_max = float(t.item())
+    value = args.steps * region_steps * world / el_max
+
+    # end to end through the public API with host buffers: inputs from pinned
+    # host memory, results read back to host every step
+    e2e = None
+    if rank == 0 or world > 1:
+        pin_W = torch.from_numpy(W).pin_memory().numpy()
+        pin_L = torch.from_numpy(L).pin_memory().numpy()
+        pin_pts = torch.from_numpy(pts).pin_memory().numpy()
+        host_fc = torch.empty((P, N, N), dtype=torch.float32).pin_memory().numpy()
+        host_fcd = torch.empty((P, nw, nw), dtype=torch.float32).pin_memory().numpy()
+        host_s = [torch.empty(P, dtype=torch.float32).pin_memory().numpy() for _ in range(4)]
+        host_st = torch.empty(P, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        k_e2e = max(1, min(args.steps, 2))
+        h2d = d2h = 0
+
+        def e2e_step():
+            nonlocal h2d, d2h
+            h = tvbx.sweep_create_points(pin_W, pin_L, pin_pts)
+            tvbx.run(h, dt_ms=cfg["dt"], n_steps=S, tavg_steps=ts, seed=cfg["seed"], p_offset=rank * P)
+            tvbx.fc(h, host_fc, host_fcd, FCD_WINDOW, FCD_STEP)
+            tvbx.summary(h, *host_s, host_st)
+            a, b = tvbx.transfer_bytes(h)
+            h2d, d2h = a + W.nbytes + L.nbytes + pts.nbytes, b
+            tvbx.sweep_destroy(h)
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            e2e_step()
+        el_e = time.perf_counter() - t0
+        barrier()
+        te = torch.tensor([el_e], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": k_e2e * region_steps * world / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    if rank == 0:
+        peaks = measured_peaks()
+        bytes_rs = algorithmic_bytes_per_region_step(W, ts)
+        achieved = bytes_rs * sim_rs / (sim_ms * 1e-3) / 1e9 if sim_ms > 0 else None
+        peak = peaks.get("hbm_gbs") if peaks else 6800.0
+        traffic_rs = ncu_traffic_per_region_step()
+        per_launch_rs = sim_rs / max(sim_launches, 1)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak if achieved else None,
+                    "traffic": traffic_rs * per_launch_rs if traffic_rs else None,
+                    "kernel": "sim_chunk_kernel", "peak_source": "measured" if peaks else "fallback",
+                    "algorithmic_bytes_per_region_step": bytes_rs,
+                    "region_steps_per_launch": per_launch_rs,
+                    "avg_launch_ms": sim_ms / max(sim_launches, 1),
+                    "sim_kernel_share_of_step": (sim_ms * 1e-3) / el if el > 0 else None}
+        base = cpu_baseline()[0] if not args.no_cpu_baseline else None
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * el_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "paper-scale plain sweep: 32768 sets (g16 x b_e16 x E_L_i16 x tau_w_e8) "
+                                       "per GPU, 68-region synthetic connectome (seed 1), 50000 steps "
+                                       "(5 s, dt 0.1 ms), v 4 m/s, FC + FCD (1000/500) + summary",
+                           "n_sets_per_gpu": P, "n_regions": N, "n_steps": S, "tavg_steps": ts,
+                           "parallelism": f"dp{world} (set slices, no collective)",
+                           "l2": "inputs larger than L2 (ring 4.3 GB, series 44.6 GB per GPU)"},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+                "cpu_baseline": base}
+        print(json.dumps(line), flush=True)
+    sw.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_engine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -200,6 +200,12 @@ tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* me
 /* Copy the E series [n_sets][n_regions][n_samples] (kHz) of the last run. */
 tvbx_status tvbx_series(const tvbx_sweep* h, int32_t mem, float* out);
 
+/* Copy a window of the E series: sets [set_begin, set_begin + set_count) and
+ * samples [t_begin, t_begin + t_count) into out [set_count][n_regions][t_count].
+ * Errors: TVBX_E_INVALID_ARG when the window leaves the series. */
+tvbx_status tvbx_series_range(const tvbx_sweep* h, int64_t set_begin, int64_t set_count,
+                              int64_t t_begin, int64_t t_count, int32_t mem, float* out);
+
 /* Copy the final state [n_sets][8][n_regions] of the last run, variables in
  * the order E, I, C_ee, C_ei, C_ii, W_e, W_i, OU (OU is the shared process of
  * each region when noise is shared). */
@@ -226,6 +232,22 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
 tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t n, int32_t mem,
                                    const float* x_e, const float* x_i, const float* W,
                                    const float* E_L, float* out);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t tvbx_launch_count(void);
+
+/* Bytes this handle has copied host->device and device->host since it was
+ * created (inputs uploaded by tvbx_run, outputs read to host memory). */
+tvbx_status tvbx_transfer_bytes(const tvbx_sweep* h, uint64_t* h2d, uint64_t* d2h);
+
+/* Kernel timing: when enabled, tvbx_run records a CUDA event pair around every
+ * launch of the simulation kernel on the run's stream. tvbx_profile_read
+ * synchronises that stream and returns the summed device time (ms), the
+ * number of timed launches and the (set, region, step) updates they made,
+ * accumulated since the last tvbx_profile_enable call. */
+tvbx_status tvbx_profile_enable(tvbx_sweep* h, int32_t enable);
+tvbx_status tvbx_profile_read(tvbx_sweep* h, double* sim_ms, int64_t* sim_launches,
+                              double* region_steps);
 
 /* Release the handle and its device memory. NULL is accepted. */
 tvbx_status tvbx_sweep_destroy(tvbx_sweep* h);

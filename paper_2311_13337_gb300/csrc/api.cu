@@ -16,7 +16,15 @@
 #include "internal.h"
 #include "tvbx.h"
 
+#include <atomic>
+
 using namespace tvbx;
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+
+void tvbx::note_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 
@@ -174,21 +182,28 @@ struct tvbx_sweep {
     tvbx_run_cfg cfg{};
     int64_t T = 0;
     cudaStream_t stream = nullptr;
+    uint64_t h2d = 0, d2h = 0;      // bytes copied host <-> device
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;    // pairs around simulation launches
+    size_t ev_used = 0;
+    double prof_region_steps = 0.0;
     std::vector<int64_t> perm;      // internal -> external
+    std::vector<int64_t> inv;       // external -> internal
     bool identity = true;
     int32_t pb = 16;
 
     DevBuf d_prm, d_ext, d_state, d_status, d_ring, d_series, d_ou_table, d_ou_state;
     DevBuf d_csr_row, d_csr_cd, d_csr_w, d_groups, d_tiles;
-    DevBuf d_blocks, d_fc, d_chi, d_meanfc, d_vec, d_fcd, d_tmp, d_perm, d_mean_e, d_mean_i;
+    DevBuf d_blocks, d_fc, d_chi, d_meanfc, d_vec, d_fcd, d_tmp, d_perm, d_inv, d_mean_e, d_mean_i;
 
     ~tvbx_sweep()
     {
         DevBuf* all[] = {&d_prm, &d_ext, &d_state, &d_status, &d_ring, &d_series, &d_ou_table,
                          &d_ou_state, &d_csr_row, &d_csr_cd, &d_csr_w, &d_groups, &d_tiles,
                          &d_blocks, &d_fc, &d_chi, &d_meanfc, &d_vec, &d_fcd, &d_tmp, &d_perm,
-                         &d_mean_e, &d_mean_i};
+                         &d_inv, &d_mean_e, &d_mean_i};
         for (DevBuf* b : all) b->release();
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
 };
 
@@ -211,15 +226,17 @@ __global__ void gather_u32_kernel(const uint32_t* __restrict__ in, uint32_t* __r
          i += (int64_t)gridDim.x * blockDim.x)
         out[perm[i]] = in[i];
 }
-// series [T][N][P] (internal) -> out [P][N][T] (external)
+// series [T][N][P] (internal order) -> out [np][N][nt] for external sets
+// [p0, p0 + np) and samples [t0, t0 + nt); inv maps external -> internal.
 __global__ void series_export_kernel(const float* __restrict__ X, float* __restrict__ out,
-                                     const int64_t* __restrict__ perm, int64_t T, int32_t N, int64_t P)
+                                     const int64_t* __restrict__ inv, int32_t N, int64_t P, int64_t p0,
+                                     int64_t np, int64_t t0, int64_t nt)
 {
-    const int64_t total = T * N * P;
+    const int64_t total = np * N * nt;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = i % P, rest = i / P, k = rest % N, t = rest / N;
-        out[(perm[p] * N + k) * T + t] = X[i];
+        const int64_t t = i % nt, rest = i / nt, k = rest % N, q = rest / N;
+        out[i] = X[((t0 + t) * N + k) * P + inv[p0 + q]];
     }
 }
 // state [SV][N][P] -> out [P][8][N]; shared OU from ou_state[k]
@@ -241,9 +258,11 @@ namespace {
 
 int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 8192); }
 
-tvbx_status copy_out(void* dst, const void* src, size_t bytes, int32_t mem, cudaStream_t s)
+tvbx_status copy_out(void* dst, const void* src, size_t bytes, int32_t mem, cudaStream_t s,
+                     uint64_t* d2h_counter = nullptr)
 {
     if (bytes == 0) return TVBX_OK;
+    if (mem == TVBX_MEM_HOST && d2h_counter) *d2h_counter += bytes;
     CK(cudaMemcpyAsync(dst, src, bytes, mem == TVBX_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s),
        "copy out");
     if (mem == TVBX_MEM_HOST) CK(cudaStreamSynchronize(s), "synchronize");
@@ -254,16 +273,17 @@ tvbx_status copy_out(void* dst, const void* src, size_t bytes, int32_t mem, cuda
 tvbx_status export_rows(tvbx_sweep* h, const float* src, int64_t len, int32_t mem, float* dst)
 {
     const size_t bytes = sizeof(float) * (size_t)h->P * len;
-    if (h->identity) return copy_out(dst, src, bytes, mem, h->stream);
+    if (h->identity) return copy_out(dst, src, bytes, mem, h->stream, &h->d2h);
     float* target = dst;
     if (mem == TVBX_MEM_HOST) {
         CK(h->d_tmp.ensure(bytes), "export buffer");
         target = h->d_tmp.as<float>();
     }
+    note_launch();
     gather_rows_kernel<<<grid_for(h->P * len), 256, 0, h->stream>>>(src, target, h->d_perm.as<int64_t>(), h->P,
                                                                        len);
     CK(cudaGetLastError(), "gather rows");
-    if (mem == TVBX_MEM_HOST) return copy_out(dst, target, bytes, mem, h->stream);
+    if (mem == TVBX_MEM_HOST) return copy_out(dst, target, bytes, mem, h->stream, &h->d2h);
     return TVBX_OK;
 }
 
@@ -494,6 +514,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     CK(h->d_prm.ensure(sizeof(float) * prm_soa.size()), "parameters");
     CK(h->d_ext.ensure(sizeof(int64_t) * P), "set index");
     CK(h->d_perm.ensure(sizeof(int64_t) * P), "set index");
+    CK(h->d_inv.ensure(sizeof(int64_t) * P), "set index");
     CK(h->d_state.ensure(sizeof(float) * (size_t)SV_COUNT * N * P), "state");
     CK(h->d_status.ensure(sizeof(uint32_t) * P), "status");
     CK(h->d_ring.ensure(sizeof(float) * (size_t)std::max<int64_t>(ring_floats, 1)), "ring buffers");
@@ -515,9 +536,15 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         d.p_base = groups[gi].p_base;
         d.pad = 0;
     }
+    h->h2d += sizeof(float) * prm_soa.size() + 3 * sizeof(int64_t) * P + sizeof(int32_t) * all_row.size() +
+              sizeof(uint32_t) * all_cd.size() + sizeof(float) * all_w.size() + sizeof(GroupDev) * gdev.size() +
+              sizeof(TileDev) * tiles.size();
     CK(cudaMemcpyAsync(h->d_prm.ptr, prm_soa.data(), sizeof(float) * prm_soa.size(), cudaMemcpyHostToDevice, s), "upload");
     CK(cudaMemcpyAsync(h->d_ext.ptr, h->perm.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice, s), "upload");
     CK(cudaMemcpyAsync(h->d_perm.ptr, h->perm.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice, s), "upload");
+    h->inv.assign((size_t)P, 0);
+    for (int64_t i = 0; i < P; ++i) h->inv[h->perm[i]] = i;
+    CK(cudaMemcpyAsync(h->d_inv.ptr, h->inv.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice, s), "upload");
     CK(cudaMemcpyAsync(h->d_csr_row.ptr, all_row.data(), sizeof(int32_t) * all_row.size(), cudaMemcpyHostToDevice, s), "upload");
     CK(cudaMemcpyAsync(h->d_csr_cd.ptr, all_cd.data(), sizeof(uint32_t) * all_cd.size(), cudaMemcpyHostToDevice, s), "upload");
     CK(cudaMemcpyAsync(h->d_csr_w.ptr, all_w.data(), sizeof(float) * all_w.size(), cudaMemcpyHostToDevice, s), "upload");
@@ -564,7 +591,20 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         if (!c.noise_per_set)
             CK(launch_ou_table(a.m, h->d_ou_table.as<float>(), h->d_ou_state.as<float>(), N, n0, a.n_chunk, c.seed, s),
                "OU table");
+        if (h->profiling) {
+            while (h->ev.size() < h->ev_used + 2) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e), "profiling event");
+                h->ev.push_back(e);
+            }
+            CK(cudaEventRecord(h->ev[h->ev_used], s), "profiling event");
+        }
         CK(launch_sim_chunk(a, (int32_t)tiles.size(), pb, s), "simulation chunk");
+        if (h->profiling) {
+            CK(cudaEventRecord(h->ev[h->ev_used + 1], s), "profiling event");
+            h->ev_used += 2;
+            h->prof_region_steps += (double)P * N * a.n_chunk;
+        }
     }
     h->cfg = c;
     h->T = T;
@@ -676,11 +716,12 @@ tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* me
         if (!h->identity) {
             CK(h->d_tmp.ensure(sizeof(uint32_t) * P), "export buffer");
             target = mem == TVBX_MEM_HOST ? h->d_tmp.as<uint32_t>() : status;
+            note_launch();
             gather_u32_kernel<<<grid_for(P), 256, 0, h->stream>>>(h->d_status.as<uint32_t>(), target,
                                                                    h->d_perm.as<int64_t>(), P);
             CK(cudaGetLastError(), "gather status");
-            if (mem == TVBX_MEM_HOST && (st = copy_out(status, target, sizeof(uint32_t) * P, mem, h->stream))) return st;
-        } else if ((st = copy_out(status, h->d_status.ptr, sizeof(uint32_t) * P, mem, h->stream))) {
+            if (mem == TVBX_MEM_HOST && (st = copy_out(status, target, sizeof(uint32_t) * P, mem, h->stream, &h->d2h))) return st;
+        } else if ((st = copy_out(status, h->d_status.ptr, sizeof(uint32_t) * P, mem, h->stream, &h->d2h))) {
             return st;
         }
     }
@@ -688,24 +729,37 @@ tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* me
     return TVBX_OK;
 }
 
-tvbx_status tvbx_series(const tvbx_sweep* hc, int32_t mem, float* out)
+tvbx_status tvbx_series_range(const tvbx_sweep* hc, int64_t set_begin, int64_t set_count, int64_t t_begin,
+                              int64_t t_count, int32_t mem, float* out)
 {
     tvbx_sweep* h = const_cast<tvbx_sweep*>(hc);
     if (!h || !out) return fail(TVBX_E_INVALID_ARG, "NULL handle or out");
     if (check_mem(mem)) return TVBX_E_INVALID_ARG;
-    if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_series before tvbx_run");
-    const size_t total = (size_t)h->T * h->N * h->P;
+    if (!h->ran) return fail(TVBX_E_BAD_STATE, "series export before tvbx_run");
+    if (set_begin < 0 || set_count < 0 || set_begin + set_count > h->P || t_begin < 0 || t_count < 0 ||
+        t_begin + t_count > h->T)
+        return fail(TVBX_E_INVALID_ARG, "series window outside [0, %lld) x [0, %lld)", (long long)h->P,
+                    (long long)h->T);
+    const size_t total = (size_t)set_count * h->N * t_count;
     if (total == 0) return TVBX_OK;
     float* target = out;
     if (mem == TVBX_MEM_HOST) {
         CK(h->d_tmp.ensure(sizeof(float) * total), "export buffer");
         target = h->d_tmp.as<float>();
     }
-    series_export_kernel<<<grid_for((int64_t)total), 256, 0, h->stream>>>(h->d_series.as<float>(), target,
-                                                                          h->d_perm.as<int64_t>(), h->T, h->N, h->P);
+    note_launch();
+    series_export_kernel<<<grid_for((int64_t)total), 256, 0, h->stream>>>(
+        h->d_series.as<float>(), target, h->d_inv.as<int64_t>(), h->N, h->P, set_begin, set_count, t_begin,
+        t_count);
     CK(cudaGetLastError(), "series export");
-    if (mem == TVBX_MEM_HOST) return copy_out(out, target, sizeof(float) * total, mem, h->stream);
+    if (mem == TVBX_MEM_HOST) return copy_out(out, target, sizeof(float) * total, mem, h->stream, &h->d2h);
     return TVBX_OK;
+}
+
+tvbx_status tvbx_series(const tvbx_sweep* h, int32_t mem, float* out)
+{
+    if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
+    return tvbx_series_range(h, 0, h->P, 0, h->T, mem, out);
 }
 
 tvbx_status tvbx_state(const tvbx_sweep* hc, int32_t mem, float* out)
@@ -720,11 +774,12 @@ tvbx_status tvbx_state(const tvbx_sweep* hc, int32_t mem, float* out)
         CK(h->d_tmp.ensure(sizeof(float) * total), "export buffer");
         target = h->d_tmp.as<float>();
     }
+    note_launch();
     state_export_kernel<<<grid_for((int64_t)total), 256, 0, h->stream>>>(
         h->d_state.as<float>(), h->cfg.noise_per_set ? nullptr : h->d_ou_state.as<float>(), target,
         h->d_perm.as<int64_t>(), h->N, h->P);
     CK(cudaGetLastError(), "state export");
-    if (mem == TVBX_MEM_HOST) return copy_out(out, target, sizeof(float) * total, mem, h->stream);
+    if (mem == TVBX_MEM_HOST) return copy_out(out, target, sizeof(float) * total, mem, h->stream, &h->d2h);
     return TVBX_OK;
 }
 
@@ -762,6 +817,42 @@ tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t
     CK(cudaDeviceSynchronize(), "synchronize");
     in.release();
     res.release();
+    return TVBX_OK;
+}
+
+uint64_t tvbx_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+tvbx_status tvbx_transfer_bytes(const tvbx_sweep* h, uint64_t* h2d, uint64_t* d2h)
+{
+    if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
+    if (h2d) *h2d = h->h2d;
+    if (d2h) *d2h = h->d2h;
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_profile_enable(tvbx_sweep* h, int32_t enable)
+{
+    if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
+    if (h->stream) CK(cudaStreamSynchronize(h->stream), "synchronize");
+    h->profiling = enable != 0;
+    h->ev_used = 0;
+    h->prof_region_steps = 0.0;
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_profile_read(tvbx_sweep* h, double* sim_ms, int64_t* sim_launches, double* region_steps)
+{
+    if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]), "event time");
+        total += ms;
+    }
+    if (sim_ms) *sim_ms = total;
+    if (sim_launches) *sim_launches = (int64_t)(h->ev_used / 2);
+    if (region_steps) *region_steps = h->prof_region_steps;
     return TVBX_OK;
 }
 

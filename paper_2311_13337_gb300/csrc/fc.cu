@@ -328,12 +328,14 @@ cudaError_t launch_fc(const FcArgs& a, cudaStream_t s)
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.P + FC_SETS - 1) / FC_SETS, chunks);
+    note_launch();
     fc_moments_kernel<<<grid, FC_THREADS, smem, s>>>(a, Npad, Tt, tasks_per_set, per_chunk);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem2 = sizeof(float) * ((size_t)a.N * a.N + a.N + 64);
     e = cudaFuncSetAttribute(fc_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
+    note_launch();
     fc_finalize_kernel<<<a.P, 512, smem2, s>>>(a);
     return cudaGetLastError();
 }
@@ -343,6 +345,7 @@ cudaError_t launch_fcd(const float* blocks, int32_t P, int32_t N, int32_t n_bloc
                        float* vec_scratch, float* fcd, cudaStream_t s)
 {
     const size_t smem = sizeof(float) * ((size_t)N + 2 * n_windows + 64);
+    note_launch();
     fcd_kernel<<<P, 256, smem, s>>>(blocks, N, n_blocks, blocks_per_window, n_windows, window_samples,
                                     vec_scratch, fcd);
     return cudaGetLastError();
@@ -351,6 +354,7 @@ cudaError_t launch_fcd(const float* blocks, int32_t P, int32_t N, int32_t n_bloc
 cudaError_t launch_summary(const float* state, int32_t N, int32_t P, int64_t n_samples,
                            float* mean_e_hz, float* mean_i_hz, cudaStream_t s)
 {
+    note_launch();
     summary_kernel<<<(P + 255) / 256, 256, 0, s>>>(state, N, P, n_samples, mean_e_hz, mean_i_hz);
     return cudaGetLastError();
 }

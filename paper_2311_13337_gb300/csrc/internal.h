@@ -8,6 +8,9 @@
 
 namespace tvbx {
 
+// Process-wide count of kernel launches made by this library.
+void note_launch(uint64_t n = 1);
+
 // Number of per-(set, region) state words kept across steps and chunks:
 // E, I, C_ee, C_ei, C_ii, W_e, W_i, OU, then the temporal-average accumulators
 // of E and I, then compensated running sums (sum, carry) of the E and I samples.

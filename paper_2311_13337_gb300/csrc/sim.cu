@@ -442,6 +442,7 @@ size_t sim_smem_bytes(int N, int pb) { return sizeof(float) * (size_t)SV_COUNT *
 cudaError_t launch_init_state(const SimArgs& a, cudaStream_t s)
 {
     const int64_t NP = (int64_t)a.N * a.P;
+    note_launch();
     init_state_kernel<<<1024, 256, 0, s>>>(a.state, a.status, NP, a.P, a.m.E0, a.m.I0);
     return cudaGetLastError();
 }
@@ -449,6 +450,7 @@ cudaError_t launch_init_state(const SimArgs& a, cudaStream_t s)
 cudaError_t launch_init_ring(float* ring, int64_t count, float value, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
+    note_launch();
     fill_kernel<<<2048, 256, 0, s>>>(ring, count, value);
     return cudaGetLastError();
 }
@@ -457,6 +459,7 @@ cudaError_t launch_ou_table(const DevModel& m, float* table, float* ou_state, in
                             int64_t n0, int32_t n_chunk, uint64_t seed, cudaStream_t s)
 {
     if (n_chunk <= 0) return cudaSuccess;
+    note_launch();
     ou_table_kernel<<<N, 256, 0, s>>>(m, table, ou_state, N, n0, n_chunk, seed);
     return cudaGetLastError();
 }
@@ -469,6 +472,7 @@ static cudaError_t launch_sim_pb(const SimArgs& a, int32_t n_tiles, cudaStream_t
     cudaError_t e = cudaFuncSetAttribute(sim_chunk_kernel<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    note_launch();
     sim_chunk_kernel<PB><<<n_tiles, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -488,6 +492,7 @@ cudaError_t launch_tf_eval(const DevModel& m, int pop, int64_t n, const float* x
                            const float* W, const float* E_L, float* out, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
+    note_launch();
     tf_eval_kernel<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(
         m, pop, n, x_e, x_i, W, E_L, out);
     return cudaGetLastError();

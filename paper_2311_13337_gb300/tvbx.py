@@ -72,7 +72,8 @@ class FcCfg(ctypes.Structure):
 _lib = None
 EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep_create",
            "tvbx_sweep_create_points", "tvbx_sweep_info", "tvbx_run", "tvbx_summary", "tvbx_series",
-           "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_sweep_destroy")
+           "tvbx_series_range", "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_launch_count",
+           "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_sweep_destroy")
 
 
 def library_path() -> str:
@@ -101,12 +102,18 @@ def load(build_if_missing: bool = False):
     L.tvbx_run.argtypes = [vp, ctypes.POINTER(RunCfg), vp]
     L.tvbx_summary.argtypes = [vp, i32, fp, fp, fp, fp, fp]
     L.tvbx_series.argtypes = [vp, i32, fp]
+    L.tvbx_series_range.argtypes = [vp, i64, i64, i64, i64, i32, fp]
     L.tvbx_state.argtypes = [vp, i32, fp]
     L.tvbx_fc.argtypes = [vp, ctypes.POINTER(FcCfg), i32, fp, fp, ctypes.POINTER(i32)]
     L.tvbx_transfer_function.argtypes = [ctypes.POINTER(Model), i32, i64, i32, fp, fp, fp, fp, fp]
     L.tvbx_sweep_destroy.argtypes = [vp]
+    L.tvbx_launch_count.restype = ctypes.c_uint64
+    L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    L.tvbx_profile_enable.argtypes = [vp, i32]
+    L.tvbx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                    ctypes.POINTER(ctypes.c_double)]
     for name in EXPORTS:
-        if name not in ("tvbx_version", "tvbx_last_error"):
+        if name not in ("tvbx_version", "tvbx_last_error", "tvbx_launch_count"):
             getattr(L, name).restype = ctypes.c_int32
     _lib = L
     return L
@@ -237,6 +244,12 @@ def series(h, out):
     _check(load().tvbx_series(h, mem, ptr), "tvbx_series")
 
 
+def series_range(h, set_begin, set_count, t_begin, t_count, out):
+    ptr, mem = _out_ptr(out)
+    _check(load().tvbx_series_range(h, int(set_begin), int(set_count), int(t_begin), int(t_count), mem, ptr),
+           "tvbx_series_range")
+
+
 def state(h, out):
     ptr, mem = _out_ptr(out)
     _check(load().tvbx_state(h, mem, ptr), "tvbx_state")
@@ -264,6 +277,26 @@ def transfer_function(pop: int, x_e, x_i, W, E_L, model: Model | None = None) ->
                                          MEM_HOST, *fptr, ctypes.c_void_p(out.ctypes.data)),
            "tvbx_transfer_function")
     return out
+
+
+def launch_count() -> int:
+    return int(load().tvbx_launch_count())
+
+
+def transfer_bytes(h) -> tuple[int, int]:
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().tvbx_transfer_bytes(h, ctypes.byref(a), ctypes.byref(b)), "tvbx_transfer_bytes")
+    return a.value, b.value
+
+
+def profile_enable(h, enable: bool = True):
+    _check(load().tvbx_profile_enable(h, int(bool(enable))), "tvbx_profile_enable")
+
+
+def profile_read(h) -> tuple[float, int, float]:
+    ms, n, rs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    _check(load().tvbx_profile_read(h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(rs)), "tvbx_profile_read")
+    return ms.value, n.value, rs.value
 
 
 def sweep_destroy(h):
@@ -301,6 +334,13 @@ class Sweep:
     def series(self) -> np.ndarray:
         x = np.zeros((self.n_sets, self.n_regions, self.n_samples), dtype=np.float32)
         series(self.h, x)
+        return x
+
+    def series_window(self, set_begin, set_count, t_begin=0, t_count=None) -> np.ndarray:
+        if t_count is None:
+            t_count = self.n_samples - t_begin
+        x = np.zeros((set_count, self.n_regions, t_count), dtype=np.float32)
+        series_range(self.h, set_begin, set_count, t_begin, t_count, x)
         return x
 
     def state(self) -> np.ndarray:

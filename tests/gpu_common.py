@@ -1,0 +1,41 @@
+"""Shared helpers of the GPU parity tests (engine through the C-ABI vs the
+FP64 oracle on the same seeded inputs)."""
+import numpy as np
+import pytest
+
+# Tolerances (FP32 engine vs FP64 oracle):
+#  - trajectories: 1e-3 relative over the first 200 ms of 1 ms samples, with
+#    a 1e-9 kHz floor on the reference magnitude;
+#  - mean rates: 1% relative (plus 1e-6 Hz for silent sets);
+#  - FC entries: 0.05 absolute;
+#  - sync/async label: agreement on >= 99% of sets.
+TRAJ_RTOL = 1e-3
+TRAJ_FLOOR = 1e-9
+RATE_RTOL = 1e-2
+FC_ATOL = 0.05
+
+
+def require_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2311_13337_gb300 import tvbx
+    return tvbx
+
+
+def rel_err(a, ref, floor=TRAJ_FLOOR):
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return np.abs(a - ref) / np.maximum(np.abs(ref), floor)
+
+
+def well_conditioned(E_ref, min_rel_std=1e-4):
+    """Sets whose every region's series varies by more than min_rel_std of its
+    mean: there FP32 rounding of the state is far below the signal and the
+    FP32 FC is meaningful."""
+    E = np.asarray(E_ref, dtype=np.float64)
+    sd = E.std(axis=-1)
+    mu = np.abs(E.mean(axis=-1))
+    return np.all(sd > min_rel_std * np.maximum(mu, 1e-12), axis=-1)

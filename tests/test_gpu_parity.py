@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA engine, called through the C-ABI, against the FP64
+oracle on the same seeded inputs, element by element.
+
+Covers each step of the hot path: the transfer function and its
+derivatives, the first integration steps of every state variable, whole
+sweeps (trajectories, mean rates, FC, FCD, synchrony labels), per-set and
+shared noise, several conduction speeds (delay groups), ragged tiles, zero
+delays, g = 0, shard invariance, non-finite parameters, and edge cases."""
+import numpy as np
+import pytest
+
+from gpu_common import FC_ATOL, RATE_RTOL, TRAJ_RTOL, rel_err, require_gpu, well_conditioned
+from paper_2311_13337_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DT = 0.1
+
+
+@pytest.fixture(scope="module")
+def tvbx():
+    return require_gpu()
+
+
+@pytest.fixture(scope="module")
+def conn():
+    return synth.connectome(68)
+
+
+def _gpu(tvbx, W, L, n_steps, ts, axes=None, points=None, **kw):
+    sw = tvbx.Sweep(W, L, axes=axes, points=points)
+    sw.run(dt_ms=DT, n_steps=n_steps, tavg_steps=ts, **kw)
+    return sw
+
+
+@pytest.mark.parametrize("pop", [0, 1])
+def test_transfer_function_and_derivatives(tvbx, oracle, pop):
+    rng = np.random.default_rng(10 + pop)
+    n = 3000
+    xe, xi = rng.uniform(0, 0.05, n), rng.uniform(0, 0.05, n)
+    W, EL = rng.uniform(0, 150, n), rng.uniform(-80, -58, n)
+    got = tvbx.transfer_function(pop, xe, xi, W, EL).astype(np.float64)
+    m = oracle.make_model()
+    ref = np.zeros((n, 7))
+    for i in range(n):
+        jet, aux = oracle.tf_eval(m, "e" if pop == 0 else "i", EL[i], xe[i], xi[i], W[i])
+        ref[i, :6], ref[i, 6] = jet, aux[1]
+    for c in range(7):
+        scale = np.abs(ref[:, c]).max()
+        rtol, atol = (2e-4, 1e-5) if c < 3 else ((2e-3, 5e-4) if c < 6 else (1e-6, 0.0))
+        bad = np.abs(got[:, c] - ref[:, c]) > rtol * np.abs(ref[:, c]) + atol * scale
+        assert not bad.any(), f"component {c}: {bad.sum()} points out of tolerance"
+
+
+@pytest.mark.parametrize("n_steps", [1, 10, 100])
+def test_first_steps_every_state_variable(tvbx, oracle, conn, n_steps):
+    W, L = conn
+    axes = synth.SMALL_SWEEP_AXES
+    sw = _gpu(tvbx, W, L, n_steps, 1, axes=axes, seed=1)
+    st = sw.state().astype(np.float64)
+    ref = oracle.simulate(oracle.make_model(), W, L, oracle.expand_grid(axes), DT, n_steps, 1, 1)["state"]
+    for v in range(8):
+        scale = np.abs(ref[:, v]).max()
+        assert np.all(np.abs(st[:, v] - ref[:, v]) <= 1e-4 * np.abs(ref[:, v]) + 1e-6 * scale), v
+
+
+def _compare_sweep(tvbx_sw, ref, oracle, traj_samples=200, label_frac=1.0):
+    E = tvbx_sw.series()
+    s = tvbx_sw.summary()
+    fc = tvbx_sw.fc()
+    rs = oracle.summary(ref["E"], ref["I"])
+    finite = (ref["status"] & oracle.ST_NONFINITE) == 0
+    assert np.array_equal(s["status"] & 1, ref["status"] & 1)
+    r = rel_err(E[finite, :, :traj_samples], ref["E"][finite, :, :traj_samples])
+    assert r.max() <= TRAJ_RTOL, f"trajectory error {r.max():.3g}"
+    for key in ("mean_e_hz", "mean_i_hz"):
+        err = np.abs(s[key][finite] - rs[key][finite])
+        assert np.all(err <= RATE_RTOL * np.abs(rs[key][finite]) + 1e-6), key
+    good = finite & well_conditioned(ref["E"])
+    if good.any():
+        assert np.abs(fc[good] - rs["fc"][good]).max() <= FC_ATOL
+    agree = (s["chi"][finite] >= 0.5) == rs["sync"][finite]
+    assert agree.mean() >= label_frac
+    return E, s, fc, rs
+
+
+def test_small_sweep_parity(tvbx, oracle, conn):
+    """16 sets (g x b_e), 68 regions, 1 s."""
+    W, L = conn
+    axes = synth.SMALL_SWEEP_AXES
+    sw = _gpu(tvbx, W, L, 10_000, 10, axes=axes, seed=1)
+    ref = oracle.simulate(oracle.make_model(), W, L, oracle.expand_grid(axes), DT, 10_000, 10, 1)
+    E, s, fc, rs = _compare_sweep(sw, ref, oracle)
+    assert rel_err(E, ref["E"]).max() <= TRAJ_RTOL   # over the whole second
+    assert np.abs(fc - rs["fc"]).max() <= FC_ATOL
+    assert np.allclose(s["chi"], rs["chi"], atol=1e-3)
+    assert np.allclose(s["mean_fc"], rs["mean_fc"], atol=1e-3)
+
+
+def test_rich_dynamics_noise_speeds_ragged(tvbx, oracle, conn):
+    """Sets with oscillating and saturating dynamics, per-set noise, three
+    conduction speeds (three delay groups), 17 sets (ragged tiles)."""
+    W, L = conn
+    rng = np.random.default_rng(3)
+    pts = oracle.expand_grid([("g", [0.05, 0.3, 0.6]), ("b_e", [10.0, 70.0, 120.0]),
+                              ("speed", [2.0, 4.0, 7.0]), ("E_L_i", [-75.0, -64.0]), ("w_noise", [1e-4])])
+    pts = pts[rng.permutation(len(pts))[:17]]
+    sw = _gpu(tvbx, W, L, 8000, 10, points=pts, seed=5, noise_per_set=True, p_offset=3)
+    ref = oracle.simulate(oracle.make_model(), W, L, pts, DT, 8000, 10, 5, noise_per_set=True, p_offset=3)
+    _compare_sweep(sw, ref, oracle, label_frac=16 / 17)
+
+
+def test_zero_delays_and_uncoupled_regions(tvbx, oracle, conn):
+    W, L = conn
+    W, L = W[:12, :12].copy(), L[:12, :12].copy()
+    axes = [("g", [0.2, 0.5]), ("b_e", [20.0, 90.0])]
+    Lz = np.zeros_like(L)
+    sw = _gpu(tvbx, W, Lz, 3000, 10, axes=axes, seed=2)
+    ref = oracle.simulate(oracle.make_model(), W, Lz, oracle.expand_grid(axes), DT, 3000, 10, 2)
+    assert rel_err(sw.series(), ref["E"]).max() <= TRAJ_RTOL
+    # g = 0: every region evolves as a lone node with its own noise stream
+    axes0 = [("g", [0.0]), ("b_e", [40.0])]
+    full = _gpu(tvbx, W, L, 2000, 10, axes=axes0, seed=4).series()
+    lone = _gpu(tvbx, np.zeros((1, 1)), np.zeros((1, 1)), 2000, 10, axes=axes0, seed=4).series()
+    assert np.array_equal(full[:, :1], lone)
+
+
+def test_shard_invariance(tvbx, conn):
+    W, L = conn
+    pts = np.array(synth_points(12))
+    full = _gpu(tvbx, W, L, 2000, 10, points=pts, seed=9, noise_per_set=True)
+    part = _gpu(tvbx, W, L, 2000, 10, points=pts[5:11], seed=9, noise_per_set=True, p_offset=5)
+    assert np.array_equal(full.series()[5:11], part.series())
+    assert np.array_equal(full.state()[5:11], part.state())
+
+
+def synth_points(n):
+    from oracle import oracle as O
+    grid = O.expand_grid([("g", (0.0, 0.8, 4)), ("b_e", (0.0, 120.0, 3))])
+    return grid[:n]
+
+
+def test_nonfinite_parameter_is_isolated(tvbx, conn):
+    W, L = conn
+    pts = np.array(synth_points(8))
+    bad = pts.copy()
+    bad[3, 0] = np.nan
+    a = _gpu(tvbx, W, L, 1500, 10, points=pts, seed=1)
+    b = _gpu(tvbx, W, L, 1500, 10, points=bad, seed=1)
+    sa, sb = a.summary(), b.summary()
+    assert sb["status"][3] & tvbx.SET_NONFINITE
+    keep = np.arange(8) != 3
+    assert np.array_equal(a.series()[keep], b.series()[keep])
+    assert np.array_equal(sa["status"][keep], sb["status"][keep])
+
+
+def test_fcd_matches_oracle(tvbx, oracle, conn):
+    W, L = conn
+    rng = np.random.default_rng(8)
+    pts = oracle.expand_grid([("g", [0.3, 0.6]), ("b_e", [60.0, 120.0]), ("E_L_i", [-78.0, -70.0]),
+                              ("w_noise", [1e-4])])
+    sw = _gpu(tvbx, W, L, 10_000, 10, points=pts, seed=6, transient_samples=100)
+    fc, fcd = sw.fc(fcd_window=200, fcd_step=100)
+    ref = oracle.simulate(oracle.make_model(), W, L, pts, DT, 10_000, 10, 6)
+    E = ref["E"][..., 100:]
+    good = well_conditioned(E) & ((ref["status"] & 1) == 0)
+    assert good.sum() >= 2
+    rfcd = oracle.fcd(E, 200, 100)
+    assert fcd.shape == rfcd.shape == (len(pts), 8, 8)
+    assert np.abs(fcd[good] - rfcd[good]).max() <= FC_ATOL
+    assert np.abs(fc[good] - oracle.fc_pearson(E)[good]).max() <= FC_ATOL
+
+
+def test_chunking_and_tavg_edge_cases(tvbx, conn):
+    W, L = conn
+    axes = [("g", [0.2]), ("b_e", [30.0, 60.0])]
+    a = _gpu(tvbx, W, L, 2100, 10, axes=axes, seed=3).series()
+    b = _gpu(tvbx, W, L, 2100, 10, axes=axes, seed=3, chunk_steps=70).series()
+    assert np.array_equal(a, b)   # chunk boundaries change nothing
+    c = _gpu(tvbx, W, L, 2105, 10, axes=axes, seed=3)  # trailing partial block dropped
+    assert c.n_samples == 210 and np.array_equal(c.series(), a)
+    one = _gpu(tvbx, W, L, 7, 1, axes=axes, seed=3)
+    assert one.series().shape == (2, 68, 7)
+    empty = _gpu(tvbx, W, L, 0, 10, axes=axes, seed=3)
+    assert empty.n_samples == 0
+    with pytest.raises(tvbx.TvbxError) as e:
+        empty.fc()
+    assert e.value.code == -6
+
+
+def test_invalid_run_arguments(tvbx, conn):
+    W, L = conn
+    sw = tvbx.Sweep(W, L, axes=[("g", [0.1])])
+    for kw in (dict(dt_ms=0.0), dict(tavg_steps=0), dict(chunk_steps=15, tavg_steps=10),
+               dict(n_steps=100, tavg_steps=10, transient_samples=10)):
+        args = dict(dt_ms=DT, n_steps=100, tavg_steps=10)
+        args.update(kw)
+        with pytest.raises(tvbx.TvbxError) as e:
+            sw.run(**args)
+        assert e.value.code == -1
+    with pytest.raises(tvbx.TvbxError) as e:
+        tvbx.Sweep(W, L, axes=[("speed", [0.0])]).run(dt_ms=DT, n_steps=10, tavg_steps=1)
+    assert e.value.code == -1
