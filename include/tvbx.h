@@ -52,6 +52,8 @@ typedef int32_t tvbx_status;
 #define TVBX_SET_CLAMP_HI  2u /* E or I was clamped at the upper bound */
 #define TVBX_SET_CLAMP_LO  4u /* E or I was clamped at the lower bound */
 #define TVBX_SET_ZERO_VAR  8u /* a region's E series had zero variance (FC row 0) */
+#define TVBX_SET_DIVERGED 16u /* a covariance passed C_div: the second-order
+                                 moment closure broke down (dynamics unaltered) */
 
 /* Sweepable axes: the per-set parameters of the sweep (Sec. "Vast parameter
  * space exploration and analysis", Table 4, plus the leak reversals of
@@ -89,6 +91,7 @@ typedef struct {
     double b_i, a_i, tau_w_i; /* inhibitory adaptation */
     double E_min, E_max;      /* E and I are clamped to [E_min, E_max] after each step, kHz */
     double E0, I0;            /* initial rates, kHz; also the constant prehistory of E */
+    double C_div;             /* |covariance| above this sets TVBX_SET_DIVERGED, kHz^2 */
     double defaults[TVBX_N_AXES]; /* value of each axis when it is not swept */
 } tvbx_model;
 
@@ -127,7 +130,15 @@ typedef struct {
     int32_t transient_samples;/* samples excluded from means, FC, chi */
     int32_t chunk_steps;      /* steps per kernel launch; 0 = automatic. Must be
                                  a multiple of tavg_steps when given. */
+    int32_t kernel;           /* TVBX_KERNEL_AUTO, TVBX_KERNEL_GENERAL, or
+                                 TVBX_KERNEL_PREFETCH + v for prefetch variant v */
+    int32_t reserved;         /* must be 0 */
 } tvbx_run_cfg;
+#define TVBX_KERNEL_AUTO     0 /* fastest kernel that fits the sweep */
+#define TVBX_KERNEL_GENERAL  1 /* any size: state in shared memory, direct gathers */
+#define TVBX_KERNEL_PREFETCH 2 /* + v: next-step gather prefetched into shared
+                                  memory; v = 0: 16 sets x 4 regions per thread,
+                                  2 CTAs/SM; 1: 32 x 4; 2: 16 x 2; 3: 16 x 4, 1 CTA/SM */
 
 /* FC settings (Sec. "Output": FC from the covariance of the series,
  * Eq. 6 Pearson; FCD over sliding windows). */

@@ -17,7 +17,10 @@
  *            over the connectome (linear coupling, delays = length / speed);
  *   - Table 1: the second-order threshold polynomial, used as printed (mV);
  *   - forward Euler for the ODEs, Euler-Maruyama for the OU term;
- *   - the temporal-average observable (block mean of tavg_steps steps).
+ *   - the temporal-average observable (block mean of tavg_steps steps);
+ *   - per-set status bits: non-finite state, E/I clamped, and "diverged" when
+ *     a covariance passes C_div (the moment closure has broken down; the
+ *     dynamics are not altered).
  * The transfer-function template (mu_V, sigma_V, tau_V and the normalisation
  * of the polynomial variables) is the semi-analytic one of Zerlaut et al. 2018,
  * which the paper cites for it; its derivatives with respect to the two input
@@ -64,6 +67,8 @@ typedef struct {
     double b_i, a_i, tau_w_i;   /* inhibitory adaptation (zero by default) */
     double E_min, E_max;        /* clamp of E and I after each step (kHz) */
     double E0, I0;              /* initial rates (kHz) */
+    double C_div;               /* a covariance beyond this magnitude marks the set
+                                   as diverged (status only; kHz^2) */
 } or_model;
 
 /* Per-set parameter vector: the sweepable axes, in this order. */
@@ -74,6 +79,7 @@ enum { OR_G, OR_B_E, OR_TAU_W_E, OR_E_L_E, OR_E_L_I, OR_SPEED, OR_A_E,
 #define OR_ST_NONFINITE 1u
 #define OR_ST_CLAMP_HI  2u
 #define OR_ST_CLAMP_LO  4u
+#define OR_ST_DIVERGED  16u
 
 /* ----------------------------------------------------------------------------
  * Philox4x32-10, from the SC'11 description: 10 rounds of the 4-word S-box
@@ -355,6 +361,8 @@ static uint32_t simulate_one(const or_model* m, int N, const double* Wc, const d
             Cee[k] = ce + dt * dCee;
             Cei[k] = cx + dt * dCei;
             Cii[k] = ci + dt * dCii;
+            if (fabs(Cee[k]) > m->C_div || fabs(Cei[k]) > m->C_div || fabs(Cii[k]) > m->C_div)
+                status |= OR_ST_DIVERGED;
             We[k] = We[k] + dt * dWe;
             Wi[k] = Wi[k] + dt * dWi;
 

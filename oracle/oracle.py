@@ -39,7 +39,7 @@ AXES = ("g", "b_e", "tau_w_e", "E_L_e", "E_L_i", "speed", "a_e", "w_noise",
         "cF_ee", "cF_ei", "cF_ie", "cF_ii")
 NPRM = len(AXES)
 
-ST_NONFINITE, ST_CLAMP_HI, ST_CLAMP_LO = 1, 2, 4
+ST_NONFINITE, ST_CLAMP_HI, ST_CLAMP_LO, ST_DIVERGED = 1, 2, 4, 16
 
 
 class Model(ctypes.Structure):
@@ -51,7 +51,7 @@ class Model(ctypes.Structure):
                [(n, ctypes.c_double) for n in
                 ("mu0", "dmu0", "sig0", "dsig0", "tau0", "dtau0", "rate_floor",
                  "tau_OU", "mu_OU", "sigma_OU", "b_i", "a_i", "tau_w_i",
-                 "E_min", "E_max", "E0", "I0")]
+                 "E_min", "E_max", "E0", "I0", "C_div")]
 
 
 def default_constants() -> dict:
@@ -69,6 +69,8 @@ def default_constants() -> dict:
     tau_e = tau_i = 5 ms, N_tot 10^4 with connection probability 0.05 and
     inhibitory fraction 0.2, T 20 ms. Eq. 4 gives mu = 0 and sigma = 1;
     tau_OU = 5 ms. E and I are clamped to [0, 0.2] kHz; they start at 1e-3 kHz.
+    A covariance beyond 1e30 kHz^2 (physically |c| <= E_max^2) flags the set
+    as diverged.
     """
     N_tot, p, gfrac = 10000.0, 0.05, 0.2
     return dict(
@@ -80,6 +82,7 @@ def default_constants() -> dict:
         mu0=-60.0, dmu0=10.0, sig0=4.0, dsig0=6.0, tau0=0.5, dtau0=1.0,
         rate_floor=1e-9, tau_OU=5.0, mu_OU=0.0, sigma_OU=1.0,
         b_i=0.0, a_i=0.0, tau_w_i=1.0, E_min=0.0, E_max=0.2, E0=1e-3, I0=1e-3,
+        C_div=1e30,
     )
 
 

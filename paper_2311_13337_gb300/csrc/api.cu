@@ -104,6 +104,7 @@ void engine_defaults(tvbx_model* m)
     m->b_i = 0.0; m->a_i = 0.0; m->tau_w_i = 1.0;
     m->E_min = 0.0; m->E_max = 0.2;
     m->E0 = 1e-3; m->I0 = 1e-3;
+    m->C_div = 1e30;
     double* d = m->defaults;
     d[TVBX_AXIS_G] = 0.0; d[TVBX_AXIS_B_E] = 0.0; d[TVBX_AXIS_TAU_W_E] = 417.0;
     d[TVBX_AXIS_E_L_E] = -64.0; d[TVBX_AXIS_E_L_I] = -64.0; d[TVBX_AXIS_SPEED] = 4.0;
@@ -130,6 +131,7 @@ DevModel to_device_model(const tvbx_model& m, double dt)
     d.b_i = (float)m.b_i; d.a_i = (float)m.a_i; d.inv_tau_w_i = (float)(1.0 / m.tau_w_i);
     d.E_min = (float)m.E_min; d.E_max = (float)m.E_max;
     d.E0 = (float)m.E0; d.I0 = (float)m.I0;
+    d.C_div = (float)std::min(m.C_div, 1e37);
     d.ou_a = (float)(dt / m.tau_OU);
     d.ou_b = (float)(m.sigma_OU * sqrt(dt) / m.tau_OU);
     d.ou_mu = (float)m.mu_OU;
@@ -143,7 +145,7 @@ bool model_ok(const tvbx_model& m)
                           m.T, m.dmu0, m.dsig0, m.dtau0, m.tau_OU, m.tau_w_i};
     for (double v : pos)
         if (!(v > 0.0) || !isfinite(v)) return false;
-    return m.E_max > m.E_min;
+    return m.E_max > m.E_min && m.C_div > 0.0;
 }
 
 int device_ready()
@@ -191,6 +193,7 @@ struct tvbx_sweep {
     std::vector<int64_t> inv;       // external -> internal
     bool identity = true;
     int32_t pb = 16;
+    int32_t variant = -1;           // simulation kernel of the last run
 
     DevBuf d_prm, d_ext, d_state, d_status, d_ring, d_series, d_ou_table, d_ou_state;
     DevBuf d_csr_row, d_csr_cd, d_csr_w, d_groups, d_tiles;
@@ -319,6 +322,10 @@ tvbx_status create_common(const double* weights, const double* tract_mm, int32_t
     *made = h;
     return TVBX_OK;
 }
+
+// Ring row stride: a group's sets rounded up to a multiple of 32 floats, so
+// that every tile's row segment starts on a 16-byte (indeed 128-byte) boundary.
+int64_t ring_stride(size_t sets) { return ((int64_t)sets + 31) / 32 * 32; }
 
 // Build the speed groups for dt: delays, CSR and ring depth per distinct speed.
 tvbx_status build_groups(tvbx_sweep* h, double dt, std::vector<Group>& groups)
@@ -474,7 +481,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         g.p_base = (int32_t)h->perm.size();
         ring_floats = (ring_floats + 63) / 64 * 64;   // 256-byte aligned ring per group
         g.ring_offset = ring_floats;
-        ring_floats += (int64_t)g.H * N * (int64_t)g.sets.size();
+        ring_floats += (int64_t)g.H * N * ring_stride(g.sets.size());
         for (int64_t e : g.sets) h->perm.push_back(e);
     }
     h->identity = true;
@@ -487,11 +494,31 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         for (int a = 0; a < TVBX_N_AXES; ++a)
             prm_soa[(size_t)a * P + i] = (float)h->prm[h->perm[i] * TVBX_N_AXES + a];
 
-    // tiles of pb sets; pb from the smem budget
+    // kernel and tile size: the prefetching kernel when its shared-memory
+    // gather buffer fits, else the general kernel
+    int nnz_max = 0;
+    for (const Group& g : groups) nnz_max = std::max(nnz_max, (int)g.col_dly.size());
+    if (c.kernel < TVBX_KERNEL_AUTO || c.kernel >= TVBX_KERNEL_PREFETCH + sim_fast_variants() || c.reserved != 0)
+        return fail(TVBX_E_INVALID_ARG, "unknown kernel %d", c.kernel);
+    int variant = -1;   // prefetch variant, -1 = general kernel
+    if (c.kernel == TVBX_KERNEL_AUTO) {
+        if (sim_fast_fits(1, N, nnz_max)) variant = 1;
+        else if (sim_fast_fits(0, N, nnz_max)) variant = 0;
+    } else if (c.kernel != TVBX_KERNEL_GENERAL) {
+        variant = c.kernel - TVBX_KERNEL_PREFETCH;
+        if (!sim_fast_fits(variant, N, nnz_max))
+            return fail(TVBX_E_UNSUPPORTED, "prefetch kernel %d does not fit %d regions / %d weights", c.kernel, N,
+                        nnz_max);
+    }
     int pb = 16;
-    while (pb > 8 && sim_smem_bytes(N, pb) > 200 * 1024) pb /= 2;
-    if (sim_smem_bytes(N, pb) > 200 * 1024) return fail(TVBX_E_UNSUPPORTED, "n_regions %d too large", N);
+    if (variant >= 0) {
+        pb = sim_fast_pb(variant);
+    } else {
+        while (pb > 8 && sim_smem_bytes(N, pb) > 200 * 1024) pb /= 2;
+        if (sim_smem_bytes(N, pb) > 200 * 1024) return fail(TVBX_E_UNSUPPORTED, "n_regions %d too large", N);
+    }
     h->pb = pb;
+    h->variant = variant;
     std::vector<TileDev> tiles;
     std::vector<GroupDev> gdev(groups.size());
     std::vector<int32_t> all_row;
@@ -534,6 +561,8 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         d.H = groups[gi].H;
         d.P_g = (int32_t)groups[gi].sets.size();
         d.p_base = groups[gi].p_base;
+        d.stride = (int32_t)ring_stride(groups[gi].sets.size());
+        d.nnz = (int32_t)groups[gi].col_dly.size();
         d.pad = 0;
     }
     h->h2d += sizeof(float) * prm_soa.size() + 3 * sizeof(int64_t) * P + sizeof(int32_t) * all_row.size() +
@@ -584,7 +613,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
 
     CK(launch_init_state(a, s), "init state");
     for (size_t gi = 0; gi < groups.size(); ++gi)
-        CK(launch_init_ring(gdev[gi].ring, (int64_t)gdev[gi].H * N * gdev[gi].P_g, a.m.E0, s), "init ring");
+        CK(launch_init_ring(gdev[gi].ring, (int64_t)gdev[gi].H * N * gdev[gi].stride, a.m.E0, s), "init ring");
     for (int64_t n0 = 0; n0 < c.n_steps; n0 += chunk) {
         a.n0 = n0;
         a.n_chunk = (int32_t)std::min<int64_t>(chunk, c.n_steps - n0);
@@ -599,7 +628,8 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
             }
             CK(cudaEventRecord(h->ev[h->ev_used], s), "profiling event");
         }
-        CK(launch_sim_chunk(a, (int32_t)tiles.size(), pb, s), "simulation chunk");
+        if (variant >= 0) CK(launch_sim_fast(a, variant, (int32_t)tiles.size(), nnz_max, s), "simulation chunk");
+        else CK(launch_sim_chunk(a, (int32_t)tiles.size(), pb, s), "simulation chunk");
         if (h->profiling) {
             CK(cudaEventRecord(h->ev[h->ev_used + 1], s), "profiling event");
             h->ev_used += 2;

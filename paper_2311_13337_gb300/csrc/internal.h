@@ -33,6 +33,7 @@ struct DevModel {
     float b_i, a_i, inv_tau_w_i;
     float E_min, E_max;
     float E0, I0;
+    float C_div;             // |covariance| above this marks the set diverged
     // OU (Eq. 4) by Euler-Maruyama: OU' = OU + ou_a (mu - OU) + ou_b xi
     float ou_a, ou_b, ou_mu;
     float dt;
@@ -45,8 +46,10 @@ struct GroupDev {
     const uint32_t* col_dly;   // [nnz] (delay << 16) | j
     const float* w;            // [nnz] u_kj
     int32_t H;                 // ring depth (max delay + 2)
-    int32_t P_g;               // sets in the group (ring stride)
+    int32_t P_g;               // sets in the group
     int32_t p_base;            // first internal set index of the group
+    int32_t stride;            // ring row stride in floats (P_g rounded up to 32)
+    int32_t nnz;               // nonzero weights (CSR entries)
     int32_t pad;
 };
 
@@ -89,6 +92,12 @@ cudaError_t launch_ou_table(const DevModel& m, float* table, float* ou_state, in
 cudaError_t launch_sim_chunk(const SimArgs& a, int32_t n_tiles, int32_t pb, cudaStream_t s);
 cudaError_t launch_tf_eval(const DevModel& m, int pop, int64_t n, const float* x_e, const float* x_i,
                            const float* W, const float* E_L, float* out, cudaStream_t s);
+// Prefetching kernel (sim_fast.cu): variant 0 = 16 sets per CTA, 1 = 32.
+cudaError_t launch_sim_fast(const SimArgs& a, int variant, int32_t n_tiles, int nnz_max, cudaStream_t s);
+bool sim_fast_fits(int variant, int N, int nnz_max);
+int sim_fast_pb(int variant);
+int sim_fast_variants();
+size_t sim_fast_smem_bytes(int N, int nnz, int pb);
 int sim_threads(int N, int pb);
 size_t sim_smem_bytes(int N, int pb);
 

@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=500)
     ap.add_argument("--fc", action="store_true")
     ap.add_argument("--noise-per-set", action="store_true")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 general, 2 + v prefetch variant v")
     args = ap.parse_args()
 
     import numpy as np
@@ -49,7 +50,7 @@ def main():
     sw = tvbx.Sweep(W, L, points=pts)
     t0 = time.time()
     sw.run(dt_ms=0.1, n_steps=args.n_steps, tavg_steps=10, seed=1, chunk_steps=args.chunk,
-           noise_per_set=args.noise_per_set)
+           noise_per_set=args.noise_per_set, kernel=args.kernel)
     if args.fc:
         sw.fc(fcd_window=min(1000, args.n_steps // 10), fcd_step=min(500, args.n_steps // 20))
     torch.cuda.synchronize()

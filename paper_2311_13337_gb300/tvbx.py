@@ -18,7 +18,7 @@ AXES = ("g", "b_e", "tau_w_e", "E_L_e", "E_L_i", "speed", "a_e", "w_noise",
         "cF_ee", "cF_ei", "cF_ie", "cF_ii")
 N_AXES = len(AXES)
 MEM_HOST, MEM_DEVICE = 0, 1
-SET_NONFINITE, SET_CLAMP_HI, SET_CLAMP_LO, SET_ZERO_VAR = 1, 2, 4, 8
+SET_NONFINITE, SET_CLAMP_HI, SET_CLAMP_LO, SET_ZERO_VAR, SET_DIVERGED = 1, 2, 4, 8, 16
 FC_FP32 = 0
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NUMERIC", -5: "TIMEOUT",
                 -6: "BAD_STATE", -7: "UNSUPPORTED"}
@@ -39,7 +39,7 @@ class Model(ctypes.Structure):
                [(n, ctypes.c_double) for n in
                 ("mu0", "dmu0", "sig0", "dsig0", "tau0", "dtau0", "rate_floor",
                  "tau_OU", "mu_OU", "sigma_OU", "b_i", "a_i", "tau_w_i",
-                 "E_min", "E_max", "E0", "I0")] + \
+                 "E_min", "E_max", "E0", "I0", "C_div")] + \
                [("defaults", ctypes.c_double * N_AXES)]
 
     def as_dict(self) -> dict:
@@ -62,7 +62,8 @@ class Grid(ctypes.Structure):
 class RunCfg(ctypes.Structure):
     _fields_ = [("dt_ms", ctypes.c_double), ("n_steps", ctypes.c_int64), ("tavg_steps", ctypes.c_int32),
                 ("noise_per_set", ctypes.c_int32), ("seed", ctypes.c_uint64), ("p_offset", ctypes.c_int64),
-                ("transient_samples", ctypes.c_int32), ("chunk_steps", ctypes.c_int32)]
+                ("transient_samples", ctypes.c_int32), ("chunk_steps", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class FcCfg(ctypes.Structure):
@@ -217,12 +218,16 @@ def sweep_info(h) -> tuple[int, int, int]:
     return p.value, n.value, t.value
 
 
+KERNEL_AUTO, KERNEL_GENERAL, KERNEL_PREFETCH = 0, 1, 2
+N_PREFETCH_VARIANTS = 4
+
+
 def run(h, dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
-        transient_samples=0, chunk_steps=0, stream=None):
+        transient_samples=0, chunk_steps=0, stream=None, kernel=KERNEL_AUTO):
     """Enqueue the integration on `stream` (a torch.cuda.Stream, a raw handle
     or None for the default stream)."""
     cfg = RunCfg(float(dt_ms), int(n_steps), int(tavg_steps), int(bool(noise_per_set)), int(seed),
-                 int(p_offset), int(transient_samples), int(chunk_steps))
+                 int(p_offset), int(transient_samples), int(chunk_steps), int(kernel), 0)
     sp = None
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))

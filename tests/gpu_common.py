@@ -39,3 +39,15 @@ def well_conditioned(E_ref, min_rel_std=1e-4):
     sd = E.std(axis=-1)
     mu = np.abs(E.mean(axis=-1))
     return np.all(sd > min_rel_std * np.maximum(mu, 1e-12), axis=-1)
+
+
+BAD = 1 | 16          # non-finite or diverged
+EVENTS = 1 | 2 | 4 | 16   # any clamp, divergence or non-finite event
+
+
+def conditioned_sets(gpu_status, ref_status):
+    """Sets on which neither side saw a clamp, divergence or non-finite event.
+    Elsewhere the dynamics pass through the non-smooth clamp of E and I, and a
+    relative perturbation of 1e-7 already moves the FP64 trajectory far (the
+    paper-scale test measures that spread)."""
+    return ((np.asarray(gpu_status) & EVENTS) == 0) & ((np.asarray(ref_status) & EVENTS) == 0)
