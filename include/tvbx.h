@@ -137,8 +137,9 @@ typedef struct {
 #define TVBX_KERNEL_AUTO     0 /* fastest kernel that fits the sweep */
 #define TVBX_KERNEL_GENERAL  1 /* any size: state in shared memory, direct gathers */
 #define TVBX_KERNEL_PREFETCH 2 /* + v: next-step gather prefetched into shared
-                                  memory; v = 0: 16 sets x 4 regions per thread,
-                                  2 CTAs/SM; 1: 32 x 4; 2: 16 x 2; 3: 16 x 4, 1 CTA/SM */
+                                  memory; CTA of 16 or 32 sets; v = 0: 16 sets,
+                                  2 sets x 1 region per thread; 1: 32 sets, 4 x 1;
+                                  2: 16 sets, 1 x 2; 3: 16 sets, 2 x 2 */
 
 /* FC settings (Sec. "Output": FC from the covariance of the series,
  * Eq. 6 Pearson; FCD over sliding windows). */

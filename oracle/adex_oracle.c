@@ -293,6 +293,8 @@ static uint32_t simulate_one(const or_model* m, int N, const double* Wc, const d
     const double cF_ie = prm[OR_CF_IE], cF_ii = prm[OR_CF_II];
     const int64_t T_out = S / ts;
     uint32_t status = 0;
+    for (int a = 0; a < OR_NPRM; ++a)
+        if (!isfinite(prm[a])) status |= OR_ST_NONFINITE;   /* a non-finite parameter */
 
     /* delays for this set's speed */
     int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (size_t)N * (size_t)N);

@@ -163,6 +163,7 @@ struct Group {
     std::vector<int64_t> sets;      // external indices
     int32_t H = 0;
     std::vector<int32_t> row_ptr;
+    std::vector<int32_t> row_mid;   // first zero-delay entry of each row
     std::vector<uint32_t> col_dly;
     std::vector<float> w;
     int64_t ring_offset = 0;        // floats into the ring allocation
@@ -346,21 +347,32 @@ tvbx_status build_groups(tvbx_sweep* h, double dt, std::vector<Group>& groups)
     const int N = h->N;
     for (Group& g : groups) {
         g.row_ptr.assign(N + 1, 0);
-        int64_t dmax = 0;
+        g.row_mid.assign(N, 0);
+        int64_t dmax = 1;   // ring of at least 3 slots (the padding entries use d = 1)
         for (int k = 0; k < N; ++k) {
+            // rows start at an index of the parity of k (zero-weight self entry pads)
+            if ((int)(g.col_dly.size() & 1) != (k & 1)) {
+                g.col_dly.push_back((1u << 16) | (uint32_t)k);
+                g.w.push_back(0.0f);
+            }
+            g.row_ptr[k] = (int32_t)g.col_dly.size();
+            std::vector<std::pair<uint32_t, float>> zero;   // zero-delay entries go last
             for (int j = 0; j < N; ++j) {
                 const double w = h->W[(size_t)k * N + j];
                 if (w == 0.0) continue;
                 // delay in steps: rint (ties to even) of length / (speed dt), in FP64
                 const double steps = rint(h->L[(size_t)k * N + j] / (g.speed * dt));
-                if (steps > 65535.0) return fail(TVBX_E_UNSUPPORTED, "delay of %g steps exceeds 65535", steps);
+                if (steps > 65533.0) return fail(TVBX_E_UNSUPPORTED, "delay of %g steps exceeds 65533", steps);
                 const int64_t d = steps < 0 ? 0 : (int64_t)steps;
                 dmax = std::max(dmax, d);
-                g.col_dly.push_back(((uint32_t)d << 16) | (uint32_t)j);
-                g.w.push_back((float)w);
+                const uint32_t cd = ((uint32_t)d << 16) | (uint32_t)j;
+                if (d == 0) zero.emplace_back(cd, (float)w);
+                else { g.col_dly.push_back(cd); g.w.push_back((float)w); }
             }
-            g.row_ptr[k + 1] = (int32_t)g.col_dly.size();
+            g.row_mid[k] = (int32_t)g.col_dly.size();
+            for (auto& z : zero) { g.col_dly.push_back(z.first); g.w.push_back(z.second); }
         }
+        g.row_ptr[N] = (int32_t)g.col_dly.size();
         g.H = (int32_t)(dmax + 2);
     }
     return TVBX_OK;
@@ -502,8 +514,9 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         return fail(TVBX_E_INVALID_ARG, "unknown kernel %d", c.kernel);
     int variant = -1;   // prefetch variant, -1 = general kernel
     if (c.kernel == TVBX_KERNEL_AUTO) {
-        if (sim_fast_fits(1, N, nnz_max)) variant = 1;
-        else if (sim_fast_fits(0, N, nnz_max)) variant = 0;
+        // preference order from measurement on the 32,768-set, 68-region sweep
+        for (int v : {0, 2, 1, 3})
+            if (sim_fast_fits(v, N, nnz_max)) { variant = v; break; }
     } else if (c.kernel != TVBX_KERNEL_GENERAL) {
         variant = c.kernel - TVBX_KERNEL_PREFETCH;
         if (!sim_fast_fits(variant, N, nnz_max))
@@ -530,6 +543,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         row_off[gi] = (int64_t)all_row.size();
         nz_off[gi] = (int64_t)all_cd.size();
         all_row.insert(all_row.end(), g.row_ptr.begin(), g.row_ptr.end());
+        all_row.insert(all_row.end(), g.row_mid.begin(), g.row_mid.end());
         all_cd.insert(all_cd.end(), g.col_dly.begin(), g.col_dly.end());
         all_w.insert(all_w.end(), g.w.begin(), g.w.end());
         const int32_t Pg = (int32_t)g.sets.size();
@@ -556,6 +570,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         GroupDev& d = gdev[gi];
         d.ring = h->d_ring.as<float>() + groups[gi].ring_offset;
         d.row_ptr = h->d_csr_row.as<int32_t>() + row_off[gi];
+        d.row_mid = h->d_csr_row.as<int32_t>() + row_off[gi] + N + 1;
         d.col_dly = h->d_csr_cd.as<uint32_t>() + nz_off[gi];
         d.w = h->d_csr_w.as<float>() + nz_off[gi];
         d.H = groups[gi].H;

@@ -42,7 +42,11 @@ struct DevModel {
 // One speed group: sets sharing a delay matrix and a ring buffer.
 struct GroupDev {
     float* ring;               // [H][N][P_g], E of the group's sets
-    const int32_t* row_ptr;    // [N + 1] CSR rows of the nonzero weights u_kj
+    const int32_t* row_ptr;    // [N + 1] CSR rows of the nonzero weights u_kj; each row
+                               // starts at an index of the parity of k (padded with a
+                               // zero-weight self entry of delay 1) and ends with its
+                               // zero-delay entries
+    const int32_t* row_mid;    // [N] first zero-delay entry of each row
     const uint32_t* col_dly;   // [nnz] (delay << 16) | j
     const float* w;            // [nnz] u_kj
     int32_t H;                 // ring depth (max delay + 2)

@@ -250,10 +250,11 @@ static __device__ __forceinline__ void transfer_x(const DevModel& m, const float
     out[5] = di * di * F.bb;
 }
 
-// Per-set parameters held in registers by the simulation kernels.
+// Per-set parameters of the simulation kernels (11 floats, in this order).
 struct SetParams {
     float g, b_e, inv_tw, ELe, ELi, a_e, wn, cFee, cFei, cFie, cFii;
 };
+static_assert(sizeof(SetParams) == 11 * sizeof(float), "SetParams must be 11 packed floats");
 
 static __device__ __forceinline__ SetParams load_set_params(const float* __restrict__ prm, int64_t P, int64_t p)
 {

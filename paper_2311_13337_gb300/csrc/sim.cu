@@ -16,7 +16,7 @@ namespace tvbx {
 // Initial state: E = E0, I = I0, everything else 0 (OU starts at 0).
 // ---------------------------------------------------------------------------
 __global__ void init_state_kernel(float* __restrict__ state, uint32_t* __restrict__ status,
-                                  int64_t NP, int64_t P, float E0, float I0)
+                                  const float* __restrict__ prm, int64_t NP, int64_t P, float E0, float I0)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NP * SV_COUNT;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -24,8 +24,12 @@ __global__ void init_state_kernel(float* __restrict__ state, uint32_t* __restric
         state[i] = v == SV_E ? E0 : (v == SV_I ? I0 : 0.0f);
     }
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P;
-         p += (int64_t)gridDim.x * blockDim.x)
-        status[p] = 0u;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t st = 0u;   // a non-finite parameter marks the set from the start
+        for (int a = 0; a < TVBX_N_AXES; ++a)
+            if (!isfinite(prm[a * P + p])) st = TVBX_SET_NONFINITE;
+        status[p] = st;
+    }
 }
 
 __global__ void fill_kernel(float* __restrict__ x, int64_t n, float v)
@@ -206,7 +210,7 @@ cudaError_t launch_init_state(const SimArgs& a, cudaStream_t s)
 {
     const int64_t NP = (int64_t)a.N * a.P;
     note_launch();
-    init_state_kernel<<<1024, 256, 0, s>>>(a.state, a.status, NP, a.P, a.m.E0, a.m.I0);
+    init_state_kernel<<<1024, 256, 0, s>>>(a.state, a.status, a.prm, NP, a.P, a.m.E0, a.m.I0);
     return cudaGetLastError();
 }
 

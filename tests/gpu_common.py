@@ -51,3 +51,16 @@ def conditioned_sets(gpu_status, ref_status):
     relative perturbation of 1e-7 already moves the FP64 trajectory far (the
     paper-scale test measures that spread)."""
     return ((np.asarray(gpu_status) & EVENTS) == 0) & ((np.asarray(ref_status) & EVENTS) == 0)
+
+
+PERTURBATION = {"T": 20.0 * (1 + 1e-7)}   # persistent relative 1e-7 change of every rate update
+
+
+def stable_sets(ref_E, pert_E, samples=200, rtol=1e-5):
+    """Sets whose FP64 trajectory moves by less than rtol (relative) over the
+    first `samples` samples when every rate update is perturbed by a relative
+    1e-7 (the time constant T scaled by 1 + 1e-7, a persistent perturbation
+    at float32 resolution): the well-conditioned sets, on which an FP32
+    engine can be held to 1e-3."""
+    d = rel_err(pert_E[..., :samples], ref_E[..., :samples])
+    return d.reshape(d.shape[0], -1).max(axis=1) <= rtol
