@@ -40,7 +40,8 @@ typedef int32_t tvbx_status;
 #define TVBX_E_OOM         (-2) /* device allocation failed (P x H x N too large) */
 #define TVBX_E_CUDA        (-3) /* CUDA runtime or launch error, or no device */
 #define TVBX_E_NUMERIC     (-4) /* every set became non-finite */
-#define TVBX_E_TIMEOUT     (-5) /* a bounded device-side wait gave up */
+#define TVBX_E_TIMEOUT     (-5) /* a bounded device-side wait gave up (reported by the
+                                   first output call after the run) */
 #define TVBX_E_BAD_STATE   (-6) /* call out of order (e.g. tvbx_fc before tvbx_run) */
 #define TVBX_E_UNSUPPORTED (-7) /* valid request this build does not implement */
 
@@ -132,14 +133,20 @@ typedef struct {
                                  a multiple of tavg_steps when given. */
     int32_t kernel;           /* TVBX_KERNEL_AUTO, TVBX_KERNEL_GENERAL, or
                                  TVBX_KERNEL_PREFETCH + v for prefetch variant v */
-    int32_t reserved;         /* must be 0 */
+    int32_t withhold_step;    /* testing the failure path: 0 = off; s > 0 makes the
+                                 TMA-copy kernels withhold the copies of step s - 1
+                                 and shorten their wait, so the wait expires and the
+                                 run reports TVBX_E_TIMEOUT (no fault, the context
+                                 stays usable). Other kernels ignore it. */
 } tvbx_run_cfg;
 #define TVBX_KERNEL_AUTO     0 /* fastest kernel that fits the sweep */
 #define TVBX_KERNEL_GENERAL  1 /* any size: state in shared memory, direct gathers */
 #define TVBX_KERNEL_PREFETCH 2 /* + v: next-step gather prefetched into shared
-                                  memory; CTA of 16 or 32 sets; v = 0: 16 sets,
-                                  2 sets x 1 region per thread; 1: 32 sets, 4 x 1;
-                                  2: 16 sets, 1 x 2; 3: 16 sets, 2 x 2 */
+                                  memory; CTA of 16 or 32 sets; cp.async into one
+                                  buffer: v = 0: 16 sets, 2 sets x 1 region per
+                                  thread; 1: 32 sets, 4 x 1; 2: 16 sets, 1 x 2;
+                                  3: 16 sets, 2 x 2; TMA bulk copies into two
+                                  buffers: 4: 16 sets, 2 x 1; 5: 16 sets, 1 x 2 */
 
 /* FC settings (Sec. "Output": FC from the covariance of the series,
  * Eq. 6 Pearson; FCD over sliding windows). */

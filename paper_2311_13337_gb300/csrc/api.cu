@@ -198,14 +198,14 @@ struct tvbx_sweep {
 
     DevBuf d_prm, d_ext, d_state, d_status, d_ring, d_series, d_ou_table, d_ou_state;
     DevBuf d_csr_row, d_csr_cd, d_csr_w, d_groups, d_tiles;
-    DevBuf d_blocks, d_fc, d_chi, d_meanfc, d_vec, d_fcd, d_tmp, d_perm, d_inv, d_mean_e, d_mean_i;
+    DevBuf d_blocks, d_fc, d_chi, d_meanfc, d_vec, d_fcd, d_tmp, d_perm, d_inv, d_mean_e, d_mean_i, d_error;
 
     ~tvbx_sweep()
     {
         DevBuf* all[] = {&d_prm, &d_ext, &d_state, &d_status, &d_ring, &d_series, &d_ou_table,
                          &d_ou_state, &d_csr_row, &d_csr_cd, &d_csr_w, &d_groups, &d_tiles,
                          &d_blocks, &d_fc, &d_chi, &d_meanfc, &d_vec, &d_fcd, &d_tmp, &d_perm,
-                         &d_inv, &d_mean_e, &d_mean_i};
+                         &d_inv, &d_mean_e, &d_mean_i, &d_error};
         for (DevBuf* b : all) b->release();
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
@@ -288,6 +288,17 @@ tvbx_status export_rows(tvbx_sweep* h, const float* src, int64_t len, int32_t me
                                                                        len);
     CK(cudaGetLastError(), "gather rows");
     if (mem == TVBX_MEM_HOST) return copy_out(dst, target, bytes, mem, h->stream, &h->d2h);
+    return TVBX_OK;
+}
+
+// Device errors recorded by the last run's kernels (bounded waits that gave up).
+tvbx_status check_device_error(tvbx_sweep* h)
+{
+    uint32_t err = 0;
+    CK(cudaMemcpyAsync(&err, h->d_error.ptr, sizeof err, cudaMemcpyDeviceToHost, h->stream), "error word");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    if (err & TVBX_DEVERR_TIMEOUT)
+        return fail(TVBX_E_TIMEOUT, "a device-side wait of the simulation kernel gave up; results are invalid");
     return TVBX_OK;
 }
 
@@ -510,8 +521,9 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     // gather buffer fits, else the general kernel
     int nnz_max = 0;
     for (const Group& g : groups) nnz_max = std::max(nnz_max, (int)g.col_dly.size());
-    if (c.kernel < TVBX_KERNEL_AUTO || c.kernel >= TVBX_KERNEL_PREFETCH + sim_fast_variants() || c.reserved != 0)
+    if (c.kernel < TVBX_KERNEL_AUTO || c.kernel >= TVBX_KERNEL_PREFETCH + sim_fast_variants())
         return fail(TVBX_E_INVALID_ARG, "unknown kernel %d", c.kernel);
+    if (c.withhold_step < 0) return fail(TVBX_E_INVALID_ARG, "withhold_step must be >= 0");
     int variant = -1;   // prefetch variant, -1 = general kernel
     if (c.kernel == TVBX_KERNEL_AUTO) {
         // preference order from measurement on the 32,768-set, 68-region sweep
@@ -561,6 +573,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     CK(h->d_ring.ensure(sizeof(float) * (size_t)std::max<int64_t>(ring_floats, 1)), "ring buffers");
     CK(h->d_series.ensure(sizeof(float) * (size_t)std::max<int64_t>(T * N * P, 1)), "series");
     CK(h->d_ou_state.ensure(sizeof(float) * N), "OU state");
+    CK(h->d_error.ensure(sizeof(uint32_t)), "error word");
     CK(h->d_csr_row.ensure(sizeof(int32_t) * all_row.size()), "CSR");
     CK(h->d_csr_cd.ensure(sizeof(uint32_t) * all_cd.size()), "CSR");
     CK(h->d_csr_w.ensure(sizeof(float) * all_w.size()), "CSR");
@@ -578,7 +591,8 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         d.p_base = groups[gi].p_base;
         d.stride = (int32_t)ring_stride(groups[gi].sets.size());
         d.nnz = (int32_t)groups[gi].col_dly.size();
-        d.pad = 0;
+        d.nnz_d = 0;
+        for (uint32_t cd : groups[gi].col_dly) d.nnz_d += (cd >> 16) != 0;
     }
     h->h2d += sizeof(float) * prm_soa.size() + 3 * sizeof(int64_t) * P + sizeof(int32_t) * all_row.size() +
               sizeof(uint32_t) * all_cd.size() + sizeof(float) * all_w.size() + sizeof(GroupDev) * gdev.size() +
@@ -596,6 +610,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     if (!tiles.empty())
         CK(cudaMemcpyAsync(h->d_tiles.ptr, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice, s), "upload");
     CK(cudaMemsetAsync(h->d_ou_state.ptr, 0, sizeof(float) * N, s), "OU state");
+    CK(cudaMemsetAsync(h->d_error.ptr, 0, sizeof(uint32_t), s), "error word");
 
     // chunking: keep each launch around 4-8 thousand steps
     int64_t chunk = c.chunk_steps > 0 ? c.chunk_steps : 0;
@@ -617,6 +632,9 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     a.series = h->d_series.as<float>();
     a.ou_table = c.noise_per_set ? nullptr : h->d_ou_table.as<float>();
     a.status = h->d_status.as<uint32_t>();
+    a.error = h->d_error.as<uint32_t>();
+    a.withhold_step = c.withhold_step > 0 ? (int64_t)c.withhold_step - 1 : -1;
+    a.wait_limit = c.withhold_step > 0 ? (1u << 12) : (1u << 26);
     a.N = N;
     a.P = (int32_t)P;
     a.ts = c.tavg_steps;
@@ -715,6 +733,7 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
     if (!h || !cfg) return fail(TVBX_E_INVALID_ARG, "NULL handle or cfg");
     if (check_mem(mem)) return TVBX_E_INVALID_ARG;
     if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_fc before tvbx_run");
+    if (tvbx_status e = check_device_error(h)) return e;
     if (cfg->precision != TVBX_FC_FP32) return fail(TVBX_E_UNSUPPORTED, "FC precision %d", cfg->precision);
     if (cfg->fcd_window < 0) return fail(TVBX_E_INVALID_ARG, "fcd_window must be >= 0");
     int32_t nw = 0;
@@ -739,6 +758,7 @@ tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* me
     if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
     if (check_mem(mem)) return TVBX_E_INVALID_ARG;
     if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_summary before tvbx_run");
+    if (tvbx_status e = check_device_error(h)) return e;
     const int64_t P = h->P;
     if ((chi || mean_fc || status) && !h->fc_valid) {
         tvbx_status st = run_fc(h, 0, 0, nullptr);
@@ -781,6 +801,7 @@ tvbx_status tvbx_series_range(const tvbx_sweep* hc, int64_t set_begin, int64_t s
     if (!h || !out) return fail(TVBX_E_INVALID_ARG, "NULL handle or out");
     if (check_mem(mem)) return TVBX_E_INVALID_ARG;
     if (!h->ran) return fail(TVBX_E_BAD_STATE, "series export before tvbx_run");
+    if (tvbx_status e = check_device_error(h)) return e;
     if (set_begin < 0 || set_count < 0 || set_begin + set_count > h->P || t_begin < 0 || t_count < 0 ||
         t_begin + t_count > h->T)
         return fail(TVBX_E_INVALID_ARG, "series window outside [0, %lld) x [0, %lld)", (long long)h->P,
@@ -813,6 +834,7 @@ tvbx_status tvbx_state(const tvbx_sweep* hc, int32_t mem, float* out)
     if (!h || !out) return fail(TVBX_E_INVALID_ARG, "NULL handle or out");
     if (check_mem(mem)) return TVBX_E_INVALID_ARG;
     if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_state before tvbx_run");
+    if (tvbx_status e = check_device_error(h)) return e;
     const size_t total = (size_t)8 * h->N * h->P;
     float* target = out;
     if (mem == TVBX_MEM_HOST) {

@@ -53,9 +53,12 @@ struct GroupDev {
     int32_t P_g;               // sets in the group
     int32_t p_base;            // first internal set index of the group
     int32_t stride;            // ring row stride in floats (P_g rounded up to 32)
-    int32_t nnz;               // nonzero weights (CSR entries)
-    int32_t pad;
+    int32_t nnz;               // CSR entries (nonzero weights and padding)
+    int32_t nnz_d;             // entries with a delay of at least one step
 };
+
+// Device error word bits (SimArgs::error).
+constexpr uint32_t TVBX_DEVERR_TIMEOUT = 1u;   // a bounded wait gave up
 
 // One CTA's work: sets [q0, q0 + nq) of group g (q relative to the group).
 struct TileDev {
@@ -76,6 +79,9 @@ struct SimArgs {
     float* series;             // [T][N][P] E samples (sets fastest)
     const float* ou_table;     // [n_chunk][N] shared OU values, or null
     uint32_t* status;          // [P]
+    uint32_t* error;           // device error word (TVBX_DEVERR_*)
+    int64_t withhold_step;     // step whose bulk copies are withheld (-1: none; testing)
+    uint32_t wait_limit;       // try_wait attempts before a wait gives up
     int64_t n0;                // global index of the chunk's first step
     int32_t n_chunk;           // steps in this chunk
     int32_t N;                 // regions
@@ -101,7 +107,7 @@ cudaError_t launch_sim_fast(const SimArgs& a, int variant, int32_t n_tiles, int 
 bool sim_fast_fits(int variant, int N, int nnz_max);
 int sim_fast_pb(int variant);
 int sim_fast_variants();
-size_t sim_fast_smem_bytes(int N, int nnz, int pb);
+size_t sim_fast_smem_bytes(int variant, int N, int nnz);
 int sim_threads(int N, int pb);
 size_t sim_smem_bytes(int N, int pb);
 

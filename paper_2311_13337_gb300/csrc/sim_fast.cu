@@ -1,136 +1,160 @@
-// Prefetching simulation kernel of the tvbx engine (arXiv 2311.13337, the
+// Prefetching simulation kernels of the tvbx engine (arXiv 2311.13337, the
 // lock-step integration of Eq. 1-5 with forward Euler).
 //
 // A CTA owns PB sets of one speed group and all N regions of each. A thread
 // owns SPT adjacent sets and RPT regions (k = t / (PB/SPT) + i * kstride),
-// with their state in registers across the whole chunk.
+// with their state in registers across the whole chunk (tile_common.cuh).
 //
 // Delays are at least one step for every nonzero weight with a positive
 // tract length, so the values the coupling needs at step n + 1,
-// E_j(n + 1 - d_kj), are all in the ring buffer when step n begins. The CTA
-// issues the whole gather of step n + 1 with 16-byte cp.async copies (one
-// PB-float row segment per delayed weight, L2 only) into a shared buffer
-// right after it has consumed the buffer for step n; the copies complete
-// while step n's transfer functions are evaluated. Zero-delay entries
-// (d = 0) sit at the end of each CSR row and read E_j(n) directly after the
-// step barrier.
+// E_j(n + 1 - d_kj), are all in the ring buffer once step n - 1 has written
+// E(n). Each CTA therefore copies the delayed rows of the next step (one
+// PB-float row segment per delayed weight) into shared memory while the
+// current step computes. Zero-delay entries (d = 0) sit at the end of each
+// CSR row and read E_j(n) directly.
+//
+// Two kernels:
+//  * sim_fast_kernel: 16-byte cp.async copies into one buffer; two CTA
+//    barriers per step (buffer consumed, then refilled).
+//  * sim_bulk_kernel: one TMA bulk copy (cp.async.bulk) per row into one of
+//    two buffers, completion counted in bytes on an mbarrier per buffer; one
+//    CTA barrier per step, and the copy for step n + 1 is issued before the
+//    wait for step n. Every mbarrier wait is bounded: on expiry the kernel
+//    records TVBX_DEVERR_TIMEOUT, finishes the step with whatever is in the
+//    buffer, and all threads leave at the next barrier after waiting (again
+//    bounded) for their copies.
 //
 // In the coupling sum, the SPT sets of a thread share one broadcast weight
 // load and one vector load of the gathered row. CSR rows start at an index
-// of the same parity as their region (a zero-weight self entry pads when
-// needed) so that the rows read at the same time by the two halves of a warp
-// fall in opposite halves of the shared-memory banks.
-//
-// Shared memory: gather buffer [nnz][PB] floats, weights, CSR (j, d), row
-// starts and the start of each row's zero-delay entries.
+// of the parity of their region (a zero-weight self entry pads) so that the
+// rows read together by consecutive regions of a warp fall in opposite
+// halves of the shared-memory banks.
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "internal.h"
 #include "model_device.cuh"
+#include "tile_common.cuh"
 
 namespace tvbx {
 
+static __device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
 static __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc)
 {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
 }
 static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 static __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-template <int SPT> struct VecT;
-template <> struct VecT<1> { using T = float; };
-template <> struct VecT<2> { using T = float2; };
-template <> struct VecT<4> { using T = float4; };
-
-static __device__ __forceinline__ float vget(const float& v, int) { return v; }
-static __device__ __forceinline__ float vget(const float2& v, int i) { return i == 0 ? v.x : v.y; }
-static __device__ __forceinline__ float vget(const float4& v, int i)
+static __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
-    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+static __device__ __forceinline__ void mbar_arm(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+static __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+static __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+static __device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+}
+static __device__ __forceinline__ void fence_mbarrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 
+// Bounded wait on an mbarrier phase. Returns false on expiry.
+static __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Shared-memory layout common to both kernels after the gather buffer(s).
+struct TileSmem {
+    float* s_w;
+    uint32_t* s_cd;
+    int* s_row;
+    int* s_mid;
+    float* s_prm;
+};
+
+template <int PB>
+static __device__ __forceinline__ TileSmem stage_tile(const SimArgs& a, const TileDev& tile, const GroupDev& grp,
+                                                      float* after_buffers)
+{
+    const int N = a.N, nnz = grp.nnz;
+    TileSmem t;
+    t.s_w = after_buffers;
+    t.s_cd = reinterpret_cast<uint32_t*>(t.s_w + nnz);
+    t.s_row = reinterpret_cast<int*>(t.s_cd + nnz);
+    t.s_mid = t.s_row + N + 1;
+    t.s_prm = reinterpret_cast<float*>(t.s_mid + N);
+    stage_set_params<PB>(a, tile, grp, t.s_prm);
+    for (int i = threadIdx.x; i < nnz; i += blockDim.x) {
+        t.s_cd[i] = grp.col_dly[i];
+        t.s_w[i] = grp.w[i];
+    }
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) t.s_row[i] = grp.row_ptr[i];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) t.s_mid[i] = grp.row_mid[i];
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// cp.async, one buffer
+// ---------------------------------------------------------------------------
 template <int PB, int SPT, int RPT, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
 sim_fast_kernel(const __grid_constant__ SimArgs a)
 {
-    using V = typename VecT<SPT>::T;
-    constexpr int TPR = PB / SPT;  // threads per region row
-    constexpr int NP_T = SPT * RPT; // pairs per thread
-    extern __shared__ __align__(16) float smem[];
+    constexpr int TPR = PB / SPT;
+    extern __shared__ __align__(128) float smem[];
     const TileDev tile = a.tiles[blockIdx.x];
     const GroupDev grp = a.groups[tile.group];
-    const DevModel& m = a.m;
     const int N = a.N;
-    const int P = a.P;
-    const int nnz = grp.nnz;
-    float* gbuf = smem;                                                    // [nnz][PB]
-    float* s_w = gbuf + (size_t)nnz * PB;                                  // [nnz]
-    uint32_t* s_cd = reinterpret_cast<uint32_t*>(s_w + nnz);               // [nnz] (d << 16) | j
-    int* s_row = reinterpret_cast<int*>(s_cd + nnz);                       // [N + 1]
-    int* s_mid = s_row + N + 1;                                            // [N] first zero-delay entry
-    float* s_prm = reinterpret_cast<float*>(s_mid + N);                    // [11][PB] set parameters
-    for (int q = threadIdx.x; q < PB; q += blockDim.x) {
-        SetParams v{};
-        if (q < tile.nq) v = load_set_params(a.prm, P, grp.p_base + tile.q0 + q);
-        const float* f = reinterpret_cast<const float*>(&v);
-        for (int c = 0; c < 11; ++c) s_prm[c * PB + q] = f[c];
-    }
-    for (int i = threadIdx.x; i < nnz; i += blockDim.x) {
-        s_cd[i] = grp.col_dly[i];
-        s_w[i] = grp.w[i];
-    }
-    for (int i = threadIdx.x; i <= N; i += blockDim.x) s_row[i] = grp.row_ptr[i];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) s_mid[i] = grp.row_mid[i];
+    float* gbuf = smem;   // [nnz][PB]
+    const TileSmem sm = stage_tile<PB>(a, tile, grp, gbuf + (size_t)grp.nnz * PB);
 
-    const int kstride = blockDim.x / TPR;
-    const int qt = (threadIdx.x % TPR) * SPT;   // first set of this thread in the tile
-    const int kr = threadIdx.x / TPR;
-    const int64_t NP = (int64_t)N * P;
-    uint32_t pn[SPT];
-    bool act[SPT];
-#pragma unroll
-    for (int s = 0; s < SPT; ++s) {
-        act[s] = qt + s < tile.nq;
-        pn[s] = act[s] ? (uint32_t)(a.p_offset + a.ext_index[grp.p_base + tile.q0 + qt + s]) : 0u;
-    }
-    PairState x[NP_T];
-    float ou[NP_T], accE[NP_T], accI[NP_T];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int k = kr + r * kstride;
-#pragma unroll
-        for (int s = 0; s < SPT; ++s) {
-            const int i = r * SPT + s;
-            if (act[s] && k < N) {
-                const int64_t o = (int64_t)k * P + grp.p_base + tile.q0 + qt + s;
-                x[i] = PairState{a.state[SV_E * NP + o], a.state[SV_I * NP + o], a.state[SV_CEE * NP + o],
-                                 a.state[SV_CEI * NP + o], a.state[SV_CII * NP + o], a.state[SV_WE * NP + o],
-                                 a.state[SV_WI * NP + o]};
-                ou[i] = a.state[SV_OU * NP + o];
-                accE[i] = a.state[SV_ACC_E * NP + o];
-                accI[i] = a.state[SV_ACC_I * NP + o];
-            } else {
-                x[i] = PairState{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                ou[i] = accE[i] = accI[i] = 0.0f;
-            }
-        }
-    }
+    ThreadSlot ts;
+    ts.kstride = blockDim.x / TPR;
+    ts.qt = (threadIdx.x % TPR) * SPT;
+    ts.kr = threadIdx.x / TPR;
+    ts.col0 = grp.p_base + tile.q0;
+    ThreadPairs<SPT, RPT> tp;
+    load_pairs<SPT, RPT>(a, tile, ts, tp);
     __syncthreads();
 
     const int H = grp.H;
     const int64_t slot_stride = (int64_t)N * grp.stride;
     float* ring_cols = grp.ring + tile.q0;
-    constexpr int CH = PB / 4;  // 16-byte chunks per row segment
-
-    // gather of step `mstep`'s delayed values (d >= 1) into gbuf
+    constexpr int CH = PB / 4;
     auto prefetch = [&](int64_t mstep) {
         const int slot_m = (int)(mstep % H);
-        for (int idx = threadIdx.x; idx < nnz * CH; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < grp.nnz * CH; idx += blockDim.x) {
             const int e = idx / CH, c = idx - e * CH;
-            const uint32_t cd = s_cd[e];
+            const uint32_t cd = sm.s_cd[e];
             const int d = (int)(cd >> 16);
             if (d == 0) continue;
             int sl = slot_m - d;
@@ -142,137 +166,142 @@ sim_fast_kernel(const __grid_constant__ SimArgs a)
     };
 
     prefetch(a.n0);
-    uint32_t flags[SPT];
-#pragma unroll
-    for (int s = 0; s < SPT; ++s) flags[s] = 0u;
-    const float inv_ts = 1.0f / (float)a.ts;
     for (int step = 0; step < a.n_chunk; ++step) {
         const int64_t n = a.n0 + step;
         const int slot_n = (int)(n % H);
         const int slot_w = slot_n + 1 == H ? 0 : slot_n + 1;
         cp_async_wait_all();
         __syncthreads();
-        float cpl[NP_T];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const int k = kr + r * kstride;
-            float acc[SPT];
-#pragma unroll
-            for (int s = 0; s < SPT; ++s) acc[s] = 0.0f;
-            if (k < N) {
-                const int e_mid = s_mid[k];
-                const int e_end = s_row[k + 1];
-                int e = s_row[k];
-#pragma unroll 4
-                for (; e < e_mid; ++e) {
-                    const float w = s_w[e];
-                    const V v = *reinterpret_cast<const V*>(gbuf + (size_t)e * PB + qt);
-#pragma unroll
-                    for (int s = 0; s < SPT; ++s) acc[s] = fmaf(w, vget(v, s), acc[s]);
-                }
-                for (; e < e_end; ++e) {   // zero delay: E_j(n), written last step
-                    const float w = s_w[e];
-                    const float* src = ring_cols + slot_n * slot_stride + (int64_t)(s_cd[e] & 0xffffu) * grp.stride + qt;
-#pragma unroll
-                    for (int s = 0; s < SPT; ++s) acc[s] = fmaf(w, src[s], acc[s]);
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < SPT; ++s) cpl[r * SPT + s] = acc[s];
-        }
+        float cpl[SPT * RPT];
+        coupling_sums<PB, SPT, RPT>(ts, N, gbuf, sm.s_w, sm.s_cd, sm.s_row, sm.s_mid, ring_cols + slot_n * slot_stride,
+                                    grp.stride, cpl);
         __syncthreads();
         if (step + 1 < a.n_chunk) prefetch(n + 1);
-
-        const bool sample_now = ((n + 1) % a.ts) == 0;
-        const int64_t t = (n + 1) / a.ts - 1;
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const int k = kr + r * kstride;
-#pragma unroll
-            for (int s = 0; s < SPT; ++s) {
-                const int i = r * SPT + s;
-                if (!(act[s] && k < N)) continue;
-                const float OU = a.noise_per_set ? ou[i] : a.ou_table[(int64_t)step * N + k];
-                SetParams spv;
-                float* f = reinterpret_cast<float*>(&spv);
-#pragma unroll
-                for (int c = 0; c < 11; ++c) f[c] = s_prm[c * PB + qt + s];
-                euler_step(m, spv, x[i], cpl[i], OU, flags[s]);
-                if (a.noise_per_set) {
-                    const float xi = std_normal(a.seed, (uint32_t)n, (uint32_t)k, pn[s]);
-                    ou[i] = fmaf(m.ou_a, m.ou_mu - OU, fmaf(m.ou_b, xi, OU));
-                }
-                ring_cols[slot_w * slot_stride + (int64_t)k * grp.stride + qt + s] = x[i].E;
-                accE[i] += x[i].E;
-                accI[i] += x[i].I;
-                if (sample_now) {
-                    if (t < a.T) {
-                        const float xE = accE[i] * inv_ts, xI = accI[i] * inv_ts;
-                        const int64_t o = (int64_t)k * P + grp.p_base + tile.q0 + qt + s;
-                        a.series[t * NP + o] = xE;
-                        if (t >= a.transient) {
-                            float sE = a.state[SV_SUM_E * NP + o], cE = a.state[SV_CMP_E * NP + o];
-                            float sI = a.state[SV_SUM_I * NP + o], cI = a.state[SV_CMP_I * NP + o];
-                            kahan_add(sE, cE, xE);
-                            kahan_add(sI, cI, xI);
-                            a.state[SV_SUM_E * NP + o] = sE;
-                            a.state[SV_CMP_E * NP + o] = cE;
-                            a.state[SV_SUM_I * NP + o] = sI;
-                            a.state[SV_CMP_I * NP + o] = cI;
-                        }
-                    }
-                    accE[i] = 0.0f;
-                    accI[i] = 0.0f;
-                }
-            }
-        }
+        advance_pairs<PB, SPT, RPT>(a, ts, sm.s_prm, tp, cpl, n, step, ring_cols + slot_w * slot_stride, grp.stride);
     }
     cp_async_wait_all();
-
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int k = kr + r * kstride;
-#pragma unroll
-        for (int s = 0; s < SPT; ++s) {
-            const int i = r * SPT + s;
-            if (act[s] && k < N) {
-                const int64_t o = (int64_t)k * P + grp.p_base + tile.q0 + qt + s;
-                a.state[SV_E * NP + o] = x[i].E;
-                a.state[SV_I * NP + o] = x[i].I;
-                a.state[SV_CEE * NP + o] = x[i].Cee;
-                a.state[SV_CEI * NP + o] = x[i].Cei;
-                a.state[SV_CII * NP + o] = x[i].Cii;
-                a.state[SV_WE * NP + o] = x[i].We;
-                a.state[SV_WI * NP + o] = x[i].Wi;
-                a.state[SV_OU * NP + o] = ou[i];
-                a.state[SV_ACC_E * NP + o] = accE[i];
-                a.state[SV_ACC_I * NP + o] = accI[i];
-            }
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < SPT; ++s)
-        if (act[s] && flags[s]) atomicOr(a.status + grp.p_base + tile.q0 + qt + s, flags[s]);
+    store_pairs<SPT, RPT>(a, ts, tp);
 }
 
 // ---------------------------------------------------------------------------
-// Variants: (sets per CTA, sets per thread, regions per thread, max threads,
-// min CTAs per SM).
+// TMA bulk copies, two buffers, one barrier per step
+// ---------------------------------------------------------------------------
+template <int PB, int SPT, int RPT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
+sim_bulk_kernel(const __grid_constant__ SimArgs a)
+{
+    constexpr int TPR = PB / SPT;
+    extern __shared__ __align__(128) float smem[];
+    const TileDev tile = a.tiles[blockIdx.x];
+    const GroupDev grp = a.groups[tile.group];
+    const int N = a.N;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);        // [2], first 32 bytes
+    int* s_abort = reinterpret_cast<int*>(smem + 8);            // timeout flag of the CTA
+    float* gbuf0 = smem + 32;                                   // [nnz][PB], 128-byte aligned
+    float* gbuf1 = gbuf0 + (size_t)grp.nnz * PB;
+    const TileSmem sm = stage_tile<PB>(a, tile, grp, gbuf1 + (size_t)grp.nnz * PB);
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        *s_abort = 0;
+        fence_mbarrier_init();
+    }
+
+    ThreadSlot ts;
+    ts.kstride = blockDim.x / TPR;
+    ts.qt = (threadIdx.x % TPR) * SPT;
+    ts.kr = threadIdx.x / TPR;
+    ts.col0 = grp.p_base + tile.q0;
+    ThreadPairs<SPT, RPT> tp;
+    load_pairs<SPT, RPT>(a, tile, ts, tp);
+
+    const int H = grp.H;
+    const int64_t slot_stride = (int64_t)N * grp.stride;
+    float* ring_cols = grp.ring + tile.q0;
+    const uint32_t row_bytes = PB * sizeof(float);
+    const uint32_t step_bytes = (uint32_t)grp.nnz_d * row_bytes;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arm(&mbar[a.n0 & 1], step_bytes);
+        if (a.n_chunk > 1) mbar_arm(&mbar[(a.n0 + 1) & 1], step_bytes);
+    }
+    __syncthreads();
+
+    auto prefetch = [&](int64_t mstep) {
+        if (mstep == a.withhold_step) return;   // failure-path test: nothing arrives
+        const int b = (int)(mstep & 1);
+        float* dst = b ? gbuf1 : gbuf0;
+        const int slot_m = (int)(mstep % H);
+        for (int e = threadIdx.x; e < grp.nnz; e += blockDim.x) {
+            const uint32_t cd = sm.s_cd[e];
+            const int d = (int)(cd >> 16);
+            if (d == 0) continue;
+            int sl = slot_m - d;
+            sl += sl < 0 ? H : 0;
+            bulk_g2s(dst + (size_t)e * PB, ring_cols + sl * slot_stride + (int64_t)(cd & 0xffffu) * grp.stride,
+                     row_bytes, &mbar[b]);
+        }
+    };
+
+    prefetch(a.n0);
+    uint32_t parity[2] = {0u, 0u};
+    for (int step = 0; step < a.n_chunk; ++step) {
+        const int64_t n = a.n0 + step;
+        const int b = (int)(n & 1);
+        const int slot_n = (int)(n % H);
+        const int slot_w = slot_n + 1 == H ? 0 : slot_n + 1;
+        if (step > 0) {
+            __syncthreads();   // step n-1 done: its reads of the other buffer and its ring writes
+            if (*s_abort) break;
+        }
+        if (step + 1 < a.n_chunk) prefetch(n + 1);
+        const bool arrived = mbar_wait_bounded(&mbar[b], parity[b], a.wait_limit);
+        if (!arrived) {
+            *s_abort = 1;
+            atomicOr(a.error, TVBX_DEVERR_TIMEOUT);
+        }
+        parity[b] ^= 1u;
+        float cpl[SPT * RPT];
+        coupling_sums<PB, SPT, RPT>(ts, N, b ? gbuf1 : gbuf0, sm.s_w, sm.s_cd, sm.s_row, sm.s_mid,
+                                    ring_cols + slot_n * slot_stride, grp.stride, cpl);
+        advance_pairs<PB, SPT, RPT>(a, ts, sm.s_prm, tp, cpl, n, step, ring_cols + slot_w * slot_stride, grp.stride);
+        fence_proxy_async_global();   // E(n+1) visible to the next bulk copies
+        // re-arm only a phase this thread saw complete (never twice in one phase)
+        if (threadIdx.x == 0 && arrived && step + 2 < a.n_chunk) mbar_arm(&mbar[b], step_bytes);
+    }
+    __syncthreads();
+    if (*s_abort) {
+        // let copies already in flight land before the CTA's shared memory is released
+        mbar_wait_bounded(&mbar[0], parity[0], a.wait_limit);
+        mbar_wait_bounded(&mbar[1], parity[1], a.wait_limit);
+    }
+    store_pairs<SPT, RPT>(a, ts, tp);
+}
+
+// ---------------------------------------------------------------------------
+// Variants: (kernel, sets per CTA, sets per thread, regions per thread, max
+// threads, min CTAs per SM).
 // ---------------------------------------------------------------------------
 struct FastVariant {
-    int pb, spt, rpt, maxt, minb;
+    int bulk, pb, spt, rpt, maxt, minb;
 };
 static const FastVariant kFast[] = {
-    {16, 2, 1, 576, 1},   // 0: 16 sets, 2 sets x 1 region per thread
-    {32, 4, 1, 576, 1},   // 1: 32 sets, 4 sets x 1 region per thread
-    {16, 1, 2, 576, 1},   // 2: 16 sets, 1 set x 2 regions per thread
-    {16, 2, 2, 320, 1},   // 3: 16 sets, 2 sets x 2 regions per thread
+    {0, 16, 2, 1, 576, 1},   // 0: cp.async, 16 sets, 2 sets x 1 region per thread
+    {0, 32, 4, 1, 576, 1},   // 1: cp.async, 32 sets, 4 x 1
+    {0, 16, 1, 2, 576, 1},   // 2: cp.async, 16 sets, 1 x 2
+    {0, 16, 2, 2, 320, 1},   // 3: cp.async, 16 sets, 2 x 2
+    {1, 16, 2, 1, 576, 1},   // 4: TMA bulk, double buffer, 16 sets, 2 x 1
+    {1, 16, 1, 2, 576, 1},   // 5: TMA bulk, double buffer, 16 sets, 1 x 2
 };
 constexpr int kNumFast = (int)(sizeof kFast / sizeof kFast[0]);
 
-size_t sim_fast_smem_bytes(int N, int nnz, int pb)
+static size_t tail_bytes(int N, int nnz, int pb) { return 8 * (size_t)nnz + 4 * (size_t)(2 * N + 1) + 4 * 11 * (size_t)pb; }
+
+size_t sim_fast_smem_bytes(int variant, int N, int nnz)
 {
-    return sizeof(float) * (size_t)nnz * pb + 8 * (size_t)nnz + 4 * (size_t)(2 * N + 1) + 4 * 11 * (size_t)pb;
+    const FastVariant& v = kFast[variant];
+    const size_t buf = sizeof(float) * (size_t)nnz * v.pb;
+    return v.bulk ? 128 + 2 * buf + tail_bytes(N, nnz, v.pb) : buf + tail_bytes(N, nnz, v.pb);
 }
 
 bool sim_fast_fits(int variant, int N, int nnz_max)
@@ -281,23 +310,24 @@ bool sim_fast_fits(int variant, int N, int nnz_max)
     const FastVariant& v = kFast[variant];
     const int kstride = (N + v.rpt - 1) / v.rpt;
     if (kstride * (v.pb / v.spt) > v.maxt) return false;
-    return sim_fast_smem_bytes(N, nnz_max, v.pb) * v.minb <= 220 * 1024;
+    if (v.bulk && (size_t)nnz_max * v.pb * sizeof(float) >= (1u << 20)) return false;   // mbarrier tx-count range
+    return sim_fast_smem_bytes(variant, N, nnz_max) * v.minb <= 220 * 1024;
 }
 
 int sim_fast_pb(int variant) { return kFast[variant].pb; }
 int sim_fast_variants() { return kNumFast; }
 
-template <int PB, int SPT, int RPT, int MAXT, int MINB>
-static cudaError_t launch_fast(const SimArgs& a, int32_t n_tiles, int nnz_max, cudaStream_t s)
+template <int BULK, int PB, int SPT, int RPT, int MAXT, int MINB>
+static cudaError_t launch_fast(const SimArgs& a, int variant, int32_t n_tiles, int nnz_max, cudaStream_t s)
 {
     const int kstride = (a.N + RPT - 1) / RPT;
     const int threads = kstride * (PB / SPT);
-    const size_t smem = sim_fast_smem_bytes(a.N, nnz_max, PB);
-    cudaError_t e = cudaFuncSetAttribute(sim_fast_kernel<PB, SPT, RPT, MAXT, MINB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sim_fast_smem_bytes(variant, a.N, nnz_max);
+    auto kern = BULK ? sim_bulk_kernel<PB, SPT, RPT, MAXT, MINB> : sim_fast_kernel<PB, SPT, RPT, MAXT, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    sim_fast_kernel<PB, SPT, RPT, MAXT, MINB><<<n_tiles, threads, smem, s>>>(a);
+    kern<<<n_tiles, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -305,10 +335,12 @@ cudaError_t launch_sim_fast(const SimArgs& a, int variant, int32_t n_tiles, int 
 {
     if (n_tiles <= 0 || a.n_chunk <= 0) return cudaSuccess;
     switch (variant) {
-    case 0: return launch_fast<16, 2, 1, 576, 1>(a, n_tiles, nnz_max, s);
-    case 1: return launch_fast<32, 4, 1, 576, 1>(a, n_tiles, nnz_max, s);
-    case 2: return launch_fast<16, 1, 2, 576, 1>(a, n_tiles, nnz_max, s);
-    case 3: return launch_fast<16, 2, 2, 320, 1>(a, n_tiles, nnz_max, s);
+    case 0: return launch_fast<0, 16, 2, 1, 576, 1>(a, variant, n_tiles, nnz_max, s);
+    case 1: return launch_fast<0, 32, 4, 1, 576, 1>(a, variant, n_tiles, nnz_max, s);
+    case 2: return launch_fast<0, 16, 1, 2, 576, 1>(a, variant, n_tiles, nnz_max, s);
+    case 3: return launch_fast<0, 16, 2, 2, 320, 1>(a, variant, n_tiles, nnz_max, s);
+    case 4: return launch_fast<1, 16, 2, 1, 576, 1>(a, variant, n_tiles, nnz_max, s);
+    case 5: return launch_fast<1, 16, 1, 2, 576, 1>(a, variant, n_tiles, nnz_max, s);
     default: return cudaErrorInvalidValue;
     }
 }

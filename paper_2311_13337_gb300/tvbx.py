@@ -63,7 +63,7 @@ class RunCfg(ctypes.Structure):
     _fields_ = [("dt_ms", ctypes.c_double), ("n_steps", ctypes.c_int64), ("tavg_steps", ctypes.c_int32),
                 ("noise_per_set", ctypes.c_int32), ("seed", ctypes.c_uint64), ("p_offset", ctypes.c_int64),
                 ("transient_samples", ctypes.c_int32), ("chunk_steps", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("withhold_step", ctypes.c_int32)]
 
 
 class FcCfg(ctypes.Structure):
@@ -219,15 +219,15 @@ def sweep_info(h) -> tuple[int, int, int]:
 
 
 KERNEL_AUTO, KERNEL_GENERAL, KERNEL_PREFETCH = 0, 1, 2
-N_PREFETCH_VARIANTS = 4
+N_PREFETCH_VARIANTS = 6
 
 
 def run(h, dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
-        transient_samples=0, chunk_steps=0, stream=None, kernel=KERNEL_AUTO):
+        transient_samples=0, chunk_steps=0, stream=None, kernel=KERNEL_AUTO, withhold_step=0):
     """Enqueue the integration on `stream` (a torch.cuda.Stream, a raw handle
     or None for the default stream)."""
     cfg = RunCfg(float(dt_ms), int(n_steps), int(tavg_steps), int(bool(noise_per_set)), int(seed),
-                 int(p_offset), int(transient_samples), int(chunk_steps), int(kernel), 0)
+                 int(p_offset), int(transient_samples), int(chunk_steps), int(kernel), int(withhold_step))
     sp = None
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))

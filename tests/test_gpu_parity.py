@@ -220,3 +220,21 @@ def test_invalid_run_arguments(tvbx, conn):
     with pytest.raises(tvbx.TvbxError) as e:
         tvbx.Sweep(W, L, axes=[("speed", [0.0])]).run(dt_ms=DT, n_steps=10, tavg_steps=1)
     assert e.value.code == -1
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(tvbx, conn):
+    """The TMA-copy kernel's waits are bounded: withholding one step's copies
+    (a flag that no copy satisfies) makes the wait expire; the run reports
+    TVBX_E_TIMEOUT and the next run on the same handle is correct."""
+    W, L = conn
+    axes = [("g", [0.2, 0.4]), ("b_e", [30.0])]
+    sw = tvbx.Sweep(W, L, axes=axes)
+    bulk = tvbx.KERNEL_PREFETCH + 4
+    sw.run(dt_ms=DT, n_steps=600, tavg_steps=10, seed=2, kernel=bulk, withhold_step=301)
+    with pytest.raises(tvbx.TvbxError) as e:
+        sw.summary()
+    assert e.value.code == -5
+    sw.run(dt_ms=DT, n_steps=600, tavg_steps=10, seed=2, kernel=bulk)
+    good = sw.series()
+    sw.run(dt_ms=DT, n_steps=600, tavg_steps=10, seed=2, kernel=tvbx.KERNEL_GENERAL)
+    assert np.array_equal(good, sw.series(), equal_nan=True)
