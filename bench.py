@@ -102,8 +102,9 @@ def stop_clock_sampler(proc):
 
 
 def kernel_source_hash() -> str:
+    """Hash of every source the simulation kernels are built from."""
     h = hashlib.sha256()
-    for f in ("sim.cu", "internal.h"):
+    for f in ("sim.cu", "sim_fast.cu", "tile_common.cuh", "model_device.cuh", "internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2311_13337_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -111,7 +112,7 @@ def kernel_source_hash() -> str:
 def ncu_traffic_per_region_step():
     """DRAM bytes per (set, region, step) of the simulation kernel from the
     committed ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "sim_chunk_traffic.json")
+    path = os.path.join(ROOT, "profiles", "sim_kernel_traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
@@ -260,6 +261,7 @@ def run_engine(args):
     clocks = stop_clock_sampler(sampler)
     launches = tvbx.launch_count() - launches0
     sim_ms, sim_launches, sim_rs = tvbx.profile_read(sw.h)
+    kernel_id, _ = tvbx.last_kernel(sw.h)
     tvbx.profile_enable(sw.h, False)
     t = torch.tensor([el], dtype=torch.float64, device=dev)
     if world > 1:
@@ -313,7 +315,8 @@ def run_engine(args):
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak if achieved else None,
                     "traffic": traffic_rs * per_launch_rs if traffic_rs else None,
-                    "kernel": "sim_chunk_kernel", "peak_source": "measured" if peaks else "fallback",
+                    "kernel": tvbx.KERNEL_NAMES.get(kernel_id, str(kernel_id)),
+                    "peak_source": "measured" if peaks else "fallback",
                     "algorithmic_bytes_per_region_step": bytes_rs,
                     "region_steps_per_launch": per_launch_rs,
                     "avg_launch_ms": sim_ms / max(sim_launches, 1),

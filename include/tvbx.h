@@ -252,6 +252,10 @@ tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t
                                    const float* x_e, const float* x_i, const float* W,
                                    const float* E_L, float* out);
 
+/* Simulation kernel used by the last tvbx_run (TVBX_KERNEL_GENERAL or
+ * TVBX_KERNEL_PREFETCH + v) and its tile size in sets. */
+tvbx_status tvbx_last_kernel(const tvbx_sweep* h, int32_t* kernel, int32_t* sets_per_tile);
+
 /* Number of kernels this library has launched in the process so far. */
 uint64_t tvbx_launch_count(void);
 

@@ -889,6 +889,15 @@ tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t
 
 uint64_t tvbx_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+tvbx_status tvbx_last_kernel(const tvbx_sweep* h, int32_t* kernel, int32_t* sets_per_tile)
+{
+    if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
+    if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_last_kernel before tvbx_run");
+    if (kernel) *kernel = h->variant < 0 ? TVBX_KERNEL_GENERAL : TVBX_KERNEL_PREFETCH + h->variant;
+    if (sets_per_tile) *sets_per_tile = h->pb;
+    return TVBX_OK;
+}
+
 tvbx_status tvbx_transfer_bytes(const tvbx_sweep* h, uint64_t* h2d, uint64_t* d2h)
 {
     if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");

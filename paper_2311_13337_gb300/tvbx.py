@@ -73,7 +73,8 @@ class FcCfg(ctypes.Structure):
 _lib = None
 EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep_create",
            "tvbx_sweep_create_points", "tvbx_sweep_info", "tvbx_run", "tvbx_summary", "tvbx_series",
-           "tvbx_series_range", "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_launch_count",
+           "tvbx_series_range", "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_last_kernel",
+           "tvbx_launch_count",
            "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_sweep_destroy")
 
 
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = False):
     L.tvbx_transfer_function.argtypes = [ctypes.POINTER(Model), i32, i64, i32, fp, fp, fp, fp, fp]
     L.tvbx_sweep_destroy.argtypes = [vp]
     L.tvbx_launch_count.restype = ctypes.c_uint64
+    L.tvbx_last_kernel.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.tvbx_profile_enable.argtypes = [vp, i32]
     L.tvbx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -282,6 +284,17 @@ def transfer_function(pop: int, x_e, x_i, W, E_L, model: Model | None = None) ->
                                          MEM_HOST, *fptr, ctypes.c_void_p(out.ctypes.data)),
            "tvbx_transfer_function")
     return out
+
+
+KERNEL_NAMES = {KERNEL_GENERAL: "sim_chunk_kernel"}
+KERNEL_NAMES.update({KERNEL_PREFETCH + v: ("sim_bulk_kernel" if v >= 4 else "sim_fast_kernel") + f" (variant {v})"
+                     for v in range(N_PREFETCH_VARIANTS)})
+
+
+def last_kernel(h) -> tuple[int, int]:
+    k, pb = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().tvbx_last_kernel(h, ctypes.byref(k), ctypes.byref(pb)), "tvbx_last_kernel")
+    return k.value, pb.value
 
 
 def launch_count() -> int:
