@@ -272,6 +272,34 @@ tvbx_status tvbx_profile_enable(tvbx_sweep* h, int32_t enable);
 tvbx_status tvbx_profile_read(tvbx_sweep* h, double* sim_ms, int64_t* sim_launches,
                               double* region_steps);
 
+/* FC without any device allocation. The paper has no counterpart: this is
+ * a service of the library for callers that cannot allocate device memory
+ * when they need an FC, e.g. hosts that fix their device-memory budget at
+ * start-up and refuse later allocations (real-time or embedded services,
+ * plugins under another framework's memory manager), or code where a
+ * cudaMalloc would synchronise the device and stall other work.
+ *   series   device, [n_samples][n_regions][n_sets] FP32 (sets fastest, the
+ *            layout the engine keeps internally);
+ *   fc_out   device, [n_sets][n_regions][n_regions] Pearson FC (Eq. 6) over
+ *            all samples, with the conventions of tvbx_fc (zero-variance rows
+ *            are zero, unit diagonal);
+ *   chi, mean_fc  device, [n_sets] each, nullable (as in tvbx_summary).
+ * Work is enqueued on cuda_stream (NULL = default stream); the call returns
+ * without waiting. The only scratch, each set's moments, lives in a fixed
+ * array of 8 Mi floats (32 MiB) reserved on every GPU that loads the library
+ * until the process exits; a call needs n_sets * (n_regions^2 + n_regions)
+ * floats of it, so n_sets <= 1,787 at 68 regions. Larger requests, more than
+ * 90 regions, NULL buffers or non-positive sizes return TVBX_E_INVALID_ARG
+ * with the limit in tvbx_last_error(). The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress with that device current);
+ * make that first call before any stream capture. Every call shares the array:
+ * calls that overlap on the GPU (other streams, other threads) race and
+ * corrupt each other's results; serialise them. Each call writes every
+ * scratch entry it reads, so nothing needs clearing between calls. No
+ * cudaMalloc, cudaFree or allocating library routine is called. */
+tvbx_status tvbx_fc_noalloc(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
+                            float* fc_out, float* chi, float* mean_fc, void* cuda_stream);
+
 /* Release the handle and its device memory. NULL is accepted. */
 tvbx_status tvbx_sweep_destroy(tvbx_sweep* h);
 

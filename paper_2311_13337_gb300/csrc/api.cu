@@ -41,6 +41,21 @@ tvbx_status fail(tvbx_status code, const char* fmt, ...)
     return code;
 }
 
+}  // namespace
+
+tvbx_status tvbx::report_error(tvbx_status code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+namespace {
+
 tvbx_status cuda_fail(cudaError_t e, const char* what)
 {
     if (e == cudaErrorMemoryAllocation)

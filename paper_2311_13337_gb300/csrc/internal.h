@@ -11,6 +11,10 @@ namespace tvbx {
 // Process-wide count of kernel launches made by this library.
 void note_launch(uint64_t n = 1);
 
+// Record the message of a failing call (returned by tvbx_last_error) and
+// return `code`.
+tvbx_status report_error(tvbx_status code, const char* fmt, ...);
+
 // Number of per-(set, region) state words kept across steps and chunks:
 // E, I, C_ee, C_ei, C_ii, W_e, W_i, OU, then the temporal-average accumulators
 // of E and I, then compensated running sums (sum, carry) of the E and I samples.

@@ -75,7 +75,8 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_sweep_create_points", "tvbx_sweep_info", "tvbx_run", "tvbx_summary", "tvbx_series",
            "tvbx_series_range", "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_last_kernel",
            "tvbx_launch_count",
-           "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_sweep_destroy")
+           "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_fc_noalloc",
+           "tvbx_sweep_destroy")
 
 
 def library_path() -> str:
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = False):
     L.tvbx_sweep_destroy.argtypes = [vp]
     L.tvbx_launch_count.restype = ctypes.c_uint64
     L.tvbx_last_kernel.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.tvbx_fc_noalloc.argtypes = [fp, i32, i64, i64, fp, fp, fp, vp]
     L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.tvbx_profile_enable.argtypes = [vp, i32]
     L.tvbx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -272,6 +274,26 @@ def fc(h, fc_out=None, fcd_out=None, fcd_window=0, fcd_step=0, precision=FC_FP32
     _check(load().tvbx_fc(h, ctypes.byref(cfg), mem, _out_ptr(fc_out)[0], _out_ptr(fcd_out)[0],
                           ctypes.byref(nw)), "tvbx_fc")
     return nw.value
+
+
+def fc_noalloc(series, n_regions: int, n_sets: int, n_samples: int, fc_out, chi=None, mean_fc=None, stream=None):
+    """FC with no device allocation (scratch in a fixed array reserved by the
+    library). series: CUDA tensor [n_samples][n_regions][n_sets]; outputs are
+    CUDA tensors. Calls that overlap on the GPU race; see tvbx.h."""
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    args = []
+    for x in (series, fc_out, chi, mean_fc):
+        if x is None:
+            args.append(None)
+        else:
+            ptr, mem = _out_ptr(x)
+            if mem != MEM_DEVICE:
+                raise ValueError("tvbx_fc_noalloc takes device buffers only")
+            args.append(ptr)
+    _check(load().tvbx_fc_noalloc(args[0], int(n_regions), int(n_sets), int(n_samples), args[1], args[2], args[3],
+                                  sp), "tvbx_fc_noalloc")
 
 
 def transfer_function(pop: int, x_e, x_i, W, E_L, model: Model | None = None) -> np.ndarray:
