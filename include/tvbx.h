@@ -146,7 +146,9 @@ typedef struct {
                                   buffer: v = 0: 16 sets, 2 sets x 1 region per
                                   thread; 1: 32 sets, 4 x 1; 2: 16 sets, 1 x 2;
                                   3: 16 sets, 2 x 2; TMA bulk copies into two
-                                  buffers: 4: 16 sets, 2 x 1; 5: 16 sets, 1 x 2 */
+                                  buffers: 4: 16 sets, 2 x 1; 5: 16 sets, 1 x 2;
+                                  cp.async, 8 sets, two CTAs per SM: 6: 2 x 1;
+                                  7: 1 x 2 */
 
 /* FC settings (Sec. "Output": FC from the covariance of the series,
  * Eq. 6 Pearson; FCD over sliding windows). */
@@ -245,12 +247,14 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
  * with Table 1) and its derivatives, evaluated on the GPU at n points, with
  * the same device code the integration uses. pop: 0 = excitatory (RS row,
  * W = W_e), 1 = inhibitory (FS row). Inputs x_e, x_i (total input rates,
- * kHz), W (pA), E_L (mV), each [n]; out [n][7] = F, dF/dx_e, dF/dx_i,
- * d2F/dx_e2, d2F/dx_e dx_i, d2F/dx_i2 (kHz-based units), mu_V (mV). All
- * arrays live in memory of kind `mem`. model NULL = defaults. Synchronous. */
+ * kHz), W (pA), E_L (mV), each [n]; C [n][3] = (C_ee, C_ei, C_ii) (kHz^2,
+ * nullable). out [n][8] = F, dF/dx_e, dF/dx_i, d2F/dx_e2, d2F/dx_e dx_i,
+ * d2F/dx_i2, mu_V (mV), and sum_ij C_ij d2F/dx_i dx_j as the integrator
+ * computes it for Eq. 1 (contracted second-order jets; 0 when C is NULL).
+ * All arrays live in memory of kind `mem`. model NULL = defaults. Synchronous. */
 tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t n, int32_t mem,
                                    const float* x_e, const float* x_i, const float* W,
-                                   const float* E_L, float* out);
+                                   const float* E_L, const float* C, float* out);
 
 /* Simulation kernel used by the last tvbx_run (TVBX_KERNEL_GENERAL or
  * TVBX_KERNEL_PREFETCH + v) and its tile size in sets. */

@@ -542,7 +542,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     int variant = -1;   // prefetch variant, -1 = general kernel
     if (c.kernel == TVBX_KERNEL_AUTO) {
         // preference order from measurement on the 32,768-set, 68-region sweep
-        for (int v : {0, 2, 1, 3})
+        for (int v : {1, 0, 2, 3})
             if (sim_fast_fits(v, N, nnz_max)) { variant = v; break; }
     } else if (c.kernel != TVBX_KERNEL_GENERAL) {
         variant = c.kernel - TVBX_KERNEL_PREFETCH;
@@ -867,7 +867,7 @@ tvbx_status tvbx_state(const tvbx_sweep* hc, int32_t mem, float* out)
 
 tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t n, int32_t mem,
                                    const float* x_e, const float* x_i, const float* W, const float* E_L,
-                                   float* out)
+                                   const float* C, float* out)
 {
     if (pop != 0 && pop != 1) return fail(TVBX_E_INVALID_ARG, "pop must be 0 or 1");
     if (n < 0) return fail(TVBX_E_INVALID_ARG, "n must be >= 0");
@@ -881,21 +881,22 @@ tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t
     if (!model_ok(m)) return fail(TVBX_E_INVALID_ARG, "model constants must be positive where they divide");
     const DevModel dm = to_device_model(m, 0.1);
     DevBuf in, res;
-    const float *dxe = x_e, *dxi = x_i, *dW = W, *dEL = E_L;
+    const float *dxe = x_e, *dxi = x_i, *dW = W, *dEL = E_L, *dC = C;
     float* dout = out;
     if (mem == TVBX_MEM_HOST) {
-        CK(in.ensure(sizeof(float) * 4 * n), "inputs");
-        CK(res.ensure(sizeof(float) * 7 * n), "outputs");
+        CK(in.ensure(sizeof(float) * 7 * n), "inputs");
+        CK(res.ensure(sizeof(float) * 8 * n), "outputs");
         float* b = in.as<float>();
         CK(cudaMemcpy(b, x_e, sizeof(float) * n, cudaMemcpyHostToDevice), "upload");
         CK(cudaMemcpy(b + n, x_i, sizeof(float) * n, cudaMemcpyHostToDevice), "upload");
         CK(cudaMemcpy(b + 2 * n, W, sizeof(float) * n, cudaMemcpyHostToDevice), "upload");
         CK(cudaMemcpy(b + 3 * n, E_L, sizeof(float) * n, cudaMemcpyHostToDevice), "upload");
-        dxe = b; dxi = b + n; dW = b + 2 * n; dEL = b + 3 * n;
+        if (C) CK(cudaMemcpy(b + 4 * n, C, sizeof(float) * 3 * n, cudaMemcpyHostToDevice), "upload");
+        dxe = b; dxi = b + n; dW = b + 2 * n; dEL = b + 3 * n; dC = C ? b + 4 * n : nullptr;
         dout = res.as<float>();
     }
-    CK(launch_tf_eval(dm, pop, n, dxe, dxi, dW, dEL, dout, 0), "transfer function");
-    if (mem == TVBX_MEM_HOST) CK(cudaMemcpy(out, dout, sizeof(float) * 7 * n, cudaMemcpyDeviceToHost), "download");
+    CK(launch_tf_eval(dm, pop, n, dxe, dxi, dW, dEL, dC, dout, 0), "transfer function");
+    if (mem == TVBX_MEM_HOST) CK(cudaMemcpy(out, dout, sizeof(float) * 8 * n, cudaMemcpyDeviceToHost), "download");
     CK(cudaDeviceSynchronize(), "synchronize");
     in.release();
     res.release();

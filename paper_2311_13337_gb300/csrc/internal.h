@@ -105,7 +105,7 @@ cudaError_t launch_ou_table(const DevModel& m, float* table, float* ou_state, in
                             int64_t n0, int32_t n_chunk, uint64_t seed, cudaStream_t s);
 cudaError_t launch_sim_chunk(const SimArgs& a, int32_t n_tiles, int32_t pb, cudaStream_t s);
 cudaError_t launch_tf_eval(const DevModel& m, int pop, int64_t n, const float* x_e, const float* x_i,
-                           const float* W, const float* E_L, float* out, cudaStream_t s);
+                           const float* W, const float* E_L, const float* C, float* out, cudaStream_t s);
 // Prefetching kernel (sim_fast.cu): variant 0 = 16 sets per CTA, 1 = 32.
 cudaError_t launch_sim_fast(const SimArgs& a, int variant, int32_t n_tiles, int nnz_max, cudaStream_t s);
 bool sim_fast_fits(int variant, int N, int nnz_max);

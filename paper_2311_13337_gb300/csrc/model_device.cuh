@@ -250,6 +250,142 @@ static __device__ __forceinline__ void transfer_x(const DevModel& m, const float
     out[5] = di * di * F.bb;
 }
 
+// ---------------------------------------------------------------------------
+// Contracted second-order jets for the integrator. Eq. 1 needs the Hessian of
+// F only through 1/2 sum_{lambda,eta} c_{lambda eta} d2F/dnu_lambda dnu_eta,
+// and Eq. 2 only its gradient, so every intermediate carries its value, its
+// gradient in (fe, fi) and l = sum_ij C~_ij d_i d_j of it, with
+// C~ = diag(K') C diag(K') (K' = dfe/dnu_e, dfi/dnu_i). The rules are those of
+// the full jets contracted with C~: for a product l(xy) = x l(y) + y l(x)
+// + 2 B(x, y), for f(x) l = f' l(x) + f'' B(x, x), with B(x, y) = grad x^T C~ grad y.
+// ---------------------------------------------------------------------------
+struct L4 {
+    float v, a, b, l;
+};
+struct Cov3 {
+    float aa, ab, bb;   // C~ in (fe, fi) coordinates
+};
+
+static __device__ __forceinline__ float lbil(const Cov3& c, const L4& x, const L4& y)
+{
+    return fmaf(x.a, fmaf(c.aa, y.a, c.ab * y.b), x.b * fmaf(c.ab, y.a, c.bb * y.b));
+}
+static __device__ __forceinline__ L4 ladd(const L4& x, const L4& y)
+{
+    return L4{x.v + y.v, x.a + y.a, x.b + y.b, x.l + y.l};
+}
+static __device__ __forceinline__ L4 laffine(const L4& x, float s, float c)
+{
+    return L4{fmaf(s, x.v, c), s * x.a, s * x.b, s * x.l};
+}
+static __device__ __forceinline__ L4 lmul(const Cov3& c, const L4& x, const L4& y)
+{
+    L4 r;
+    r.v = x.v * y.v;
+    r.a = fmaf(x.a, y.v, x.v * y.a);
+    r.b = fmaf(x.b, y.v, x.v * y.b);
+    r.l = fmaf(x.l, y.v, fmaf(x.v, y.l, 2.0f * lbil(c, x, y)));
+    return r;
+}
+static __device__ __forceinline__ L4 lchain(const Cov3& c, const L4& x, float f0, float f1, float f2)
+{
+    return L4{f0, f1 * x.a, f1 * x.b, fmaf(f1, x.l, f2 * lbil(c, x, x))};
+}
+static __device__ __forceinline__ L4 lrcp(const Cov3& c, const L4& x)
+{
+    const float q = fast_rcp(x.v);
+    const float q2 = q * q;
+    return lchain(c, x, q, -q2, 2.0f * q2 * q);
+}
+
+// Transfer function of one population with the contracted jet (same
+// template and polynomial as transfer()).
+static __device__ __forceinline__ L4 transfer_lap(const DevModel& m, const float* __restrict__ P, float E_L, float W,
+                                                  float fe, float fi, const Cov3& c, float& muV_out)
+{
+    const float qe = m.qe, qi = m.qi;
+    const float muG = fmaf(qe, fe, fmaf(qi, fi, m.g_L));
+    const float r = fast_rcp(muG);
+    const float r2 = r * r;
+    const float num = fmaf(qe * m.E_e, fe, fmaf(qi * m.E_i, fi, fmaf(m.g_L, E_L, -W)));
+    const float muV = num * r;
+    muV_out = muV;
+    const float u = qe * (m.E_e - muV) * r;
+    const float w = qi * (m.E_i - muV) * r;
+    const float s = fmaf(qe, w, qi * u);
+    const float cu = 2.0f * qe * r2 * fmaf(2.0f * qi, u, qe * w);
+    const float cw = 2.0f * qi * r2 * fmaf(2.0f * qe, w, qi * u);
+    const L4 jmuV{muV, u, w, -2.0f * r * fmaf(c.aa * qe, u, fmaf(c.ab, s, c.bb * qi * w))};
+    const L4 ju{u, -2.0f * qe * r * u, -s * r, fmaf(c.aa, 6.0f * qe * qe * r2 * u, fmaf(2.0f * c.ab, cu, c.bb * cw))};
+    const L4 jw{w, -s * r, -2.0f * qi * r * w, fmaf(c.aa, cu, fmaf(2.0f * c.ab, cw, c.bb * 6.0f * qi * qi * r2 * w))};
+    const float cr = m.C_m * r, cr2 = cr * r, cr3 = cr2 * r;
+    const L4 jTm{cr, -qe * cr2, -qi * cr2, 2.0f * cr3 * fmaf(c.aa * qe, qe, fmaf(2.0f * c.ab * qe, qi, c.bb * qi * qi))};
+    const L4 u2 = lmul(c, ju, ju), w2 = lmul(c, jw, jw);
+    // A_e = fe u^2 (grad fe = (1, 0)), A_i = fi w^2 (grad fi = (0, 1))
+    const L4 Ae{fe * u2.v, fmaf(fe, u2.a, u2.v), fe * u2.b, fmaf(fe, u2.l, 2.0f * fmaf(c.aa, u2.a, c.ab * u2.b))};
+    const L4 Ai{fi * w2.v, fi * w2.a, fmaf(fi, w2.b, w2.v), fmaf(fi, w2.l, 2.0f * fmaf(c.ab, w2.a, c.bb * w2.b))};
+    L4 De = jTm;
+    De.v += m.tau_e;
+    L4 Di = jTm;
+    Di.v += m.tau_i;
+    const L4 s2 = ladd(lmul(c, Ae, lrcp(c, De)), lmul(c, Ai, lrcp(c, Di)));
+    const float h = 0.5f * s2.v;
+    const float rs = fast_rsqrt(h);
+    const float rs3 = rs * rs * rs;
+    const L4 hs = laffine(s2, 0.5f, 0.0f);
+    const float bh = lbil(c, hs, hs);
+    const L4 sig{h * rs, 0.5f * rs * hs.a, 0.5f * rs * hs.b, fmaf(0.5f * rs, hs.l, -0.25f * rs3 * bh)};
+    const L4 isig{rs, -0.5f * rs3 * hs.a, -0.5f * rs3 * hs.b, fmaf(-0.5f * rs3, hs.l, 0.75f * rs3 * rs * rs * bh)};
+    const L4 tV = lmul(c, ladd(Ae, Ai), lrcp(c, s2));
+    const L4 V = laffine(jmuV, m.inv_dmu0, -m.mu0 * m.inv_dmu0);
+    const L4 S = laffine(sig, m.inv_dsig0, -m.sig0 * m.inv_dsig0);
+    const L4 Z = laffine(tV, m.gL_over_Cm * m.inv_dtau0, -m.tau0 * m.inv_dtau0);
+    // threshold polynomial P0 + p.v + v^T Q v / 2; l = sum_ij C~_ij v_i^T Q v_j + g . l(v)
+    const float gV = fmaf(2.0f * P[4], V.v, fmaf(P[7], S.v, fmaf(P[8], Z.v, P[1])));
+    const float gS = fmaf(P[7], V.v, fmaf(2.0f * P[5], S.v, fmaf(P[9], Z.v, P[2])));
+    const float gZ = fmaf(P[8], V.v, fmaf(P[9], S.v, fmaf(2.0f * P[6], Z.v, P[3])));
+    const float QaV = fmaf(2.0f * P[4], V.a, fmaf(P[7], S.a, P[8] * Z.a));
+    const float QaS = fmaf(P[7], V.a, fmaf(2.0f * P[5], S.a, P[9] * Z.a));
+    const float QaZ = fmaf(P[8], V.a, fmaf(P[9], S.a, 2.0f * P[6] * Z.a));
+    const float QbV = fmaf(2.0f * P[4], V.b, fmaf(P[7], S.b, P[8] * Z.b));
+    const float QbS = fmaf(P[7], V.b, fmaf(2.0f * P[5], S.b, P[9] * Z.b));
+    const float QbZ = fmaf(P[8], V.b, fmaf(P[9], S.b, 2.0f * P[6] * Z.b));
+    const float aQa = fmaf(QaV, V.a, fmaf(QaS, S.a, QaZ * Z.a));
+    const float aQb = fmaf(QbV, V.a, fmaf(QbS, S.a, QbZ * Z.a));
+    const float bQb = fmaf(QbV, V.b, fmaf(QbS, S.b, QbZ * Z.b));
+    L4 th;
+    th.v = P[0] + fmaf(V.v, fmaf(P[4], V.v, fmaf(P[7], S.v, fmaf(P[8], Z.v, P[1]))),
+                       fmaf(S.v, fmaf(P[5], S.v, fmaf(P[9], Z.v, P[2])), Z.v * fmaf(P[6], Z.v, P[3])));
+    th.a = fmaf(gV, V.a, fmaf(gS, S.a, gZ * Z.a));
+    th.b = fmaf(gV, V.b, fmaf(gS, S.b, gZ * Z.b));
+    th.l = fmaf(c.aa, aQa, fmaf(2.0f * c.ab, aQb, fmaf(c.bb, bQb, fmaf(gV, V.l, fmaf(gS, S.l, gZ * Z.l)))));
+    const L4 d{th.v - jmuV.v, th.a - jmuV.a, th.b - jmuV.b, th.l - jmuV.l};
+    const L4 arg = laffine(lmul(c, d, isig), 0.70710678118654752f, 0.0f);
+    const float x = arg.v;
+    float ev, g;
+    erfc_gauss(x, ev, g);
+    const L4 ec = lchain(c, arg, ev, -g, 2.0f * x * g);
+    return laffine(lmul(c, ec, lrcp(c, tV)), 0.5f, 0.0f);
+}
+
+// F, its gradient in the input rates (x_e, x_i) and sum_ij C_ij d2F/dx_i dx_j
+// for the covariance C = [[Cee, Cei], [Cei, Cii]] of the pair.
+static __device__ __forceinline__ void transfer_x_lap(const DevModel& m, const float* __restrict__ P, float E_L,
+                                                      float W, float x_e, float x_i, float Cee, float Cei, float Cii,
+                                                      float out[4], float& muV)
+{
+    const float de = x_e > 0.0f ? m.K_e : 0.0f;
+    const float di = x_i > 0.0f ? m.K_i : 0.0f;
+    const float fe = fmaf(m.K_e, fmaxf(x_e, 0.0f), m.rate_floor);
+    const float fi = fmaf(m.K_i, fmaxf(x_i, 0.0f), m.rate_floor);
+    const Cov3 c{de * de * Cee, de * di * Cei, di * di * Cii};
+    const L4 F = transfer_lap(m, P, E_L, W, fe, fi, c, muV);
+    out[0] = F.v;
+    out[1] = de * F.a;
+    out[2] = di * F.b;
+    out[3] = F.l;
+}
+
 // Per-set parameters of the simulation kernels (11 floats, in this order).
 struct SetParams {
     float g, b_e, inv_tw, ELe, ELi, a_e, wn, cFee, cFei, cFie, cFii;
@@ -286,14 +422,15 @@ static __device__ __forceinline__ void euler_step(const DevModel& m, const SetPa
 {
     const float E = x.E, I = x.I, ce = x.Cee, cx = x.Cei, ci = x.Cii, We = x.We, Wi = x.Wi;
     const float exc = fmaf(sp.wn, OU, fmaf(sp.g, coupling, E));
-    float Fe[6], Fi[6], muVe, muVi;
-    transfer_x(m, m.P_e, sp.ELe, We, exc + sp.cFee, I + sp.cFei, Fe, muVe);
-    transfer_x(m, m.P_i, sp.ELi, Wi, exc + sp.cFie, I + sp.cFii, Fi, muVi);
+    // F, gradient in (nu_e, nu_i), and sum c_{lambda eta} d2F/dnu_lambda dnu_eta
+    float Fe[4], Fi[4], muVe, muVi;
+    transfer_x_lap(m, m.P_e, sp.ELe, We, exc + sp.cFee, I + sp.cFei, ce, cx, ci, Fe, muVe);
+    transfer_x_lap(m, m.P_i, sp.ELi, Wi, exc + sp.cFie, I + sp.cFii, ce, cx, ci, Fi, muVi);
     const float rT = m.inv_T;
     const float dFe = Fe[0] - E, dFi = Fi[0] - I;
     // Eq. 1
-    const float dE = (dFe + 0.5f * fmaf(ce, Fe[3], fmaf(2.0f * cx, Fe[4], ci * Fe[5]))) * rT;
-    const float dI = (dFi + 0.5f * fmaf(ce, Fi[3], fmaf(2.0f * cx, Fi[4], ci * Fi[5]))) * rT;
+    const float dE = fmaf(0.5f, Fe[3], dFe) * rT;
+    const float dI = fmaf(0.5f, Fi[3], dFi) * rT;
     // Eq. 2
     const float dCee = (Fe[0] * (rT - Fe[0]) * m.inv_Ne + dFe * dFe
                         + 2.0f * fmaf(ce, Fe[1], cx * Fe[2]) - 2.0f * ce) * rT;

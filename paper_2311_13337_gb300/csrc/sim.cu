@@ -182,14 +182,19 @@ sim_chunk_kernel(const __grid_constant__ SimArgs a)
 // ---------------------------------------------------------------------------
 __global__ void tf_eval_kernel(DevModel m, int pop, int64_t n, const float* __restrict__ x_e,
                                const float* __restrict__ x_i, const float* __restrict__ W,
-                               const float* __restrict__ E_L, float* __restrict__ out)
+                               const float* __restrict__ E_L, const float* __restrict__ C,
+                               float* __restrict__ out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        const float* P = pop == 0 ? m.P_e : m.P_i;
         float F[6], muV;
-        transfer_x(m, pop == 0 ? m.P_e : m.P_i, E_L[i], W[i], x_e[i], x_i[i], F, muV);
-        for (int c = 0; c < 6; ++c) out[i * 7 + c] = F[c];
-        out[i * 7 + 6] = muV;
+        transfer_x(m, P, E_L[i], W[i], x_e[i], x_i[i], F, muV);
+        for (int c = 0; c < 6; ++c) out[i * 8 + c] = F[c];
+        out[i * 8 + 6] = muV;
+        float L[4] = {0.f, 0.f, 0.f, 0.f};
+        if (C) transfer_x_lap(m, P, E_L[i], W[i], x_e[i], x_i[i], C[3 * i], C[3 * i + 1], C[3 * i + 2], L, muV);
+        out[i * 8 + 7] = L[3];
     }
 }
 
@@ -256,12 +261,12 @@ cudaError_t launch_sim_chunk(const SimArgs& a, int32_t n_tiles, int32_t pb, cuda
 }
 
 cudaError_t launch_tf_eval(const DevModel& m, int pop, int64_t n, const float* x_e, const float* x_i,
-                           const float* W, const float* E_L, float* out, cudaStream_t s)
+                           const float* W, const float* E_L, const float* C, float* out, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     note_launch();
     tf_eval_kernel<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(
-        m, pop, n, x_e, x_i, W, E_L, out);
+        m, pop, n, x_e, x_i, W, E_L, C, out);
     return cudaGetLastError();
 }
 

@@ -292,6 +292,8 @@ static const FastVariant kFast[] = {
     {0, 16, 2, 2, 320, 1},   // 3: cp.async, 16 sets, 2 x 2
     {1, 16, 2, 1, 576, 1},   // 4: TMA bulk, double buffer, 16 sets, 2 x 1
     {1, 16, 1, 2, 576, 1},   // 5: TMA bulk, double buffer, 16 sets, 1 x 2
+    {0, 8, 2, 1, 288, 2},    // 6: cp.async, 8 sets, 2 x 1, two CTAs per SM
+    {0, 8, 1, 2, 288, 2},    // 7: cp.async, 8 sets, 1 x 2, two CTAs per SM
 };
 constexpr int kNumFast = (int)(sizeof kFast / sizeof kFast[0]);
 
@@ -341,6 +343,8 @@ cudaError_t launch_sim_fast(const SimArgs& a, int variant, int32_t n_tiles, int 
     case 3: return launch_fast<0, 16, 2, 2, 320, 1>(a, variant, n_tiles, nnz_max, s);
     case 4: return launch_fast<1, 16, 2, 1, 576, 1>(a, variant, n_tiles, nnz_max, s);
     case 5: return launch_fast<1, 16, 1, 2, 576, 1>(a, variant, n_tiles, nnz_max, s);
+    case 6: return launch_fast<0, 8, 2, 1, 288, 2>(a, variant, n_tiles, nnz_max, s);
+    case 7: return launch_fast<0, 8, 1, 2, 288, 2>(a, variant, n_tiles, nnz_max, s);
     default: return cudaErrorInvalidValue;
     }
 }

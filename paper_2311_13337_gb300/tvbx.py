@@ -108,7 +108,7 @@ def load(build_if_missing: bool = False):
     L.tvbx_series_range.argtypes = [vp, i64, i64, i64, i64, i32, fp]
     L.tvbx_state.argtypes = [vp, i32, fp]
     L.tvbx_fc.argtypes = [vp, ctypes.POINTER(FcCfg), i32, fp, fp, ctypes.POINTER(i32)]
-    L.tvbx_transfer_function.argtypes = [ctypes.POINTER(Model), i32, i64, i32, fp, fp, fp, fp, fp]
+    L.tvbx_transfer_function.argtypes = [ctypes.POINTER(Model), i32, i64, i32, fp, fp, fp, fp, fp, fp]
     L.tvbx_sweep_destroy.argtypes = [vp]
     L.tvbx_launch_count.restype = ctypes.c_uint64
     L.tvbx_last_kernel.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -223,7 +223,7 @@ def sweep_info(h) -> tuple[int, int, int]:
 
 
 KERNEL_AUTO, KERNEL_GENERAL, KERNEL_PREFETCH = 0, 1, 2
-N_PREFETCH_VARIANTS = 6
+N_PREFETCH_VARIANTS = 8
 
 
 def run(h, dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
@@ -296,47 +296,19 @@ def fc_noalloc(series, n_regions: int, n_sets: int, n_samples: int, fc_out, chi=
                                   sp), "tvbx_fc_noalloc")
 
 
-def transfer_function(pop: int, x_e, x_i, W, E_L, model: Model | None = None) -> np.ndarray:
-    """[n][7] = F, F_e, F_i, F_ee, F_ei, F_ii, mu_V from the device code."""
+def transfer_function(pop: int, x_e, x_i, W, E_L, C=None, model: Model | None = None) -> np.ndarray:
+    """[n][8] = F, F_e, F_i, F_ee, F_ei, F_ii, mu_V, sum_ij C_ij F_ij (the
+    integrator's contracted term, 0 without C) from the device code."""
     arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (x_e, x_i, W, E_L)]
     n = arrs[0].shape[0]
-    out = np.zeros((n, 7), dtype=np.float32)
+    c = None if C is None else np.ascontiguousarray(C, dtype=np.float32).reshape(n, 3)
+    out = np.zeros((n, 8), dtype=np.float32)
     fptr = [ctypes.c_void_p(a.ctypes.data) for a in arrs]
     _check(load().tvbx_transfer_function(ctypes.byref(model) if model is not None else None, int(pop), n,
-                                         MEM_HOST, *fptr, ctypes.c_void_p(out.ctypes.data)),
+                                         MEM_HOST, *fptr, ctypes.c_void_p(c.ctypes.data) if c is not None else None,
+                                         ctypes.c_void_p(out.ctypes.data)),
            "tvbx_transfer_function")
     return out
-
-
-KERNEL_NAMES = {KERNEL_GENERAL: "sim_chunk_kernel"}
-KERNEL_NAMES.update({KERNEL_PREFETCH + v: ("sim_bulk_kernel" if v >= 4 else "sim_fast_kernel") + f" (variant {v})"
-                     for v in range(N_PREFETCH_VARIANTS)})
-
-
-def last_kernel(h) -> tuple[int, int]:
-    k, pb = ctypes.c_int32(), ctypes.c_int32()
-    _check(load().tvbx_last_kernel(h, ctypes.byref(k), ctypes.byref(pb)), "tvbx_last_kernel")
-    return k.value, pb.value
-
-
-def launch_count() -> int:
-    return int(load().tvbx_launch_count())
-
-
-def transfer_bytes(h) -> tuple[int, int]:
-    a, b = ctypes.c_uint64(), ctypes.c_uint64()
-    _check(load().tvbx_transfer_bytes(h, ctypes.byref(a), ctypes.byref(b)), "tvbx_transfer_bytes")
-    return a.value, b.value
-
-
-def profile_enable(h, enable: bool = True):
-    _check(load().tvbx_profile_enable(h, int(bool(enable))), "tvbx_profile_enable")
-
-
-def profile_read(h) -> tuple[float, int, float]:
-    ms, n, rs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
-    _check(load().tvbx_profile_read(h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(rs)), "tvbx_profile_read")
-    return ms.value, n.value, rs.value
 
 
 def sweep_destroy(h):

@@ -39,12 +39,18 @@ def test_transfer_function_and_derivatives(tvbx, oracle, pop):
     n = 3000
     xe, xi = rng.uniform(0, 0.05, n), rng.uniform(0, 0.05, n)
     W, EL = rng.uniform(0, 150, n), rng.uniform(-80, -58, n)
-    got = tvbx.transfer_function(pop, xe, xi, W, EL).astype(np.float64)
+    C = np.stack([rng.uniform(0, 1e-5, n), rng.uniform(-5e-6, 5e-6, n), rng.uniform(0, 1e-5, n)], axis=1)
+    got = tvbx.transfer_function(pop, xe, xi, W, EL, C=C).astype(np.float64)
     m = oracle.make_model()
-    ref = np.zeros((n, 7))
+    ref = np.zeros((n, 8))
     for i in range(n):
         jet, aux = oracle.tf_eval(m, "e" if pop == 0 else "i", EL[i], xe[i], xi[i], W[i])
         ref[i, :6], ref[i, 6] = jet, aux[1]
+        # the integrator's term: sum_ij C_ij d2F/dx_i dx_j
+        ref[i, 7] = C[i, 0] * jet[3] + 2 * C[i, 1] * jet[4] + C[i, 2] * jet[5]
+    scale7 = np.abs(C[:, :1] * ref[:, 3:4]).max() + np.abs(C[:, 2:3] * ref[:, 5:6]).max()
+    bad = np.abs(got[:, 7] - ref[:, 7]) > 2e-3 * np.abs(ref[:, 7]) + 5e-4 * scale7
+    assert not bad.any(), f"contracted Hessian: {bad.sum()} points out of tolerance"
     for c in range(7):
         scale = np.abs(ref[:, c]).max()
         rtol, atol = (2e-4, 1e-5) if c < 3 else ((2e-3, 5e-4) if c < 6 else (1e-6, 0.0))
