@@ -153,12 +153,25 @@ typedef struct {
 /* FC settings (Sec. "Output": FC from the covariance of the series,
  * Eq. 6 Pearson; FCD over sliding windows). */
 typedef struct {
-    int32_t precision;        /* TVBX_FC_FP32 (SIMT, FP32 accumulation) */
+    int32_t precision;        /* one of TVBX_FC_* below */
     int32_t fcd_window;       /* samples per FCD window; 0 = no FCD */
     int32_t fcd_step;         /* samples between window starts; fcd_window must
                                  be a multiple of fcd_step */
 } tvbx_fc_cfg;
-#define TVBX_FC_FP32 0
+/* The Gram matrix G = Z Z^T of the shifted series Z (the contraction behind
+ * the covariance of Eq. 6) is formed
+ *   FP32:    with FP32 CUDA-core FMAs;
+ *   BF16:    on the tensor cores from Z rounded to BF16, FP32 accumulation;
+ *   BF16X3:  split precision, Z = H + L with H, L in BF16, G = H H^T + H L^T
+ *            + L H^T (two MMAs and a symmetrisation), FP32 accumulation;
+ *   TF32, TF32X3: the same with TF32 operands.
+ * The tensor-core forms need n_regions <= 128; the row sums of Z use
+ * compensated FP32 summation in every form. */
+#define TVBX_FC_FP32   0
+#define TVBX_FC_BF16   1
+#define TVBX_FC_BF16X3 2
+#define TVBX_FC_TF32   3
+#define TVBX_FC_TF32X3 4
 
 /* Library version string. */
 const char* tvbx_version(void);
@@ -242,6 +255,28 @@ tvbx_status tvbx_state(const tvbx_sweep* h, int32_t mem, float* out);
  * window; TVBX_E_UNSUPPORTED for an unknown precision. */
 tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* fc_out,
                     float* fcd_out, int32_t* n_windows);
+
+/* Pearson FC (Eq. 6), FCD, synchrony index chi and mean off-diagonal FC of
+ * series that are not the output of a sweep (the FC stage on its own).
+ * series: DEVICE pointer, [n_samples][n_regions][n_sets] FP32 (sets
+ * fastest, the layout tvbx_series exports with mem = TVBX_MEM_DEVICE),
+ * read-only. Outputs are DEVICE pointers owned by the caller, each nullable:
+ * fc_out [n_sets][n_regions][n_regions], fcd_out [n_sets][W][W] with
+ * W = (n_samples - fcd_window) / fcd_step + 1 (written to *n_windows when
+ * non-NULL), chi and mean_fc [n_sets], set_status [n_sets] (OR-ed with
+ * TVBX_SET_ZERO_VAR; not cleared). The shift of each row is the mean of up to
+ * 64 evenly spaced samples. Scratch of n_sets x blocks x (n_regions^2 +
+ * n_regions) floats (blocks = 1 without FCD, else ceil(n_samples /
+ * fcd_step)) is allocated stream-ordered on cuda_stream (NULL = the legacy
+ * default stream) and freed before return. The call synchronises
+ * cuda_stream before it returns.
+ * Errors: TVBX_E_INVALID_ARG (NULL series, sizes < 1, bad window, a
+ * tensor-core precision with n_regions > 128), TVBX_E_OOM, TVBX_E_CUDA,
+ * TVBX_E_TIMEOUT (a bounded wait of the tensor-core kernel expired; the
+ * outputs are then invalid), TVBX_E_UNSUPPORTED (unknown precision). */
+tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
+                           const tvbx_fc_cfg* cfg, float* fc_out, float* fcd_out, int32_t* n_windows,
+                           float* chi, float* mean_fc, uint32_t* set_status, void* cuda_stream);
 
 /* The transfer function of one population (Sec. "Transfer Function", Eq. 5
  * with Table 1) and its derivatives, evaluated on the GPU at n points, with

@@ -313,7 +313,7 @@ tvbx_status check_device_error(tvbx_sweep* h)
     CK(cudaMemcpyAsync(&err, h->d_error.ptr, sizeof err, cudaMemcpyDeviceToHost, h->stream), "error word");
     CK(cudaStreamSynchronize(h->stream), "synchronize");
     if (err & TVBX_DEVERR_TIMEOUT)
-        return fail(TVBX_E_TIMEOUT, "a device-side wait of the simulation kernel gave up; results are invalid");
+        return fail(TVBX_E_TIMEOUT, "a bounded device-side wait (simulation or FC kernel) gave up; results are invalid");
     return TVBX_OK;
 }
 
@@ -690,7 +690,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     return TVBX_OK;
 }
 
-static tvbx_status run_fc(tvbx_sweep* h, int32_t fcd_window, int32_t fcd_step, int32_t* nw_out)
+static tvbx_status run_fc(tvbx_sweep* h, int32_t precision, int32_t fcd_window, int32_t fcd_step, int32_t* nw_out)
 {
     const int N = h->N;
     const int64_t P = h->P;
@@ -728,7 +728,14 @@ static tvbx_status run_fc(tvbx_sweep* h, int32_t fcd_window, int32_t fcd_step, i
     f.chi = h->d_chi.as<float>();
     f.mean_fc = h->d_meanfc.as<float>();
     f.status = h->d_status.as<uint32_t>();
-    CK(launch_fc(f, h->stream), "FC");
+    f.error = h->d_error.as<uint32_t>();
+    f.wait_limit = 1u << 22;
+    if (precision == TVBX_FC_FP32) {
+        CK(launch_fc(f, h->stream), "FC");
+    } else {
+        CK(launch_fc_tc_moments(f, precision, h->stream), "FC tensor-core moments");
+        CK(launch_fc_finalize(f, h->stream), "FC finalize");
+    }
     if (fcd_window > 0) {
         const size_t M = (size_t)N * (N - 1) / 2;
         CK(h->d_vec.ensure(sizeof(float) * (size_t)P * nw * M), "FCD vectors");
@@ -749,11 +756,15 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
     if (check_mem(mem)) return TVBX_E_INVALID_ARG;
     if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_fc before tvbx_run");
     if (tvbx_status e = check_device_error(h)) return e;
-    if (cfg->precision != TVBX_FC_FP32) return fail(TVBX_E_UNSUPPORTED, "FC precision %d", cfg->precision);
+    if (cfg->precision < TVBX_FC_FP32 || cfg->precision > TVBX_FC_TF32X3)
+        return fail(TVBX_E_UNSUPPORTED, "FC precision %d", cfg->precision);
+    if (cfg->precision != TVBX_FC_FP32 && !fc_tc_supported(h->N, cfg->precision))
+        return fail(TVBX_E_INVALID_ARG, "tensor-core FC needs n_regions <= 128 (have %d)", h->N);
     if (cfg->fcd_window < 0) return fail(TVBX_E_INVALID_ARG, "fcd_window must be >= 0");
     int32_t nw = 0;
-    tvbx_status st = run_fc(h, cfg->fcd_window, cfg->fcd_step, &nw);
+    tvbx_status st = run_fc(h, cfg->precision, cfg->fcd_window, cfg->fcd_step, &nw);
     if (st != TVBX_OK) return st;
+    if (cfg->precision != TVBX_FC_FP32 && (st = check_device_error(h)) != TVBX_OK) return st;
     if (n_windows) *n_windows = nw;
     if (fc_out) {
         st = export_rows(h, h->d_fc.as<float>(), (int64_t)h->N * h->N, mem, fc_out);
@@ -767,6 +778,104 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
     return TVBX_OK;
 }
 
+tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
+                           const tvbx_fc_cfg* cfg, float* fc_out, float* fcd_out, int32_t* n_windows, float* chi,
+                           float* mean_fc, uint32_t* set_status, void* cuda_stream)
+{
+    if (!series || !cfg) return fail(TVBX_E_INVALID_ARG, "NULL series or cfg");
+    const int N = n_regions;
+    const int64_t P = n_sets, Tn = n_samples;
+    if (N < 1 || P < 1 || Tn < 1) return fail(TVBX_E_INVALID_ARG, "sizes must be >= 1");
+    if (P > (int64_t)INT32_MAX) return fail(TVBX_E_INVALID_ARG, "n_sets must be < 2^31");
+    if (cfg->precision < TVBX_FC_FP32 || cfg->precision > TVBX_FC_TF32X3)
+        return fail(TVBX_E_UNSUPPORTED, "FC precision %d", cfg->precision);
+    if (cfg->precision != TVBX_FC_FP32 && !fc_tc_supported(N, cfg->precision))
+        return fail(TVBX_E_INVALID_ARG, "tensor-core FC needs n_regions <= 128 (have %d)", N);
+    if (cfg->precision == TVBX_FC_FP32 && N > 384) return fail(TVBX_E_INVALID_ARG, "FC needs n_regions <= 384");
+    int32_t blk = 0, n_blocks = 1, m = 0, nw = 0;
+    if (cfg->fcd_window < 0) return fail(TVBX_E_INVALID_ARG, "fcd_window must be >= 0");
+    if (cfg->fcd_window > 0) {
+        if (cfg->fcd_step < 1 || cfg->fcd_window % cfg->fcd_step != 0)
+            return fail(TVBX_E_INVALID_ARG, "fcd_window must be a positive multiple of fcd_step");
+        if (cfg->fcd_window > Tn) return fail(TVBX_E_INVALID_ARG, "fcd_window exceeds n_samples");
+        if (N < 3) return fail(TVBX_E_INVALID_ARG, "FCD needs at least 3 regions");
+        blk = cfg->fcd_step;
+        n_blocks = (int32_t)((Tn + blk - 1) / blk);
+        m = cfg->fcd_window / cfg->fcd_step;
+        nw = (int32_t)((Tn - cfg->fcd_window) / cfg->fcd_step + 1);
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t stride_b = (size_t)N * N + N;
+    const size_t M = (size_t)N * (N - 1) / 2;
+    const size_t sz_blocks = sizeof(float) * (size_t)P * n_blocks * stride_b;
+    const size_t sz_shift = sizeof(float) * (size_t)N * P;
+    const size_t sz_fc = fc_out ? 0 : sizeof(float) * (size_t)P * N * N;
+    const size_t sz_small = sizeof(float) * (size_t)P * 3 + 256;
+    const size_t sz_vec = nw > 0 ? sizeof(float) * (size_t)P * nw * M : 0;
+    const size_t sz_fcd = (nw > 0 && !fcd_out) ? sizeof(float) * (size_t)P * nw * nw : 0;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t total = up(sz_blocks) + up(sz_shift) + up(sz_fc) + up(sz_small) + up(sz_vec) + up(sz_fcd);
+    void* scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, total, s), "FC scratch");
+    char* q = static_cast<char*>(scratch);
+    auto take = [&](size_t b) { char* r = q; q += up(b); return r; };
+    float* d_blocks = reinterpret_cast<float*>(take(sz_blocks));
+    float* d_shift = reinterpret_cast<float*>(take(sz_shift));
+    float* d_fc = fc_out ? fc_out : reinterpret_cast<float*>(take(sz_fc));
+    char* small = take(sz_small);
+    float* d_chi = chi ? chi : reinterpret_cast<float*>(small);
+    float* d_mfc = mean_fc ? mean_fc : reinterpret_cast<float*>(small) + P;
+    uint32_t* d_status = set_status ? set_status : reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(small) + 2 * P);
+    uint32_t* d_err = reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(small) + 3 * P);
+    float* d_vec = nw > 0 ? reinterpret_cast<float*>(take(sz_vec)) : nullptr;
+    float* d_fcd = nw > 0 ? (fcd_out ? fcd_out : reinterpret_cast<float*>(take(sz_fcd))) : nullptr;
+
+    tvbx_status st = TVBX_OK;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMemsetAsync(small, 0, sz_small, s)) != cudaSuccess) break;
+        if ((e = launch_fc_shift(series, N, P, 0, Tn, d_shift, s)) != cudaSuccess) break;
+        FcArgs f;
+        memset(&f, 0, sizeof f);
+        f.series = series;
+        f.state = nullptr;
+        f.shift = d_shift;
+        f.N = N;
+        f.P = (int32_t)P;
+        f.t_begin = 0;
+        f.t_end = Tn;
+        f.blk = blk;
+        f.n_blocks = n_blocks;
+        f.blocks = d_blocks;
+        f.fc = d_fc;
+        f.chi = d_chi;
+        f.mean_fc = d_mfc;
+        f.status = d_status;
+        f.error = d_err;
+        f.wait_limit = 1u << 22;
+        if (cfg->precision == TVBX_FC_FP32) {
+            if ((e = launch_fc(f, s)) != cudaSuccess) break;
+        } else {
+            if ((e = launch_fc_tc_moments(f, cfg->precision, s)) != cudaSuccess) break;
+            if ((e = launch_fc_finalize(f, s)) != cudaSuccess) break;
+        }
+        if (nw > 0 && (e = launch_fcd(d_blocks, (int32_t)P, N, n_blocks, m, nw, cfg->fcd_window, d_vec, d_fcd, s)) !=
+                          cudaSuccess)
+            break;
+    } while (0);
+    uint32_t err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof err, cudaMemcpyDeviceToHost, s);
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    cudaError_t es = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "FC of series");
+    else if (ef != cudaSuccess) st = cuda_fail(ef, "FC scratch free");
+    else if (es != cudaSuccess) st = cuda_fail(es, "synchronize");
+    else if (err & TVBX_DEVERR_TIMEOUT)
+        st = fail(TVBX_E_TIMEOUT, "a bounded device-side wait of the FC kernel gave up; results are invalid");
+    if (st == TVBX_OK && n_windows) *n_windows = nw;
+    return st;
+}
+
 tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* mean_i_hz, float* chi,
                          float* mean_fc, uint32_t* status)
 {
@@ -776,7 +885,7 @@ tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* me
     if (tvbx_status e = check_device_error(h)) return e;
     const int64_t P = h->P;
     if ((chi || mean_fc || status) && !h->fc_valid) {
-        tvbx_status st = run_fc(h, 0, 0, nullptr);
+        tvbx_status st = run_fc(h, TVBX_FC_FP32, 0, 0, nullptr);
         if (st != TVBX_OK) return st;
     }
     tvbx_status st = TVBX_OK;

@@ -6,8 +6,8 @@
 // form block moments over the samples [t_begin, t_end):
 //   G_b[k][j] = sum_{t in block b} (x_k(t) - m_k)(x_j(t) - m_j),
 //   s_b[k]    = sum_{t in block b} (x_k(t) - m_k),
-// with the shift m_k = the running mean kept by the simulation (any shift is
-// exact; a close one avoids cancellation). The covariance over a union of
+// with the shift m_k = the running mean kept by the simulation, or a given
+// shift (any shift is exact; a close one avoids cancellation). The covariance over a union of
 // blocks of length L is sum G_b - (sum s_b)(sum s_b)^T / L.
 
 #include <cuda_runtime.h>
@@ -41,7 +41,8 @@ fc_moments_kernel(const __grid_constant__ FcArgs a, int32_t Npad, int32_t Tt, in
         float mval = 0.0f;
         if (q < nsets && Tn > 0) {
             const int64_t p = p0 + q;
-            mval = a.state[(int64_t)SV_SUM_E * N * a.P + (int64_t)k * a.P + p] / (float)Tn;
+            if (a.state) mval = a.state[(int64_t)SV_SUM_E * N * a.P + (int64_t)k * a.P + p] / (float)Tn;
+            else if (a.shift) mval = a.shift[(int64_t)k * a.P + p];
         }
         shift[q * N + k] = mval;
     }
@@ -332,11 +333,45 @@ cudaError_t launch_fc(const FcArgs& a, cudaStream_t s)
     fc_moments_kernel<<<grid, FC_THREADS, smem, s>>>(a, Npad, Tt, tasks_per_set, per_chunk);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    return launch_fc_finalize(a, s);
+}
+
+cudaError_t launch_fc_finalize(const FcArgs& a, cudaStream_t s)
+{
+    cudaError_t e;
     const size_t smem2 = sizeof(float) * ((size_t)a.N * a.N + a.N + 64);
     e = cudaFuncSetAttribute(fc_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
     note_launch();
     fc_finalize_kernel<<<a.P, 512, smem2, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Shift of each (region, set): mean of up to 64 evenly spaced samples of
+// [t_begin, t_end). Any shift gives the same moments in exact arithmetic; one
+// within a few standard deviations of the mean keeps the low-precision
+// operands of the tensor-core path small relative to the fluctuations.
+__global__ void fc_shift_kernel(const float* __restrict__ series, int32_t N, int64_t P, int64_t t_begin,
+                                int64_t t_end, float* __restrict__ shift)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * P) return;
+    const int64_t Tn = t_end - t_begin;
+    const int64_t n = Tn < 64 ? Tn : 64;
+    float s = 0.0f;
+    for (int64_t q = 0; q < n; ++q) {
+        const int64_t t = t_begin + (q * Tn) / n;
+        s += series[t * N * P + i];
+    }
+    shift[i] = n > 0 ? s / (float)n : 0.0f;
+}
+
+cudaError_t launch_fc_shift(const float* series, int32_t N, int64_t P, int64_t t_begin, int64_t t_end,
+                            float* shift, cudaStream_t s)
+{
+    const int64_t n = (int64_t)N * P;
+    note_launch();
+    fc_shift_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(series, N, P, t_begin, t_end, shift);
     return cudaGetLastError();
 }
 

@@ -128,8 +128,21 @@ struct FcArgs {
     float* chi;                // [P]
     float* mean_fc;            // [P]
     uint32_t* status;          // [P]
+    const float* shift;        // [N][P] shift m_k when state is NULL (nullable: 0)
+    uint32_t* error;           // device error word (tensor-core path)
+    uint32_t wait_limit;       // try_wait attempts before a wait gives up
 };
+// Block moments (SIMT, FP32) followed by the finalize kernel.
 cudaError_t launch_fc(const FcArgs& a, cudaStream_t s);
+// Tensor-core block moments (precision TVBX_FC_BF16 .. TVBX_FC_TF32X3);
+// N <= 128.
+cudaError_t launch_fc_tc_moments(const FcArgs& a, int prec, cudaStream_t s);
+bool fc_tc_supported(int N, int prec);
+// Pearson FC, chi and mean FC from the block moments.
+cudaError_t launch_fc_finalize(const FcArgs& a, cudaStream_t s);
+// Shift m_k = mean of up to 64 evenly spaced samples (standalone series).
+cudaError_t launch_fc_shift(const float* series, int32_t N, int64_t P, int64_t t_begin, int64_t t_end,
+                            float* shift, cudaStream_t s);
 cudaError_t launch_fcd(const float* blocks, int32_t P, int32_t N, int32_t n_blocks,
                        int32_t blocks_per_window, int32_t n_windows, int64_t window_samples,
                        float* vec_scratch, float* fcd, cudaStream_t s);

@@ -20,6 +20,11 @@ N_AXES = len(AXES)
 MEM_HOST, MEM_DEVICE = 0, 1
 SET_NONFINITE, SET_CLAMP_HI, SET_CLAMP_LO, SET_ZERO_VAR, SET_DIVERGED = 1, 2, 4, 8, 16
 FC_FP32 = 0
+FC_BF16 = 1
+FC_BF16X3 = 2
+FC_TF32 = 3
+FC_TF32X3 = 4
+FC_NAMES = {FC_FP32: "fp32", FC_BF16: "bf16", FC_BF16X3: "bf16x3", FC_TF32: "tf32", FC_TF32X3: "tf32x3"}
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NUMERIC", -5: "TIMEOUT",
                 -6: "BAD_STATE", -7: "UNSUPPORTED"}
 STATE_VARS = ("E", "I", "C_ee", "C_ei", "C_ii", "W_e", "W_i", "OU")
@@ -75,7 +80,7 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_sweep_create_points", "tvbx_sweep_info", "tvbx_run", "tvbx_summary", "tvbx_series",
            "tvbx_series_range", "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_last_kernel",
            "tvbx_launch_count",
-           "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_fc_noalloc",
+           "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_fc_noalloc", "tvbx_fc_series",
            "tvbx_sweep_destroy")
 
 
@@ -113,6 +118,8 @@ def load(build_if_missing: bool = False):
     L.tvbx_launch_count.restype = ctypes.c_uint64
     L.tvbx_last_kernel.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.tvbx_fc_noalloc.argtypes = [fp, i32, i64, i64, fp, fp, fp, vp]
+    L.tvbx_fc_series.argtypes = [fp, i32, i64, i64, ctypes.POINTER(FcCfg), fp, fp, ctypes.POINTER(i32), fp, fp, fp,
+                                 vp]
     L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.tvbx_profile_enable.argtypes = [vp, i32]
     L.tvbx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -296,6 +303,30 @@ def fc_noalloc(series, n_regions: int, n_sets: int, n_samples: int, fc_out, chi=
                                   sp), "tvbx_fc_noalloc")
 
 
+def fc_series(series, n_regions: int, n_sets: int, n_samples: int, precision=FC_FP32, fc_out=None, fcd_out=None,
+              fcd_window=0, fcd_step=0, chi=None, mean_fc=None, set_status=None, stream=None) -> int:
+    """FC / FCD / chi / mean FC of device series [n_samples][n_regions][n_sets]
+    (tvbx_fc_series). Every buffer is a CUDA tensor; returns the number of FCD
+    windows. Synchronises the stream."""
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    args = []
+    for x in (series, fc_out, fcd_out, chi, mean_fc, set_status):
+        if x is None:
+            args.append(None)
+        else:
+            ptr, mem = _out_ptr(x)
+            if mem != MEM_DEVICE:
+                raise ValueError("tvbx_fc_series takes device buffers only")
+            args.append(ptr)
+    cfg = FcCfg(int(precision), int(fcd_window), int(fcd_step))
+    nw = ctypes.c_int32(0)
+    _check(load().tvbx_fc_series(args[0], int(n_regions), int(n_sets), int(n_samples), ctypes.byref(cfg), args[1],
+                                 args[2], ctypes.byref(nw), args[3], args[4], args[5], sp), "tvbx_fc_series")
+    return nw.value
+
+
 def transfer_function(pop: int, x_e, x_i, W, E_L, C=None, model: Model | None = None) -> np.ndarray:
     """[n][8] = F, F_e, F_i, F_ee, F_ei, F_ii, mu_V, sum_ij C_ij F_ij (the
     integrator's contracted term, 0 without C) from the device code."""
@@ -360,17 +391,17 @@ class Sweep:
         state(self.h, x)
         return x
 
-    def fc(self, fcd_window=0, fcd_step=0):
+    def fc(self, fcd_window=0, fcd_step=0, precision=FC_FP32):
         P, N = self.n_sets, self.n_regions
         out = np.zeros((P, N, N), dtype=np.float32)
         if fcd_window > 0:
             T = self.n_samples - getattr(self, "_transient", 0)
             nw = (T - fcd_window) // fcd_step + 1 if fcd_step > 0 and T >= fcd_window else 1
             fcd_out = np.zeros((P, nw, nw), dtype=np.float32)
-            got = fc(self.h, out, fcd_out, fcd_window, fcd_step)
+            got = fc(self.h, out, fcd_out, fcd_window, fcd_step, precision=precision)
             assert got == nw
             return out, fcd_out
-        fc(self.h, out)
+        fc(self.h, out, precision=precision)
         return out
 
     def close(self):
