@@ -7,6 +7,12 @@ FC, FCD (1,000-sample windows, 500-sample step) and the per-set summary.
 
 Prints one JSON line (rank 0). Metric: region-steps/s, whole job.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+                  [--fc-precision fp32|bf16|bf16x3|tf32|tf32x3]
+The FC of the step runs in --fc-precision (default bf16x3, tensor cores); the
+line states its largest error against the FP64 Pearson FC of the same series.
+  python bench.py --workload fc ...
+times the FC stage alone (32,768 series of 68 x 5,000 samples: FC, FCD,
+chi, mean FC) and reports time and FP64 error of every precision form.
 Under torchrun each rank integrates its own 32,768-set slice of an
 N x 32,768-set sweep (tau_w_e resolution 8N): weak scaling, no collective on
 the data path; a barrier and a max-reduce of the elapsed time only.
@@ -137,6 +143,18 @@ def measured_peaks():
         return None
 
 
+def fp64_pearson(x):
+    """Pearson correlation of the rows of x [N][T] in FP64 (unit diagonal,
+    zero rows and columns for constant rows)."""
+    xc = x - x.mean(axis=-1, keepdims=True)
+    c = xc @ xc.T
+    d = np.sqrt(np.diag(c))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(np.outer(d, d) > 0, c / np.outer(d, d), 0.0)
+    np.fill_diagonal(r, 1.0)
+    return r
+
+
 # ---------------------------------------------------------------------------
 def cpu_baseline(target_seconds=15.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
@@ -233,10 +251,12 @@ def run_engine(args):
     summ = {k: torch.empty(P, dtype=torch.float32, device=dev) for k in ("e", "i", "chi", "mfc")}
     status = torch.empty(P, dtype=torch.int32, device=dev)
 
+    fc_prec = getattr(tvbx, "FC_" + args.fc_precision.upper())
+
     def step():
         tvbx.run(sw.h, dt_ms=cfg["dt"], n_steps=S, tavg_steps=ts, seed=cfg["seed"], p_offset=rank * P,
                  stream=stream)
-        tvbx.fc(sw.h, fc_dev, fcd_dev, FCD_WINDOW, FCD_STEP)
+        tvbx.fc(sw.h, fc_dev, fcd_dev, FCD_WINDOW, FCD_STEP, precision=fc_prec)
         tvbx.summary(sw.h, summ["e"], summ["i"], summ["chi"], summ["mfc"], status)
 
     def barrier():
@@ -287,7 +307,7 @@ def run_engine(args):
             nonlocal h2d, d2h
             h = tvbx.sweep_create_points(pin_W, pin_L, pin_pts)
             tvbx.run(h, dt_ms=cfg["dt"], n_steps=S, tavg_steps=ts, seed=cfg["seed"], p_offset=rank * P)
-            tvbx.fc(h, host_fc, host_fcd, FCD_WINDOW, FCD_STEP)
+            tvbx.fc(h, host_fc, host_fcd, FCD_WINDOW, FCD_STEP, precision=fc_prec)
             tvbx.summary(h, *host_s, host_st)
             a, b = tvbx.transfer_bytes(h)
             h2d, d2h = a + W.nbytes + L.nbytes + pts.nbytes, b
@@ -304,6 +324,20 @@ def run_engine(args):
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": k_e2e * region_steps * world / float(te.item()), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    fc_err = None
+    if rank == 0:
+        # FC error of the timed path against the FP64 Pearson FC of the same
+        # series, on 16 evenly spaced sets
+        fc_host = fc_dev.cpu().numpy()
+        errs = []
+        for s_ in np.linspace(0, P - 1, 16).astype(int):
+            x = sw.series_window(int(s_), 1)[0].astype(np.float64)
+            if not np.all(np.isfinite(x)):
+                continue
+            errs.append(float(np.abs(fc_host[s_] - fp64_pearson(x)).max()))
+        fc_err = {"precision": args.fc_precision, "max_abs_err_vs_fp64": max(errs) if errs else None,
+                  "sets_checked": len(errs)}
 
     if rank == 0:
         peaks = measured_peaks()
@@ -332,9 +366,225 @@ def run_engine(args):
                            "parallelism": f"dp{world} (set slices, no collective)",
                            "l2": "inputs larger than L2 (ring 4.3 GB, series 44.6 GB per GPU)"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-                "cpu_baseline": base}
+                "fc": fc_err, "cpu_baseline": base}
         print(json.dumps(line), flush=True)
     sw.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# The FC stage alone: 32,768 series of 68 regions x 5,000 samples (the
+# paper-scale sweep's output), Pearson FC + FCD (1,000/500) + chi + mean FC.
+FC_P, FC_N, FC_T = 32768, 68, 5000
+FC_METRIC = "FC region-samples/s on 1 GB300 (at stated FC error vs FP64)"
+FC_UNIT = "region-samples/s"
+
+
+def fc_series_on_device(torch, dev, P, N, T, seed):
+    """Rate-like synthetic series [T][N][P] (kHz): 5 Hz mean, 0.1 Hz
+    fluctuations mixed with a per-set common mode (correlations of about
+    0.2), and a start-up ramp decaying over 50 samples."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    X = torch.empty((T, N, P), dtype=torch.float32, device=dev)
+    ramp_scale = torch.linspace(0.5, 1.5, N, device=dev).view(1, N, 1)
+    for t0 in range(0, T, 250):
+        t1 = min(T, t0 + 250)
+        z = torch.randn((t1 - t0, N, P), generator=g, device=dev)
+        common = torch.randn((t1 - t0, 1, P), generator=g, device=dev)
+        tt = torch.arange(t0, t1, device=dev, dtype=torch.float32).view(-1, 1, 1)
+        X[t0:t1] = 5e-3 + 1e-4 * (z + 0.5 * common) + 4e-3 * torch.exp(-tt / 50.0) * ramp_scale
+        del z, common
+    return X
+
+
+def fp64_fcd(x, window, step):
+    """FCD of one set's series x [N][T] in FP64: Pearson correlation between
+    the upper triangles of the window FCs."""
+    T = x.shape[-1]
+    iu = np.triu_indices(x.shape[0], k=1)
+    vecs = np.stack([fp64_pearson(x[:, s:s + window])[iu] for s in range(0, T - window + 1, step)])
+    return fp64_pearson(vecs)
+
+
+def fc_cpu_baseline(target_seconds=15.0, series=None):
+    """The oracle's FP64 FC + FCD + chi on a bounded sample of sets."""
+    from oracle import oracle as O
+    rng = np.random.Generator(np.random.PCG64(7))
+    x = series if series is not None else 5e-3 + 1e-4 * rng.standard_normal((64, FC_N, FC_T))
+    t0 = time.time()
+    O.fc_pearson(x[:4]); O.fcd(x[:4], 1000, 500); O.chi(x[:4])
+    per = (time.time() - t0) / 4
+    n = int(max(4, min(x.shape[0], target_seconds / max(per, 1e-9))))
+    reps = max(1, int(target_seconds / max(per * x.shape[0], 1e-9))) if n >= x.shape[0] else 1
+    t0 = time.time()
+    done = 0
+    for _ in range(reps):
+        O.fc_pearson(x[:n]); O.fcd(x[:n], 1000, 500); O.chi(x[:n])
+        done += n
+    el = time.time() - t0
+    return {"value": done * FC_N * FC_T / el, "unit": FC_UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} series of 68 x 5000 (FP64 numpy FC, FCD 1000/500, chi); {el:.1f} s"}
+
+
+def run_fc_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    rng = np.random.Generator(np.random.PCG64(7))
+    x = 5e-3 + 1e-4 * rng.standard_normal((16, FC_N, FC_T))
+
+    def one():
+        O.fc_pearson(x); O.fcd(x, 1000, 500); O.chi(x)
+    for _ in range(args.warmup):
+        one()
+    t0 = time.time()
+    for _ in range(args.steps):
+        one()
+    el = time.time() - t0
+    value = args.steps * x.shape[0] * FC_N * FC_T / el
+    line = {"impl": "reference", "metric": FC_METRIC, "value": value, "unit": FC_UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "FC stage, bounded sample of 16 series on host cores (FP64 oracle)",
+                       "n_sets": 16, "n_regions": FC_N, "n_samples": FC_T},
+            "cpu_baseline": {"value": value, "unit": FC_UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"16 series of 68 x 5000, {args.steps} timed steps"},
+            "e2e": {"value": value, "unit": FC_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fc_engine(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2311_13337_gb300 import tvbx
+
+    P, N, T = FC_P, FC_N, FC_T
+    X = fc_series_on_device(torch, dev, P, N, T, seed=1000 + rank)
+    nw = (T - FCD_WINDOW) // FCD_STEP + 1
+    fc = torch.empty((P, N, N), dtype=torch.float32, device=dev)
+    fcd = torch.empty((P, nw, nw), dtype=torch.float32, device=dev)
+    chi = torch.empty(P, dtype=torch.float32, device=dev)
+    mfc = torch.empty(P, dtype=torch.float32, device=dev)
+    st = torch.zeros(P, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    prec = getattr(tvbx, "FC_" + args.fc_precision.upper())
+
+    def step(pr=prec):
+        tvbx.fc_series(X, N, P, T, precision=pr, fc_out=fc, fcd_out=fcd, fcd_window=FCD_WINDOW,
+                       fcd_step=FCD_STEP, chi=chi, mean_fc=mfc, set_status=st, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # error of every precision form against FP64 on 32 sampled sets
+    sample = np.linspace(0, P - 1, 32).astype(int)
+    xs = X[:, :, torch.as_tensor(sample, device=dev)].permute(2, 1, 0).double().cpu().numpy()
+    ref_fc = [fp64_pearson(x) for x in xs]
+    ref_fcd = [fp64_fcd(x, FCD_WINDOW, FCD_STEP) for x in xs]
+    forms = {}
+    for name in ("fp32", "bf16", "bf16x3", "tf32", "tf32x3"):
+        pr = getattr(tvbx, "FC_" + name.upper())
+        step(pr)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        step(pr)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        f, d = fc.cpu().numpy(), fcd.cpu().numpy()
+        forms[name] = {"ms": ev[0].elapsed_time(ev[1]),
+                       "fc_max_abs_err": float(max(np.abs(f[s_] - r).max() for s_, r in zip(sample, ref_fc))),
+                       "fcd_max_abs_err": float(max(np.abs(d[s_] - r).max() for s_, r in zip(sample, ref_fcd)))}
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    launches0 = tvbx.launch_count()
+    sampler = start_clock_sampler(local) if rank == 0 else None
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    barrier()
+    clocks = stop_clock_sampler(sampler)
+    launches = tvbx.launch_count() - launches0
+    dev_ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([el], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    el_max = float(t.item())
+    units = float(P) * N * T
+    value = args.steps * units * world / el_max
+
+    # end to end: series from pinned host memory, FC / chi / mean FC back to host
+    pin_X = torch.empty((T, N, P), dtype=torch.float32).pin_memory()
+    pin_X.copy_(X)
+    host_fc = torch.empty((P, N, N), dtype=torch.float32).pin_memory()
+    host_s = [torch.empty(P, dtype=torch.float32).pin_memory() for _ in range(2)]
+    k_e2e = max(1, min(args.steps, 2))
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            X.copy_(pin_X, non_blocking=True)
+            step()
+            host_fc.copy_(fc, non_blocking=True)
+            host_s[0].copy_(chi, non_blocking=True)
+            host_s[1].copy_(mfc, non_blocking=True)
+        stream.synchronize()
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    el_e = time.perf_counter() - t0
+    barrier()
+    e2e = {"value": k_e2e * units * world / el_e, "unit": FC_UNIT, "h2d_bytes_per_step": int(X.numel() * 4),
+           "d2h_bytes_per_step": int((fc.numel() + 2 * P) * 4)}
+
+    if rank == 0:
+        peaks = measured_peaks()
+        peak = peaks.get("hbm_gbs") if peaks else 6800.0
+        alg_bytes = 4.0 * units + 4.0 * P * (N * N + nw * nw + 2)
+        achieved = alg_bytes / (dev_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": "fc_tc_kernel (" + args.fc_precision + ")",
+                    "peak_source": "measured" if peaks else "fallback",
+                    "timed": "whole FC stage per step (shift, tensor-core moments, finalize, FCD), CUDA events",
+                    "algorithmic_bytes_per_step": alg_bytes, "avg_step_device_ms": dev_ms}
+        base = fc_cpu_baseline(series=xs) if not args.no_cpu_baseline else None
+        line = {"metric": FC_METRIC, "value": value, "unit": FC_UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * el_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.fc_precision, "data": "synthetic",
+                "config": {"workload": "FC stage: 32768 series of 68 regions x 5000 samples per GPU, Pearson FC "
+                                       "+ FCD (1000/500) + chi + mean FC",
+                           "n_sets_per_gpu": P, "n_regions": N, "n_samples": T, "fc_precision": args.fc_precision,
+                           "parallelism": f"dp{world} (set slices, no collective)",
+                           "l2": "inputs larger than L2 (series 44.6 GB per GPU)"},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+                "fc_forms": forms, "cpu_baseline": base}
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -347,7 +597,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["sweep", "fc"], default="sweep",
+                    help="sweep: the paper-scale sweep (default); fc: the FC stage alone on 32,768 "
+                         "series of 68 regions x 5,000 samples")
+    ap.add_argument("--fc-precision", choices=["fp32", "bf16", "bf16x3", "tf32", "tf32x3"], default="bf16x3")
     args = ap.parse_args()
+    if args.workload == "fc":
+        return run_fc_reference(args) if args.impl == "reference" else run_fc_engine(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_engine(args)

@@ -342,6 +342,37 @@ def transfer_function(pop: int, x_e, x_i, W, E_L, C=None, model: Model | None = 
     return out
 
 
+KERNEL_NAMES = {KERNEL_GENERAL: "sim_chunk_kernel"}
+KERNEL_NAMES.update({KERNEL_PREFETCH + v: ("sim_bulk_kernel" if v in (4, 5) else "sim_fast_kernel") + f" (variant {v})"
+                     for v in range(N_PREFETCH_VARIANTS)})
+
+
+def last_kernel(h) -> tuple[int, int]:
+    k, pb = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().tvbx_last_kernel(h, ctypes.byref(k), ctypes.byref(pb)), "tvbx_last_kernel")
+    return k.value, pb.value
+
+
+def launch_count() -> int:
+    return int(load().tvbx_launch_count())
+
+
+def transfer_bytes(h) -> tuple[int, int]:
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().tvbx_transfer_bytes(h, ctypes.byref(a), ctypes.byref(b)), "tvbx_transfer_bytes")
+    return a.value, b.value
+
+
+def profile_enable(h, enable: bool = True):
+    _check(load().tvbx_profile_enable(h, int(bool(enable))), "tvbx_profile_enable")
+
+
+def profile_read(h) -> tuple[float, int, float]:
+    ms, n, rs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    _check(load().tvbx_profile_read(h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(rs)), "tvbx_profile_read")
+    return ms.value, n.value, rs.value
+
+
 def sweep_destroy(h):
     if h is not None and h.value:
         _check(load().tvbx_sweep_destroy(h), "tvbx_sweep_destroy")

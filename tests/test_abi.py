@@ -87,3 +87,17 @@ def test_no_cpu_fallback_without_a_device(lib):
     with pytest.raises(lib.TvbxError) as e:
         lib.transfer_function(0, [0.01], [0.01], [0.0], [-64.0])
     assert e.value.code == -3
+
+
+def test_binding_has_every_function_its_callers_use():
+    """bench.py, the entry points and the profiling scripts call the binding
+    by name; every name they use must exist (no GPU needed)."""
+    import re
+    from paper_2311_13337_gb300 import tvbx
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    files = ["bench.py", "__graft_entry__.py", os.path.join("paper_2311_13337_gb300", "profile_case.py")]
+    used = set()
+    for f in files:
+        used |= set(re.findall(r"\btvbx\.([A-Za-z_][A-Za-z_0-9]*)", open(os.path.join(root, f)).read()))
+    missing = sorted(n for n in used if not hasattr(tvbx, n))
+    assert not missing, missing
