@@ -382,24 +382,6 @@ FC_METRIC = "FC region-samples/s on 1 GB300 (at stated FC error vs FP64)"
 FC_UNIT = "region-samples/s"
 
 
-def fc_series_on_device(torch, dev, P, N, T, seed):
-    """Rate-like synthetic series [T][N][P] (kHz): 5 Hz mean, 0.1 Hz
-    fluctuations mixed with a per-set common mode (correlations of about
-    0.2), and a start-up ramp decaying over 50 samples."""
-    g = torch.Generator(device=dev)
-    g.manual_seed(seed)
-    X = torch.empty((T, N, P), dtype=torch.float32, device=dev)
-    ramp_scale = torch.linspace(0.5, 1.5, N, device=dev).view(1, N, 1)
-    for t0 in range(0, T, 250):
-        t1 = min(T, t0 + 250)
-        z = torch.randn((t1 - t0, N, P), generator=g, device=dev)
-        common = torch.randn((t1 - t0, 1, P), generator=g, device=dev)
-        tt = torch.arange(t0, t1, device=dev, dtype=torch.float32).view(-1, 1, 1)
-        X[t0:t1] = 5e-3 + 1e-4 * (z + 0.5 * common) + 4e-3 * torch.exp(-tt / 50.0) * ramp_scale
-        del z, common
-    return X
-
-
 def fp64_fcd(x, window, step):
     """FCD of one set's series x [N][T] in FP64: Pearson correlation between
     the upper triangles of the window FCs."""
@@ -474,7 +456,8 @@ def run_fc_engine(args):
     from paper_2311_13337_gb300 import tvbx
 
     P, N, T = FC_P, FC_N, FC_T
-    X = fc_series_on_device(torch, dev, P, N, T, seed=1000 + rank)
+    from paper_2311_13337_gb300 import synth
+    X = synth.rate_series_device(torch, dev, P, N, T, seed=1000 + rank)
     nw = (T - FCD_WINDOW) // FCD_STEP + 1
     fc = torch.empty((P, N, N), dtype=torch.float32, device=dev)
     fcd = torch.empty((P, nw, nw), dtype=torch.float32, device=dev)

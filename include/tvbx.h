@@ -268,8 +268,9 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
  * 64 evenly spaced samples. Scratch of n_sets x blocks x (n_regions^2 +
  * n_regions) floats (blocks = 1 without FCD, else ceil(n_samples /
  * fcd_step)) is allocated stream-ordered on cuda_stream (NULL = the legacy
- * default stream) and freed before return. The call synchronises
- * cuda_stream before it returns.
+ * default stream) from a memory pool the library owns per device, and freed
+ * into it before return; the pool keeps that memory for later calls until the
+ * process exits. The call synchronises cuda_stream before it returns.
  * Errors: TVBX_E_INVALID_ARG (NULL series, sizes < 1, bad window, a
  * tensor-core precision with n_regions > 128), TVBX_E_OOM, TVBX_E_CUDA,
  * TVBX_E_TIMEOUT (a bounded wait of the tensor-core kernel expired; the

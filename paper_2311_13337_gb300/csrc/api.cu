@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -730,20 +731,20 @@ static tvbx_status run_fc(tvbx_sweep* h, int32_t precision, int32_t fcd_window, 
     f.status = h->d_status.as<uint32_t>();
     f.error = h->d_error.as<uint32_t>();
     f.wait_limit = 1u << 22;
-    if (precision == TVBX_FC_FP32) {
-        CK(launch_fc(f, h->stream), "FC");
-    } else {
-        CK(launch_fc_tc_moments(f, precision, h->stream), "FC tensor-core moments");
-        CK(launch_fc_finalize(f, h->stream), "FC finalize");
-    }
+    if (precision == TVBX_FC_FP32) CK(launch_fc_moments(f, h->stream), "FC moments");
+    else CK(launch_fc_tc_moments(f, precision, h->stream), "FC tensor-core moments");
+    float* vec = nullptr;
+    float* fcd = nullptr;
     if (fcd_window > 0) {
         const size_t M = (size_t)N * (N - 1) / 2;
-        CK(h->d_vec.ensure(sizeof(float) * (size_t)P * nw * M), "FCD vectors");
+        if (fc_reduce_needs_vec_scratch(N, n_blocks, nw)) {
+            CK(h->d_vec.ensure(sizeof(float) * (size_t)P * nw * M), "FCD vectors");
+            vec = h->d_vec.as<float>();
+        }
         CK(h->d_fcd.ensure(sizeof(float) * (size_t)P * nw * nw), "FCD");
-        CK(launch_fcd(f.blocks, (int32_t)P, N, n_blocks, m, nw, fcd_window, h->d_vec.as<float>(), h->d_fcd.as<float>(),
-                      h->stream),
-           "FCD");
+        fcd = h->d_fcd.as<float>();
     }
+    CK(launch_fc_reduce(f, m, nw, fcd_window, vec, fcd, h->stream), "FC / FCD reduction");
     if (nw_out) *nw_out = nw;
     h->fc_valid = true;
     return TVBX_OK;
@@ -778,6 +779,38 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
     return TVBX_OK;
 }
 
+namespace {
+// Stream-ordered pool of the FC scratch of tvbx_fc_series, one per device,
+// owned by the library: it keeps freed memory for the next call instead of
+// returning it to the driver (so repeated calls do not re-map gigabytes).
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+
+cudaError_t scratch_pool(cudaMemPool_t* out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
 tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
                            const tvbx_fc_cfg* cfg, float* fc_out, float* fcd_out, int32_t* n_windows, float* chi,
                            float* mean_fc, uint32_t* set_status, void* cuda_stream)
@@ -811,12 +844,14 @@ tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_set
     const size_t sz_shift = sizeof(float) * (size_t)N * P;
     const size_t sz_fc = fc_out ? 0 : sizeof(float) * (size_t)P * N * N;
     const size_t sz_small = sizeof(float) * (size_t)P * 3 + 256;
-    const size_t sz_vec = nw > 0 ? sizeof(float) * (size_t)P * nw * M : 0;
+    const size_t sz_vec = nw > 0 && fc_reduce_needs_vec_scratch(N, n_blocks, nw) ? sizeof(float) * (size_t)P * nw * M : 0;
     const size_t sz_fcd = (nw > 0 && !fcd_out) ? sizeof(float) * (size_t)P * nw * nw : 0;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t total = up(sz_blocks) + up(sz_shift) + up(sz_fc) + up(sz_small) + up(sz_vec) + up(sz_fcd);
     void* scratch = nullptr;
-    CK(cudaMallocAsync(&scratch, total, s), "FC scratch");
+    cudaMemPool_t pool;
+    CK(scratch_pool(&pool), "FC scratch pool");
+    CK(cudaMallocFromPoolAsync(&scratch, total, pool, s), "FC scratch");
     char* q = static_cast<char*>(scratch);
     auto take = [&](size_t b) { char* r = q; q += up(b); return r; };
     float* d_blocks = reinterpret_cast<float*>(take(sz_blocks));
@@ -827,7 +862,7 @@ tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_set
     float* d_mfc = mean_fc ? mean_fc : reinterpret_cast<float*>(small) + P;
     uint32_t* d_status = set_status ? set_status : reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(small) + 2 * P);
     uint32_t* d_err = reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(small) + 3 * P);
-    float* d_vec = nw > 0 ? reinterpret_cast<float*>(take(sz_vec)) : nullptr;
+    float* d_vec = sz_vec > 0 ? reinterpret_cast<float*>(take(sz_vec)) : nullptr;
     float* d_fcd = nw > 0 ? (fcd_out ? fcd_out : reinterpret_cast<float*>(take(sz_fcd))) : nullptr;
 
     tvbx_status st = TVBX_OK;
@@ -853,15 +888,10 @@ tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_set
         f.status = d_status;
         f.error = d_err;
         f.wait_limit = 1u << 22;
-        if (cfg->precision == TVBX_FC_FP32) {
-            if ((e = launch_fc(f, s)) != cudaSuccess) break;
-        } else {
-            if ((e = launch_fc_tc_moments(f, cfg->precision, s)) != cudaSuccess) break;
-            if ((e = launch_fc_finalize(f, s)) != cudaSuccess) break;
-        }
-        if (nw > 0 && (e = launch_fcd(d_blocks, (int32_t)P, N, n_blocks, m, nw, cfg->fcd_window, d_vec, d_fcd, s)) !=
-                          cudaSuccess)
-            break;
+        if (cfg->precision == TVBX_FC_FP32) e = launch_fc_moments(f, s);
+        else e = launch_fc_tc_moments(f, cfg->precision, s);
+        if (e != cudaSuccess) break;
+        if ((e = launch_fc_reduce(f, m, nw, cfg->fcd_window, d_vec, d_fcd, s)) != cudaSuccess) break;
     } while (0);
     uint32_t err = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof err, cudaMemcpyDeviceToHost, s);

@@ -154,7 +154,7 @@ __global__ void fc_finalize_kernel(const __grid_constant__ FcArgs a)
         const int k = i / N, j = i - k * N;
         float g = 0.0f, sk = 0.0f, sj = 0.0f;
         for (int b = 0; b < a.n_blocks; ++b) {
-            g += B[b * stride_b + i];
+            g += 0.5f * (B[b * stride_b + i] + B[b * stride_b + (int64_t)j * N + k]);
             sk += B[b * stride_b + (int64_t)N * N + k];
             sj += B[b * stride_b + (int64_t)N * N + j];
         }
@@ -237,7 +237,7 @@ __global__ void fcd_kernel(const float* __restrict__ blocks, int32_t N, int32_t 
             const int j = k + 1 + r;
             float g = 0.0f, sk = 0.0f, sj = 0.0f;
             for (int b = w; b < w + m; ++b) {
-                g += B[b * stride_b + (int64_t)k * N + j];
+                g += 0.5f * (B[b * stride_b + (int64_t)k * N + j] + B[b * stride_b + (int64_t)j * N + k]);
                 sk += B[b * stride_b + (int64_t)N * N + k];
                 sj += B[b * stride_b + (int64_t)N * N + j];
             }
@@ -313,7 +313,7 @@ __global__ void summary_kernel(const float* __restrict__ state, int32_t N, int32
     mean_i_hz[p] = si * scale;
 }
 
-cudaError_t launch_fc(const FcArgs& a, cudaStream_t s)
+cudaError_t launch_fc_moments(const FcArgs& a, cudaStream_t s)
 {
     if (a.N > 384) return cudaErrorInvalidValue;
     const int Npad = (a.N + 3) / 4 * 4;
@@ -331,9 +331,7 @@ cudaError_t launch_fc(const FcArgs& a, cudaStream_t s)
     dim3 grid((a.P + FC_SETS - 1) / FC_SETS, chunks);
     note_launch();
     fc_moments_kernel<<<grid, FC_THREADS, smem, s>>>(a, Npad, Tt, tasks_per_set, per_chunk);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_fc_finalize(a, s);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fc_finalize(const FcArgs& a, cudaStream_t s)
@@ -374,6 +372,211 @@ cudaError_t launch_fc_shift(const float* series, int32_t N, int64_t P, int64_t t
     fc_shift_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(series, N, P, t_begin, t_end, shift);
     return cudaGetLastError();
 }
+
+// Per set, from the block moments: Pearson FC over all samples, chi, mean
+// off-diagonal FC and, when nw > 0, the FCD over nw windows of m blocks
+// (Lw samples each) in one pass. One CTA per set; one warp per FC row; the
+// window FC vectors (upper triangles) stay in shared memory. MW > 0: m == MW
+// and n_blocks <= FCR_MAXB, block values in registers with compile-time
+// indices; MW == 0: any m and n_blocks, block values re-read.
+constexpr int RED_THREADS = 512;
+constexpr int FCR_MAXB = 12;
+
+template <int MW>
+__global__ void __launch_bounds__(RED_THREADS)
+fc_reduce_kernel(const __grid_constant__ FcArgs a, int32_t m, int32_t nw, int64_t Lw, float* __restrict__ fcd)
+{
+    extern __shared__ float sm[];
+    const int N = a.N, nb = a.n_blocks;
+    const int64_t p = blockIdx.x;
+    const int M = N * (N - 1) / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int64_t stride_b = (int64_t)N * N + N;
+    const float* B = a.blocks + p * nb * stride_b;
+    const int64_t Tn = a.t_end - a.t_begin;
+    float* sSf = sm;                        // [N] row sums over all blocks
+    float* isd = sSf + N;                   // [N] 1 / sd over all samples (0 if sd = 0)
+    float* cdg = isd + N;                   // [N] variance over all samples
+    float* sSw = cdg + N;                   // [nw][N] window row sums
+    float* isdw = sSw + nw * N;             // [nw][N] window 1 / sd
+    float* V = isdw + nw * N;               // [nw][M] window FC upper triangles
+    float* red = V + (size_t)nw * M;        // [48] + [nw]
+    const float invT = Tn > 0 ? 1.0f / (float)Tn : 0.0f;
+    const float invL = Lw > 0 ? 1.0f / (float)Lw : 0.0f;
+
+    for (int k = tid; k < N; k += blockDim.x) {
+        const float* sk_b = B + (int64_t)N * N + k;
+        const float* dk_b = B + (int64_t)k * N + k;
+        float g = 0.0f, sk = 0.0f;
+        for (int b = 0; b < nb; ++b) { g += dk_b[b * stride_b]; sk += sk_b[b * stride_b]; }
+        const float v = g - sk * sk * invT;
+        sSf[k] = sk;
+        cdg[k] = v;
+        isd[k] = v > 0.0f ? rsqrtf(v) : 0.0f;
+        for (int w = 0; w < nw; ++w) {
+            float gw = 0.0f, sw = 0.0f;
+            for (int b = w; b < w + m; ++b) { gw += dk_b[b * stride_b]; sw += sk_b[b * stride_b]; }
+            const float vw = gw - sw * sw * invL;
+            sSw[w * N + k] = sw;
+            isdw[w * N + k] = vw > 0.0f ? rsqrtf(vw) : 0.0f;
+        }
+    }
+    __syncthreads();
+
+    float s_all = 0.0f, s_diag = 0.0f, s_fc = 0.0f;
+    bool zero = false;
+    float* fc = a.fc ? a.fc + p * N * N : nullptr;
+    for (int k = tid; k < N; k += blockDim.x) {
+        s_all += cdg[k];
+        s_diag += cdg[k];
+        if (!(isd[k] > 0.0f)) zero = true;
+        if (fc) fc[(int64_t)k * N + k] = 1.0f;
+    }
+    for (int r = warp; r < N; r += nwarps) {
+        const float sr = sSf[r], ir = isd[r];
+        const int e0 = r * N - r * (r + 1) / 2 - r - 1;   // triangle index of (r, jj) is e0 + jj
+        const float* Br = B + (int64_t)r * N;              // row r of block 0
+        const float* Bc = B + r;                           // column r of block 0
+        for (int jj = r + 1 + lane; jj < N; jj += 32) {
+            // symmetric part of the stored block matrices at (r, jj)
+            float g = 0.0f;
+            float pre[FCR_MAXB + 1];
+            if constexpr (MW > 0) {
+                pre[0] = 0.0f;
+#pragma unroll
+                for (int b = 0; b < FCR_MAXB; ++b) {
+                    const float gb = b < nb ? 0.5f * (Br[b * stride_b + jj] + Bc[b * stride_b + (int64_t)jj * N]) : 0.0f;
+                    pre[b + 1] = pre[b] + gb;
+                }
+                g = pre[FCR_MAXB];
+            } else {
+                for (int b = 0; b < nb; ++b) g += 0.5f * (Br[b * stride_b + jj] + Bc[b * stride_b + (int64_t)jj * N]);
+            }
+            const float c = g - sr * sSf[jj] * invT;
+            const float f = c * ir * isd[jj];
+            s_all += 2.0f * c;
+            s_fc += 2.0f * f;
+            if (fc) {
+                fc[(int64_t)r * N + jj] = f;
+                fc[(int64_t)jj * N + r] = f;
+            }
+            if constexpr (MW > 0) {
+#pragma unroll
+                for (int w = 0; w + MW <= FCR_MAXB; ++w) {
+                    if (w < nw) {
+                        const float gw = pre[w + MW] - pre[w];
+                        const float cw = gw - sSw[w * N + r] * sSw[w * N + jj] * invL;
+                        V[(size_t)w * M + e0 + jj] = cw * isdw[w * N + r] * isdw[w * N + jj];
+                    }
+                }
+            } else {
+                for (int w = 0; w < nw; ++w) {
+                    float gw = 0.0f;
+                    for (int b = w; b < w + m; ++b)
+                        gw += 0.5f * (Br[b * stride_b + jj] + Bc[b * stride_b + (int64_t)jj * N]);
+                    const float cw = gw - sSw[w * N + r] * sSw[w * N + jj] * invL;
+                    V[(size_t)w * M + e0 + jj] = cw * isdw[w * N + r] * isdw[w * N + jj];
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s_all += __shfl_xor_sync(0xffffffffu, s_all, o);
+        s_diag += __shfl_xor_sync(0xffffffffu, s_diag, o);
+        s_fc += __shfl_xor_sync(0xffffffffu, s_fc, o);
+    }
+    if (lane == 0) { red[warp] = s_all; red[16 + warp] = s_diag; red[32 + warp] = s_fc; }
+    if (zero) atomicOr(a.status + p, TVBX_SET_ZERO_VAR);
+    __syncthreads();
+    if (tid == 0) {
+        float A = 0.0f, D = 0.0f, F = 0.0f;
+        for (int w = 0; w < nwarps; ++w) { A += red[w]; D += red[16 + w]; F += red[32 + w]; }
+        const float num = A / ((float)N * (float)N), den = D / (float)N;
+        a.chi[p] = den > 0.0f ? sqrtf(fmaxf(num / den, 0.0f)) : 0.0f;
+        a.mean_fc[p] = N > 1 ? F / ((float)N * (float)(N - 1)) : 0.0f;
+    }
+    if (nw == 0) return;
+
+    // FCD: centre and normalise each window vector, then all pairwise products
+    float* mom = red + 48;   // [nw] inverse norms
+    for (int w = warp; w < nw; w += nwarps) {
+        float* v = V + (size_t)w * M;
+        float sum = 0.0f;
+        for (int i = lane; i < M; i += 32) sum += v[i];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        const float mu = sum / (float)M;
+        float ss = 0.0f;
+        for (int i = lane; i < M; i += 32) {
+            const float x = v[i] - mu;
+            v[i] = x;
+            ss += x * x;
+        }
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) mom[w] = ss > 0.0f ? rsqrtf(ss) : 0.0f;
+    }
+    __syncthreads();
+    const int npair = nw * (nw + 1) / 2;
+    for (int q = warp; q < npair; q += nwarps) {
+        int u = 0, rem = q;
+        while (rem >= nw - u) { rem -= nw - u; ++u; }
+        const int v2 = u + rem;
+        float dot = 0.0f;
+        if (u != v2) {
+            const float* x = V + (size_t)u * M;
+            const float* y = V + (size_t)v2 * M;
+            for (int i = lane; i < M; i += 32) dot += x[i] * y[i];
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        }
+        if (lane == 0) {
+            const float r = u == v2 ? 1.0f : dot * mom[u] * mom[v2];
+            fcd[(p * nw + u) * nw + v2] = r;
+            fcd[(p * nw + v2) * nw + u] = r;
+        }
+    }
+}
+
+static size_t fc_reduce_smem(int N, int nb, int nw)
+{
+    (void)nb;
+    const size_t M = (size_t)N * (N - 1) / 2;
+    return sizeof(float) * (3 * (size_t)N + 2 * (size_t)nw * N + (size_t)nw * M + 48 + nw);
+}
+
+template <int MW>
+static cudaError_t launch_reduce_mw(const FcArgs& a, int32_t m, int32_t nw, int64_t Lw, float* fcd, size_t smem,
+                                    cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(fc_reduce_kernel<MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    fc_reduce_kernel<MW><<<a.P, RED_THREADS, smem, s>>>(a, m, nw, Lw, fcd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fc_reduce(const FcArgs& a, int32_t m, int32_t nw, int64_t Lw, float* vec_scratch, float* fcd,
+                             cudaStream_t s)
+{
+    const size_t smem = fc_reduce_smem(a.N, a.n_blocks, nw);
+    if (smem > 200 * 1024) {
+        // too large for shared memory: the two-kernel form
+        cudaError_t e = launch_fc_finalize(a, s);
+        if (e != cudaSuccess || nw == 0) return e;
+        return launch_fcd(a.blocks, a.P, a.N, a.n_blocks, m, nw, Lw, vec_scratch, fcd, s);
+    }
+    if (a.n_blocks <= FCR_MAXB) {
+        const int mw = nw == 0 ? 1 : m;   // without windows only the block sum is used
+        switch (mw) {
+        case 1: return launch_reduce_mw<1>(a, m, nw, Lw, fcd, smem, s);
+        case 2: return launch_reduce_mw<2>(a, m, nw, Lw, fcd, smem, s);
+        case 3: return launch_reduce_mw<3>(a, m, nw, Lw, fcd, smem, s);
+        case 4: return launch_reduce_mw<4>(a, m, nw, Lw, fcd, smem, s);
+        default: break;
+        }
+    }
+    return launch_reduce_mw<0>(a, m, nw, Lw, fcd, smem, s);
+}
+
+size_t fc_reduce_needs_vec_scratch(int N, int nb, int nw) { return fc_reduce_smem(N, nb, nw) > 200 * 1024; }
 
 cudaError_t launch_fcd(const float* blocks, int32_t P, int32_t N, int32_t n_blocks,
                        int32_t blocks_per_window, int32_t n_windows, int64_t window_samples,

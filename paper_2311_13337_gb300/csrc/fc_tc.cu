@@ -18,17 +18,18 @@
 //
 // Layout. A CTA owns SC consecutive sets (one 16- or 8-byte piece of every
 // (t, k) row of the [T][N][P] series) and all their samples. Per chunk of 128
-// bytes of K (64 BF16 or 32 TF32 samples) each thread (k, j) loads samples
-// j*SPC .. j*SPC+SPC-1 of region k for the SC sets, subtracts the shift,
-// splits, and writes one 16-byte piece of row k of each operand buffer in the
-// 128-byte swizzled K-major layout the MMA reads. Two stages: the loads of
-// chunk c+1 are in flight while chunk c is converted, and the MMAs of chunk c
-// run while chunk c+1 is converted. Thread 0 issues the MMAs (M = 128 rows,
-// of which the first N are regions; N_mma = N rounded up to 16) and commits
-// them to the stage's mbarrier, which the loaders wait on (bounded) before
-// overwriting the stage. After the last chunk of a block, warps 0-3 read the
-// accumulator rows out of tensor memory (lane = region) into shared memory,
-// and all threads write the symmetrised block moments.
+// bytes of K (64 BF16 or 32 TF32 samples) each loader thread (k, j) copies
+// samples j*SPC .. j*SPC+SPC-1 of region k for the SC sets into its own raw
+// slot in shared memory (cp.async, one chunk ahead), then subtracts the
+// shift, splits, and writes one 16-byte piece of row k of each operand buffer
+// in the 128-byte swizzled K-major layout the MMA reads. Two operand stages:
+// the MMAs of chunk c run while chunk c+1 is converted. One lane of the MMA
+// warp issues the MMAs (M = 128 rows, of which the first N are regions;
+// N_mma = N rounded up to 16) and commits them to the stage's mbarrier. At
+// the end of a block four warps read the accumulator rows out of tensor
+// memory (lane = region) and write them to global memory as they are; the
+// x3 forms leave D unsymmetric and every reader of the block moments takes
+// (D + D^T) / 2.
 //
 // Rows N .. 127 of the A operand and N .. N_mma - 1 of the B operand are
 // whatever follows the buffer in shared memory (in bounds by construction);
@@ -78,6 +79,18 @@ static __device__ __forceinline__ uint32_t tf32_rna(float x)
     return r;
 }
 
+// cp.async of `bytes` (4, 8 or 16) with zero fill: src_bytes = 0 writes zeros
+// and reads nothing (src must still be a valid address).
+template <int BYTES>
+static __device__ __forceinline__ void cp_async_zfill(uint32_t dst, const void* src, uint32_t src_bytes)
+{
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src), "n"(BYTES), "r"(src_bytes)
+                     : "memory");
+}
+
 static __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
 {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
@@ -86,10 +99,33 @@ static __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, u
 
 }  // namespace
 
+// Bounded wait by lane 0 of a warp, then the whole warp proceeds. After an
+// expiry (or once any wait of the CTA has expired) the wait is skipped: the
+// kernel then runs to its end without blocking and reports the error.
+static __device__ __forceinline__ void warp_wait(uint64_t* bar, uint32_t parity, uint32_t limit,
+                                                 volatile int* abort, uint32_t* error, uint32_t sleep_ns = 0)
+{
+    if ((threadIdx.x & 31) == 0 && !*abort &&
+        !(sleep_ns ? mbar_wait_sleep(bar, parity, limit, sleep_ns) : mbar_wait_bounded(bar, parity, limit))) {
+        atomicOr(error, TVBX_DEVERR_TIMEOUT);
+        *abort = 1;
+    }
+    __syncwarp();
+}
+
 // PREC: 1 BF16, 2 BF16x3, 3 TF32, 4 TF32x3 (the TVBX_FC_* values).
+//
+// Roles. Warps 0 .. NLW-1 load, shift, split and store (thread (k, j) =
+// region k, 16-byte piece j of each 128-byte row); warp NLW issues the MMAs
+// (one lane); warps NLW .. NLW+3 drain the accumulator of each finished
+// block from tensor memory (warp w reads lanes 32 (w % 4) ..). Hand-offs are
+// mbarriers: full[s] (one arrival per loader warp), empty[s] (MMA commit),
+// accf (MMA commit after a block's last chunk), drained (one arrival per
+// draining warp) -- no CTA-wide barrier inside the loop.
 template <int PREC, int SC, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1)
-fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_t tmem_cols, int32_t vec_ok)
+fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_t tmem_cols, int32_t vec_ok,
+             int32_t n_loader_warps)
 {
     constexpr int KIND = (PREC <= 2) ? 0 : 1;        // 0: kind::f16 (bf16), 1: kind::tf32
     constexpr bool SPLIT = (PREC == 2 || PREC == 4);
@@ -99,7 +135,7 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
     using V = typename LoadVec<SC>::T;
 
     extern __shared__ uint8_t dyn_smem[];
-    __shared__ uint64_t s_mbar[2];
+    __shared__ uint64_t s_full, s_empty, s_accf, s_drained;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
 
@@ -107,24 +143,25 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
     const int64_t P = a.P;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int k = tid >> 3, j = tid & 7;
-    const bool loader = k < N;
+    const int NLW = n_loader_warps;
     const int64_t p0 = (int64_t)blockIdx.x * SC;
+    const bool all_sets = p0 + SC <= P;
     const int64_t Tn = a.t_end - a.t_begin;
     const int64_t blk = a.blk > 0 ? (int64_t)a.blk : Tn;
     const int64_t NP = (int64_t)N * P;
+    const int64_t n_blocks = a.n_blocks;
     const uint32_t buf_bytes = (uint32_t)R * 128u;
     const uint32_t stage_bytes = (uint32_t)SC * NBUF * buf_bytes;
-
-    // 1024-byte aligned operand area
     const uint32_t raw = smem_u32(dyn_smem);
-    const uint32_t base = (raw + 1023u) & ~1023u;
-    float* dmat = reinterpret_cast<float*>(dyn_smem + (base - raw));   // drain area (overlaps the stages)
+    const uint32_t base = (raw + 1023u) & ~1023u;     // 1024-byte aligned operand stages
+    volatile int* abort = &s_abort;
 
-    if (warp == 0) tmem_alloc(&s_tmem, tmem_cols);
+    if (warp == NLW) tmem_alloc(&s_tmem, tmem_cols);
     if (tid == 0) {
-        mbar_init(&s_mbar[0], 1);
-        mbar_init(&s_mbar[1], 1);
+        mbar_init(&s_full, NLW);
+        mbar_init(&s_empty, 1);
+        mbar_init(&s_accf, 1);
+        mbar_init(&s_drained, 4);
         s_abort = 0;
         fence_mbarrier_init();
     }
@@ -133,207 +170,224 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    // shift of this thread's region for each set
-    float sh[SC];
-#pragma unroll
-    for (int s = 0; s < SC; ++s) {
-        float m = 0.0f;
-        if (loader && p0 + s < P) {
-            const int64_t o = (int64_t)k * P + p0 + s;
-            if (a.state) m = Tn > 0 ? a.state[(int64_t)SV_SUM_E * NP + o] / (float)Tn : 0.0f;
-            else if (a.shift) m = a.shift[o];
-        }
-        sh[s] = m;
-    }
+    auto block_len = [&](int64_t b) { return ((b * blk + blk < Tn) ? b * blk + blk : Tn) - b * blk; };
 
-    // global chunk sequence: blocks b, chunks c of KC samples (last one partial)
-    auto chunk_range = [&](int64_t b, int64_t c, int64_t& ts, int64_t& te) {
-        const int64_t b0 = b * blk;
-        const int64_t b1 = (b0 + blk < Tn) ? b0 + blk : Tn;
-        ts = b0 + c * KC;
-        te = (ts + KC < b1) ? ts + KC : b1;
-    };
-    auto load_chunk = [&](int64_t ts, int64_t te, V* v) {
+    if (warp < NLW) {
+        // ------------------------------------------------------------ loaders
+        const int k = tid >> 3, j = tid & 7;
+        const bool loader = k < N;
+        float sh[SC];
 #pragma unroll
-        for (int i = 0; i < SPC; ++i) {
-            const int64_t t = ts + j * SPC + i;
-            V x;
+        for (int s = 0; s < SC; ++s) {
+            float m = 0.0f;
+            if (loader && p0 + s < P) {
+                const int64_t o = (int64_t)k * P + p0 + s;
+                if (a.state) m = Tn > 0 ? a.state[(int64_t)SV_SUM_E * NP + o] / (float)Tn : 0.0f;
+                else if (a.shift) m = a.shift[o];
+            }
+            sh[s] = m;
+        }
+        const float* src0 = a.series + (a.t_begin + (int64_t)j * SPC) * NP + (int64_t)k * P + p0;
+        const bool fast_sets = loader && all_sets && vec_ok;
+        // this thread's raw slots (two, alternating by chunk): SPC pieces of SC
+        // floats, piece i of slot q at raw_base + ((q * SPC + i) * NLT + tid) * 4 SC
+        // (a warp's pieces are contiguous)
+        constexpr int PBYTES = 4 * SC;
+        const int NLT = 32 * NLW;
+        const uint32_t raw_base = base + stage_bytes + (uint32_t)(128 - R) * 128u;
+        // copy samples [ts, te) of this thread's piece into raw slot q; samples
+        // outside and sets >= P are zero-filled
+        auto issue_chunk = [&](int64_t ts, int64_t te, int q) {
+            const float* src = src0 + ts * NP;
+            if (fast_sets && te - ts == KC) {
+                const uint32_t dst0 = raw_base + (uint32_t)(q * SPC * NLT + tid) * PBYTES;
 #pragma unroll
-            for (int s = 0; s < SC; ++s) lset(x, s, 0.0f);
-            if (loader && t < te) {
-                const float* src = a.series + (a.t_begin + t) * NP + (int64_t)k * P + p0;
-                if (vec_ok) {
-                    x = __ldcs(reinterpret_cast<const V*>(src));
-                } else {
+                for (int i = 0; i < SPC; ++i)
+                    cp_async_zfill<PBYTES>(dst0 + (uint32_t)(i * NLT * PBYTES), src + i * NP, PBYTES);
+            } else if (all_sets && vec_ok) {
 #pragma unroll
-                    for (int s = 0; s < SC; ++s)
-                        if (p0 + s < P) lset(x, s, __ldcs(src + s));
+                for (int i = 0; i < SPC; ++i) {
+                    const uint32_t dst = raw_base + (uint32_t)((q * SPC + i) * NLT + tid) * PBYTES;
+                    const bool tv = loader && ts + j * SPC + i < te;
+                    cp_async_zfill<PBYTES>(dst, tv ? (const void*)(src + i * NP) : (const void*)a.series,
+                                           tv ? PBYTES : 0u);
+                }
+            } else {   // sets not a multiple of SC or an unaligned series: 4-byte copies
+#pragma unroll 1
+                for (int i = 0; i < SPC; ++i) {
+                    const uint32_t dst = raw_base + (uint32_t)((q * SPC + i) * NLT + tid) * PBYTES;
+                    const bool tv = loader && ts + j * SPC + i < te;
+#pragma unroll 1
+                    for (int s = 0; s < SC; ++s) {
+                        const bool ok_s = tv && p0 + s < P;
+                        cp_async_zfill<4>(dst + 4 * s, ok_s ? (const void*)(src + i * NP + s) : (const void*)a.series,
+                                          ok_s ? 4u : 0u);
+                    }
                 }
             }
-            v[i] = x;
-        }
-    };
-
-    float S[SC], C[SC];
+        };
+        const uint32_t row_off = (uint32_t)(k >> 3) * 1024u + (uint32_t)(k & 7) * 128u +
+                                 (uint32_t)((j ^ (k & 7)) << 4);
+        float S[SC], C[SC];
 #pragma unroll
-    for (int s = 0; s < SC; ++s) S[s] = C[s] = 0.0f;
-
-    const uint32_t row_off = (uint32_t)(k >> 3) * 1024u + (uint32_t)(k & 7) * 128u +
-                             (uint32_t)((j ^ (k & 7)) << 4);
-    const uint32_t idesc = tc_idesc(KIND == 0 ? 1u : 2u, 128u, (uint32_t)Ncols);
-    const int64_t n_blocks = a.n_blocks;
-
-    V cur[SPC], nxt[SPC];
-    int64_t gc = 0;      // chunks issued so far
-    bool ok = true;
-    {
-        int64_t ts, te;
-        chunk_range(0, 0, ts, te);
-        load_chunk(ts, te, cur);
-    }
-    for (int64_t b = 0; b < n_blocks && ok; ++b) {
-        int64_t bs, be;
-        chunk_range(b, 0, bs, be);
-        const int64_t blen = ((b * blk + blk < Tn) ? b * blk + blk : Tn) - b * blk;
-        const int64_t nck = (blen + KC - 1) / KC;
-        for (int64_t c = 0; c < nck; ++c) {
-            int64_t ts, te;
-            chunk_range(b, c, ts, te);
-            // prefetch the next chunk (in this block or the next one)
-            {
-                int64_t nb = b, ncn = c + 1;
-                if (ncn >= nck) { nb = b + 1; ncn = 0; }
-                if (nb < n_blocks) {
-                    int64_t nts, nte;
-                    chunk_range(nb, ncn, nts, nte);
-                    load_chunk(nts, nte, nxt);
+        for (int s = 0; s < SC; ++s) S[s] = C[s] = 0.0f;
+        issue_chunk(0, block_len(0) < KC ? block_len(0) : KC, 0);
+        cp_async_commit();
+        int64_t gc = 0;
+        for (int64_t b = 0; b < n_blocks; ++b) {
+            const int64_t b0 = b * blk, blen = block_len(b);
+            const int64_t nck = (blen + KC - 1) / KC;
+            for (int64_t c = 0; c < nck; ++c) {
+                const int64_t ts = b0 + c * KC;
+                const int64_t te = (ts + KC < b0 + blen) ? ts + KC : b0 + blen;
+                const int q = (int)(gc & 1);
+                // copy the next chunk (in this block or the next one) into the
+                // other slot, whose contents were consumed by the previous chunk
+                if (c + 1 < nck) {
+                    const int64_t nts = ts + KC;
+                    issue_chunk(nts, (nts + KC < b0 + blen) ? nts + KC : b0 + blen, q ^ 1);
+                } else if (b + 1 < n_blocks) {
+                    const int64_t nts = b0 + blk, nl = block_len(b + 1);
+                    issue_chunk(nts, nts + (nl < KC ? nl : KC), q ^ 1);
                 }
-            }
-            const int stage = (int)(gc & 1);
-            if (gc >= 2 && !mbar_wait_bounded(&s_mbar[stage], (uint32_t)(((gc - 2) >> 1) & 1), a.wait_limit)) {
-                atomicOr(a.error, TVBX_DEVERR_TIMEOUT);
-                s_abort = 1;
-            }
-            // convert and store this thread's piece of every operand buffer
-            if (loader) {
-                const uint32_t sbase = base + (uint32_t)stage * stage_bytes;
+                cp_async_commit();
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this chunk has landed
+                // the operand stage is free once the previous chunk's MMAs completed
+                if (gc >= 1) warp_wait(&s_empty, (uint32_t)((gc - 1) & 1), a.wait_limit, abort, a.error, 20);
+                // shift, split, store
+                const bool full_chunk = fast_sets && te - ts == KC;
+                const uint8_t* slot = dyn_smem + (raw_base - raw) + (size_t)(q * SPC * NLT + tid) * PBYTES;
 #pragma unroll
                 for (int s = 0; s < SC; ++s) {
                     float z[SPC];
 #pragma unroll
-                    for (int i = 0; i < SPC; ++i) {
-                        const int64_t t = ts + j * SPC + i;
-                        z[i] = (t < te && p0 + s < P) ? lv(cur[i], s) - sh[s] : 0.0f;
-                        kahan(S[s], C[s], z[i]);
+                    for (int i = 0; i < SPC; ++i)
+                        z[i] = reinterpret_cast<const float*>(slot + (size_t)i * NLT * PBYTES)[s] - sh[s];
+                    if (!full_chunk) {   // padding samples and missing sets are 0
+#pragma unroll
+                        for (int i = 0; i < SPC; ++i)
+                            if (!(loader && ts + j * SPC + i < te && p0 + s < P)) z[i] = 0.0f;
                     }
+                    float part[SPC];
+#pragma unroll
+                    for (int i = 0; i < SPC; ++i) part[i] = z[i];
+#pragma unroll
+                    for (int w = SPC / 2; w > 0; w >>= 1)
+#pragma unroll
+                        for (int i = 0; i < w; ++i) part[i] += part[i + w];
+                    kahan(S[s], C[s], part[0]);
                     uint32_t hw[4], lw[4];
                     if constexpr (KIND == 0) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const __nv_bfloat162 h = __floats2bfloat162_rn(z[2 * q], z[2 * q + 1]);
-                            hw[q] = *reinterpret_cast<const uint32_t*>(&h);
+                        for (int u = 0; u < 4; ++u) {
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(z[2 * u], z[2 * u + 1]);
+                            hw[u] = *reinterpret_cast<const uint32_t*>(&h);
                             if constexpr (SPLIT) {
                                 const float2 hf = __bfloat1622float2(h);
-                                const __nv_bfloat162 l =
-                                    __floats2bfloat162_rn(2.0f * (z[2 * q] - hf.x), 2.0f * (z[2 * q + 1] - hf.y));
-                                lw[q] = *reinterpret_cast<const uint32_t*>(&l);
+                                const __nv_bfloat162 l = __floats2bfloat162_rn(2.0f * (z[2 * u] - hf.x),
+                                                                               2.0f * (z[2 * u + 1] - hf.y));
+                                lw[u] = *reinterpret_cast<const uint32_t*>(&l);
                             }
                         }
                     } else {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            hw[q] = tf32_rna(z[q]);
-                            if constexpr (SPLIT) lw[q] = __float_as_uint(2.0f * (z[q] - __uint_as_float(hw[q])));
+                        for (int u = 0; u < 4; ++u) {
+                            hw[u] = tf32_rna(z[u]);
+                            if constexpr (SPLIT) lw[u] = __float_as_uint(2.0f * (z[u] - __uint_as_float(hw[u])));
                         }
                     }
-                    const uint32_t hb = sbase + (uint32_t)s * NBUF * buf_bytes;
-                    st_shared_v4(hb + row_off, hw[0], hw[1], hw[2], hw[3]);
-                    if constexpr (SPLIT) st_shared_v4(hb + buf_bytes + row_off, lw[0], lw[1], lw[2], lw[3]);
-                }
-            }
-            fence_proxy_async_shared();
-            __syncthreads();
-            if (s_abort) { ok = false; break; }
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t sbase = base + (uint32_t)stage * stage_bytes;
-#pragma unroll 1
-                for (int s = 0; s < SC; ++s) {
-                    const uint32_t hb = sbase + (uint32_t)s * NBUF * buf_bytes;
-                    const uint32_t d = tmem + (uint32_t)(s * Ncols);
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t ad = sw128_desc(hb + 32u * ks);
-                        tc_mma<KIND>(d, ad, ad, idesc, (c == 0 && ks == 0) ? 0u : 1u);
-                        if constexpr (SPLIT) tc_mma<KIND>(d, ad, sw128_desc(hb + buf_bytes + 32u * ks), idesc, 1u);
+                    if (loader) {
+                        const uint32_t hb = base + (uint32_t)s * NBUF * buf_bytes;
+                        st_shared_v4(hb + row_off, hw[0], hw[1], hw[2], hw[3]);
+                        if constexpr (SPLIT) st_shared_v4(hb + buf_bytes + row_off, lw[0], lw[1], lw[2], lw[3]);
                     }
                 }
-                tc_commit(&s_mbar[stage]);
+                fence_proxy_async_shared();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_full);
+                ++gc;
             }
-            ++gc;
+            // this block's row sums
+            const int64_t stride_b = (int64_t)N * N + N;
 #pragma unroll
-            for (int i = 0; i < SPC; ++i) cur[i] = nxt[i];
-        }
-        if (!ok) break;
-
-        // ---- block epilogue: wait for the last MMAs, drain, write ----
-        if (!mbar_wait_bounded(&s_mbar[(gc - 1) & 1], (uint32_t)(((gc - 1) >> 1) & 1), a.wait_limit)) {
-            atomicOr(a.error, TVBX_DEVERR_TIMEOUT);
-            s_abort = 1;
-        }
-        __syncthreads();
-        if (s_abort) { ok = false; break; }
-        tc_fence_after();
-        if (warp < 4) {
-            const int row = warp * 32 + lane;
             for (int s = 0; s < SC; ++s) {
+                float v = S[s] - C[s];
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                if (loader && j == 0 && p0 + s < P)
+                    a.blocks[((p0 + s) * n_blocks + b) * stride_b + (int64_t)N * N + k] = v;
+                S[s] = C[s] = 0.0f;
+            }
+        }
+    } else {
+        // ------------------------------------------------ MMA issue and drain
+        const bool issuer = warp == NLW;
+        const uint32_t idesc = tc_idesc(KIND == 0 ? 1u : 2u, 128u, (uint32_t)Ncols);
+        const int quarter = warp & 3;
+        int64_t gc = 0;
+        for (int64_t b = 0; b < n_blocks; ++b) {
+            if (issuer) {
+                const int64_t nck = (block_len(b) + KC - 1) / KC;
+                for (int64_t c = 0; c < nck; ++c) {
+                    warp_wait(&s_full, (uint32_t)(gc & 1), a.wait_limit, abort, a.error, 32);
+                    if (c == 0 && b > 0)   // the accumulator of block b-1 must have been read
+                        warp_wait(&s_drained, (uint32_t)((b - 1) & 1), a.wait_limit, abort, a.error, 32);
+                    tc_fence_after();
+                    if (lane == 0) {
+#pragma unroll 1
+                        for (int s = 0; s < SC; ++s) {
+                            const uint32_t hb = base + (uint32_t)s * NBUF * buf_bytes;
+                            const uint32_t d = tmem + (uint32_t)(s * Ncols);
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t ad = sw128_desc(hb + 32u * ks);
+                                tc_mma<KIND>(d, ad, ad, idesc, (c == 0 && ks == 0) ? 0u : 1u);
+                                if constexpr (SPLIT)
+                                    tc_mma<KIND>(d, ad, sw128_desc(hb + buf_bytes + 32u * ks), idesc, 1u);
+                            }
+                        }
+                        tc_commit(&s_empty);
+                        if (c + 1 == nck) tc_commit(&s_accf);
+                    }
+                    __syncwarp();
+                    ++gc;
+                }
+            }
+            // drain block b: accumulator rows (lane = region) straight to global
+            warp_wait(&s_accf, (uint32_t)(b & 1), a.wait_limit, abort, a.error, issuer ? 32 : 500);
+            tc_fence_after();
+            const int row = quarter * 32 + lane;
+            const int64_t stride_b = (int64_t)N * N + N;
+            for (int s = 0; s < SC; ++s) {
+                float* out = a.blocks + ((p0 + s) * n_blocks + b) * stride_b + (int64_t)row * N;
+                const bool w_ok = row < N && p0 + s < P;
                 for (int cb = 0; cb * 16 < N; ++cb) {
                     float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * Ncols + cb * 16), v);
-                    if (row < N) {
+                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * Ncols + cb * 16), v);
+                    if (w_ok) {
+                        if (cb * 16 + 16 <= N) {
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const int col = cb * 16 + q;
-                            if (col < N) dmat[((int64_t)s * N + row) * (N + 1) + col] = v[q];
+                            for (int q = 0; q < 16; q += 4)
+                                *reinterpret_cast<float4*>(out + cb * 16 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                if (cb * 16 + q < N) out[cb * 16 + q] = v[q];
                         }
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_drained);
         }
-        tc_fence_before();
-        __syncthreads();
-        const int64_t stride_b = (int64_t)N * N + N;
-        for (int idx = tid; idx < SC * N * N; idx += blockDim.x) {
-            const int s = idx / (N * N);
-            const int r = idx - s * N * N;
-            const int i = r / N, jj = r - i * N;
-            if (p0 + s < P) {
-                const float* Ds = dmat + (int64_t)s * N * (N + 1);
-                float g = 0.5f * (Ds[i * (N + 1) + jj] + Ds[jj * (N + 1) + i]);
-                a.blocks[((p0 + s) * a.n_blocks + b) * stride_b + r] = g;
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < SC; ++s) {
-            float v = S[s] - C[s];
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            v += __shfl_xor_sync(0xffffffffu, v, 4);
-            if (loader && j == 0 && p0 + s < P)
-                a.blocks[((p0 + s) * a.n_blocks + b) * stride_b + (int64_t)N * N + k] = v;
-            S[s] = C[s] = 0.0f;
-        }
-        __syncthreads();   // the drain area is the next block's stage area
     }
 
-    // leave: make sure no MMA is still running, then free tensor memory
-    if (tid == 0 && gc > 0) {
-        mbar_wait_bounded(&s_mbar[(gc - 1) & 1], (uint32_t)(((gc - 1) >> 1) & 1), a.wait_limit);
-        if (gc > 1) mbar_wait_bounded(&s_mbar[gc & 1], (uint32_t)(((gc - 2) >> 1) & 1), a.wait_limit);
-    }
+    // every MMA has completed (its block was drained); free tensor memory
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == NLW) {
         tc_fence_after();
         tmem_dealloc(tmem, tmem_cols);
     }
@@ -341,32 +395,31 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
 
 // Geometry shared by the launcher and the host-side checks.
 struct FcTcGeom {
-    int SC, R, Ncols, threads;
+    int SC, R, Ncols, threads, loader_warps;
     uint32_t tmem_cols;
     size_t smem;
 };
 
 static bool fc_tc_geom(int N, int prec, FcTcGeom& g)
 {
-    if (N < 1 || N > 128) return false;
-    g.SC = N <= 72 ? 4 : 2;
+    if (N < 1 || N > 112) return false;
+    g.SC = N <= 68 ? 4 : 2;
     g.R = (N + 7) / 8 * 8;
     g.Ncols = (N + 15) / 16 * 16;
-    int t = (8 * N + 31) / 32 * 32;
-    g.threads = t < 128 ? 128 : t;
+    g.loader_warps = (8 * N + 31) / 32;
+    g.threads = 32 * g.loader_warps + 128;
     const int nbuf = (prec == TVBX_FC_BF16X3 || prec == TVBX_FC_TF32X3) ? 2 : 1;
     const size_t buf = (size_t)g.R * 128;
     const size_t stage = (size_t)g.SC * nbuf * buf;
-    const size_t main_bytes = 2 * stage + (size_t)(128 - g.R) * 128;
-    const size_t drain = sizeof(float) * (size_t)g.SC * N * (N + 1);
-    g.smem = 1024 + (main_bytes > drain ? main_bytes : drain);
+    const int spc = (prec == TVBX_FC_BF16 || prec == TVBX_FC_BF16X3) ? 8 : 4;
+    g.smem = 1024 + stage + (size_t)(128 - g.R) * 128 + (size_t)2 * 32 * g.loader_warps * spc * 4 * g.SC;
     uint32_t need = (uint32_t)(g.SC * g.Ncols), cols = 32;
     while (cols < need) cols <<= 1;
     g.tmem_cols = cols;
     // more than half of the tensor memory: keep a second CTA off the SM (its
     // allocation would only wait for this one's release)
     if (cols > 256 && g.smem < 116 * 1024) g.smem = 116 * 1024;
-    return cols <= 512 && g.smem <= 227 * 1024;
+    return cols <= 512 && g.smem <= 227 * 1024 && g.threads <= (g.SC == 4 ? 672 : 1024);
 }
 
 bool fc_tc_supported(int N, int prec)
@@ -383,7 +436,7 @@ static cudaError_t launch_one(const FcArgs& a, const FcTcGeom& g, int vec_ok, cu
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((a.P + SC - 1) / SC);
     note_launch();
-    kern<<<grid, g.threads, g.smem, s>>>(a, g.R, g.Ncols, g.tmem_cols, vec_ok);
+    kern<<<grid, g.threads, g.smem, s>>>(a, g.R, g.Ncols, g.tmem_cols, vec_ok, g.loader_warps);
     return cudaGetLastError();
 }
 
@@ -391,7 +444,7 @@ template <int PREC>
 static cudaError_t launch_prec(const FcArgs& a, const FcTcGeom& g, cudaStream_t s)
 {
     const int vec_ok = (a.P % g.SC == 0) && ((uintptr_t)a.series % 16 == 0) ? 1 : 0;
-    if (g.SC == 4) return launch_one<PREC, 4, 576>(a, g, vec_ok, s);
+    if (g.SC == 4) return launch_one<PREC, 4, 672>(a, g, vec_ok, s);
     return launch_one<PREC, 2, 1024>(a, g, vec_ok, s);
 }
 

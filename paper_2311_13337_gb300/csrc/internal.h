@@ -132,8 +132,14 @@ struct FcArgs {
     uint32_t* error;           // device error word (tensor-core path)
     uint32_t wait_limit;       // try_wait attempts before a wait gives up
 };
-// Block moments (SIMT, FP32) followed by the finalize kernel.
-cudaError_t launch_fc(const FcArgs& a, cudaStream_t s);
+// Block moments (SIMT, FP32 CUDA-core FMAs).
+cudaError_t launch_fc_moments(const FcArgs& a, cudaStream_t s);
+// From the block moments: Pearson FC, chi, mean FC and (nw > 0) the FCD over
+// nw windows of m blocks of Lw samples, in one kernel when its shared memory
+// fits; vec_scratch ([P][nw][N(N-1)/2]) is used only when it does not.
+cudaError_t launch_fc_reduce(const FcArgs& a, int32_t m, int32_t nw, int64_t Lw, float* vec_scratch, float* fcd,
+                             cudaStream_t s);
+size_t fc_reduce_needs_vec_scratch(int N, int nb, int nw);
 // Tensor-core block moments (precision TVBX_FC_BF16 .. TVBX_FC_TF32X3);
 // N <= 128.
 cudaError_t launch_fc_tc_moments(const FcArgs& a, int prec, cudaStream_t s);

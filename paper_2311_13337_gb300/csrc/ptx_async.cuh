@@ -24,6 +24,10 @@ static __device__ __forceinline__ void mbar_arm(uint64_t* bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+static __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
 static __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
     uint32_t ok;
@@ -38,6 +42,16 @@ static __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t
 {
     for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// Bounded wait that sleeps ns nanoseconds between polls (for waits expected
+// to last much longer than a poll). Returns false after limit polls.
+static __device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t limit, uint32_t ns)
+{
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        __nanosleep(ns);
+    }
     return false;
 }
 static __device__ __forceinline__ void fence_mbarrier_init()

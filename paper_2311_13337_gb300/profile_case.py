@@ -1,11 +1,14 @@
 """Run one sized sweep of the paper-scale grid for profiling.
 
   python -m paper_2311_13337_gb300.profile_case --sets 8192 --n-steps 1000 --chunk 500 [--fc]
+  python -m paper_2311_13337_gb300.profile_case --fc-series --sets 4096 --samples 5000 --fc-precision bf16x3
 
 Takes the first `--sets` sets of the 32,768-set grid (68 regions, v 4 m/s),
 integrates `--n-steps` steps in launches of `--chunk` steps and optionally
-runs the FC/FCD pass, then prints the wall time. Sized so that a profiler
-can capture single launches on a few GB of device memory.
+runs the FC/FCD pass, then prints the wall time. With --fc-series, runs
+only the FC stage (tvbx_fc_series, FCD 1000/500 unless --no-fcd) on
+synthetic rate-like series of `--sets` x 68 regions x `--samples`. Sized so
+that a profiler can capture single launches on a few GB of device memory.
 """
 from __future__ import annotations
 
@@ -27,7 +30,14 @@ def main():
     ap.add_argument("--fc", action="store_true")
     ap.add_argument("--noise-per-set", action="store_true")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 general, 2 + v prefetch variant v")
+    ap.add_argument("--fc-series", action="store_true")
+    ap.add_argument("--samples", type=int, default=5000)
+    ap.add_argument("--fc-precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3", "tf32", "tf32x3"])
+    ap.add_argument("--no-fcd", action="store_true")
+    ap.add_argument("--repeat", type=int, default=2)
     args = ap.parse_args()
+    if args.fc_series:
+        return fc_series_case(args)
 
     import numpy as np
     import torch
@@ -56,6 +66,27 @@ def main():
     torch.cuda.synchronize()
     print(f"sets {P} steps {args.n_steps} chunk {args.chunk}: {time.time() - t0:.3f} s")
     sw.close()
+
+
+def fc_series_case(args):
+    import torch
+
+    from paper_2311_13337_gb300 import build, synth, tvbx
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    P, N, T = args.sets, 68, args.samples
+    X = synth.rate_series_device(torch, dev, P, N, T, seed=1000)
+    fc = torch.empty((P, N, N), dtype=torch.float32, device=dev)
+    w, s = (0, 0) if args.no_fcd else (min(1000, T), min(500, T))
+    nw = (T - w) // s + 1 if w else 0
+    fcd = torch.empty((P, max(nw, 1), max(nw, 1)), dtype=torch.float32, device=dev)
+    prec = getattr(tvbx, "FC_" + args.fc_precision.upper())
+    for i in range(args.repeat):
+        t0 = time.time()
+        tvbx.fc_series(X, N, P, T, precision=prec, fc_out=fc, fcd_out=fcd if w else None, fcd_window=w,
+                       fcd_step=s)
+        print(f"fc series {P} x {N} x {T} {args.fc_precision}: {time.time() - t0:.4f} s")
 
 
 if __name__ == "__main__":

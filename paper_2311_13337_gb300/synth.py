@@ -70,3 +70,24 @@ def correlated_series(n_sets: int, n_regions: int, n_samples: int, seed: int,
         xs[p] = lo @ z * rng.uniform(0.5, 2.0, size=(n_regions, 1)) + rng.uniform(-1, 1, size=(n_regions, 1))
         cs[p] = corr
     return xs, cs
+
+
+def rate_series_device(torch, device, n_sets: int, n_regions: int, n_samples: int, seed: int):
+    """Rate-like synthetic E series [T][N][P] (kHz, FP32) made on the device
+    with a seeded torch generator, the layout the engine keeps: 5 Hz mean,
+    0.1 Hz fluctuations mixed with a per-set common mode (correlations of
+    about 0.2), and a start-up ramp decaying over 50 samples. Stands in for
+    the paper-scale sweep's output when the FC stage is measured alone."""
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    T, N, P = n_samples, n_regions, n_sets
+    X = torch.empty((T, N, P), dtype=torch.float32, device=device)
+    ramp_scale = torch.linspace(0.5, 1.5, N, device=device).view(1, N, 1)
+    for t0 in range(0, T, 250):
+        t1 = min(T, t0 + 250)
+        z = torch.randn((t1 - t0, N, P), generator=g, device=device)
+        common = torch.randn((t1 - t0, 1, P), generator=g, device=device)
+        tt = torch.arange(t0, t1, device=device, dtype=torch.float32).view(-1, 1, 1)
+        X[t0:t1] = 5e-3 + 1e-4 * (z + 0.5 * common) + 4e-3 * torch.exp(-tt / 50.0) * ramp_scale
+        del z, common
+    return X

@@ -71,7 +71,7 @@ CASES = [
     (68, 12, 1300),   # four sets per CTA, partial last chunk
     (68, 10, 777),    # n_sets not a multiple of the CTA's sets: scalar loads, ragged set group
     (84, 6, 1000),    # two sets per CTA
-    (128, 4, 640),    # largest tensor-core size
+    (112, 4, 640),    # largest tensor-core size
     (5, 3, 100),      # tiny
     (16, 8, 64),      # exactly one chunk
 ]
