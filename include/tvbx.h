@@ -343,6 +343,89 @@ tvbx_status tvbx_fc_noalloc(const float* series, int32_t n_regions, int64_t n_se
 /* Release the handle and its device memory. NULL is accepted. */
 tvbx_status tvbx_sweep_destroy(tvbx_sweep* h);
 
+/* ---- Surrogate network ---------------------------------------------------
+ * The paper has no surrogate model; it motivates guided exploration of the
+ * parameter space (Sec. "Discussion"). This is the learned form of the
+ * exploration: an ensemble of multilayer perceptrons, trained on the GPU by
+ * the library's own kernels, that maps sweep parameters (e.g. g, b_e,
+ * tau_w_e, E_L_i, v) to summary statistics of a simulation (e.g. mean rates,
+ * chi, mean FC, FC principal-component coefficients) and proposes where the
+ * sweep should be refined; the simulation stays the judge of every proposal.
+ *
+ * Network: inputs mapped to [-1, 1] by the domain box; n_layers hidden layers
+ * of n_hidden units, a = max(0, a_prev W^T + b); linear output layer that
+ * predicts the outputs standardised by the last training set's per-output
+ * mean and population standard deviation. Loss: mean squared error over rows
+ * and outputs. Optimiser: AdamW (decoupled weight decay on weight matrices
+ * only; beta1 0.9, beta2 0.999, eps 1e-8). Weights: FP32 master copy and a
+ * BF16 copy read by the matrix products; FP32 accumulation. Initial weights:
+ * He-uniform from Philox (key = seed), zero biases. Members differ by their
+ * initial weights and shuffles.
+ * Flattened parameter layout of one member (host arrays below): layer by
+ * layer, W [out][in] row-major, then b [out]. Handles are not thread-safe;
+ * each owns a CUDA stream and every call returns after its work completed. */
+typedef struct tvbx_surrogate tvbx_surrogate;
+typedef struct {
+    int32_t n_in;        /* inputs, 1..64 */
+    int32_t n_hidden;    /* units per hidden layer, 1..1024 */
+    int32_t n_layers;    /* hidden layers, 1..8 */
+    int32_t n_out;       /* outputs, 1..256 */
+    int32_t n_members;   /* ensemble size, 1..16 */
+    uint64_t seed;       /* initial weights, shuffles, candidates */
+    const double* in_lo; /* [n_in] domain box (copied); finite, in_lo < in_hi */
+    const double* in_hi; /* [n_in] */
+} tvbx_surrogate_cfg;
+
+/* Create; *out receives the handle. Errors: TVBX_E_INVALID_ARG (sizes, box),
+ * TVBX_E_OOM, TVBX_E_CUDA. */
+tvbx_status tvbx_surrogate_create(const tvbx_surrogate_cfg* cfg, tvbx_surrogate** out);
+
+/* Parameters per member and ensemble size (either pointer nullable). */
+tvbx_status tvbx_surrogate_info(const tvbx_surrogate* s, int64_t* n_params, int32_t* n_members);
+
+/* Train every member on X [n][n_in], Y [n][n_out] (FP32; mem = TVBX_MEM_HOST
+ * or TVBX_MEM_DEVICE): recompute the output standardisation from Y, then
+ * `epochs` passes in mini-batches of `batch` rows (the last one may be
+ * shorter), one AdamW step (learning rate lr, weight decay weight_decay) per
+ * mini-batch. shuffle != 0: each member visits the rows in its own
+ * pseudo-random order per pass; 0: in order. loss_out (host, nullable)
+ * receives the mean training loss of each pass [epochs] (over members and
+ * mini-batches, in standardised units). */
+tvbx_status tvbx_surrogate_train(tvbx_surrogate* s, int32_t mem, const float* X, const float* Y, int64_t n,
+                                 int32_t epochs, int32_t batch, float lr, float weight_decay, int32_t shuffle,
+                                 float* loss_out);
+
+/* Ensemble mean y_mean [n][n_out] and variance y_var [n][n_out] (nullable)
+ * across members of the predictions in output units, for X [n][n_in]; all on
+ * the host or all on the device (mem). */
+tvbx_status tvbx_surrogate_predict(tvbx_surrogate* s, int32_t mem, const float* X, int64_t n, float* y_mean,
+                                   float* y_var);
+
+/* Propose n_propose points where output `output` is closest to `threshold`
+ * and the ensemble disagrees most: n_candidates points drawn uniformly in the
+ * domain box (Philox, counter = (candidate, round, input), key = seed) are
+ * scored by -|mean - threshold| / sd + var_weight sqrt(var) / sd (sd = the
+ * output's training standard deviation) and the best n_propose (ties to the
+ * lower candidate index) are written, best first, to points_out
+ * [n_propose][n_in] (host) with their scores (host, nullable). */
+tvbx_status tvbx_surrogate_propose(tvbx_surrogate* s, int64_t n_candidates, uint64_t round, int32_t output,
+                                   float threshold, float var_weight, int32_t n_propose, float* points_out,
+                                   float* scores_out);
+
+/* Read (get_out) and/or replace (set_in) the FP32 parameters of one member
+ * (host arrays of tvbx_surrogate_info's n_params; either nullable). Setting
+ * also rounds the BF16 copy and clears that member's optimiser state. */
+tvbx_status tvbx_surrogate_params(tvbx_surrogate* s, int32_t member, float* get_out, const float* set_in);
+
+/* Loss and gradient (host, [n_params], flattened layout) of one member on
+ * host X [n][n_in], Y [n][n_out] with the current standardisation, without
+ * an update; n <= 2^20. */
+tvbx_status tvbx_surrogate_gradients(tvbx_surrogate* s, int32_t member, const float* X, const float* Y, int64_t n,
+                                     float* loss, float* grads);
+
+/* Release the handle. NULL is accepted. */
+tvbx_status tvbx_surrogate_destroy(tvbx_surrogate* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,13 +75,21 @@ class FcCfg(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("fcd_window", ctypes.c_int32), ("fcd_step", ctypes.c_int32)]
 
 
+class SurrogateCfg(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("n_hidden", ctypes.c_int32), ("n_layers", ctypes.c_int32),
+                ("n_out", ctypes.c_int32), ("n_members", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("in_lo", ctypes.POINTER(ctypes.c_double)), ("in_hi", ctypes.POINTER(ctypes.c_double))]
+
+
 _lib = None
 EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep_create",
            "tvbx_sweep_create_points", "tvbx_sweep_info", "tvbx_run", "tvbx_summary", "tvbx_series",
            "tvbx_series_range", "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_last_kernel",
            "tvbx_launch_count",
            "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_fc_noalloc", "tvbx_fc_series",
-           "tvbx_sweep_destroy")
+           "tvbx_sweep_destroy", "tvbx_surrogate_create", "tvbx_surrogate_info", "tvbx_surrogate_train",
+           "tvbx_surrogate_predict", "tvbx_surrogate_propose", "tvbx_surrogate_params", "tvbx_surrogate_gradients",
+           "tvbx_surrogate_destroy")
 
 
 def library_path() -> str:
@@ -120,6 +128,14 @@ def load(build_if_missing: bool = False):
     L.tvbx_fc_noalloc.argtypes = [fp, i32, i64, i64, fp, fp, fp, vp]
     L.tvbx_fc_series.argtypes = [fp, i32, i64, i64, ctypes.POINTER(FcCfg), fp, fp, ctypes.POINTER(i32), fp, fp, fp,
                                  vp]
+    L.tvbx_surrogate_create.argtypes = [ctypes.POINTER(SurrogateCfg), ctypes.POINTER(vp)]
+    L.tvbx_surrogate_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    L.tvbx_surrogate_train.argtypes = [vp, i32, fp, fp, i64, i32, i32, ctypes.c_float, ctypes.c_float, i32, fp]
+    L.tvbx_surrogate_predict.argtypes = [vp, i32, fp, i64, fp, fp]
+    L.tvbx_surrogate_propose.argtypes = [vp, i64, ctypes.c_uint64, i32, ctypes.c_float, ctypes.c_float, i32, fp, fp]
+    L.tvbx_surrogate_params.argtypes = [vp, i32, fp, fp]
+    L.tvbx_surrogate_gradients.argtypes = [vp, i32, fp, fp, i64, ctypes.POINTER(ctypes.c_float), fp]
+    L.tvbx_surrogate_destroy.argtypes = [vp]
     L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.tvbx_profile_enable.argtypes = [vp, i32]
     L.tvbx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -445,3 +461,87 @@ class Sweep:
                 self.close()
         except Exception:
             pass
+
+
+class Surrogate:
+    """Ensemble MLP surrogate (tvbx_surrogate_*): parameters -> summary
+    statistics, trained and evaluated by the library's CUDA kernels."""
+
+    def __init__(self, lo, hi, n_out, n_hidden=256, n_layers=3, n_members=4, seed=1):
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        self.n_in, self.n_out = lo.size, int(n_out)
+        cfg = SurrogateCfg(self.n_in, int(n_hidden), int(n_layers), self.n_out, int(n_members), int(seed),
+                           _dptr(lo), _dptr(hi))
+        self.h = ctypes.c_void_p()
+        _check(load().tvbx_surrogate_create(ctypes.byref(cfg), ctypes.byref(self.h)), "tvbx_surrogate_create")
+        n, e = ctypes.c_int64(), ctypes.c_int32()
+        _check(load().tvbx_surrogate_info(self.h, ctypes.byref(n), ctypes.byref(e)), "tvbx_surrogate_info")
+        self.n_params, self.n_members = n.value, e.value
+        self.dims = [self.n_in] + [int(n_hidden)] * int(n_layers) + [self.n_out]
+
+    def _ptr(self, a, cols):
+        if hasattr(a, "data_ptr"):
+            return ctypes.c_void_p(a.data_ptr()), (MEM_DEVICE if a.is_cuda else MEM_HOST), a.shape[0], a
+        a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1, cols)
+        return ctypes.c_void_p(a.ctypes.data), MEM_HOST, a.shape[0], a
+
+    def train(self, X, Y, epochs=1, batch=1024, lr=1e-3, weight_decay=1e-4, shuffle=True):
+        px, mx, n, kx = self._ptr(X, self.n_in)
+        py, my, _, ky = self._ptr(Y, self.n_out)
+        if mx != my:
+            raise ValueError("X and Y must both be host or both be device arrays")
+        losses = np.zeros(int(epochs), dtype=np.float32)
+        _check(load().tvbx_surrogate_train(self.h, mx, px, py, n, int(epochs), int(batch), float(lr),
+                                           float(weight_decay), int(bool(shuffle)),
+                                           ctypes.c_void_p(losses.ctypes.data)), "tvbx_surrogate_train")
+        return losses
+
+    def predict(self, X, want_var=False):
+        px, mx, n, kx = self._ptr(X, self.n_in)
+        if mx == MEM_DEVICE:
+            import torch
+            mean = torch.empty((n, self.n_out), dtype=torch.float32, device=X.device)
+            var = torch.empty((n, self.n_out), dtype=torch.float32, device=X.device) if want_var else None
+            pm, pv = ctypes.c_void_p(mean.data_ptr()), (ctypes.c_void_p(var.data_ptr()) if want_var else None)
+        else:
+            mean = np.zeros((n, self.n_out), dtype=np.float32)
+            var = np.zeros((n, self.n_out), dtype=np.float32) if want_var else None
+            pm, pv = ctypes.c_void_p(mean.ctypes.data), (ctypes.c_void_p(var.ctypes.data) if want_var else None)
+        _check(load().tvbx_surrogate_predict(self.h, mx, px, n, pm, pv), "tvbx_surrogate_predict")
+        return (mean, var) if want_var else mean
+
+    def propose(self, n_candidates, n_propose, output, threshold, var_weight=1.0, round=0):
+        pts = np.zeros((int(n_propose), self.n_in), dtype=np.float32)
+        sc = np.zeros(int(n_propose), dtype=np.float32)
+        _check(load().tvbx_surrogate_propose(self.h, int(n_candidates), int(round), int(output), float(threshold),
+                                             float(var_weight), int(n_propose), ctypes.c_void_p(pts.ctypes.data),
+                                             ctypes.c_void_p(sc.ctypes.data)), "tvbx_surrogate_propose")
+        return pts, sc
+
+    def params(self, member=0) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().tvbx_surrogate_params(self.h, int(member), ctypes.c_void_p(out.ctypes.data), None),
+               "tvbx_surrogate_params")
+        return out
+
+    def set_params(self, vec, member=0):
+        v = np.ascontiguousarray(vec, dtype=np.float32)
+        assert v.size == self.n_params
+        _check(load().tvbx_surrogate_params(self.h, int(member), None, ctypes.c_void_p(v.ctypes.data)),
+               "tvbx_surrogate_params")
+
+    def gradients(self, X, Y, member=0):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(load().tvbx_surrogate_gradients(self.h, int(member), ctypes.c_void_p(X.ctypes.data),
+                                               ctypes.c_void_p(Y.ctypes.data), X.shape[0], ctypes.byref(loss),
+                                               ctypes.c_void_p(g.ctypes.data)), "tvbx_surrogate_gradients")
+        return loss.value, g
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            _check(load().tvbx_surrogate_destroy(self.h), "tvbx_surrogate_destroy")
+            self.h = None
