@@ -343,6 +343,31 @@ tvbx_status tvbx_fc_noalloc(const float* series, int32_t n_regions, int64_t n_se
 /* Release the handle and its device memory. NULL is accepted. */
 tvbx_status tvbx_sweep_destroy(tvbx_sweep* h);
 
+/* Principal components of FC matrices (the FC coefficients the surrogate
+ * predicts). fc: DEVICE [n_sets][n_regions][n_regions] Pearson FC (tvbx_fc
+ * or tvbx_fc_series layout). The upper triangles (k < j, row by row; M =
+ * n_regions (n_regions - 1) / 2 entries) are centred by their mean
+ * (mean_out, DEVICE [M]); the n_comp leading eigenvectors of their
+ * covariance matrix (comps_out, DEVICE [n_comp][M], orthonormal, largest
+ * eigenvalue first, largest-magnitude entry positive) come from n_iter steps
+ * of subspace iteration with n_comp + 12 vectors followed by a Rayleigh-Ritz
+ * step; eigvals_out (HOST [n_comp], nullable) receives the eigenvalues of
+ * the covariance (sum over sets / n_sets) and coef_out (DEVICE
+ * [n_sets][n_comp], nullable) the coefficients of each set. Scratch of
+ * n_sets * M + M * M floats is allocated on cuda_stream; the call
+ * synchronises it. Errors: TVBX_E_INVALID_ARG (3 <= n_regions <= 512,
+ * n_sets >= 2, 1 <= n_comp <= min(64, M), 1 <= n_iter <= 1000),
+ * TVBX_E_NUMERIC (the FC vectors span fewer than n_comp + 12 directions),
+ * TVBX_E_OOM, TVBX_E_CUDA. */
+tvbx_status tvbx_fc_pca(const float* fc, int32_t n_regions, int64_t n_sets, int32_t n_comp, int32_t n_iter,
+                        float* mean_out, float* comps_out, float* coef_out, float* eigvals_out,
+                        void* cuda_stream);
+
+/* Coefficients coef_out (DEVICE [n_sets][n_comp]) of further FC matrices fc
+ * (DEVICE) on a basis from tvbx_fc_pca (mean, comps: DEVICE). */
+tvbx_status tvbx_fc_pca_project(const float* fc, int32_t n_regions, int64_t n_sets, int32_t n_comp,
+                                const float* mean, const float* comps, float* coef_out, void* cuda_stream);
+
 /* ---- Surrogate network ---------------------------------------------------
  * The paper has no surrogate model; it motivates guided exploration of the
  * parameter space (Sec. "Discussion"). This is the learned form of the

@@ -89,7 +89,7 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_fc_noalloc", "tvbx_fc_series",
            "tvbx_sweep_destroy", "tvbx_surrogate_create", "tvbx_surrogate_info", "tvbx_surrogate_train",
            "tvbx_surrogate_predict", "tvbx_surrogate_propose", "tvbx_surrogate_params", "tvbx_surrogate_gradients",
-           "tvbx_surrogate_destroy")
+           "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project")
 
 
 def library_path() -> str:
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = False):
     L.tvbx_surrogate_params.argtypes = [vp, i32, fp, fp]
     L.tvbx_surrogate_gradients.argtypes = [vp, i32, fp, fp, i64, ctypes.POINTER(ctypes.c_float), fp]
     L.tvbx_surrogate_destroy.argtypes = [vp]
+    L.tvbx_fc_pca.argtypes = [fp, i32, i64, i32, i32, fp, fp, fp, fp, vp]
+    L.tvbx_fc_pca_project.argtypes = [fp, i32, i64, i32, fp, fp, fp, vp]
     L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.tvbx_profile_enable.argtypes = [vp, i32]
     L.tvbx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -461,6 +463,35 @@ class Sweep:
                 self.close()
         except Exception:
             pass
+
+
+def fc_pca(fc, n_comp=20, n_iter=40, stream=None):
+    """Principal components of device FC matrices [P][N][N] (tvbx_fc_pca):
+    returns (mean [M], comps [n_comp][M], coef [P][n_comp]) as CUDA tensors and
+    the eigenvalues (numpy)."""
+    import torch
+    P, N = fc.shape[0], fc.shape[1]
+    M = N * (N - 1) // 2
+    mean = torch.empty(M, dtype=torch.float32, device=fc.device)
+    comps = torch.empty((n_comp, M), dtype=torch.float32, device=fc.device)
+    coef = torch.empty((P, n_comp), dtype=torch.float32, device=fc.device)
+    ev = np.zeros(n_comp, dtype=np.float32)
+    sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(load().tvbx_fc_pca(ctypes.c_void_p(fc.data_ptr()), N, P, int(n_comp), int(n_iter),
+                              ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(comps.data_ptr()),
+                              ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(ev.ctypes.data), sp), "tvbx_fc_pca")
+    return mean, comps, coef, ev
+
+
+def fc_pca_project(fc, mean, comps, stream=None):
+    import torch
+    P, N = fc.shape[0], fc.shape[1]
+    coef = torch.empty((P, comps.shape[0]), dtype=torch.float32, device=fc.device)
+    sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(load().tvbx_fc_pca_project(ctypes.c_void_p(fc.data_ptr()), N, P, comps.shape[0],
+                                      ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(comps.data_ptr()),
+                                      ctypes.c_void_p(coef.data_ptr()), sp), "tvbx_fc_pca_project")
+    return coef
 
 
 class Surrogate:
