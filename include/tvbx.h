@@ -343,6 +343,53 @@ tvbx_status tvbx_fc_noalloc(const float* series, int32_t n_regions, int64_t n_se
 /* Release the handle and its device memory. NULL is accepted. */
 tvbx_status tvbx_sweep_destroy(tvbx_sweep* h);
 
+/* ---- Batches of sweeps ----------------------------------------------------
+ * Runs several sweeps -- different connectomes (region counts), durations,
+ * conduction speeds (delay horizons) and grids -- as one persistent kernel
+ * launch captured in a CUDA graph (the batched form of the lock-step
+ * integration of Eq. 1-5). Every (job, tile of sets) is a work item; CTAs
+ * take items from a global counter, most expensive first, and integrate the
+ * tile over the job's whole duration with the general kernel (state in
+ * shared memory, any region count). The graph holds the per-job state, ring
+ * and OU-table initialisation, the queue reset and the persistent kernel;
+ * one tvbx_batch_run is one graph launch. Each job's results are read
+ * through its own handle afterwards (tvbx_summary, tvbx_fc, tvbx_series ...),
+ * and equal those of tvbx_run with kernel = TVBX_KERNEL_GENERAL bit for bit
+ * (the tile width does not change any set's arithmetic). */
+typedef struct tvbx_batch tvbx_batch;
+
+/* jobs: n_jobs distinct sweep handles (borrowed: they must outlive the
+ * batch); cfgs: their run configurations (copied; kernel and chunk_steps are
+ * ignored, withhold_step must be 0, 1 <= n_steps < 2^31). Preparing a job
+ * handle again with tvbx_run makes the next tvbx_batch_run rebuild the
+ * graph. */
+tvbx_status tvbx_batch_create(tvbx_sweep* const* jobs, const tvbx_run_cfg* cfgs, int32_t n_jobs,
+                              tvbx_batch** out);
+
+/* Autotuner: builds and times (two graph launches each, CUDA events) the
+ * batch with each candidate tiling -- threads per CTA in {128, 256, 512}
+ * (regions per thread = ceil(N pb / threads)) and a shared-memory budget in
+ * {64, 100, 200} KB, which sets each job's sets per CTA pb in {32, 16, 8}
+ * (the widest whose state fits) and the CTAs per SM -- on runs shortened to
+ * trial_steps steps per job, keeps the fastest and rebuilds the full batch
+ * with it. threads_out, smem_kb_out: the choice; trial_ms [n_trials] (host,
+ * nullable; 6 entries, INFINITY where a candidate does not fit). */
+tvbx_status tvbx_batch_tune(tvbx_batch* b, int64_t trial_steps, int32_t* threads_out, int32_t* smem_kb_out,
+                            float* trial_ms, int32_t* n_trials);
+
+/* Run every job (one graph launch; the first call builds the graph with
+ * 512 threads and a 200 KB budget unless tvbx_batch_tune chose otherwise).
+ * The jobs' later calls run on the batch's stream. Synchronises it. */
+tvbx_status tvbx_batch_run(tvbx_batch* b);
+
+/* Current tiling, work items, persistent grid size and graph nodes. */
+tvbx_status tvbx_batch_info(const tvbx_batch* b, int32_t* threads, int32_t* smem_kb, int64_t* n_items,
+                            int32_t* grid, int64_t* graph_nodes);
+
+/* Release the batch (not its jobs; they keep their results and use the
+ * default stream from then on). NULL is accepted. */
+tvbx_status tvbx_batch_destroy(tvbx_batch* b);
+
 /* Principal components of FC matrices (the FC coefficients the surrogate
  * predicts). fc: DEVICE [n_sets][n_regions][n_regions] Pearson FC (tvbx_fc
  * or tvbx_fc_series layout). The upper triangles (k < j, row by row; M =

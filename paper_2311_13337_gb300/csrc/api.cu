@@ -211,6 +211,7 @@ struct tvbx_sweep {
     bool identity = true;
     int32_t pb = 16;
     int32_t variant = -1;           // simulation kernel of the last run
+    uint64_t gen = 0;               // incremented by every run preparation
 
     DevBuf d_prm, d_ext, d_state, d_status, d_ring, d_series, d_ou_table, d_ou_state;
     DevBuf d_csr_row, d_csr_cd, d_csr_w, d_groups, d_tiles;
@@ -488,10 +489,26 @@ tvbx_status tvbx_sweep_info(const tvbx_sweep* h, int64_t* n_sets, int32_t* n_reg
     return TVBX_OK;
 }
 
-tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
+// Everything a run needs before its first simulation launch: argument
+// checks, delay groups, internal set order, kernel and tile choice, device
+// buffers and uploads; with device_init also the state and ring
+// initialisation on stream s. general_pb > 0 forces the general kernel with
+// that tile width (used by batches).
+struct RunPlan {
+    SimArgs a;
+    int variant = -1;
+    int pb = 16;
+    int32_t n_tiles = 0;
+    int nnz_max = 0;
+    int64_t chunk = 0;
+    std::vector<GroupDev> gdev;
+    std::vector<TileDev> tiles;
+    std::vector<int64_t> tile_nnz;   // weights per row of the tile's group (cost model)
+};
+
+static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_t s, int general_pb,
+                               bool device_init, RunPlan& plan)
 {
-    if (!h || !cfg) return fail(TVBX_E_INVALID_ARG, "NULL handle or cfg");
-    const tvbx_run_cfg c = *cfg;
     if (!(c.dt_ms > 0.0) || !isfinite(c.dt_ms)) return fail(TVBX_E_INVALID_ARG, "dt_ms must be > 0");
     if (c.n_steps < 0 || c.n_steps > ((int64_t)1 << 32) - 2)
         return fail(TVBX_E_INVALID_ARG, "n_steps must be in [0, 2^32 - 1)");
@@ -502,10 +519,10 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     if (c.transient_samples < 0 || (T > 0 && c.transient_samples >= T))
         return fail(TVBX_E_INVALID_ARG, "transient_samples must be in [0, n_samples)");
     if (c.p_offset < 0) return fail(TVBX_E_INVALID_ARG, "p_offset must be >= 0");
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     h->stream = s;
     h->ran = false;
     h->fc_valid = false;
+    h->gen += 1;
 
     std::vector<Group> groups;
     tvbx_status st = build_groups(h, c.dt_ms, groups);
@@ -541,7 +558,9 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         return fail(TVBX_E_INVALID_ARG, "unknown kernel %d", c.kernel);
     if (c.withhold_step < 0) return fail(TVBX_E_INVALID_ARG, "withhold_step must be >= 0");
     int variant = -1;   // prefetch variant, -1 = general kernel
-    if (c.kernel == TVBX_KERNEL_AUTO) {
+    if (general_pb > 0) {
+        // batch: general kernel with the batch's tile width
+    } else if (c.kernel == TVBX_KERNEL_AUTO) {
         // preference order from measurement on the 32,768-set, 68-region sweep
         for (int v : {1, 0, 2, 3})
             if (sim_fast_fits(v, N, nnz_max)) { variant = v; break; }
@@ -552,7 +571,10 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
                         nnz_max);
     }
     int pb = 16;
-    if (variant >= 0) {
+    if (general_pb > 0) {
+        pb = general_pb;
+        if (sim_smem_bytes(N, pb) > 227 * 1024) return fail(TVBX_E_UNSUPPORTED, "n_regions %d too large", N);
+    } else if (variant >= 0) {
         pb = sim_fast_pb(variant);
     } else {
         while (pb > 8 && sim_smem_bytes(N, pb) > 200 * 1024) pb /= 2;
@@ -575,7 +597,10 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
         all_cd.insert(all_cd.end(), g.col_dly.begin(), g.col_dly.end());
         all_w.insert(all_w.end(), g.w.begin(), g.w.end());
         const int32_t Pg = (int32_t)g.sets.size();
-        for (int32_t q0 = 0; q0 < Pg; q0 += pb) tiles.push_back(TileDev{(int32_t)gi, q0, std::min(pb, Pg - q0), 0});
+        for (int32_t q0 = 0; q0 < Pg; q0 += pb) {
+            tiles.push_back(TileDev{(int32_t)gi, q0, std::min(pb, Pg - q0), 0});
+            plan.tile_nnz.push_back((int64_t)g.col_dly.size());
+        }
     }
     if (all_cd.empty()) { all_cd.push_back(0); all_w.push_back(0.f); }
 
@@ -660,9 +685,43 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
     a.seed = c.seed;
     a.p_offset = c.p_offset;
 
-    CK(launch_init_state(a, s), "init state");
-    for (size_t gi = 0; gi < groups.size(); ++gi)
-        CK(launch_init_ring(gdev[gi].ring, (int64_t)gdev[gi].H * N * gdev[gi].stride, a.m.E0, s), "init ring");
+    if (device_init) {
+        CK(launch_init_state(a, s), "init state");
+        for (size_t gi = 0; gi < groups.size(); ++gi)
+            CK(launch_init_ring(gdev[gi].ring, (int64_t)gdev[gi].H * N * gdev[gi].stride, a.m.E0, s), "init ring");
+    }
+    plan.a = a;
+    plan.variant = variant;
+    plan.pb = pb;
+    plan.n_tiles = (int32_t)tiles.size();
+    plan.nnz_max = nnz_max;
+    plan.chunk = chunk;
+    plan.gdev = gdev;
+    plan.tiles = tiles;
+    return TVBX_OK;
+}
+
+// Mark a handle's run as complete (results may be read).
+static void finish_run(tvbx_sweep* h, const tvbx_run_cfg& c)
+{
+    h->cfg = c;
+    h->T = c.n_steps / c.tavg_steps;
+    h->ran = true;
+}
+
+tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
+{
+    if (!h || !cfg) return fail(TVBX_E_INVALID_ARG, "NULL handle or cfg");
+    const tvbx_run_cfg c = *cfg;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    RunPlan plan;
+    tvbx_status st = prepare_run(h, c, s, 0, true, plan);
+    if (st != TVBX_OK) return st;
+    SimArgs a = plan.a;
+    const int N = h->N;
+    const int64_t P = h->P;
+    const int64_t chunk = plan.chunk;
+    const int variant = plan.variant;
     for (int64_t n0 = 0; n0 < c.n_steps; n0 += chunk) {
         a.n0 = n0;
         a.n_chunk = (int32_t)std::min<int64_t>(chunk, c.n_steps - n0);
@@ -677,17 +736,15 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
             }
             CK(cudaEventRecord(h->ev[h->ev_used], s), "profiling event");
         }
-        if (variant >= 0) CK(launch_sim_fast(a, variant, (int32_t)tiles.size(), nnz_max, s), "simulation chunk");
-        else CK(launch_sim_chunk(a, (int32_t)tiles.size(), pb, s), "simulation chunk");
+        if (variant >= 0) CK(launch_sim_fast(a, variant, plan.n_tiles, plan.nnz_max, s), "simulation chunk");
+        else CK(launch_sim_chunk(a, plan.n_tiles, plan.pb, s), "simulation chunk");
         if (h->profiling) {
             CK(cudaEventRecord(h->ev[h->ev_used + 1], s), "profiling event");
             h->ev_used += 2;
             h->prof_region_steps += (double)P * N * a.n_chunk;
         }
     }
-    h->cfg = c;
-    h->T = T;
-    h->ran = true;
+    finish_run(h, c);
     return TVBX_OK;
 }
 
@@ -1092,6 +1149,312 @@ tvbx_status tvbx_sweep_destroy(tvbx_sweep* h)
     if (!h) return TVBX_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     delete h;
+    return TVBX_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of sweeps: one persistent launch, captured in a CUDA graph
+// ---------------------------------------------------------------------------
+struct tvbx_batch {
+    std::vector<tvbx_sweep*> jobs;
+    std::vector<tvbx_run_cfg> cfgs;
+    std::vector<uint64_t> gens;     // generation of each job when the graph was built
+    std::vector<tvbx_run_cfg> cfgs_run;   // configurations the graph runs (trial runs are shorter)
+    cudaStream_t stream = nullptr;
+    int32_t threads = 512;
+    size_t smem_budget = 200 * 1024;
+    DevBuf d_jobs, d_items, d_head, d_ou;
+    int32_t n_items = 0, grid = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_nodes = 0, graph_kernels = 0;
+    bool built = false;
+
+    void drop_graph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        built = false;
+    }
+    ~tvbx_batch()
+    {
+        drop_graph();
+        d_jobs.release();
+        d_items.release();
+        d_head.release();
+        d_ou.release();
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+// Tile width of a job under a shared-memory budget: the widest of 32, 16, 8
+// sets whose state fits.
+int batch_pb(int N, size_t budget, int threads)
+{
+    for (int pb : {32, 16, 8})
+        if (sim_smem_bytes(N, pb) <= budget && threads % pb == 0) return pb;
+    return 0;
+}
+
+// Prepare every job (tile width from the budget; trial_steps > 0 shortens
+// each job), build the LPT-ordered work list, and capture the device work of
+// one run -- per-job state, ring and OU-table initialisation, the queue reset
+// and the persistent kernel -- in a CUDA graph.
+// Work enqueued on a job's own stream must finish before the batch's stream
+// (non-blocking: it does not order with the legacy default stream) touches
+// the job's buffers.
+tvbx_status batch_adopt_jobs(tvbx_batch* b)
+{
+    for (tvbx_sweep* h : b->jobs)
+        if (h->stream != b->stream) {
+            CK(cudaStreamSynchronize(h->stream), "job stream");
+            h->stream = b->stream;
+        }
+    return TVBX_OK;
+}
+
+tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t trial_steps)
+{
+    b->drop_graph();
+    if (tvbx_status st = batch_adopt_jobs(b)) return st;
+    const size_t nj = b->jobs.size();
+    std::vector<RunPlan> plans(nj);
+    std::vector<tvbx_run_cfg> run_cfgs(b->cfgs);
+    std::vector<int> pbs(nj);
+    size_t smem = 0;
+    int64_t ou_floats = 0;
+    std::vector<int64_t> ou_off(nj, -1);
+    for (size_t j = 0; j < nj; ++j) {
+        tvbx_run_cfg& c = run_cfgs[j];
+        if (trial_steps > 0) {   // timing run only: shortened, no transient
+            c.n_steps = std::min<int64_t>(c.n_steps, std::max<int64_t>(trial_steps / c.tavg_steps, 1) * c.tavg_steps);
+            c.transient_samples = 0;
+        }
+        if (c.n_steps > INT32_MAX) return fail(TVBX_E_INVALID_ARG, "batch job %zu: n_steps must be < 2^31", j);
+        const int pb = batch_pb(b->jobs[j]->N, budget, threads);
+        if (!pb) return fail(TVBX_E_UNSUPPORTED, "batch job %zu: %d regions do not fit %zu bytes of shared memory", j,
+                             b->jobs[j]->N, budget);
+        pbs[j] = pb;
+        smem = std::max(smem, sim_smem_bytes(b->jobs[j]->N, pb));
+        c.chunk_steps = 0;
+        tvbx_status st = prepare_run(b->jobs[j], c, b->stream, pb, false, plans[j]);
+        if (st != TVBX_OK) return st;
+        if (!c.noise_per_set) {
+            ou_off[j] = ou_floats;
+            ou_floats += ((int64_t)c.n_steps * b->jobs[j]->N + 63) / 64 * 64;
+        }
+    }
+    CK(b->d_ou.ensure(sizeof(float) * (size_t)std::max<int64_t>(ou_floats, 1)), "batch OU tables");
+    std::vector<BatchJob> jobs(nj);
+    struct Cost { double c; int32_t job, tile; };
+    std::vector<Cost> costs;
+    for (size_t j = 0; j < nj; ++j) {
+        SimArgs a = plans[j].a;
+        a.n0 = 0;
+        a.n_chunk = (int32_t)run_cfgs[j].n_steps;
+        a.ou_table = ou_off[j] >= 0 ? b->d_ou.as<float>() + ou_off[j] : nullptr;
+        jobs[j] = BatchJob{a, pbs[j]};
+        const int N = b->jobs[j]->N;
+        for (int32_t t = 0; t < plans[j].n_tiles; ++t) {
+            const double per_step = (double)N * 40.0 + (double)plans[j].tile_nnz[t];   // TF work + gathers
+            costs.push_back(Cost{per_step * (double)run_cfgs[j].n_steps * plans[j].tiles[t].nq, (int32_t)j, t});
+        }
+    }
+    std::stable_sort(costs.begin(), costs.end(), [](const Cost& x, const Cost& y) { return x.c > y.c; });
+    std::vector<BatchItem> items(costs.size());
+    for (size_t i = 0; i < costs.size(); ++i) items[i] = BatchItem{costs[i].job, costs[i].tile};
+    b->n_items = (int32_t)items.size();
+    CK(b->d_jobs.ensure(sizeof(BatchJob) * nj), "batch jobs");
+    CK(b->d_items.ensure(sizeof(BatchItem) * std::max<size_t>(items.size(), 1)), "batch items");
+    CK(b->d_head.ensure(sizeof(int32_t)), "batch queue");
+    CK(cudaMemcpyAsync(b->d_jobs.ptr, jobs.data(), sizeof(BatchJob) * nj, cudaMemcpyHostToDevice, b->stream), "upload");
+    if (!items.empty())
+        CK(cudaMemcpyAsync(b->d_items.ptr, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                           b->stream),
+           "upload");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev), "device");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
+    const int per_sm = sim_batch_ctas_per_sm(threads, smem);
+    if (per_sm < 1) return fail(TVBX_E_UNSUPPORTED, "batch kernel does not fit %d threads / %zu bytes", threads, smem);
+    b->grid = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (int64_t)items.size()));
+    b->threads = threads;
+    b->smem_budget = budget;
+    CK(cudaStreamSynchronize(b->stream), "batch upload");
+
+    // capture the device work of one run
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    cudaError_t ce = cudaSuccess;
+    int64_t kernels = 0;
+    for (size_t j = 0; j < nj && ce == cudaSuccess; ++j) {
+        tvbx_sweep* h = b->jobs[j];
+        const SimArgs& a = jobs[j].a;
+        if ((ce = cudaMemsetAsync(h->d_error.ptr, 0, sizeof(uint32_t), b->stream)) != cudaSuccess) break;
+        if ((ce = launch_init_state(a, b->stream)) != cudaSuccess) break;
+        ++kernels;
+        for (const GroupDev& g : plans[j].gdev) {
+            if ((ce = launch_init_ring(g.ring, (int64_t)g.H * h->N * g.stride, a.m.E0, b->stream)) != cudaSuccess) break;
+            ++kernels;
+        }
+        if (ce != cudaSuccess) break;
+        if (a.ou_table) {
+            if ((ce = cudaMemsetAsync(h->d_ou_state.ptr, 0, sizeof(float) * h->N, b->stream)) != cudaSuccess) break;
+            if ((ce = launch_ou_table(a.m, const_cast<float*>(a.ou_table), h->d_ou_state.as<float>(), h->N, 0,
+                                      a.n_chunk, a.seed, b->stream)) != cudaSuccess)
+                break;
+            ++kernels;
+        }
+    }
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_head.ptr, 0, sizeof(int32_t), b->stream);
+    if (ce == cudaSuccess && b->n_items > 0) {
+        ce = launch_sim_batch(b->d_jobs.as<BatchJob>(), b->d_items.as<BatchItem>(), b->n_items,
+                              b->d_head.as<int32_t>(), b->grid, threads, smem, b->stream);
+        ++kernels;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        return cuda_fail(ce != cudaSuccess ? ce : ee, "batch graph capture");
+    }
+    b->graph = g;
+    CK(cudaGraphInstantiate(&b->exec, g, 0), "batch graph instantiate");
+    size_t nodes = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &nodes), "batch graph");
+    b->graph_nodes = (int64_t)nodes;
+    b->graph_kernels = kernels;
+    b->cfgs_run = run_cfgs;
+    b->gens.resize(nj);
+    for (size_t j = 0; j < nj; ++j) b->gens[j] = b->jobs[j]->gen;
+    b->built = true;
+    return TVBX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tvbx_status tvbx_batch_create(tvbx_sweep* const* jobs, const tvbx_run_cfg* cfgs, int32_t n_jobs, tvbx_batch** out)
+{
+    if (!jobs || !cfgs || !out || n_jobs < 1) return fail(TVBX_E_INVALID_ARG, "need jobs, cfgs, out and n_jobs >= 1");
+    *out = nullptr;
+    for (int32_t j = 0; j < n_jobs; ++j) {
+        if (!jobs[j]) return fail(TVBX_E_INVALID_ARG, "job %d: NULL handle", j);
+        for (int32_t i = 0; i < j; ++i)
+            if (jobs[i] == jobs[j]) return fail(TVBX_E_INVALID_ARG, "job %d repeats job %d", j, i);
+        const tvbx_run_cfg& c = cfgs[j];
+        if (!(c.dt_ms > 0.0) || c.tavg_steps < 1 || c.n_steps < 1 || c.n_steps > INT32_MAX)
+            return fail(TVBX_E_INVALID_ARG, "job %d: need dt_ms > 0, tavg_steps >= 1, 1 <= n_steps < 2^31", j);
+        if (c.withhold_step != 0) return fail(TVBX_E_INVALID_ARG, "job %d: withhold_step is not used by batches", j);
+    }
+    auto* b = new tvbx_batch;
+    b->jobs.assign(jobs, jobs + n_jobs);
+    b->cfgs.assign(cfgs, cfgs + n_jobs);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "batch stream");
+    }
+    *out = b;
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_batch_tune(tvbx_batch* b, int64_t trial_steps, int32_t* threads_out, int32_t* smem_kb_out,
+                            float* trial_ms, int32_t* n_trials)
+{
+    if (!b) return fail(TVBX_E_INVALID_ARG, "NULL batch");
+    if (trial_steps < 1) return fail(TVBX_E_INVALID_ARG, "trial_steps must be >= 1");
+    struct Cand { int32_t threads; size_t budget; };
+    const Cand cands[] = {{256, 100 * 1024}, {512, 100 * 1024}, {256, 200 * 1024}, {512, 200 * 1024},
+                          {128, 64 * 1024}, {256, 64 * 1024}};
+    float best = INFINITY;
+    Cand win{0, 0};
+    int32_t k = 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    for (const Cand& c : cands) {
+        float ms = INFINITY;
+        if (batch_build(b, c.threads, c.budget, trial_steps) == TVBX_OK) {
+            cudaError_t e = cudaGraphLaunch(b->exec, b->stream);   // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(e, "batch trial");
+            }
+            note_launch(2 * b->graph_kernels);
+        } else {
+            (void)cudaGetLastError();
+        }
+        if (trial_ms) trial_ms[k] = ms;
+        ++k;
+        if (ms < best) { best = ms; win = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!(best < INFINITY)) return fail(TVBX_E_UNSUPPORTED, "no batch configuration fits every job");
+    if (n_trials) *n_trials = k;
+    tvbx_status st = batch_build(b, win.threads, win.budget, 0);
+    if (st != TVBX_OK) return st;
+    if (threads_out) *threads_out = win.threads;
+    if (smem_kb_out) *smem_kb_out = (int32_t)(win.budget / 1024);
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_batch_run(tvbx_batch* b)
+{
+    if (!b) return fail(TVBX_E_INVALID_ARG, "NULL batch");
+    if (tvbx_status st = batch_adopt_jobs(b)) return st;
+    bool stale = !b->built;
+    for (size_t j = 0; j < b->jobs.size() && !stale; ++j) stale = b->jobs[j]->gen != b->gens[j];
+    for (size_t j = 0; j < b->jobs.size() && !stale; ++j) stale = b->cfgs_run[j].n_steps != b->cfgs[j].n_steps;
+    if (stale) {
+        tvbx_status st = batch_build(b, b->threads, b->smem_budget, 0);
+        if (st != TVBX_OK) return st;
+    }
+    CK(cudaGraphLaunch(b->exec, b->stream), "batch launch");
+    note_launch(b->graph_kernels);
+    for (size_t j = 0; j < b->jobs.size(); ++j) {
+        b->jobs[j]->stream = b->stream;
+        finish_run(b->jobs[j], b->cfgs_run[j]);
+    }
+    CK(cudaStreamSynchronize(b->stream), "batch run");
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_batch_info(const tvbx_batch* b, int32_t* threads, int32_t* smem_kb, int64_t* n_items, int32_t* grid,
+                            int64_t* graph_nodes)
+{
+    if (!b) return fail(TVBX_E_INVALID_ARG, "NULL batch");
+    if (threads) *threads = b->threads;
+    if (smem_kb) *smem_kb = (int32_t)(b->smem_budget / 1024);
+    if (n_items) *n_items = b->n_items;
+    if (grid) *grid = b->grid;
+    if (graph_nodes) *graph_nodes = b->graph_nodes;
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_batch_destroy(tvbx_batch* b)
+{
+    if (!b) return TVBX_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    // the jobs ran on the batch's stream: hand them back to the default
+    // stream before that stream is destroyed
+    for (tvbx_sweep* h : b->jobs)
+        if (h->stream == b->stream) h->stream = nullptr;
+    delete b;
     return TVBX_OK;
 }
 

@@ -116,6 +116,19 @@ int sim_threads(int N, int pb);
 size_t sim_smem_bytes(int N, int pb);
 
 // FC (fc.cu).
+// One job of a batch (device): its SimArgs cover all steps (n0 = 0,
+// n_chunk = n_steps, OU table for every step); pb = its tile width.
+struct BatchJob {
+    SimArgs a;
+    int32_t pb;
+};
+struct BatchItem {
+    int32_t job, tile;
+};
+cudaError_t launch_sim_batch(const BatchJob* jobs, const BatchItem* items, int32_t n_items, int32_t* head,
+                             int32_t grid, int32_t threads, size_t smem, cudaStream_t s);
+int sim_batch_ctas_per_sm(int32_t threads, size_t smem);
+
 struct FcArgs {
     const float* series;       // [T][N][P]
     const float* state;        // [SV_COUNT][N][P] (running sums give the shift)

@@ -82,27 +82,28 @@ __global__ void ou_table_kernel(DevModel m, float* __restrict__ table, float* __
 // its sets is one contiguous segment). A CTA barrier separates steps: all
 // cross-region reads stay inside the CTA's own sets.
 // ---------------------------------------------------------------------------
+// One tile of PB sets (PB a template constant or, with PB = 0, the runtime
+// width pb) for a.n_chunk steps from step a.n0. st: shared memory
+// [SV_COUNT][N][pb].
 template <int PB>
-__global__ void __launch_bounds__(512)
-sim_chunk_kernel(const __grid_constant__ SimArgs a)
+static __device__ __forceinline__ void chunk_body(const SimArgs& a, const TileDev tile, int pb_rt, float* st)
 {
-    extern __shared__ float st[];  // [SV_COUNT][N][PB]
-    const TileDev tile = a.tiles[blockIdx.x];
+    const int pb = PB > 0 ? PB : pb_rt;
     const GroupDev grp = a.groups[tile.group];
     const DevModel& m = a.m;
     const int N = a.N;
     const int P = a.P;
-    const int npairs = N * PB;
+    const int npairs = N * pb;
 
     for (int i = threadIdx.x; i < SV_COUNT * npairs; i += blockDim.x) {
-        const int v = i / npairs, rem = i - v * npairs, k = rem / PB, q = rem - k * PB;
+        const int v = i / npairs, rem = i - v * npairs, k = rem / pb, q = rem - k * pb;
         st[i] = q < tile.nq ? a.state[((int64_t)v * N + k) * P + grp.p_base + tile.q0 + q] : 0.0f;
     }
     __syncthreads();
 
-    const int q = threadIdx.x % PB;
-    const int kstart = threadIdx.x / PB;
-    const int kstride = blockDim.x / PB;
+    const int q = threadIdx.x % pb;
+    const int kstart = threadIdx.x / pb;
+    const int kstride = blockDim.x / pb;
     const bool active = q < tile.nq;
     const int qg = tile.q0 + q;           // column in the group's ring
     const int p = grp.p_base + qg;        // internal set index
@@ -134,7 +135,7 @@ sim_chunk_kernel(const __grid_constant__ SimArgs a)
                     sl += sl < 0 ? grp.H : 0;
                     acc = fmaf(__ldg(grp.w + e), grp.ring[sl * slot_stride + (int64_t)j * grp.stride + qg], acc);
                 }
-                float* sk = st + k * PB + q;
+                float* sk = st + k * pb + q;
                 PairState x{sk[SV_E * npairs], sk[SV_I * npairs], sk[SV_CEE * npairs], sk[SV_CEI * npairs],
                             sk[SV_CII * npairs], sk[SV_WE * npairs], sk[SV_WI * npairs]};
                 const float OU = a.noise_per_set ? sk[SV_OU * npairs] : a.ou_table[(int64_t)s * N + k];
@@ -171,10 +172,46 @@ sim_chunk_kernel(const __grid_constant__ SimArgs a)
     }
 
     for (int i = threadIdx.x; i < SV_COUNT * npairs; i += blockDim.x) {
-        const int v = i / npairs, rem = i - v * npairs, k = rem / PB, qq = rem - k * PB;
+        const int v = i / npairs, rem = i - v * npairs, k = rem / pb, qq = rem - k * pb;
         if (qq < tile.nq) a.state[((int64_t)v * N + k) * P + grp.p_base + tile.q0 + qq] = st[i];
     }
     if (active && flags) atomicOr(a.status + p, flags);
+}
+
+template <int PB>
+__global__ void __launch_bounds__(512)
+sim_chunk_kernel(const __grid_constant__ SimArgs a)
+{
+    extern __shared__ float st[];  // [SV_COUNT][N][PB]
+    chunk_body<PB>(a, a.tiles[blockIdx.x], PB, st);
+}
+
+// Persistent kernel of a batch of sweeps (any region counts, durations and
+// delay horizons): each CTA takes work items (job, tile) from a global
+// counter, most expensive first, and integrates the tile over the job's
+// whole duration (the job's SimArgs have n0 = 0, n_chunk = n_steps and an OU
+// table for all steps). The tile width pb is per job.
+__global__ void __launch_bounds__(512)
+sim_batch_kernel(const BatchJob* __restrict__ jobs, const BatchItem* __restrict__ items, int32_t n_items,
+                 int32_t* __restrict__ head)
+{
+    extern __shared__ float st[];
+    __shared__ int s_item;
+    __shared__ BatchJob s_job;   // the item's job descriptor, read once per item
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const BatchItem bi = items[it];
+        static_assert(sizeof(BatchJob) % 4 == 0, "BatchJob copied as words");
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(jobs + bi.job);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_job);
+        for (int w = threadIdx.x; w < (int)(sizeof(BatchJob) / 4); w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        chunk_body<0>(s_job.a, s_job.a.tiles[bi.tile], s_job.pb, st);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -258,6 +295,25 @@ cudaError_t launch_sim_chunk(const SimArgs& a, int32_t n_tiles, int32_t pb, cuda
     case 32: return launch_sim_pb<32>(a, n_tiles, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_sim_batch(const BatchJob* jobs, const BatchItem* items, int32_t n_items, int32_t* head,
+                             int32_t grid, int32_t threads, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(sim_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    sim_batch_kernel<<<grid, threads, smem, s>>>(jobs, items, n_items, head);
+    return cudaGetLastError();
+}
+
+int sim_batch_ctas_per_sm(int32_t threads, size_t smem)
+{
+    int n = 0;
+    if (cudaFuncSetAttribute(sim_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_batch_kernel, threads, smem) != cudaSuccess) return 0;
+    return n;
 }
 
 cudaError_t launch_tf_eval(const DevModel& m, int pop, int64_t n, const float* x_e, const float* x_i,

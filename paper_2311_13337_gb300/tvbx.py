@@ -89,7 +89,8 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_fc_noalloc", "tvbx_fc_series",
            "tvbx_sweep_destroy", "tvbx_surrogate_create", "tvbx_surrogate_info", "tvbx_surrogate_train",
            "tvbx_surrogate_predict", "tvbx_surrogate_propose", "tvbx_surrogate_params", "tvbx_surrogate_gradients",
-           "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project")
+           "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project", "tvbx_batch_create", "tvbx_batch_tune",
+           "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy")
 
 
 def library_path() -> str:
@@ -136,6 +137,12 @@ def load(build_if_missing: bool = False):
     L.tvbx_surrogate_params.argtypes = [vp, i32, fp, fp]
     L.tvbx_surrogate_gradients.argtypes = [vp, i32, fp, fp, i64, ctypes.POINTER(ctypes.c_float), fp]
     L.tvbx_surrogate_destroy.argtypes = [vp]
+    L.tvbx_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(RunCfg), i32, ctypes.POINTER(vp)]
+    L.tvbx_batch_tune.argtypes = [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i32), fp, ctypes.POINTER(i32)]
+    L.tvbx_batch_run.argtypes = [vp]
+    L.tvbx_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                  ctypes.POINTER(i32), ctypes.POINTER(i64)]
+    L.tvbx_batch_destroy.argtypes = [vp]
     L.tvbx_fc_pca.argtypes = [fp, i32, i64, i32, i32, fp, fp, fp, fp, vp]
     L.tvbx_fc_pca_project.argtypes = [fp, i32, i64, i32, fp, fp, fp, vp]
     L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
@@ -251,12 +258,18 @@ KERNEL_AUTO, KERNEL_GENERAL, KERNEL_PREFETCH = 0, 1, 2
 N_PREFETCH_VARIANTS = 8
 
 
+def _run_cfg(dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
+             transient_samples=0, chunk_steps=0, kernel=KERNEL_AUTO, withhold_step=0) -> RunCfg:
+    return RunCfg(float(dt_ms), int(n_steps), int(tavg_steps), int(bool(noise_per_set)), int(seed),
+                  int(p_offset), int(transient_samples), int(chunk_steps), int(kernel), int(withhold_step))
+
+
 def run(h, dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
         transient_samples=0, chunk_steps=0, stream=None, kernel=KERNEL_AUTO, withhold_step=0):
     """Enqueue the integration on `stream` (a torch.cuda.Stream, a raw handle
     or None for the default stream)."""
-    cfg = RunCfg(float(dt_ms), int(n_steps), int(tavg_steps), int(bool(noise_per_set)), int(seed),
-                 int(p_offset), int(transient_samples), int(chunk_steps), int(kernel), int(withhold_step))
+    cfg = _run_cfg(dt_ms, n_steps, tavg_steps, seed, noise_per_set, p_offset, transient_samples, chunk_steps,
+                   kernel, withhold_step)
     sp = None
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -575,4 +588,43 @@ class Surrogate:
     def close(self):
         if self.h is not None and self.h.value:
             _check(load().tvbx_surrogate_destroy(self.h), "tvbx_surrogate_destroy")
+            self.h = None
+
+
+class Batch:
+    """Several sweeps run as one persistent launch in a CUDA graph
+    (tvbx_batch_*). jobs: list of (Sweep, dict of run settings)."""
+
+    def __init__(self, jobs):
+        self.sweeps = [sw for sw, _ in jobs]
+        handles = (ctypes.c_void_p * len(jobs))(*[sw.h.value for sw in self.sweeps])
+        cfgs = (RunCfg * len(jobs))(*[_run_cfg(**kw) for _, kw in jobs])
+        self._keep = (handles, cfgs)
+        self.h = ctypes.c_void_p()
+        _check(load().tvbx_batch_create(ctypes.cast(handles, ctypes.POINTER(ctypes.c_void_p)), cfgs, len(jobs),
+                                        ctypes.byref(self.h)), "tvbx_batch_create")
+        for sw, kw in jobs:
+            sw._transient = int(kw.get("transient_samples", 0))
+
+    def tune(self, trial_steps=200):
+        t, k, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ms = np.zeros(16, dtype=np.float32)
+        _check(load().tvbx_batch_tune(self.h, int(trial_steps), ctypes.byref(t), ctypes.byref(k),
+                                      ctypes.c_void_p(ms.ctypes.data), ctypes.byref(n)), "tvbx_batch_tune")
+        return t.value, k.value, ms[:n.value]
+
+    def run(self):
+        _check(load().tvbx_batch_run(self.h), "tvbx_batch_run")
+        return self
+
+    def info(self) -> dict:
+        t, k, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        n, nodes = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().tvbx_batch_info(self.h, ctypes.byref(t), ctypes.byref(k), ctypes.byref(n), ctypes.byref(g),
+                                      ctypes.byref(nodes)), "tvbx_batch_info")
+        return {"threads": t.value, "smem_kb": k.value, "items": n.value, "grid": g.value, "graph_nodes": nodes.value}
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            _check(load().tvbx_batch_destroy(self.h), "tvbx_batch_destroy")
             self.h = None
