@@ -573,6 +573,98 @@ def run_fc_engine(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Uneven batch: 20 sweeps of 68/84/192/360 regions x speeds 1-16 m/s, grids
+# 8x8 - 64x64 (g x b_e), durations (1, 2, 5, 10, 20) s x --batch-scale.
+BATCH_METRIC = "region-steps/s on 1 GB300, uneven batch of sweeps (batched vs plain)"
+
+
+def batch_jobs(scale):
+    Ns, vs, sides, durs = [68, 84, 192, 360], [1.0, 2.0, 4.0, 8.0, 16.0], [8, 16, 32, 64], [1, 2, 5, 10, 20]
+    jobs = []
+    for j in range(20):
+        N, v, side, dur = Ns[j // 5], vs[j % 5], sides[j % 4], durs[j % 5]
+        steps = max(10, int(round(dur * 10000 * scale / 10.0)) * 10)
+        jobs.append(dict(N=N, v=v, side=side, steps=steps))
+    return jobs
+
+
+def run_batch_engine(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2311_13337_gb300 import synth, tvbx
+    m = tvbx.make_model()
+    specs = batch_jobs(args.batch_scale)
+    sweeps, kws = [], []
+    total_rs = 0.0
+    for sp in specs:
+        W, L = synth.connectome(sp["N"])
+        g = np.linspace(0.0, 0.9, sp["side"])
+        be = np.linspace(0.0, 120.0, sp["side"])
+        pts = np.tile(np.array([m.defaults[i] for i in range(tvbx.N_AXES)]), (sp["side"] ** 2, 1))
+        pts[:, tvbx.AXES.index("g")] = np.repeat(g, sp["side"])
+        pts[:, tvbx.AXES.index("b_e")] = np.tile(be, sp["side"])
+        pts[:, tvbx.AXES.index("speed")] = sp["v"]
+        sweeps.append(tvbx.Sweep(W, L, points=pts))
+        kws.append(dict(dt_ms=0.1, n_steps=sp["steps"], tavg_steps=10, seed=1))
+        total_rs += float(sp["side"] ** 2) * sp["N"] * sp["steps"]
+
+    def plain(kernel):
+        for sw, kw in zip(sweeps, kws):
+            tvbx.run(sw.h, kernel=kernel, **kw)
+        torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        fn()   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    b = tvbx.Batch(list(zip(sweeps, kws)))
+    t0 = time.perf_counter()
+    threads, smem_kb, trials = b.tune(trial_steps=200)
+    tune_s = time.perf_counter() - t0
+    for _ in range(max(args.warmup - 1, 0)):
+        b.run()
+    launches0 = tvbx.launch_count()
+    sampler = start_clock_sampler(0)
+    t_batch = timed(b.run, args.steps)
+    clocks = stop_clock_sampler(sampler)
+    launches = (tvbx.launch_count() - launches0) / (args.steps + 1)
+    fc_batch = sweeps[3].fc(precision=tvbx.FC_FP32)          # the 64 x 64, 68-region job
+    X_batch = sweeps[3].series()
+    t_general = timed(lambda: plain(tvbx.KERNEL_GENERAL), 1)
+    X_general = sweeps[3].series()
+    t_auto = timed(lambda: plain(tvbx.KERNEL_AUTO), 1)
+    fc_auto = sweeps[3].fc(precision=tvbx.FC_FP32)
+    fin = np.all(np.isfinite(fc_auto), axis=(1, 2)) & np.all(np.isfinite(fc_batch), axis=(1, 2))
+    line = {"metric": BATCH_METRIC, "value": total_rs / t_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "uneven batch: 20 sweeps, N in {68,84,192,360} x v in {1,2,4,8,16} m/s, "
+                                   "g x b_e grids side (8,16,32,64)[j mod 4], durations (1,2,5,10,20)[j mod 5] s x "
+                                   f"{args.batch_scale}", "duration_scale": args.batch_scale,
+                       "region_steps_per_step": total_rs, "jobs": specs},
+            "clocks": clocks, "gpu_launches": launches,
+            "batched": {"s": t_batch, "region_steps_per_s": total_rs / t_batch, "threads": threads, "smem_kb": smem_kb,
+                        "tune_s": tune_s, "trial_ms": [float(x) for x in trials], **b.info()},
+            "plain_general": {"s": t_general, "region_steps_per_s": total_rs / t_general,
+                              "series_equal_to_batched": bool(np.array_equal(X_general, X_batch, equal_nan=True))},
+            "plain_auto": {"s": t_auto, "region_steps_per_s": total_rs / t_auto},
+            "speedup_vs_plain_general": t_general / t_batch, "speedup_vs_plain_auto": t_auto / t_batch,
+            "fc_max_abs_diff_batched_vs_plain_auto_68_regions": float(np.abs(fc_batch[fin] - fc_auto[fin]).max())}
+    print(json.dumps(line), flush=True)
+    b.close()
+    for sw in sweeps:
+        sw.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -580,11 +672,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep", "fc"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "fc", "batch"], default="sweep",
                     help="sweep: the paper-scale sweep (default); fc: the FC stage alone on 32,768 "
                          "series of 68 regions x 5,000 samples")
     ap.add_argument("--fc-precision", choices=["fp32", "bf16", "bf16x3", "tf32", "tf32x3"], default="bf16x3")
+    ap.add_argument("--batch-scale", type=float, default=0.25, help="duration scale of the uneven batch")
     args = ap.parse_args()
+    if args.workload == "batch":
+        return run_batch_engine(args)
     if args.workload == "fc":
         return run_fc_reference(args) if args.impl == "reference" else run_fc_engine(args)
     if args.impl == "reference":
