@@ -665,6 +665,202 @@ def run_batch_engine(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Surrogate-guided exploration: an ensemble MLP (5 -> 256 x 3 -> 24) trained
+# on the paper-scale sweep's outputs (+ a speed-augmented set) maps the
+# sync/async boundary of a (g, b_e) slice; the simulator judges proposals.
+SUR_METRIC = "speedup of the time-to-map of a regime boundary on 1 GB300 (surrogate-guided vs plain dense sweep)"
+REGIME_HZ = 50.0
+SUR_IN = ("g", "b_e", "tau_w_e", "E_L_i", "speed")
+SUR_LO = np.array([0.0, 0.0, 100.0, -80.0, 1.0])
+SUR_HI = np.array([0.9, 120.0, 1000.0, -60.0, 16.0])
+
+
+def run_surrogate_engine(args):
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2311_13337_gb300 import synth, tvbx
+    W, L = synth.connectome(68)
+    mdl = tvbx.make_model()
+    rng = np.random.Generator(np.random.PCG64(2311))
+    steps, N = 50000, 68
+    timings = {}
+
+    def rows(X):
+        pts = np.tile(np.array([mdl.defaults[i] for i in range(tvbx.N_AXES)]), (X.shape[0], 1))
+        for c, name in enumerate(SUR_IN):
+            pts[:, tvbx.AXES.index(name)] = X[:, c]
+        return pts
+
+    def simulate(X, want_fc=True):
+        """Summary (and device FC) of 5-s simulations of the rows of X."""
+        sw = tvbx.Sweep(W, L, points=rows(np.asarray(X, dtype=np.float64)))
+        P = sw.n_sets
+        tvbx.run(sw.h, dt_ms=0.1, n_steps=steps, tavg_steps=10, seed=1)
+        fc = torch.empty((P, N, N), dtype=torch.float32, device=dev)
+        tvbx.fc(sw.h, fc, precision=tvbx.FC_BF16X3)
+        out = sw.summary()
+        sw.close()
+        out["fc"] = fc if want_fc else None
+        return out
+
+    def targets(out, mean, comps):
+        coef = tvbx.fc_pca_project(out["fc"], mean, comps).cpu().numpy()
+        y = np.column_stack([out["mean_e_hz"], out["mean_i_hz"], out["chi"], out["mean_fc"], coef])
+        return y.astype(np.float32)
+
+    # training data: the paper-scale grid (v = 4 m/s) and a speed-augmented random set
+    g = np.linspace(0.0, 0.9, 16); be = np.linspace(0.0, 120.0, 16)
+    eli = np.linspace(-80.0, -60.0, 16); tw = np.linspace(100.0, 1000.0, 8)
+    grid = np.array(np.meshgrid(g, be, eli, tw, indexing="ij")).reshape(4, -1).T      # last axis fastest
+    X_grid = np.column_stack([grid[:, 0], grid[:, 1], grid[:, 3], grid[:, 2], np.full(len(grid), 4.0)])
+    X_aug = SUR_LO + (SUR_HI - SUR_LO) * rng.uniform(size=(8192, 5))
+    X_aug[:, 4] = rng.choice([1.0, 2.0, 4.0, 8.0, 16.0], size=8192)
+    t0 = time.perf_counter()
+    d_grid = simulate(X_grid)
+    d_aug = simulate(X_aug)
+    fc_all = torch.cat([d_grid["fc"], d_aug["fc"]])
+    ok = torch.isfinite(fc_all).all(dim=2).all(dim=1).cpu().numpy()
+    mean, comps, _, ev = tvbx.fc_pca(fc_all[torch.as_tensor(ok, device=dev)], n_comp=20, n_iter=40)
+    Y = np.concatenate([targets(d_grid, mean, comps), targets(d_aug, mean, comps)])
+    X = np.concatenate([X_grid, X_aug]).astype(np.float32)
+    keep = ok & np.all(np.isfinite(Y), axis=1)
+    # the regime boundary to map: low activity vs the high-activity
+    # (paroxysmal, ~190 Hz) state, label = mean E rate >= REGIME_HZ; the
+    # slice: the (E_L_i, tau_w_e) slice of the grid whose high-activity
+    # fraction over its 16 x 16 (g, b_e) points is closest to 1/2
+    rate_grid = Y[:len(X_grid), 0].reshape(16, 16, 16, 8)           # g, b_e, E_L_i, tau_w_e
+    finite = np.isfinite(rate_grid).mean(axis=(0, 1))
+    frac = np.nanmean(rate_grid >= REGIME_HZ, axis=(0, 1))
+    # slices where the integration stays finite (no divergence) for >= 95% of the points
+    ie, it = np.unravel_index(np.argmin(np.where(finite >= 0.95, np.abs(frac - 0.5), np.inf)), frac.shape)
+    slice_eli, slice_tw, slice_frac = float(eli[ie]), float(tw[it]), float(frac[ie, it])
+    slice_finite = float(finite[ie, it])
+    torch.cuda.synchronize()
+    timings["training_data_s"] = time.perf_counter() - t0
+    del fc_all, d_grid, d_aug
+
+    sur = tvbx.Surrogate(SUR_LO, SUR_HI, 24, n_hidden=256, n_layers=3, n_members=4, seed=7)
+    t0 = time.perf_counter()
+    losses = sur.train(X[keep], Y[keep], epochs=args.sur_epochs, batch=1024, lr=1e-3, weight_decay=1e-4)
+    timings["train_s"] = time.perf_counter() - t0
+
+    # surrogate error on held-out simulations (v = 4 and v != 4 separately)
+    X_te = SUR_LO + (SUR_HI - SUR_LO) * rng.uniform(size=(2048, 5))
+    X_te[:1024, 4] = 4.0
+    X_te[1024:, 4] = rng.choice([1.0, 2.0, 8.0, 16.0], size=1024)
+    d_te = simulate(X_te)
+    Y_te = targets(d_te, mean, comps)
+    P_te = sur.predict(X_te.astype(np.float32))
+    sd = np.nanstd(Y[keep], axis=0)
+    err = {}
+    for name, sl in (("v4", slice(0, 1024)), ("v_other", slice(1024, 2048))):
+        fin = np.all(np.isfinite(Y_te[sl]), axis=1)
+        r = (P_te[sl][fin] - Y_te[sl][fin]) / sd
+        err[name] = {"regime_label_agreement": float(np.mean((P_te[sl][fin, 0] >= REGIME_HZ) ==
+                                                            (Y_te[sl][fin, 0] >= REGIME_HZ))),
+                     "rmse_over_sd": {"mean_e": float(np.sqrt(np.mean(r[:, 0] ** 2))),
+                                      "mean_i": float(np.sqrt(np.mean(r[:, 1] ** 2))),
+                                      "chi": float(np.sqrt(np.mean(r[:, 2] ** 2))),
+                                      "mean_fc": float(np.sqrt(np.mean(r[:, 3] ** 2))),
+                                      "pca": float(np.sqrt(np.mean(r[:, 4:] ** 2)))},
+                     "sync_label_agreement": float(np.mean((P_te[sl][fin, 2] >= 0.5) == (Y_te[sl][fin, 2] >= 0.5)))}
+
+    # the map: sync/async labels on a 128 x 128 (g, b_e) slice at the chosen (tau_w_e, E_L_i), v 4
+    side = 128
+    gg, bb = np.meshgrid(np.linspace(0.0, 0.9, side), np.linspace(0.0, 120.0, side), indexing="ij")
+    X_map = np.column_stack([gg.ravel(), bb.ravel(), np.full(side * side, slice_tw), np.full(side * side, slice_eli),
+                             np.full(side * side, 4.0)]).astype(np.float32)
+    box = (np.array([0.0, 0.0, slice_tw, slice_eli, 4.0]), np.array([0.9, 120.0, slice_tw, slice_eli, 4.0]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d_map = simulate(X_map, want_fc=False)
+    truth = d_map["mean_e_hz"] >= REGIME_HZ
+    t_dense = time.perf_counter() - t0
+    map_nan = float(np.mean(~np.isfinite(d_map["mean_e_hz"])))
+    map_status = {str(bit): float(np.mean((d_map["status"] & bit) != 0)) for bit in (1, 2, 4, 8, 16)}
+    # speckle of the dense map: points whose label disagrees with the majority of their 8 neighbours
+    tg = truth.reshape(side, side).astype(np.int32)
+    pad = np.pad(tg, 1, mode="edge")
+    nb = sum(np.roll(np.roll(pad, dx, 0), dy, 1)[1:-1, 1:-1] for dx in (-1, 0, 1) for dy in (-1, 0, 1)) - tg
+    speckle = float(np.mean((nb >= 5) != (tg == 1)))
+
+    # plain coarse sweep with one round's budget (64 x 64), nearest-neighbour map
+    cs = 64
+    cg, cb = np.meshgrid(np.linspace(0.0, 0.9, cs), np.linspace(0.0, 120.0, cs), indexing="ij")
+    X_c = np.column_stack([cg.ravel(), cb.ravel(), np.full(cs * cs, 500.0), np.full(cs * cs, -64.0),
+                           np.full(cs * cs, 4.0)])
+    t0 = time.perf_counter()
+    lab_c = (simulate(X_c, want_fc=False)["mean_e_hz"] >= REGIME_HZ).reshape(cs, cs)
+    t_coarse = time.perf_counter() - t0
+    ig = np.rint(np.linspace(0, cs - 1, side)).astype(int)
+    err_coarse = float(np.mean(lab_c[np.ix_(ig, ig)].ravel() != truth))
+
+    # surrogate-guided: predict the map, then rounds of proposals judged by the simulator
+    rounds = []
+    t0 = time.perf_counter()
+    lab = sur.predict(X_map)[:, 0] >= REGIME_HZ
+    t_pred = time.perf_counter() - t0
+    rounds.append({"round": 0, "map_error": float(np.mean(lab != truth)), "elapsed_s": t_pred, "simulations": 0})
+    elapsed, n_sims = t_pred, 0
+    Xr, Yr = X[keep], Y[keep]
+    for r in range(1, args.sur_rounds + 1):
+        t0 = time.perf_counter()
+        props, _ = sur.propose(1 << 20, 4096, output=0, threshold=REGIME_HZ, var_weight=1.0, round=r, box=box)
+        d_p = simulate(props)
+        prop_status = {str(bit): float(np.mean((d_p["status"] & bit) != 0)) for bit in (1, 2, 4, 8, 16)}
+        prop_sample = props[:3].tolist()
+        Y_p = targets(d_p, mean, comps)
+        pred_p = sur.predict(props)[:, 0]
+        rate_ok = np.isfinite(Y_p[:, 0])
+        fin = np.all(np.isfinite(Y_p), axis=1)
+        judged = float(np.mean((pred_p[rate_ok] >= REGIME_HZ) == (Y_p[rate_ok, 0] >= REGIME_HZ)))
+        if fin.any():
+            sub = rng.choice(len(Xr), min(len(Xr), 4 * int(fin.sum())), replace=False)
+            Xf = np.concatenate([props[fin], Xr[sub]])
+            Yf = np.concatenate([Y_p[fin], Yr[sub]])
+            sur.train(Xf, Yf, epochs=args.sur_finetune_epochs, batch=512, lr=3e-4, weight_decay=1e-4)
+        lab = sur.predict(X_map)[:, 0] >= REGIME_HZ
+        torch.cuda.synchronize()
+        elapsed += time.perf_counter() - t0
+        n_sims += 4096
+        Xr, Yr = np.concatenate([Xr, props[fin]]), np.concatenate([Yr, Y_p[fin]])
+        rounds.append({"round": r, "map_error": float(np.mean(lab != truth)), "elapsed_s": elapsed,
+                       "simulations": n_sims, "proposal_label_agreement": judged,
+                       "proposals_with_finite_rate": int(rate_ok.sum()), "proposals_all_finite": int(fin.sum()),
+                       "proposal_status_bit_fractions": prop_status, "first_proposals": prop_sample})
+    reach = [x for x in rounds if x["map_error"] <= err_coarse]
+    t_guided = reach[0]["elapsed_s"] if reach else None
+    line = {"metric": SUR_METRIC, "value": (t_dense / t_guided) if t_guided else None, "unit": "x",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1000.0 * (t_guided or elapsed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights / f32",
+            "data": "synthetic",
+            "config": {"workload": "surrogate 5->256x3->24 (4 members) trained on the 32,768-set paper-scale sweep "
+                                   "(v 4) + 8,192 speed-augmented sets (5 s each); map: 128 x 128 (g, b_e) slice at "
+                                   "v 4 m/s and the (tau_w_e, E_L_i) of the grid closest to half high-activity "
+                                   "among the slices that stay finite for >= 95% of their points; "
+                                   "regime label: mean E rate >= 50 Hz (low activity vs the ~190 Hz state); "
+                                   "target map error = that of a plain 64 x 64 sweep", "training_sets": int(keep.sum()), "epochs": args.sur_epochs,
+                       "rounds": args.sur_rounds, "proposals_per_round": 4096},
+            "map_slice": {"tau_w_e": slice_tw, "E_L_i": slice_eli, "speed": 4.0, "label": f"mean E >= {REGIME_HZ} Hz",
+                          "grid_high_fraction": slice_frac, "grid_finite_fraction": slice_finite,
+                          "dense_high_fraction": float(truth.mean()),
+                          "dense_map_speckle": speckle, "dense_nonfinite_rate_fraction": map_nan,
+                          "dense_status_bit_fractions": map_status},
+            "time_to_map": {"plain_dense_s": t_dense, "plain_dense_simulations": side * side,
+                            "plain_coarse_s": t_coarse, "plain_coarse_map_error": err_coarse,
+                            "guided_s": t_guided, "rounds": rounds},
+            "one_off": {**timings, "final_train_loss": float(losses[-1]),
+                        "pca_eigenvalues": [float(x) for x in ev[:5]]},
+            "surrogate_error": err}
+    print(json.dumps(line), flush=True)
+    sur.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -672,14 +868,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep", "fc", "batch"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "fc", "batch", "surrogate"], default="sweep",
                     help="sweep: the paper-scale sweep (default); fc: the FC stage alone on 32,768 "
                          "series of 68 regions x 5,000 samples")
     ap.add_argument("--fc-precision", choices=["fp32", "bf16", "bf16x3", "tf32", "tf32x3"], default="bf16x3")
     ap.add_argument("--batch-scale", type=float, default=0.25, help="duration scale of the uneven batch")
+    ap.add_argument("--sur-epochs", type=int, default=60)
+    ap.add_argument("--sur-rounds", type=int, default=3)
+    ap.add_argument("--sur-finetune-epochs", type=int, default=15)
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch_engine(args)
+    if args.workload == "surrogate":
+        return run_surrogate_engine(args)
     if args.workload == "fc":
         return run_fc_reference(args) if args.impl == "reference" else run_fc_engine(args)
     if args.impl == "reference":

@@ -475,13 +475,16 @@ tvbx_status tvbx_surrogate_predict(tvbx_surrogate* s, int32_t mem, const float* 
 
 /* Propose n_propose points where output `output` is closest to `threshold`
  * and the ensemble disagrees most: n_candidates points drawn uniformly in the
- * domain box (Philox, counter = (candidate, round, input), key = seed) are
- * scored by -|mean - threshold| / sd + var_weight sqrt(var) / sd (sd = the
- * output's training standard deviation) and the best n_propose (ties to the
- * lower candidate index) are written, best first, to points_out
- * [n_propose][n_in] (host) with their scores (host, nullable). */
+ * candidate box (Philox, counter = (candidate, round, input), key = seed) --
+ * cand_lo/cand_hi (host [n_in], both or neither; cand_lo[i] == cand_hi[i]
+ * fixes input i, e.g. to map a 2-D slice), else the domain box -- are scored
+ * by -|mean - threshold| / sd + var_weight sqrt(var) / sd (sd = the output's
+ * training standard deviation) and the best n_propose (ties to the lower
+ * candidate index) are written, best first, to points_out [n_propose][n_in]
+ * (host) with their scores (host, nullable). */
 tvbx_status tvbx_surrogate_propose(tvbx_surrogate* s, int64_t n_candidates, uint64_t round, int32_t output,
-                                   float threshold, float var_weight, int32_t n_propose, float* points_out,
+                                   float threshold, float var_weight, const double* cand_lo,
+                                   const double* cand_hi, int32_t n_propose, float* points_out,
                                    float* scores_out);
 
 /* Read (get_out) and/or replace (set_in) the FP32 parameters of one member

@@ -291,7 +291,7 @@ struct tvbx_surrogate {
     Buf<int64_t> seg;                    // [4 L]
     Buf<float> lo, hi, mu, sd;           // box, output standardisation
     Buf<float> act, dz0, dz1, tb;        // work buffers
-    Buf<float> xin, yin, ymean, yvar, cand, score;
+    Buf<float> xin, yin, ymean, yvar, cand, score, cbox;
     Buf<double> loss;
     int work_rows = 0;
 };
@@ -513,7 +513,7 @@ tvbx_status tvbx_surrogate_destroy(tvbx_surrogate* s)
     if (!s) return TVBX_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (Buf<float>* b : {&s->p, &s->m1, &s->m2, &s->g, &s->lo, &s->hi, &s->mu, &s->sd, &s->act, &s->dz0, &s->dz1,
-                          &s->tb, &s->xin, &s->yin, &s->ymean, &s->yvar, &s->cand, &s->score})
+                          &s->tb, &s->xin, &s->yin, &s->ymean, &s->yvar, &s->cand, &s->score, &s->cbox})
         b->release();
     s->pb.release();
     s->decay.release();
@@ -695,19 +695,36 @@ tvbx_status tvbx_surrogate_predict(tvbx_surrogate* s, int32_t mem, const float* 
 }
 
 tvbx_status tvbx_surrogate_propose(tvbx_surrogate* s, int64_t n_candidates, uint64_t round, int32_t output,
-                                   float threshold, float var_weight, int32_t n_propose, float* points_out,
-                                   float* scores_out)
+                                   float threshold, float var_weight, const double* cand_lo, const double* cand_hi,
+                                   int32_t n_propose, float* points_out, float* scores_out)
 {
     if (tvbx_status st = check_handle(s)) return st;
     if (n_candidates < 1 || n_candidates > (1ll << 26) || n_propose < 1 || n_propose > n_candidates || !points_out)
         return report_error(TVBX_E_INVALID_ARG, "need 1 <= n_propose <= n_candidates <= 2^26 and points_out");
     if (output < 0 || output >= s->n_out) return report_error(TVBX_E_INVALID_ARG, "output index out of range");
+    if ((cand_lo == nullptr) != (cand_hi == nullptr))
+        return report_error(TVBX_E_INVALID_ARG, "give both cand_lo and cand_hi or neither");
+    const float *clo = s->lo.p, *chi = s->hi.p;
+    if (cand_lo) {
+        std::vector<float> b(2 * (size_t)s->n_in);
+        for (int i = 0; i < s->n_in; ++i) {
+            if (!(cand_lo[i] <= cand_hi[i]) || !isfinite(cand_lo[i]) || !isfinite(cand_hi[i]))
+                return report_error(TVBX_E_INVALID_ARG, "candidate box: need finite cand_lo[%d] <= cand_hi[%d]", i, i);
+            b[i] = (float)cand_lo[i];
+            b[s->n_in + i] = (float)cand_hi[i];
+        }
+        SCK(s->cbox.ensure(b.size()), "candidate box");
+        SCK(cudaMemcpyAsync(s->cbox.p, b.data(), sizeof(float) * b.size(), cudaMemcpyHostToDevice, s->stream),
+            "candidate box");
+        clo = s->cbox.p;
+        chi = s->cbox.p + s->n_in;
+    }
     SCK(s->cand.ensure((size_t)n_candidates * s->n_in), "candidates");
     SCK(s->ymean.ensure((size_t)n_candidates * s->n_out), "candidate predictions");
     SCK(s->yvar.ensure((size_t)n_candidates * s->n_out), "candidate predictions");
     note_launch();
     mlp_candidates_kernel<<<(unsigned)((n_candidates + 255) / 256), 256, 0, s->stream>>>(
-        s->cand.p, n_candidates, s->n_in, s->lo.p, s->hi.p, s->seed, round);
+        s->cand.p, n_candidates, s->n_in, clo, chi, s->seed, round);
     SCK(cudaGetLastError(), "candidates");
     if (tvbx_status st = predict_device(s, s->cand.p, n_candidates, s->ymean.p, s->yvar.p)) return st;
     // scores on the device; the n_propose best (ties by index) on the host

@@ -133,7 +133,8 @@ def load(build_if_missing: bool = False):
     L.tvbx_surrogate_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
     L.tvbx_surrogate_train.argtypes = [vp, i32, fp, fp, i64, i32, i32, ctypes.c_float, ctypes.c_float, i32, fp]
     L.tvbx_surrogate_predict.argtypes = [vp, i32, fp, i64, fp, fp]
-    L.tvbx_surrogate_propose.argtypes = [vp, i64, ctypes.c_uint64, i32, ctypes.c_float, ctypes.c_float, i32, fp, fp]
+    L.tvbx_surrogate_propose.argtypes = [vp, i64, ctypes.c_uint64, i32, ctypes.c_float, ctypes.c_float, dp, dp, i32,
+                                         fp, fp]
     L.tvbx_surrogate_params.argtypes = [vp, i32, fp, fp]
     L.tvbx_surrogate_gradients.argtypes = [vp, i32, fp, fp, i64, ctypes.POINTER(ctypes.c_float), fp]
     L.tvbx_surrogate_destroy.argtypes = [vp]
@@ -555,12 +556,18 @@ class Surrogate:
         _check(load().tvbx_surrogate_predict(self.h, mx, px, n, pm, pv), "tvbx_surrogate_predict")
         return (mean, var) if want_var else mean
 
-    def propose(self, n_candidates, n_propose, output, threshold, var_weight=1.0, round=0):
+    def propose(self, n_candidates, n_propose, output, threshold, var_weight=1.0, round=0, box=None):
+        """box: optional (lo, hi) candidate box; lo[i] == hi[i] fixes input i."""
         pts = np.zeros((int(n_propose), self.n_in), dtype=np.float32)
         sc = np.zeros(int(n_propose), dtype=np.float32)
+        lo = hi = None
+        if box is not None:
+            lo, hi = (np.ascontiguousarray(b, dtype=np.float64) for b in box)
         _check(load().tvbx_surrogate_propose(self.h, int(n_candidates), int(round), int(output), float(threshold),
-                                             float(var_weight), int(n_propose), ctypes.c_void_p(pts.ctypes.data),
-                                             ctypes.c_void_p(sc.ctypes.data)), "tvbx_surrogate_propose")
+                                             float(var_weight), _dptr(lo) if lo is not None else None,
+                                             _dptr(hi) if hi is not None else None, int(n_propose),
+                                             ctypes.c_void_p(pts.ctypes.data), ctypes.c_void_p(sc.ctypes.data)),
+               "tvbx_surrogate_propose")
         return pts, sc
 
     def params(self, member=0) -> np.ndarray:
