@@ -53,7 +53,7 @@ def points_for_rank(axes, n_ranks, rank, per_rank=32768):
     m = make_model()
     vals = []
     for name, (lo, hi, n) in axes:
-        vals.append((AXES.index(name), [lo + (hi - lo) * i / (n - 1) for i in range(n)]))
+        vals.append((AXES.index(name), [lo + (hi - lo) * i / (n - 1) for i in range(n)] if n > 1 else [lo]))
     total = int(np.prod([len(v) for _, v in vals]))
     assert total == per_rank * n_ranks
     idx = np.arange(rank * per_rank, (rank + 1) * per_rank)

@@ -1,0 +1,71 @@
+"""The multi-rank path on CPU (gloo, world size 2): each rank takes its
+contiguous slice of the parameter grid (bench.py's partition), integrates it
+with the global set offset as the noise-counter base (per-set noise, so the
+offset matters), and the per-set results are gathered to rank 0, which
+checks that the slices are disjoint and cover the grid and that the gathered
+results equal one single-process run of the whole grid bit for bit (shard
+invariance). The integration here is the FP64 oracle: no GPU is needed, and
+the engine's own shard invariance is a GPU test (test_gpu_parity.py)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+WORLD = 2
+PER_RANK = 8
+
+
+def _axes(world):
+    return [("g", (0.0, 0.9, 2)), ("b_e", (0.0, 120.0, 2)), ("E_L_i", (-80.0, -60.0, 1)),
+            ("tau_w_e", (100.0, 1000.0, 2 * world))]
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_path):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from oracle import oracle as O
+    from paper_2311_13337_gb300 import synth
+    W, L = synth.connectome(16)
+    pts = bench.points_for_rank(_axes(world), world, rank, per_rank=PER_RANK)
+    r = O.simulate(O.make_model(), W, L, pts, 0.1, 400, 10, 3, noise_per_set=True, p_offset=rank * PER_RANK,
+                   n_threads=1, want_I=False, want_state=False)
+    mine = torch.from_numpy(np.concatenate([r["E"].reshape(PER_RANK, -1), pts], axis=1))
+    gathered = [torch.zeros_like(mine) for _ in range(world)]
+    dist.all_gather(gathered, mine)
+    if rank == 0:
+        np.save(out_path, torch.cat(gathered).numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_sweep_gathers_to_the_single_process_result(tmp_path, oracle):
+    from paper_2311_13337_gb300 import synth
+    import bench
+    out = str(tmp_path / "gathered.npy")
+    mp.start_processes(_rank_main, args=(WORLD, _free_port(), out), nprocs=WORLD, start_method="spawn")
+    got = np.load(out)
+    W, L = synth.connectome(16)
+    full = bench.points_for_rank(_axes(WORLD), 1, 0, per_rank=WORLD * PER_RANK)
+    ncol = full.shape[1]
+    # the slices cover the grid in order, without overlap
+    assert np.array_equal(got[:, -ncol:], full)
+    assert len({tuple(r) for r in full}) == WORLD * PER_RANK
+    ref = oracle.simulate(oracle.make_model(), W, L, full, 0.1, 400, 10, 3, noise_per_set=True, p_offset=0,
+                          n_threads=1, want_I=False, want_state=False)
+    assert np.array_equal(got[:, :-ncol], ref["E"].reshape(WORLD * PER_RANK, -1))
