@@ -422,7 +422,7 @@ tvbx_status tvbx_fc_pca_project(const float* fc, int32_t n_regions, int64_t n_se
  * the library's own kernels, that maps sweep parameters (e.g. g, b_e,
  * tau_w_e, E_L_i, v) to summary statistics of a simulation (e.g. mean rates,
  * chi, mean FC, FC principal-component coefficients) and proposes where the
- * sweep should be refined; the simulation stays the judge of every proposal.
+ * sweep should be refined; every proposal is then simulated and checked.
  *
  * Network: inputs mapped to [-1, 1] by the domain box; n_layers hidden layers
  * of n_hidden units, a = max(0, a_prev W^T + b); linear output layer that
