@@ -39,6 +39,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "ptx_async.cuh"
 
@@ -113,15 +115,48 @@ static __device__ __forceinline__ void warp_wait(uint64_t* bar, uint32_t parity,
     __syncwarp();
 }
 
+// Accumulator rows of one lane quarter (the calling warp's) of every set
+// to the block-moment rows in global memory (16-byte stores where the rows
+// are 16-byte aligned, i.e. N a multiple of 4).
+template <int SC>
+static __device__ __forceinline__ void drain_quarter(const FcArgs& a, uint32_t tmem, int quarter, int Ncols, int64_t p0,
+                                                     int64_t b)
+{
+    const int N = a.N;
+    const int64_t P = a.P;
+    const int row = quarter * 32 + (threadIdx.x & 31);
+    const int64_t stride_b = (int64_t)N * N + N;
+    const bool vec = (N & 3) == 0;
+    for (int s = 0; s < SC; ++s) {
+        float* out = a.blocks + ((p0 + s) * a.n_blocks + b) * stride_b + (int64_t)row * N;
+        const bool w_ok = row < N && p0 + s < P;
+        for (int cb = 0; cb * 16 < N; ++cb) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * Ncols + cb * 16), v);
+            if (w_ok) {
+                if (vec && cb * 16 + 16 <= N) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4*>(out + cb * 16 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (cb * 16 + q < N) out[cb * 16 + q] = v[q];
+                }
+            }
+        }
+    }
+}
+
 // PREC: 1 BF16, 2 BF16x3, 3 TF32, 4 TF32x3 (the TVBX_FC_* values).
 //
 // Roles. Warps 0 .. NLW-1 load, shift, split and store (thread (k, j) =
 // region k, 16-byte piece j of each 128-byte row); warp NLW issues the MMAs
-// (one lane); warps NLW .. NLW+3 drain the accumulator of each finished
-// block from tensor memory (warp w reads lanes 32 (w % 4) ..). Hand-offs are
-// mbarriers: full[s] (one arrival per loader warp), empty[s] (MMA commit),
-// accf (MMA commit after a block's last chunk), drained (one arrival per
-// draining warp) -- no CTA-wide barrier inside the loop.
+// (one lane); loader warps 0 .. 3 also drain the accumulator of each finished
+// block from tensor memory (warp w reads lanes 32 w ..). Hand-offs are
+// mbarriers: full (one arrival per loader warp), empty (MMA commit), accf
+// (MMA commit after a block's last chunk), drained (one arrival per draining
+// warp) -- no CTA-wide barrier inside the loop.
 template <int PREC, int SC, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1)
 fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_t tmem_cols, int32_t vec_ok,
@@ -252,17 +287,21 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
                 }
                 cp_async_commit();
                 asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this chunk has landed
-                // the operand stage is free once the previous chunk's MMAs completed
-                if (gc >= 1) warp_wait(&s_empty, (uint32_t)((gc - 1) & 1), a.wait_limit, abort, a.error, 20);
-                // shift, split, store
+                // shift and split into registers while the previous chunk's MMAs run
+                uint32_t hw[SC][4], lw[SC][4];
                 const bool full_chunk = fast_sets && te - ts == KC;
                 const uint8_t* slot = dyn_smem + (raw_base - raw) + (size_t)(q * SPC * NLT + tid) * PBYTES;
+                float2 raw2[SPC];   // two sets of every sample per 8-byte load
 #pragma unroll
                 for (int s = 0; s < SC; ++s) {
+                    if ((s & 1) == 0) {
+#pragma unroll
+                        for (int i = 0; i < SPC; ++i)
+                            raw2[i] = *reinterpret_cast<const float2*>(slot + (size_t)i * NLT * PBYTES + 4 * s);
+                    }
                     float z[SPC];
 #pragma unroll
-                    for (int i = 0; i < SPC; ++i)
-                        z[i] = reinterpret_cast<const float*>(slot + (size_t)i * NLT * PBYTES)[s] - sh[s];
+                    for (int i = 0; i < SPC; ++i) z[i] = ((s & 1) ? raw2[i].y : raw2[i].x) - sh[s];
                     if (!full_chunk) {   // padding samples and missing sets are 0
 #pragma unroll
                         for (int i = 0; i < SPC; ++i)
@@ -276,30 +315,34 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
 #pragma unroll
                         for (int i = 0; i < w; ++i) part[i] += part[i + w];
                     kahan(S[s], C[s], part[0]);
-                    uint32_t hw[4], lw[4];
                     if constexpr (KIND == 0) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const __nv_bfloat162 h = __floats2bfloat162_rn(z[2 * u], z[2 * u + 1]);
-                            hw[u] = *reinterpret_cast<const uint32_t*>(&h);
+                            hw[s][u] = *reinterpret_cast<const uint32_t*>(&h);
                             if constexpr (SPLIT) {
                                 const float2 hf = __bfloat1622float2(h);
                                 const __nv_bfloat162 l = __floats2bfloat162_rn(2.0f * (z[2 * u] - hf.x),
                                                                                2.0f * (z[2 * u + 1] - hf.y));
-                                lw[u] = *reinterpret_cast<const uint32_t*>(&l);
+                                lw[s][u] = *reinterpret_cast<const uint32_t*>(&l);
                             }
                         }
                     } else {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
-                            hw[u] = tf32_rna(z[u]);
-                            if constexpr (SPLIT) lw[u] = __float_as_uint(2.0f * (z[u] - __uint_as_float(hw[u])));
+                            hw[s][u] = tf32_rna(z[u]);
+                            if constexpr (SPLIT) lw[s][u] = __float_as_uint(2.0f * (z[u] - __uint_as_float(hw[s][u])));
                         }
                     }
-                    if (loader) {
+                }
+                // the operand stage is free once the previous chunk's MMAs completed
+                if (gc >= 1) warp_wait(&s_empty, (uint32_t)((gc - 1) & 1), a.wait_limit, abort, a.error, 20);
+                if (loader) {
+#pragma unroll
+                    for (int s = 0; s < SC; ++s) {
                         const uint32_t hb = base + (uint32_t)s * NBUF * buf_bytes;
-                        st_shared_v4(hb + row_off, hw[0], hw[1], hw[2], hw[3]);
-                        if constexpr (SPLIT) st_shared_v4(hb + buf_bytes + row_off, lw[0], lw[1], lw[2], lw[3]);
+                        st_shared_v4(hb + row_off, hw[s][0], hw[s][1], hw[s][2], hw[s][3]);
+                        if constexpr (SPLIT) st_shared_v4(hb + buf_bytes + row_off, lw[s][0], lw[s][1], lw[s][2], lw[s][3]);
                     }
                 }
                 fence_proxy_async_shared();
@@ -319,69 +362,49 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
                     a.blocks[((p0 + s) * n_blocks + b) * stride_b + (int64_t)N * N + k] = v;
                 S[s] = C[s] = 0.0f;
             }
+            // warps 0-3: drain block b (accumulator rows, lane = region) to global
+            if (warp < 4) {
+                warp_wait(&s_accf, (uint32_t)(b & 1), a.wait_limit, abort, a.error, 64);
+                tc_fence_after();
+                drain_quarter<SC>(a, tmem, warp, Ncols, p0, b);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_drained);
+            }
         }
     } else {
-        // ------------------------------------------------ MMA issue and drain
-        const bool issuer = warp == NLW;
+        // ------------------------------------------------------- MMA issue
         const uint32_t idesc = tc_idesc(KIND == 0 ? 1u : 2u, 128u, (uint32_t)Ncols);
-        const int quarter = warp & 3;
         int64_t gc = 0;
         for (int64_t b = 0; b < n_blocks; ++b) {
-            if (issuer) {
-                const int64_t nck = (block_len(b) + KC - 1) / KC;
-                for (int64_t c = 0; c < nck; ++c) {
-                    warp_wait(&s_full, (uint32_t)(gc & 1), a.wait_limit, abort, a.error, 32);
-                    if (c == 0 && b > 0)   // the accumulator of block b-1 must have been read
-                        warp_wait(&s_drained, (uint32_t)((b - 1) & 1), a.wait_limit, abort, a.error, 32);
-                    tc_fence_after();
-                    if (lane == 0) {
+            const int64_t nck = (block_len(b) + KC - 1) / KC;
+            for (int64_t c = 0; c < nck; ++c) {
+                warp_wait(&s_full, (uint32_t)(gc & 1), a.wait_limit, abort, a.error, 32);
+                if (c == 0 && b > 0)   // the accumulator of block b-1 must have been read
+                    warp_wait(&s_drained, (uint32_t)((b - 1) & 1), a.wait_limit, abort, a.error, 32);
+                tc_fence_after();
+                if (lane == 0) {
 #pragma unroll 1
-                        for (int s = 0; s < SC; ++s) {
-                            const uint32_t hb = base + (uint32_t)s * NBUF * buf_bytes;
-                            const uint32_t d = tmem + (uint32_t)(s * Ncols);
+                    for (int s = 0; s < SC; ++s) {
+                        const uint32_t hb = base + (uint32_t)s * NBUF * buf_bytes;
+                        const uint32_t d = tmem + (uint32_t)(s * Ncols);
 #pragma unroll
-                            for (int ks = 0; ks < 4; ++ks) {
-                                const uint64_t ad = sw128_desc(hb + 32u * ks);
-                                tc_mma<KIND>(d, ad, ad, idesc, (c == 0 && ks == 0) ? 0u : 1u);
-                                if constexpr (SPLIT)
-                                    tc_mma<KIND>(d, ad, sw128_desc(hb + buf_bytes + 32u * ks), idesc, 1u);
-                            }
-                        }
-                        tc_commit(&s_empty);
-                        if (c + 1 == nck) tc_commit(&s_accf);
-                    }
-                    __syncwarp();
-                    ++gc;
-                }
-            }
-            // drain block b: accumulator rows (lane = region) straight to global
-            warp_wait(&s_accf, (uint32_t)(b & 1), a.wait_limit, abort, a.error, issuer ? 32 : 500);
-            tc_fence_after();
-            const int row = quarter * 32 + lane;
-            const int64_t stride_b = (int64_t)N * N + N;
-            for (int s = 0; s < SC; ++s) {
-                float* out = a.blocks + ((p0 + s) * n_blocks + b) * stride_b + (int64_t)row * N;
-                const bool w_ok = row < N && p0 + s < P;
-                for (int cb = 0; cb * 16 < N; ++cb) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * Ncols + cb * 16), v);
-                    if (w_ok) {
-                        if (cb * 16 + 16 <= N) {
-#pragma unroll
-                            for (int q = 0; q < 16; q += 4)
-                                *reinterpret_cast<float4*>(out + cb * 16 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < 16; ++q)
-                                if (cb * 16 + q < N) out[cb * 16 + q] = v[q];
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t ad = sw128_desc(hb + 32u * ks);
+                            tc_mma<KIND>(d, ad, ad, idesc, (c == 0 && ks == 0) ? 0u : 1u);
+                            if constexpr (SPLIT)
+                                tc_mma<KIND>(d, ad, sw128_desc(hb + buf_bytes + 32u * ks), idesc, 1u);
                         }
                     }
+                    tc_commit(&s_empty);
+                    if (c + 1 == nck) tc_commit(&s_accf);
                 }
+                __syncwarp();
+                ++gc;
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s_drained);
         }
+        // the last block's drain ends every MMA before tensor memory is freed
+        if (n_blocks > 0) warp_wait(&s_drained, (uint32_t)((n_blocks - 1) & 1), a.wait_limit, abort, a.error, 64);
     }
 
     // every MMA has completed (its block was drained); free tensor memory
@@ -406,8 +429,8 @@ static bool fc_tc_geom(int N, int prec, FcTcGeom& g)
     g.SC = N <= 68 ? 4 : 2;
     g.R = (N + 7) / 8 * 8;
     g.Ncols = (N + 15) / 16 * 16;
-    g.loader_warps = (8 * N + 31) / 32;
-    g.threads = 32 * g.loader_warps + 128;
+    g.loader_warps = std::max(4, (8 * N + 31) / 32);   // warps 0-3 also drain the accumulator
+    g.threads = 32 * g.loader_warps + 32;
     const int nbuf = (prec == TVBX_FC_BF16X3 || prec == TVBX_FC_TF32X3) ? 2 : 1;
     const size_t buf = (size_t)g.R * 128;
     const size_t stage = (size_t)g.SC * nbuf * buf;
@@ -419,7 +442,7 @@ static bool fc_tc_geom(int N, int prec, FcTcGeom& g)
     // more than half of the tensor memory: keep a second CTA off the SM (its
     // allocation would only wait for this one's release)
     if (cols > 256 && g.smem < 116 * 1024) g.smem = 116 * 1024;
-    return cols <= 512 && g.smem <= 227 * 1024 && g.threads <= (g.SC == 4 ? 672 : 1024);
+    return cols <= 512 && g.smem <= 227 * 1024 && g.threads <= (g.SC == 4 ? 576 : 1024);
 }
 
 bool fc_tc_supported(int N, int prec)
@@ -444,7 +467,7 @@ template <int PREC>
 static cudaError_t launch_prec(const FcArgs& a, const FcTcGeom& g, cudaStream_t s)
 {
     const int vec_ok = (a.P % g.SC == 0) && ((uintptr_t)a.series % 16 == 0) ? 1 : 0;
-    if (g.SC == 4) return launch_one<PREC, 4, 672>(a, g, vec_ok, s);
+    if (g.SC == 4) return launch_one<PREC, 4, 576>(a, g, vec_ok, s);
     return launch_one<PREC, 2, 1024>(a, g, vec_ok, s);
 }
 
