@@ -415,6 +415,37 @@ tvbx_status tvbx_fc_pca(const float* fc, int32_t n_regions, int64_t n_sets, int3
 tvbx_status tvbx_fc_pca_project(const float* fc, int32_t n_regions, int64_t n_sets, int32_t n_comp,
                                 const float* mean, const float* comps, float* coef_out, void* cuda_stream);
 
+/* ---- Fitness and grid search ----------------------------------------------
+ * Sec. "Output": the simulated FC is compared with an externally obtained
+ * reference FC and with the structural connectivity (FCSC) by the Pearson
+ * coefficient (Eq. 6); Sec. "Validation using Functional Connectivity": the
+ * fitness is that coefficient; Sec. "MPI": the results of a sweep are sorted
+ * and the ten fittest reported (grid search).
+ *
+ * tvbx_fc_fitness: out[p][t] = Pearson coefficient between the strict upper
+ * triangles (k < j) of fc[p] and of targets[t]: the fitness against a
+ * reference FC, or the FCSC when the target is the connectome's weight
+ * matrix. fc: DEVICE [n_sets][n_regions][n_regions] (e.g. tvbx_fc's output);
+ * targets: DEVICE [n_targets][n_regions][n_regions], 1 <= n_targets <= 8,
+ * 3 <= n_regions <= 1024; out: DEVICE [n_sets][n_targets], caller-owned.
+ * A set whose triangle is constant or not finite gets NaN. A target whose
+ * triangle is constant or not finite: TVBX_E_INVALID_ARG (checked before any
+ * set is read; the call synchronises the stream once for this check).
+ * Sums in FP32 over the centred triangle (the target's in FP64): the result
+ * differs from the FP64 coefficient of the same FP32 inputs by about 1e-6.
+ *
+ * tvbx_top_k: the k largest finite entries of values (DEVICE [n],
+ * 1 <= n < 2^31), largest first, ties to the lower index; 1 <= k <= 1024.
+ * idx_out (DEVICE int64 [k]) and val_out (DEVICE [k]) are caller-owned;
+ * positions beyond the number of finite entries get index -1 and NaN.
+ * Selection compares values exactly (no rounding). Both calls are
+ * asynchronous on cuda_stream (NULL = legacy default stream) apart from the
+ * target check; scratch comes from the stream-ordered allocator. */
+tvbx_status tvbx_fc_fitness(const float* fc, int64_t n_sets, int32_t n_regions, const float* targets,
+                            int32_t n_targets, float* out, void* cuda_stream);
+tvbx_status tvbx_top_k(const float* values, int64_t n, int32_t k, int64_t* idx_out, float* val_out,
+                       void* cuda_stream);
+
 /* ---- Surrogate network ---------------------------------------------------
  * The paper has no surrogate model; it motivates guided exploration of the
  * parameter space (Sec. "Discussion"). This is the learned form of the

@@ -19,17 +19,19 @@
 // Layout. A CTA owns SC consecutive sets (one 16- or 8-byte piece of every
 // (t, k) row of the [T][N][P] series) and all their samples. Per chunk of 128
 // bytes of K (64 BF16 or 32 TF32 samples) each loader thread (k, j) copies
-// samples j*SPC .. j*SPC+SPC-1 of region k for the SC sets into its own raw
-// slot in shared memory (cp.async, one chunk ahead), then subtracts the
-// shift, splits, and writes one 16-byte piece of row k of each operand buffer
-// in the 128-byte swizzled K-major layout the MMA reads. Two operand stages:
-// the MMAs of chunk c run while chunk c+1 is converted. One lane of the MMA
-// warp issues the MMAs (M = 128 rows, of which the first N are regions;
-// N_mma = N rounded up to 16) and commits them to the stage's mbarrier. At
-// the end of a block four warps read the accumulator rows out of tensor
-// memory (lane = region) and write them to global memory as they are; the
-// x3 forms leave D unsymmetric and every reader of the block moments takes
-// (D + D^T) / 2.
+// samples j*SPC .. j*SPC+SPC-1 of region k for the SC sets into one of its two
+// raw slots in shared memory (cp.async, one chunk ahead), then subtracts the
+// shift, splits into registers, and only then waits for the MMAs of the
+// previous chunk to release the single operand stage, so the conversion of
+// chunk c+1 overlaps the MMAs of chunk c; it writes one 16-byte piece of row k
+// of each operand buffer in the 128-byte swizzled K-major layout the MMA
+// reads. One lane of the MMA warp issues the MMAs (M = 128 rows, of which the
+// first N are regions; N_mma = N rounded up to 16) and commits them to the
+// stage's mbarrier. At the end of a block loader warps 0-3 read the
+// accumulator rows out of tensor memory (lane = region) and write them to
+// global memory as they are, while the other loader warps already stage the
+// next block's first chunk; the x3 forms leave D unsymmetric and every reader
+// of the block moments takes (D + D^T) / 2.
 //
 // Rows N .. 127 of the A operand and N .. N_mma - 1 of the B operand are
 // whatever follows the buffer in shared memory (in bounds by construction);

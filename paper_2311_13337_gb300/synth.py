@@ -72,6 +72,21 @@ def correlated_series(n_sets: int, n_regions: int, n_samples: int, seed: int,
     return xs, cs
 
 
+def reference_fc(W: np.ndarray, seed: int = 11) -> np.ndarray:
+    """A synthetic external reference FC for a connectome W [N][N] (FP64):
+    the correlation matrix of cov = I + 2 W / max(W) + B B^T / N with B a
+    seeded Gaussian [N][N] * 0.5, so it resembles an empirical FC that partly
+    follows the structural weights. Stands in for the reference FC files of
+    earlier CPU simulations, which are not available."""
+    n = W.shape[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = rng.standard_normal((n, n)) * 0.5
+    wmax = np.abs(W).max()
+    cov = np.eye(n) + 2.0 * W / (wmax if wmax > 0 else 1.0) + b @ b.T / n
+    d = np.sqrt(np.diag(cov))
+    return cov / np.outer(d, d)
+
+
 def rate_series_device(torch, device, n_sets: int, n_regions: int, n_samples: int, seed: int):
     """Rate-like synthetic E series [T][N][P] (kHz, FP32) made on the device
     with a seeded torch generator, the layout the engine keeps: 5 Hz mean,

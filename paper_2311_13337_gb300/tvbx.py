@@ -90,7 +90,7 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_sweep_destroy", "tvbx_surrogate_create", "tvbx_surrogate_info", "tvbx_surrogate_train",
            "tvbx_surrogate_predict", "tvbx_surrogate_propose", "tvbx_surrogate_params", "tvbx_surrogate_gradients",
            "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project", "tvbx_batch_create", "tvbx_batch_tune",
-           "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy")
+           "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy", "tvbx_fc_fitness", "tvbx_top_k")
 
 
 def library_path() -> str:
@@ -146,6 +146,8 @@ def load(build_if_missing: bool = False):
     L.tvbx_batch_destroy.argtypes = [vp]
     L.tvbx_fc_pca.argtypes = [fp, i32, i64, i32, i32, fp, fp, fp, fp, vp]
     L.tvbx_fc_pca_project.argtypes = [fp, i32, i64, i32, fp, fp, fp, vp]
+    L.tvbx_fc_fitness.argtypes = [fp, i64, i32, fp, i32, fp, vp]
+    L.tvbx_top_k.argtypes = [fp, i64, i32, fp, fp, vp]
     L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.tvbx_profile_enable.argtypes = [vp, i32]
     L.tvbx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -506,6 +508,41 @@ def fc_pca_project(fc, mean, comps, stream=None):
                                       ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(comps.data_ptr()),
                                       ctypes.c_void_p(coef.data_ptr()), sp), "tvbx_fc_pca_project")
     return coef
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def fc_fitness(fc, targets, stream=None):
+    """Pearson coefficient of the upper triangles of every FC matrix of
+    fc (CUDA [P][N][N]) with every target (CUDA [n_t][N][N] or [N][N])
+    (tvbx_fc_fitness): a CUDA tensor [P][n_t] (or [P] for one 2-D target)."""
+    import torch
+    one = targets.dim() == 2
+    tg = targets.reshape(-1, targets.shape[-2], targets.shape[-1]).contiguous()
+    fc = fc.contiguous()
+    P, N = fc.shape[0], fc.shape[-1]
+    out = torch.empty((P, tg.shape[0]), dtype=torch.float32, device=fc.device)
+    _check(load().tvbx_fc_fitness(ctypes.c_void_p(fc.data_ptr()), P, N, ctypes.c_void_p(tg.data_ptr()),
+                                  tg.shape[0], ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "tvbx_fc_fitness")
+    return out[:, 0] if one else out
+
+
+def top_k(values, k=10, stream=None):
+    """The k largest finite entries of a CUDA vector, largest first, ties to
+    the lower index (tvbx_top_k): (indices int64, values) CUDA tensors, -1 and
+    NaN past the number of finite entries."""
+    import torch
+    v = values.contiguous().reshape(-1)
+    idx = torch.empty(int(k), dtype=torch.int64, device=v.device)
+    val = torch.empty(int(k), dtype=torch.float32, device=v.device)
+    _check(load().tvbx_top_k(ctypes.c_void_p(v.data_ptr()), v.numel(), int(k), ctypes.c_void_p(idx.data_ptr()),
+                             ctypes.c_void_p(val.data_ptr()), _stream_ptr(stream)), "tvbx_top_k")
+    return idx, val
 
 
 class Surrogate:

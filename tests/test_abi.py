@@ -76,6 +76,19 @@ def test_version_and_error_reporting(lib):
     assert L.tvbx_sweep_destroy(None) == 0
 
 
+def test_fitness_and_top_k_reject_bad_arguments_before_device_use(lib):
+    L = lib.load()
+    one = ctypes.c_void_p(16)   # never dereferenced: every check below fails first
+    assert L.tvbx_fc_fitness(None, 4, 5, one, 1, one, None) == -1
+    assert L.tvbx_fc_fitness(one, 4, 2, one, 1, one, None) == -1 and "n_regions" in lib.last_error()
+    assert L.tvbx_fc_fitness(one, 4, 5, one, 9, one, None) == -1 and "n_targets" in lib.last_error()
+    assert L.tvbx_fc_fitness(one, -1, 5, one, 1, one, None) == -1
+    assert L.tvbx_top_k(None, 10, 3, one, one, None) == -1
+    assert L.tvbx_top_k(one, 0, 3, one, one, None) == -1
+    assert L.tvbx_top_k(one, 10, 0, one, one, None) == -1 and "k" in lib.last_error()
+    assert L.tvbx_top_k(one, 10, 1025, one, one, None) == -1
+
+
 def test_no_cpu_fallback_without_a_device(lib):
     import torch
     if torch.cuda.is_available():

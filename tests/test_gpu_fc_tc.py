@@ -74,6 +74,9 @@ CASES = [
     (112, 4, 640),    # largest tensor-core size
     (5, 3, 100),      # tiny
     (16, 8, 64),      # exactly one chunk
+    (17, 6, 300),     # N not a multiple of 4: scalar accumulator stores
+    (30, 5, 200),     # N = 2 mod 4, two-set pieces
+    (70, 3, 129),     # first size with two sets per CTA, one sample past a chunk
 ]
 
 

@@ -69,3 +69,57 @@ def test_sharded_sweep_gathers_to_the_single_process_result(tmp_path, oracle):
     ref = oracle.simulate(oracle.make_model(), W, L, full, 0.1, 400, 10, 3, noise_per_set=True, p_offset=0,
                           n_threads=1, want_I=False, want_state=False)
     assert np.array_equal(got[:, :-ncol], ref["E"].reshape(WORLD * PER_RANK, -1))
+
+
+def _fit_rank_main(rank, world, port, out_path):
+    """Each rank: the oracle's fitness of its contiguous share of the FC
+    matrices, its 10 fittest with global indices, then the library's gather
+    and merge (selection by the oracle's rule: no GPU here)."""
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import analysis as A
+    from paper_2311_13337_gb300 import gridsearch
+    fc, target = _fit_inputs()
+    share = fc.shape[0] // world
+    lo = rank * share
+    fit = A.fitness(fc[lo:lo + share], target).astype(np.float32)
+    i, v = A.grid_search(fit, 10)
+    gi, gv = gridsearch.gather_fittest(i + lo, v, 10, select=lambda x, k: A.grid_search(x, k)[0])
+    if rank == 0:
+        np.save(out_path, np.stack([gi.astype(np.float64), gv.astype(np.float64)]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _fit_inputs():
+    from paper_2311_13337_gb300 import synth
+    rng = np.random.default_rng(7)
+    W, _ = synth.connectome(12)
+    target = synth.reference_fc(W)
+    P = 64
+    noise = rng.standard_normal((P, 12, 12)) * rng.uniform(0.05, 0.6, (P, 1, 1))
+    fc = np.clip(target + (noise + np.swapaxes(noise, 1, 2)) / 2, -1, 1)
+    fc[:, np.arange(12), np.arange(12)] = 1.0
+    fc[40] = np.clip(target + 0.01 * (noise[0] + noise[0].T), -1, 1)
+    fc[40][np.arange(12), np.arange(12)] = 1.0
+    fc[9] = fc[40]          # the fittest pair, tied across the two ranks: the lower index first
+    fc[3] = 0.5             # a constant FC: no fitness
+    return fc, target
+
+
+def test_grid_search_gathers_the_global_ten_fittest(tmp_path):
+    from oracle import analysis as A
+    out = str(tmp_path / "fittest.npy")
+    mp.start_processes(_fit_rank_main, args=(WORLD, _free_port(), out), nprocs=WORLD, start_method="spawn")
+    got = np.load(out)
+    fc, target = _fit_inputs()
+    fit = A.fitness(fc, target).astype(np.float32)
+    wi, wv = A.grid_search(fit, 10)
+    assert got[0].astype(np.int64).tolist() == wi.tolist()
+    assert np.array_equal(got[1].astype(np.float32), wv.astype(np.float32))
+    assert 3 not in wi.tolist()
+    assert wi[:2].tolist() == [9, 40]
