@@ -601,6 +601,120 @@ def run_fc_engine(args):
 
 
 # ---------------------------------------------------------------------------
+# Table 2 metrics (mean PLI, PSD peak and power-law fit, UP / DOWN durations)
+# of 32,768 series of 68 regions x 5,000 samples (the paper-scale sweep's
+# output, 1 ms samples).
+AN_METRIC = "analysis region-samples/s on 1 GB300 (Table 2 metrics: PLI, PSD peak and fit, UP/DOWN)"
+
+
+def analysis_flops_per_set(N, T):
+    """Algorithmic FP32 work of one set: two complex transforms per region at
+    the radix-2 count 5 n log2 n, and 3 operations (two products, one
+    difference) per region pair and sample for the phase-lag signs."""
+    return 2.0 * N * 5.0 * T * np.log2(T) + 3.0 * (N * (N - 1) / 2) * T
+
+
+def run_analysis_engine(args):
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2311_13337_gb300 import synth, tvbx
+    P, N, T = FC_P, FC_N, FC_T
+    X = synth.rate_series_device(torch, dev, P, N, T, seed=1000).permute(2, 1, 0).contiguous()   # [P][N][T]
+    out = torch.empty((P, len(tvbx.AN_FIELDS)), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        return tvbx.series_analysis(X, 1.0, out=out, stream=stream)[1]
+
+    for _ in range(args.warmup):
+        used = step()
+    torch.cuda.synchronize(dev)
+    launches0 = tvbx.launch_count()
+    sampler = start_clock_sampler(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    clocks = stop_clock_sampler(sampler)
+    launches = tvbx.launch_count() - launches0
+    dev_ms = ev0.elapsed_time(ev1) / args.steps
+    units = float(P) * N * T
+    value = args.steps * units / el
+
+    # parity on sampled sets against the FP64 oracle
+    from oracle import analysis as A
+    sample = np.linspace(0, P - 1, 8).astype(int)
+    got = out.cpu().numpy()
+    errs = {"mean_pli": 0.0, "psd_a": 0.0, "psd_ampmax_rel": 0.0, "up_down_counts_equal": True}
+    xs = X[torch.as_tensor(sample, device=dev)].cpu().numpy()
+    for i, s_ in enumerate(sample):
+        w = A.table2_metrics(xs[i].astype(np.float64), 1.0)
+        errs["mean_pli"] = max(errs["mean_pli"], abs(float(got[s_, 0]) - w["mean_pli"]))
+        errs["psd_a"] = max(errs["psd_a"], abs(float(got[s_, 3]) - w["psd_a"]))
+        errs["psd_ampmax_rel"] = max(errs["psd_ampmax_rel"], abs(float(got[s_, 2]) / w["psd_ampmax"] - 1.0))
+        errs["up_down_counts_equal"] &= [float(got[s_, j]) for j in (7, 8, 9, 10)] == \
+            [w["n_up"], w["up_samples"], w["n_down"], w["down_samples"]]
+
+    # end to end: series from pinned host memory, metrics back to host
+    pin_X = torch.empty((P, N, T), dtype=torch.float32).pin_memory()
+    pin_X.copy_(X)
+    host_out = torch.empty_like(out, device="cpu").pin_memory()
+    k_e2e = max(1, min(args.steps, 2))
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            X.copy_(pin_X, non_blocking=True)
+            step()
+            host_out.copy_(out, non_blocking=True)
+        stream.synchronize()
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    el_e = time.perf_counter() - t0
+    e2e = {"value": k_e2e * units / el_e, "unit": FC_UNIT, "h2d_bytes_per_step": int(X.numel() * 4),
+           "d2h_bytes_per_step": int(out.numel() * 4)}
+
+    fl = analysis_flops_per_set(N, used) * P
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = fl / (dev_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "an_series_kernel + an_pli_kernel + an_finalize_kernel",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "algorithmic_flops_per_step": fl, "avg_step_device_ms": dev_ms,
+                "hbm_view": {"algorithmic_bytes_per_step": 4.0 * units,
+                             "achieved_gbs": 4.0 * units / (dev_ms * 1e-3) / 1e9}}
+    base = None
+    if not args.no_cpu_baseline:
+        t0 = time.time()
+        n_cpu = 0
+        while time.time() - t0 < 10.0 and n_cpu < len(sample):
+            A.table2_metrics(xs[n_cpu].astype(np.float64), 1.0)
+            n_cpu += 1
+        cel = time.time() - t0
+        base = {"value": n_cpu * N * T / cel, "unit": FC_UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{n_cpu} sets of 68 x 5000 samples (FP64 numpy, one core); {cel:.1f} s"}
+    line = {"metric": AN_METRIC, "value": value, "unit": FC_UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Table 2 metrics of 32768 series of 68 regions x 5000 samples (1 ms)",
+                       "n_sets": P, "n_regions": N, "n_samples": T, "samples_used": used,
+                       "l2": "inputs larger than L2 (series 44.6 GB)"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+            "parity_vs_fp64_on_8_sets": errs, "cpu_baseline": base}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # Uneven batch: 20 sweeps of 68/84/192/360 regions x speeds 1-16 m/s, grids
 # 8x8 - 64x64 (g x b_e), durations (1, 2, 5, 10, 20) s x --batch-scale.
 BATCH_METRIC = "region-steps/s on 1 GB300, uneven batch of sweeps (batched vs plain)"
@@ -907,7 +1021,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep", "fc", "batch", "surrogate"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "fc", "batch", "surrogate", "analysis"], default="sweep",
                     help="sweep: the paper-scale sweep (default); fc: the FC stage alone on 32,768 "
                          "series of 68 regions x 5,000 samples")
     ap.add_argument("--fc-precision", choices=["fp32", "bf16", "bf16x3", "tf32", "tf32x3"], default="bf16x3")
@@ -920,6 +1034,8 @@ def main():
         return run_batch_engine(args)
     if args.workload == "surrogate":
         return run_surrogate_engine(args)
+    if args.workload == "analysis":
+        return run_analysis_engine(args)
     if args.workload == "fc":
         return run_fc_reference(args) if args.impl == "reference" else run_fc_engine(args)
     if args.impl == "reference":

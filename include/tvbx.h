@@ -446,6 +446,51 @@ tvbx_status tvbx_fc_fitness(const float* fc, int64_t n_sets, int32_t n_regions, 
 tvbx_status tvbx_top_k(const float* values, int64_t n, int32_t k, int64_t* idx_out, float* val_out,
                        void* cuda_stream);
 
+/* ---- Table 2 analysis metrics ---------------------------------------------
+ * Sec. "Analysis metrics", Table 2: mean_PLI (Sec. "Vast parameter space
+ * exploration and analysis": the mean phase lag index), mean_UD_duration,
+ * psd_fmax_ampmax and fit_psd_slope (log PSD = log(b / f^a)), computed on the
+ * GPU from the excitatory rate series. The paper gives the metrics' names and
+ * purpose only; this library's definitions:
+ *  - samples: the last T' of each series, T' the largest number <=
+ *    min(n_samples, 8192) whose prime factors are 2, 3 and 5; every discrete
+ *    Fourier transform has length T' (the count is returned in *n_used);
+ *  - PLI_kj = |mean_t sign(Im(z_k(t) conj(z_j(t))))| with z the analytic
+ *    signal of the mean-removed series (one-sided spectrum doubled, inverse
+ *    transform), sign(0) = 0; mean_PLI = mean over region pairs k < j;
+ *  - PSD: per region the periodogram 2 dt |X(f)|^2 / T' of the mean-removed
+ *    rate in Hz (dt the sample interval in s) at f_i = i / (T' dt),
+ *    1 <= i < T'/2, averaged over regions; peak: the largest value for f in
+ *    [1, 100] Hz (ties to the lower frequency); fit: least squares of
+ *    log10 PSD = log10 b - a log10 f over the same band;
+ *  - UP / DOWN: a region is UP while its rate exceeds its mean over the T'
+ *    samples (the FP64 mean rounded to FP32); durations are lengths of
+ *    maximal runs that neither start at the first nor end at the last
+ *    sample, times dt; the set's means pool the runs of all regions.
+ * Output row per set (TVBX_AN_COUNT floats, in this order); NaN where a
+ * metric is undefined (no complete run, no band bin, N < 2 for the PLI). */
+#define TVBX_AN_MEAN_PLI      0
+#define TVBX_AN_PSD_FMAX      1  /* Hz */
+#define TVBX_AN_PSD_AMPMAX    2  /* Hz^2 / Hz */
+#define TVBX_AN_PSD_A         3  /* exponent a of b / f^a */
+#define TVBX_AN_PSD_B         4  /* b, Hz^2 / Hz at 1 Hz */
+#define TVBX_AN_UP_MS         5
+#define TVBX_AN_DOWN_MS       6
+#define TVBX_AN_N_UP          7  /* complete UP runs (exact integer) */
+#define TVBX_AN_UP_SAMPLES    8  /* their total length in samples */
+#define TVBX_AN_N_DOWN        9
+#define TVBX_AN_DOWN_SAMPLES 10
+#define TVBX_AN_COUNT        11
+
+/* series: DEVICE [n_sets][n_regions][n_samples] FP32 rates in kHz (the
+ * layout tvbx_series_range writes), sample interval dt_ms; out: DEVICE
+ * [n_sets][TVBX_AN_COUNT], caller-owned; n_used: host, nullable. 1 <=
+ * n_regions <= 4096, n_samples >= 2. Asynchronous on cuda_stream (NULL =
+ * legacy default stream); scratch (the analytic signals of up to 1 GiB of
+ * sets at a time) comes from the stream-ordered allocator. */
+tvbx_status tvbx_series_analysis(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
+                                 double dt_ms, float* out, int32_t* n_used, void* cuda_stream);
+
 /* ---- Surrogate network ---------------------------------------------------
  * The paper has no surrogate model; it motivates guided exploration of the
  * parameter space (Sec. "Discussion"). This is the learned form of the

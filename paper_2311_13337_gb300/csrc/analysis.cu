@@ -1,0 +1,507 @@
+// Table 2 analysis metrics of the excitatory rate series (arXiv 2311.13337,
+// Sec. "Analysis metrics", Table 2: mean_PLI, mean_UD_duration,
+// psd_fmax_ampmax, fit_psd_slope; Sec. "Vast parameter space exploration and
+// analysis" names the PLI the mean phase lag index).
+//
+// Input: series [P][N][T] (set-major, time fastest; the layout of
+// tvbx_series_range). Each series contributes its last T' samples, T' the
+// largest number <= T whose prime factors are 2, 3 and 5, so every discrete
+// Fourier transform below has length T'.
+//
+// Sets are processed in batches of B (scratch: the analytic signals of B
+// sets, B * N * T' complex floats):
+//  * an_series_kernel, one CTA per (set, region): the FP64 mean of the row;
+//    UP / DOWN runs against that mean (rounded to FP32); the forward DFT of
+//    the mean-removed row (Stockham autosort, radices 2, 3, 4, 5, in shared
+//    memory; twiddles from a host FP64 table); the periodogram on the PSD
+//    band; the analytic signal (one-sided spectrum doubled) by the inverse
+//    DFT, written to scratch;
+//  * an_pli_kernel, one CTA per set: time tiles of the N analytic signals in
+//    shared memory; a thread owns a 4 x 4 block of region pairs and counts
+//    sign(Im(z_k conj(z_j))) (products rounded separately, so identical
+//    signals give exactly 0);
+//  * an_finalize_kernel, one CTA per set: region-mean PSD, its peak on the
+//    band, the least-squares fit of log10 PSD on log10 f (FP64), the pooled
+//    UP / DOWN durations.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+#include "tvbx.h"
+
+namespace tvbx {
+namespace {
+
+constexpr int AN_MAX_T = 8192;
+constexpr int AN_MAX_STAGES = 16;
+constexpr int AN_THREADS = 256;
+constexpr int PLI_TT = 32;          // samples per time tile of the PLI kernel
+constexpr int PLI_TS = PLI_TT + 1; // padded row stride of the tile
+constexpr int PLI_THREADS = 256;
+
+struct FftPlan {
+    int n;
+    int n_stages;
+    int radix[AN_MAX_STAGES];
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e, bool inv)
+{
+    float2 w = __ldg(tw + e);
+    if (inv) w.y = -w.y;
+    return w;
+}
+
+// One Stockham stage of radix R: in viewed as [n/(L1 R)][L1], out as
+// [n/(L1 R)][L1 R]; out[a][b1 + L1 b2] = sum_q w_R^{b2 q} w_L^{b1 q} in[a + Rr q][b1]
+// with L = L1 R, Rr = n / L, w_m = exp(-+2 pi i / m).
+template <int R>
+__device__ void fft_stage(const float2* in, float2* out, int n, int L1, const float2* __restrict__ tw, bool inv)
+{
+    const int L = L1 * R, Rr = n / L, m = n / R;
+    const int nl = n / L;
+    float2 wr[R];   // w_R^j
+#pragma unroll
+    for (int j = 0; j < R; ++j) wr[j] = twiddle(tw, j * (n / R), inv);
+    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+        const int a = idx / L1, b1 = idx - a * L1;
+        float2 u[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float2 y = in[(a + Rr * q) * L1 + b1];
+            u[q] = q == 0 ? y : cmul(y, twiddle(tw, nl * b1 * q, inv));
+        }
+        float2* o = out + a * L + b1;
+        if constexpr (R == 2) {
+            o[0] = cadd(u[0], u[1]);
+            o[L1] = csub(u[0], u[1]);
+        } else if constexpr (R == 4) {
+            // w_4 = -i (forward) or +i (inverse)
+            const float2 s02 = cadd(u[0], u[2]), d02 = csub(u[0], u[2]);
+            const float2 s13 = cadd(u[1], u[3]), d13 = csub(u[1], u[3]);
+            const float2 jd13 = inv ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+            o[0] = cadd(s02, s13);
+            o[L1] = cadd(d02, jd13);
+            o[2 * L1] = csub(s02, s13);
+            o[3 * L1] = csub(d02, jd13);
+        } else {
+#pragma unroll
+            for (int b2 = 0; b2 < R; ++b2) {
+                float2 v = u[0];
+#pragma unroll
+                for (int q = 1; q < R; ++q) v = cadd(v, cmul(u[q], wr[(b2 * q) % R]));
+                o[L1 * b2] = v;
+            }
+        }
+    }
+}
+
+// Full transform of buf[0] (length n) using buf[1] as the other stage buffer;
+// returns the buffer holding the result.
+__device__ float2* fft(float2* b0, float2* b1, const FftPlan& plan, const float2* __restrict__ tw, bool inv)
+{
+    float2* in = b0;
+    float2* out = b1;
+    int L1 = 1;
+    for (int s = 0; s < plan.n_stages; ++s) {
+        const int r = plan.radix[s];
+        switch (r) {
+        case 2: fft_stage<2>(in, out, plan.n, L1, tw, inv); break;
+        case 3: fft_stage<3>(in, out, plan.n, L1, tw, inv); break;
+        case 4: fft_stage<4>(in, out, plan.n, L1, tw, inv); break;
+        default: fft_stage<5>(in, out, plan.n, L1, tw, inv); break;
+        }
+        __syncthreads();
+        L1 *= r;
+        float2* t = in;
+        in = out;
+        out = t;
+    }
+    return in;
+}
+
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+// One CTA per (set in batch, region).
+__global__ void __launch_bounds__(AN_THREADS)
+an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan plan, const float2* __restrict__ tw,
+                 int band_lo, int band_n, float psd_scale, int64_t p0, float* __restrict__ psd_out,
+                 int* __restrict__ ud_out, float2* __restrict__ z_out)
+{
+    extern __shared__ float2 an_smem[];
+    __shared__ double red_d[AN_THREADS / 32];
+    __shared__ int chunk_first[AN_THREADS], chunk_last[AN_THREADS];
+    __shared__ int red_i[4][AN_THREADS / 32];
+    const int n = plan.n;
+    float2* b0 = an_smem;
+    float2* b1 = an_smem + n;
+    const int b = blockIdx.x / N, k = blockIdx.x - b * N;
+    const float* row = series + ((p0 + b) * (int64_t)N + k) * T + (T - n);
+    double s = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const float x = row[t];
+        b0[t] = make_float2(x, 0.0f);
+        s += (double)x;
+    }
+    const float theta = (float)(block_sum(s, red_d) / (double)n);
+
+    // UP / DOWN: runs between consecutive transitions (a transition at t >= 1
+    // where the state differs from t - 1); thread c scans [c0, c1)
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int c0 = threadIdx.x * per, c1 = min(n, c0 + per);
+    int first = -1, last = -1, nu = 0, su = 0, nd = 0, sd = 0;
+    for (int t = max(c0, 1); t < c1; ++t) {
+        const bool up = b0[t].x > theta, was = b0[t - 1].x > theta;
+        if (up != was) {
+            if (last >= 0) {   // complete run [last, t) in state `was`
+                if (was) { ++nu; su += t - last; } else { ++nd; sd += t - last; }
+            }
+            if (first < 0) first = t;
+            last = t;
+        }
+    }
+    chunk_first[threadIdx.x] = first;
+    chunk_last[threadIdx.x] = last;
+    nu = block_sum(nu, red_i[0]);
+    su = block_sum(su, red_i[1]);
+    nd = block_sum(nd, red_i[2]);
+    sd = block_sum(sd, red_i[3]);
+    if (threadIdx.x == 0) {
+        // runs that cross chunk boundaries, in chunk order
+        int prev = -1;
+        for (int c = 0; c < (int)blockDim.x; ++c) {
+            if (chunk_first[c] < 0) continue;
+            if (prev >= 0) {
+                const int t = chunk_first[c];
+                if (b0[prev].x > theta) { ++nu; su += t - prev; } else { ++nd; sd += t - prev; }
+            }
+            prev = chunk_last[c];
+        }
+        int* u = ud_out + ((int64_t)b * N + k) * 4;
+        u[0] = nu; u[1] = su; u[2] = nd; u[3] = sd;
+    }
+    __syncthreads();   // thread 0 read the raw row above
+    // mean-removed row
+    for (int t = threadIdx.x; t < n; t += blockDim.x) b0[t].x -= theta;
+    __syncthreads();
+    float2* X = fft(b0, b1, plan, tw, false);
+    float2* other = X == b0 ? b1 : b0;
+    float* pr = psd_out + ((int64_t)b * N + k) * band_n;
+    for (int i = threadIdx.x; i < band_n; i += blockDim.x) {
+        const float2 v = X[band_lo + i];
+        pr[i] = psd_scale * fmaf(v.x, v.x, v.y * v.y);
+    }
+    __syncthreads();   // the band is read before X is overwritten
+    // analytic signal: spectrum times h (h_0 = 1, h_i = 2 below n/2, h_{n/2} = 1, 0 above)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float h = 0.0f;
+        if (i == 0 || 2 * i == n) h = 1.0f;
+        else if (2 * i < n) h = 2.0f;
+        const float2 v = X[i];
+        X[i] = make_float2(h * v.x, h * v.y);
+    }
+    __syncthreads();
+    float2* z = fft(X, other, plan, tw, true);
+    const float inv_n = 1.0f / (float)n;
+    float2* zr = z_out + ((int64_t)b * N + k) * n;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const float2 v = z[t];
+        zr[t] = make_float2(v.x * inv_n, v.y * inv_n);
+    }
+}
+
+// One CTA per set: mean over k < j of |mean_t sign(Im(z_k conj(z_j)))|.
+__global__ void __launch_bounds__(PLI_THREADS)
+an_pli_kernel(const float2* __restrict__ z_all, int N, int n, float* __restrict__ pli_out)
+{
+    // tile[(r mod 4) * NB + r / 4][PLI_TT + 1]: the rows a warp reads
+    // together (4 apart in r) are adjacent, and the padded stride spreads
+    // them over the banks
+    extern __shared__ float2 tile[];
+    __shared__ float red[PLI_THREADS / 32];
+    const int b = blockIdx.x;
+    const float2* z = z_all + (int64_t)b * N * n;
+    const int NB = (N + 3) / 4, NR = NB * 4;
+    const int nbp = NB * (NB + 1) / 2;
+    float acc = 0.0f;
+    for (int base = 0; base < nbp; base += blockDim.x) {
+        const int bp = base + threadIdx.x;
+        int bk = 0, bj = 0;
+        if (bp < nbp) {   // block pair (bk <= bj), row by row
+            int rem = bp;
+            while (rem >= NB - bk) { rem -= NB - bk; ++bk; }
+            bj = bk + rem;
+        }
+        int cnt[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) cnt[u][v] = 0;
+        for (int t0 = 0; t0 < n; t0 += PLI_TT) {
+            const int tl = min(PLI_TT, n - t0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < NR * PLI_TT; i += blockDim.x) {
+                const int r = i / PLI_TT, t = i - r * PLI_TT;
+                tile[((r & 3) * NB + (r >> 2)) * PLI_TS + t] =
+                    (r < N && t < tl) ? z[(int64_t)r * n + t0 + t] : make_float2(0.0f, 0.0f);
+            }
+            __syncthreads();
+            if (bp < nbp) {
+                for (int t = 0; t < tl; ++t) {
+                    float2 zk[4], zj[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        zk[u] = tile[(u * NB + bk) * PLI_TS + t];
+                        zj[u] = tile[(u * NB + bj) * PLI_TS + t];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            // Im(z_k conj(z_j)) = y_k x_j - x_k y_j, each product rounded
+                            const float im = __fsub_rn(__fmul_rn(zk[u].y, zj[v].x), __fmul_rn(zk[u].x, zj[v].y));
+                            cnt[u][v] += (im > 0.0f) - (im < 0.0f);
+                        }
+                }
+            }
+        }
+        if (bp < nbp) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int kk = bk * 4 + u, jj = bj * 4 + v;
+                    if (kk < jj && jj < N) acc += (float)abs(cnt[u][v]) / (float)n;
+                }
+        }
+    }
+    const float tot = block_sum(acc, red);
+    if (threadIdx.x == 0) pli_out[b] = N > 1 ? tot / (float)(N * (N - 1) / 2) : __int_as_float(0x7fc00000);
+}
+
+// One CTA per set: PSD mean over regions, peak, fit; UP / DOWN means.
+__global__ void __launch_bounds__(AN_THREADS)
+an_finalize_kernel(const float* __restrict__ psd, const int* __restrict__ ud, const float* __restrict__ pli, int N,
+                   int band_lo, int band_n, double df, double dt_ms, int64_t p0, float* __restrict__ out)
+{
+    extern __shared__ float an_psd[];   // [band_n]
+    __shared__ double red_d[4][AN_THREADS / 32];
+    __shared__ float s_best[AN_THREADS];
+    __shared__ int s_besti[AN_THREADS];
+    __shared__ int s_pos;
+    const int b = blockIdx.x;
+    const float* pb = psd + (int64_t)b * N * band_n;
+    for (int i = threadIdx.x; i < band_n; i += blockDim.x) {
+        float s = 0.0f;
+        for (int k = 0; k < N; ++k) s += pb[(int64_t)k * band_n + i];
+        an_psd[i] = s / (float)N;
+    }
+    if (threadIdx.x == 0) s_pos = 1;
+    __syncthreads();
+    // peak: largest value, ties to the lower frequency
+    float best = -INFINITY;
+    int bi = -1;
+    for (int i = threadIdx.x; i < band_n; i += blockDim.x)
+        if (an_psd[i] > best) { best = an_psd[i]; bi = i; }
+    s_best[threadIdx.x] = best;
+    s_besti[threadIdx.x] = bi;
+    // least squares of log10 PSD on log10 f (FP64)
+    double su = 0.0, sv = 0.0, suu = 0.0, suv = 0.0;
+    for (int i = threadIdx.x; i < band_n; i += blockDim.x) {
+        const float pv = an_psd[i];
+        if (!(pv > 0.0f)) { s_pos = 0; continue; }
+        const double u = log10((double)(band_lo + i) * df), v = log10((double)pv);
+        su += u; sv += v; suu += u * u; suv += u * v;
+    }
+    su = block_sum(su, red_d[0]);
+    sv = block_sum(sv, red_d[1]);
+    suu = block_sum(suu, red_d[2]);
+    suv = block_sum(suv, red_d[3]);
+    if (threadIdx.x == 0) {
+        float bv = -INFINITY;
+        int bix = -1;
+        for (int t = 0; t < (int)blockDim.x; ++t)
+            if (s_besti[t] >= 0 && (s_best[t] > bv || (s_best[t] == bv && s_besti[t] < bix))) {
+                bv = s_best[t];
+                bix = s_besti[t];
+            }
+        int64_t nu = 0, suL = 0, nd = 0, sdL = 0;
+        for (int k = 0; k < N; ++k) {
+            const int* u = ud + ((int64_t)b * N + k) * 4;
+            nu += u[0]; suL += u[1]; nd += u[2]; sdL += u[3];
+        }
+        const float nan = __int_as_float(0x7fc00000);
+        float* o = out + (p0 + b) * (int64_t)TVBX_AN_COUNT;
+        o[TVBX_AN_MEAN_PLI] = pli[b];
+        o[TVBX_AN_PSD_FMAX] = bix >= 0 ? (float)((double)(band_lo + bix) * df) : nan;
+        o[TVBX_AN_PSD_AMPMAX] = bix >= 0 ? bv : nan;
+        const double nb = (double)band_n;
+        const double den = nb * suu - su * su;
+        if (band_n >= 2 && s_pos && den != 0.0) {
+            const double slope = (nb * suv - su * sv) / den;
+            o[TVBX_AN_PSD_A] = (float)(-slope);
+            o[TVBX_AN_PSD_B] = (float)pow(10.0, (sv - slope * su) / nb);
+        } else {
+            o[TVBX_AN_PSD_A] = nan;
+            o[TVBX_AN_PSD_B] = nan;
+        }
+        o[TVBX_AN_UP_MS] = nu ? (float)((double)suL * dt_ms / (double)nu) : nan;
+        o[TVBX_AN_DOWN_MS] = nd ? (float)((double)sdL * dt_ms / (double)nd) : nan;
+        o[TVBX_AN_N_UP] = (float)nu;
+        o[TVBX_AN_UP_SAMPLES] = (float)suL;
+        o[TVBX_AN_N_DOWN] = (float)nd;
+        o[TVBX_AN_DOWN_SAMPLES] = (float)sdL;
+    }
+}
+
+int smooth_length(int64_t n)
+{
+    for (int64_t m = std::min<int64_t>(n, AN_MAX_T); m > 0; --m) {
+        int64_t r = m;
+        for (int f : {2, 3, 5})
+            while (r % f == 0) r /= f;
+        if (r == 1) return (int)m;
+    }
+    return 0;
+}
+
+bool make_plan(int n, FftPlan& p)
+{
+    p.n = n;
+    p.n_stages = 0;
+    int r = n;
+    // radix 5s, then 3s, then 4s, then a final 2
+    for (int f : {5, 3, 4, 2}) {
+        while (r % f == 0) {
+            if (p.n_stages == AN_MAX_STAGES) return false;
+            p.radix[p.n_stages++] = f;
+            r /= f;
+        }
+    }
+    return r == 1;
+}
+
+#define ACK(call, what)                                                                              \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ == cudaErrorMemoryAllocation) return report_error(TVBX_E_OOM, "%s: out of memory", what); \
+        if (e_ != cudaSuccess) return report_error(TVBX_E_CUDA, "%s: %s", what, cudaGetErrorString(e_)); \
+    } while (0)
+
+struct AnScratch {
+    std::vector<void*> ptrs;
+    cudaStream_t s;
+    explicit AnScratch(cudaStream_t st) : s(st) {}
+    template <class T> cudaError_t get(T** p, size_t n)
+    {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (n ? n : 1), s);
+        if (e == cudaSuccess) {
+            ptrs.push_back(q);
+            *p = static_cast<T*>(q);
+        }
+        return e;
+    }
+    ~AnScratch()
+    {
+        for (void* q : ptrs) cudaFreeAsync(q, s);
+    }
+};
+
+}  // namespace
+}  // namespace tvbx
+
+using namespace tvbx;
+
+extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
+                                            double dt_ms, float* out, int32_t* n_used, void* cuda_stream)
+{
+    const int N = n_regions;
+    const int64_t P = n_sets, T = n_samples;
+    if (!series || !out) return report_error(TVBX_E_INVALID_ARG, "NULL series or out");
+    if (N < 1 || N > 4096 || P < 1 || T < 2) return report_error(TVBX_E_INVALID_ARG, "need 1 <= n_regions <= 4096, n_sets >= 1, n_samples >= 2");
+    if (!(dt_ms > 0.0) || !std::isfinite(dt_ms)) return report_error(TVBX_E_INVALID_ARG, "dt_ms must be > 0");
+    const int n = smooth_length(T);
+    FftPlan plan;
+    if (n < 2 || !make_plan(n, plan)) return report_error(TVBX_E_INVALID_ARG, "no transform length for %lld samples", (long long)T);
+    // PSD band [1, 100] Hz: bins 1 <= i < n/2 with f_i = i / (n dt) in the band
+    const double dt_s = dt_ms * 1e-3;
+    int band_lo = -1, band_hi = -1;
+    for (int i = 1; 2 * i < n; ++i) {
+        const double f = (double)i / ((double)n * dt_s);
+        if (f >= 1.0 && f <= 100.0) {
+            if (band_lo < 0) band_lo = i;
+            band_hi = i;
+        }
+    }
+    const int band_n = band_lo < 0 ? 0 : band_hi - band_lo + 1;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // batch of sets: analytic signals of B sets at most ~1 GiB
+    const int64_t per_set = (int64_t)N * n * 8;
+    const int64_t B = std::max<int64_t>(1, std::min<int64_t>(P, ((int64_t)1 << 30) / std::max<int64_t>(per_set, 1)));
+    std::vector<float2> htw(n);
+    for (int e = 0; e < n; ++e) {
+        const double ang = -2.0 * 3.14159265358979323846 * (double)e / (double)n;
+        htw[e] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    AnScratch scr(s);
+    float2 *tw, *z;
+    float *psd, *pli;
+    int* ud;
+    ACK(scr.get(&tw, n), "analysis twiddles");
+    ACK(scr.get(&z, (size_t)B * N * n), "analysis signals");
+    ACK(scr.get(&psd, (size_t)B * N * std::max(band_n, 1)), "analysis PSD");
+    ACK(scr.get(&pli, (size_t)B), "analysis PLI");
+    ACK(scr.get(&ud, (size_t)B * N * 4), "analysis UP/DOWN");
+    ACK(cudaMemcpyAsync(tw, htw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s), "analysis twiddles");
+    const size_t smem_series = sizeof(float2) * 2 * (size_t)n;
+    ACK(cudaFuncSetAttribute(an_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_series),
+        "analysis shared memory");
+    const size_t smem_pli = sizeof(float2) * (size_t)((N + 3) / 4 * 4) * PLI_TS;
+    if (smem_pli > 200 * 1024) return report_error(TVBX_E_INVALID_ARG, "too many regions for the PLI tile");
+    ACK(cudaFuncSetAttribute(an_pli_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pli),
+        "analysis shared memory");
+    const size_t smem_fin = sizeof(float) * (size_t)std::max(band_n, 1);
+    ACK(cudaFuncSetAttribute(an_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fin),
+        "analysis shared memory");
+    const float psd_scale = (float)(2.0 * dt_s / (double)n * 1e6);   // kHz^2 -> Hz^2, one-sided
+    const double df = 1.0 / ((double)n * dt_s);
+    for (int64_t p0 = 0; p0 < P; p0 += B) {
+        const int64_t nb = std::min<int64_t>(B, P - p0);
+        note_launch(3);
+        an_series_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_series, s>>>(series, N, T, plan, tw, band_lo,
+                                                                           band_n, psd_scale, p0, psd, ud, z);
+        ACK(cudaGetLastError(), "analysis series");
+        an_pli_kernel<<<(unsigned)nb, PLI_THREADS, smem_pli, s>>>(z, N, n, pli);
+        ACK(cudaGetLastError(), "analysis PLI");
+        an_finalize_kernel<<<(unsigned)nb, AN_THREADS, smem_fin, s>>>(psd, ud, pli, N, band_lo, band_n, df, dt_ms,
+                                                                       p0, out);
+        ACK(cudaGetLastError(), "analysis finalize");
+    }
+    if (n_used) *n_used = n;
+    return TVBX_OK;
+}

@@ -90,7 +90,8 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_sweep_destroy", "tvbx_surrogate_create", "tvbx_surrogate_info", "tvbx_surrogate_train",
            "tvbx_surrogate_predict", "tvbx_surrogate_propose", "tvbx_surrogate_params", "tvbx_surrogate_gradients",
            "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project", "tvbx_batch_create", "tvbx_batch_tune",
-           "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy", "tvbx_fc_fitness", "tvbx_top_k")
+           "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy", "tvbx_fc_fitness", "tvbx_top_k",
+           "tvbx_series_analysis")
 
 
 def library_path() -> str:
@@ -148,6 +149,7 @@ def load(build_if_missing: bool = False):
     L.tvbx_fc_pca_project.argtypes = [fp, i32, i64, i32, fp, fp, fp, vp]
     L.tvbx_fc_fitness.argtypes = [fp, i64, i32, fp, i32, fp, vp]
     L.tvbx_top_k.argtypes = [fp, i64, i32, fp, fp, vp]
+    L.tvbx_series_analysis.argtypes = [fp, i32, i64, i64, ctypes.c_double, fp, ctypes.POINTER(i32), vp]
     L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.tvbx_profile_enable.argtypes = [vp, i32]
     L.tvbx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -543,6 +545,42 @@ def top_k(values, k=10, stream=None):
     _check(load().tvbx_top_k(ctypes.c_void_p(v.data_ptr()), v.numel(), int(k), ctypes.c_void_p(idx.data_ptr()),
                              ctypes.c_void_p(val.data_ptr()), _stream_ptr(stream)), "tvbx_top_k")
     return idx, val
+
+
+AN_FIELDS = ("mean_pli", "psd_fmax", "psd_ampmax", "psd_a", "psd_b", "up_ms", "down_ms", "n_up", "up_samples",
+             "n_down", "down_samples")
+
+
+def series_analysis(series, dt_ms, out=None, stream=None):
+    """Table 2 metrics (tvbx_series_analysis) of CUDA series [P][N][T] (kHz):
+    (CUDA tensor [P][len(AN_FIELDS)], samples used)."""
+    import torch
+    x = series.contiguous()
+    P, N, T = x.shape
+    if out is None:
+        out = torch.empty((P, len(AN_FIELDS)), dtype=torch.float32, device=x.device)
+    used = ctypes.c_int32(0)
+    _check(load().tvbx_series_analysis(ctypes.c_void_p(x.data_ptr()), N, P, T, float(dt_ms),
+                                       ctypes.c_void_p(out.data_ptr()), ctypes.byref(used), _stream_ptr(stream)),
+           "tvbx_series_analysis")
+    return out, used.value
+
+
+def sweep_analysis(sw, dt_ms, transient_samples=0, batch_sets=4096, stream=None):
+    """Table 2 metrics of a sweep's series from sample transient_samples on:
+    the series of batch_sets sets at a time are exported to the device
+    ([P][N][T]) and analysed. Returns a CUDA tensor [P][len(AN_FIELDS)] and
+    the samples used."""
+    import torch
+    nt = sw.n_samples - int(transient_samples)
+    out = torch.empty((sw.n_sets, len(AN_FIELDS)), dtype=torch.float32, device="cuda")
+    buf = torch.empty((min(batch_sets, sw.n_sets), sw.n_regions, nt), dtype=torch.float32, device="cuda")
+    used = 0
+    for p0 in range(0, sw.n_sets, batch_sets):
+        m = min(batch_sets, sw.n_sets - p0)
+        series_range(sw.h, p0, m, int(transient_samples), nt, buf[:m])
+        _, used = series_analysis(buf[:m], dt_ms, out=out[p0:p0 + m], stream=stream)
+    return out, used
 
 
 class Surrogate:
