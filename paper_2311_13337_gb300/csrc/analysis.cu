@@ -18,8 +18,8 @@
 //    DFT, written to scratch;
 //  * an_pli_kernel, one CTA per set: time tiles of the N analytic signals in
 //    shared memory; a thread owns a 4 x 4 block of region pairs and counts
-//    sign(Im(z_k conj(z_j))) (products rounded separately, so identical
-//    signals give exactly 0);
+//    sign(Im(z_k conj(z_j))) by comparing the two rounded products, so
+//    identical signals give exactly 0;
 //  * an_finalize_kernel, one CTA per set: region-mean PSD, its peak on the
 //    band, the least-squares fit of log10 PSD on log10 f (FP64), the pooled
 //    UP / DOWN durations.
@@ -42,13 +42,14 @@ constexpr int AN_MAX_T = 8192;
 constexpr int AN_MAX_STAGES = 16;
 constexpr int AN_THREADS = 256;
 constexpr int PLI_TT = 32;          // samples per time tile of the PLI kernel
-constexpr int PLI_TS = PLI_TT + 1; // padded row stride of the tile
+constexpr int PLI_TS = PLI_TT + 2; // padded row stride of a tile plane (floats)
 constexpr int PLI_THREADS = 256;
 
 struct FftPlan {
     int n;
     int n_stages;
     int radix[AN_MAX_STAGES];
+    uint32_t magic[AN_MAX_STAGES];   // ceil(2^32 / L1) of the stage (0 for L1 = 1): idx / L1 = umulhi(idx, magic)
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -67,44 +68,61 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e, 
 
 // One Stockham stage of radix R: in viewed as [n/(L1 R)][L1], out as
 // [n/(L1 R)][L1 R]; out[a][b1 + L1 b2] = sum_q w_R^{b2 q} w_L^{b1 q} in[a + Rr q][b1]
-// with L = L1 R, Rr = n / L, w_m = exp(-+2 pi i / m).
+// with L = L1 R, Rr = n / L, w_m = exp(-+2 pi i / m). The R-point transforms
+// use the symmetric forms (cos and sin of 2 pi / 3 and 2 pi k / 5).
 template <int R>
-__device__ void fft_stage(const float2* in, float2* out, int n, int L1, const float2* __restrict__ tw, bool inv)
+__device__ void fft_stage(const float2* in, float2* out, int n, int L1, uint32_t magic, const float2* __restrict__ tw,
+                          bool inv)
 {
     const int L = L1 * R, Rr = n / L, m = n / R;
     const int nl = n / L;
-    float2 wr[R];   // w_R^j
-#pragma unroll
-    for (int j = 0; j < R; ++j) wr[j] = twiddle(tw, j * (n / R), inv);
+    const float sg = inv ? 1.0f : -1.0f;   // sign of the exponent
     for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
-        const int a = idx / L1, b1 = idx - a * L1;
+        const int a = magic ? (int)__umulhi((uint32_t)idx, magic) : idx;
+        const int b1 = idx - a * L1;
         float2 u[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const float2 y = in[(a + Rr * q) * L1 + b1];
-            u[q] = q == 0 ? y : cmul(y, twiddle(tw, nl * b1 * q, inv));
+            u[q] = (q == 0 || b1 == 0) ? y : cmul(y, twiddle(tw, nl * b1 * q, inv));
         }
         float2* o = out + a * L + b1;
         if constexpr (R == 2) {
             o[0] = cadd(u[0], u[1]);
             o[L1] = csub(u[0], u[1]);
         } else if constexpr (R == 4) {
-            // w_4 = -i (forward) or +i (inverse)
             const float2 s02 = cadd(u[0], u[2]), d02 = csub(u[0], u[2]);
             const float2 s13 = cadd(u[1], u[3]), d13 = csub(u[1], u[3]);
-            const float2 jd13 = inv ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+            // (sg i) d13
+            const float2 jd13 = make_float2(-sg * d13.y, sg * d13.x);
             o[0] = cadd(s02, s13);
             o[L1] = cadd(d02, jd13);
             o[2 * L1] = csub(s02, s13);
             o[3 * L1] = csub(d02, jd13);
+        } else if constexpr (R == 3) {
+            constexpr float S3 = 0.86602540378443865f;   // sin(2 pi / 3); cos(2 pi / 3) = -1/2
+            const float2 t1 = cadd(u[1], u[2]), t2 = csub(u[1], u[2]);
+            const float2 a0 = make_float2(fmaf(-0.5f, t1.x, u[0].x), fmaf(-0.5f, t1.y, u[0].y));
+            const float bx = sg * S3 * t2.x, by = sg * S3 * t2.y;   // (sg S3) t2, times i below
+            o[0] = cadd(u[0], t1);
+            o[L1] = make_float2(a0.x - by, a0.y + bx);
+            o[2 * L1] = make_float2(a0.x + by, a0.y - bx);
         } else {
-#pragma unroll
-            for (int b2 = 0; b2 < R; ++b2) {
-                float2 v = u[0];
-#pragma unroll
-                for (int q = 1; q < R; ++q) v = cadd(v, cmul(u[q], wr[(b2 * q) % R]));
-                o[L1 * b2] = v;
-            }
+            // cos and sin of 2 pi / 5 and 4 pi / 5
+            constexpr float C1 = 0.30901699437494742f, C2 = -0.80901699437494742f;
+            constexpr float S1 = 0.95105651629515357f, S2 = 0.58778525229247313f;
+            const float2 t1 = cadd(u[1], u[4]), t2 = cadd(u[2], u[3]);
+            const float2 t3 = csub(u[1], u[4]), t4 = csub(u[2], u[3]);
+            const float2 a1 = make_float2(fmaf(C1, t1.x, fmaf(C2, t2.x, u[0].x)), fmaf(C1, t1.y, fmaf(C2, t2.y, u[0].y)));
+            const float2 a2 = make_float2(fmaf(C2, t1.x, fmaf(C1, t2.x, u[0].x)), fmaf(C2, t1.y, fmaf(C1, t2.y, u[0].y)));
+            // b1 = sg (S1 t3 + S2 t4), b2 = sg (S2 t3 - S1 t4); outputs a -+ ... with i b
+            const float b1x = sg * fmaf(S1, t3.x, S2 * t4.x), b1y = sg * fmaf(S1, t3.y, S2 * t4.y);
+            const float b2x = sg * fmaf(S2, t3.x, -S1 * t4.x), b2y = sg * fmaf(S2, t3.y, -S1 * t4.y);
+            o[0] = make_float2(u[0].x + t1.x + t2.x, u[0].y + t1.y + t2.y);
+            o[L1] = make_float2(a1.x - b1y, a1.y + b1x);       // a1 + i b1
+            o[4 * L1] = make_float2(a1.x + b1y, a1.y - b1x);   // a1 - i b1
+            o[2 * L1] = make_float2(a2.x - b2y, a2.y + b2x);   // a2 + i b2
+            o[3 * L1] = make_float2(a2.x + b2y, a2.y - b2x);   // a2 - i b2
         }
     }
 }
@@ -118,11 +136,12 @@ __device__ float2* fft(float2* b0, float2* b1, const FftPlan& plan, const float2
     int L1 = 1;
     for (int s = 0; s < plan.n_stages; ++s) {
         const int r = plan.radix[s];
+        const uint32_t mg = plan.magic[s];
         switch (r) {
-        case 2: fft_stage<2>(in, out, plan.n, L1, tw, inv); break;
-        case 3: fft_stage<3>(in, out, plan.n, L1, tw, inv); break;
-        case 4: fft_stage<4>(in, out, plan.n, L1, tw, inv); break;
-        default: fft_stage<5>(in, out, plan.n, L1, tw, inv); break;
+        case 2: fft_stage<2>(in, out, plan.n, L1, mg, tw, inv); break;
+        case 3: fft_stage<3>(in, out, plan.n, L1, mg, tw, inv); break;
+        case 4: fft_stage<4>(in, out, plan.n, L1, mg, tw, inv); break;
+        default: fft_stage<5>(in, out, plan.n, L1, mg, tw, inv); break;
         }
         __syncthreads();
         L1 *= r;
@@ -234,18 +253,42 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
     }
 }
 
+__device__ __forceinline__ uint64_t mul_f32x2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// sign(p - q) summed over both lanes, by comparison: the packed products are
+// not subtracted, because a packed subtraction of two packed products may be
+// contracted into a fused multiply-add (observed), which leaves the rounding
+// error of one product instead of an exact 0 for identical signals. For
+// distinct finite p and q, p - q is never 0, so the comparison is sign(p - q).
+__device__ __forceinline__ int sign_diff2(uint64_t p, uint64_t q)
+{
+    const float p0 = __uint_as_float((uint32_t)p), p1 = __uint_as_float((uint32_t)(p >> 32));
+    const float q0 = __uint_as_float((uint32_t)q), q1 = __uint_as_float((uint32_t)(q >> 32));
+    return (p0 > q0) - (p0 < q0) + (p1 > q1) - (p1 < q1);
+}
+
 // One CTA per set: mean over k < j of |mean_t sign(Im(z_k conj(z_j)))|.
+// The tile holds the real and imaginary parts in separate planes, time
+// fastest, so one 8-byte load gives two consecutive samples and the packed
+// two-lane FP32 products handle two samples of a pair per instruction (each
+// lane rounds like the scalar product).
 __global__ void __launch_bounds__(PLI_THREADS)
 an_pli_kernel(const float2* __restrict__ z_all, int N, int n, float* __restrict__ pli_out)
 {
-    // tile[(r mod 4) * NB + r / 4][PLI_TT + 1]: the rows a warp reads
-    // together (4 apart in r) are adjacent, and the padded stride spreads
-    // them over the banks
-    extern __shared__ float2 tile[];
+    // planes [2][(r mod 4) * NB + r / 4][PLI_TS]: the rows a half-warp reads
+    // together (4 apart in r) are adjacent, and the stride (2 mod 32 words)
+    // puts their 8-byte pieces in distinct banks
+    extern __shared__ float tile[];
     __shared__ float red[PLI_THREADS / 32];
     const int b = blockIdx.x;
     const float2* z = z_all + (int64_t)b * N * n;
     const int NB = (N + 3) / 4, NR = NB * 4;
+    float* TX = tile;
+    float* TY = tile + NR * PLI_TS;
     const int nbp = NB * (NB + 1) / 2;
     float acc = 0.0f;
     for (int base = 0; base < nbp; base += blockDim.x) {
@@ -266,25 +309,29 @@ an_pli_kernel(const float2* __restrict__ z_all, int N, int n, float* __restrict_
             __syncthreads();
             for (int i = threadIdx.x; i < NR * PLI_TT; i += blockDim.x) {
                 const int r = i / PLI_TT, t = i - r * PLI_TT;
-                tile[((r & 3) * NB + (r >> 2)) * PLI_TS + t] =
-                    (r < N && t < tl) ? z[(int64_t)r * n + t0 + t] : make_float2(0.0f, 0.0f);
+                const float2 v = (r < N && t < tl) ? z[(int64_t)r * n + t0 + t] : make_float2(0.0f, 0.0f);
+                const int o = ((r & 3) * NB + (r >> 2)) * PLI_TS + t;
+                TX[o] = v.x;
+                TY[o] = v.y;
             }
             __syncthreads();
             if (bp < nbp) {
-                for (int t = 0; t < tl; ++t) {
-                    float2 zk[4], zj[4];
+                // padded samples are 0 and add sign(0) = 0
+                for (int t = 0; t < PLI_TT; t += 2) {
+                    uint64_t xk[4], yk[4], xj[4], yj[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        zk[u] = tile[(u * NB + bk) * PLI_TS + t];
-                        zj[u] = tile[(u * NB + bj) * PLI_TS + t];
+                        xk[u] = *reinterpret_cast<const uint64_t*>(TX + (u * NB + bk) * PLI_TS + t);
+                        yk[u] = *reinterpret_cast<const uint64_t*>(TY + (u * NB + bk) * PLI_TS + t);
+                        xj[u] = *reinterpret_cast<const uint64_t*>(TX + (u * NB + bj) * PLI_TS + t);
+                        yj[u] = *reinterpret_cast<const uint64_t*>(TY + (u * NB + bj) * PLI_TS + t);
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
                             // Im(z_k conj(z_j)) = y_k x_j - x_k y_j, each product rounded
-                            const float im = __fsub_rn(__fmul_rn(zk[u].y, zj[v].x), __fmul_rn(zk[u].x, zj[v].y));
-                            cnt[u][v] += (im > 0.0f) - (im < 0.0f);
+                            cnt[u][v] += sign_diff2(mul_f32x2(yk[u], xj[v]), mul_f32x2(xk[u], yj[v]));
                         }
                 }
             }
@@ -402,7 +449,14 @@ bool make_plan(int n, FftPlan& p)
             r /= f;
         }
     }
-    return r == 1;
+    if (r != 1) return false;
+    uint64_t L1 = 1;
+    for (int s = 0; s < p.n_stages; ++s) {
+        // idx < 2^13 and L1 < 2^13: floor(idx * ceil(2^32 / L1) / 2^32) = floor(idx / L1)
+        p.magic[s] = L1 == 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + L1 - 1) / L1);
+        L1 *= (uint64_t)p.radix[s];
+    }
+    return true;
 }
 
 #define ACK(call, what)                                                                              \
@@ -481,7 +535,7 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
     const size_t smem_series = sizeof(float2) * 2 * (size_t)n;
     ACK(cudaFuncSetAttribute(an_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_series),
         "analysis shared memory");
-    const size_t smem_pli = sizeof(float2) * (size_t)((N + 3) / 4 * 4) * PLI_TS;
+    const size_t smem_pli = sizeof(float) * 2 * (size_t)((N + 3) / 4 * 4) * PLI_TS;
     if (smem_pli > 200 * 1024) return report_error(TVBX_E_INVALID_ARG, "too many regions for the PLI tile");
     ACK(cudaFuncSetAttribute(an_pli_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pli),
         "analysis shared memory");
