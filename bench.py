@@ -715,6 +715,104 @@ def run_analysis_engine(args):
 
 
 # ---------------------------------------------------------------------------
+# The paper's vast exploration (Table 4): the full 10-axis grid of 262,144
+# parameter sets on the 68-region connectome, run as four sweeps of 65,536
+# sets (one per conduction speed), each followed by FC (bf16x3), FCD, the
+# summary, the fitness grid search and the Table 2 metrics.
+T4_METRIC = "region-steps/s on 1 GB300, full Table 4 grid (262,144 sets) with FC, grid search and Table 2 metrics"
+
+
+def run_table4_engine(args):
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2311_13337_gb300 import gridsearch, synth, tvbx
+    W, L = synth.connectome(68)
+    m = tvbx.make_model()
+    names = [a for a, _ in synth.TABLE4_AXES]
+    vals = [np.linspace(lo, hi, n) for _, (lo, hi, n) in synth.TABLE4_AXES]
+    Pt = int(np.prod([len(v) for v in vals]))
+    idx = np.arange(Pt)
+    pts = np.tile(np.array([m.defaults[i] for i in range(tvbx.N_AXES)]), (Pt, 1))
+    rem = idx.copy()
+    for name, v in reversed(list(zip(names, vals))):
+        pts[:, tvbx.AXES.index(name)] = v[rem % len(v)]
+        rem //= len(v)
+    speeds = vals[names.index("speed")]
+    parts = [np.flatnonzero(pts[:, tvbx.AXES.index("speed")] == v) for v in speeds]
+    N, ts = 68, 10
+    S = int(round(args.t4_seconds * 10000))
+    T = S // ts
+    nw = (T - min(FCD_WINDOW, T)) // min(FCD_STEP, T) + 1
+    ref_dev = torch.from_numpy(synth.reference_fc(W).astype(np.float32)).to(dev)
+    chi = np.zeros(Pt, dtype=np.float32)
+    pli = np.zeros(Pt, dtype=np.float32)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        best = []
+        for part in parts:
+            sw = tvbx.Sweep(W, L, points=pts[part])
+            P = len(part)
+            tvbx.run(sw.h, dt_ms=0.1, n_steps=S, tavg_steps=ts, seed=1, stream=stream)
+            fc = torch.empty((P, N, N), dtype=torch.float32, device=dev)
+            fcd = torch.empty((P, nw, nw), dtype=torch.float32, device=dev)
+            tvbx.fc(sw.h, fc, fcd, min(FCD_WINDOW, T), min(FCD_STEP, T), precision=tvbx.FC_BF16X3)
+            summ = [torch.empty(P, dtype=torch.float32, device=dev) for _ in range(4)]
+            st = torch.empty(P, dtype=torch.int32, device=dev)
+            tvbx.summary(sw.h, *summ, st)
+            with torch.cuda.stream(stream):
+                fit = tvbx.fc_fitness(fc, ref_dev, stream=stream)
+                i, v = tvbx.top_k(fit, 10, stream=stream)
+                an, _ = tvbx.sweep_analysis(sw, 1.0, stream=stream)
+            stream.synchronize()
+            i = i.cpu().numpy()
+            best.append((np.where(i >= 0, part[np.maximum(i, 0)], -1), v.cpu().numpy()))
+            chi[part] = summ[2].cpu().numpy()
+            pli[part] = an[:, 0].cpu().numpy()
+            del fc, fcd, an
+            sw.close()
+        # the ten fittest of the whole grid (partitions are not contiguous in
+        # the grid, so merge by value with the global indices)
+        gi = np.concatenate([b[0] for b in best])
+        gv = np.concatenate([b[1] for b in best])
+        keep = gi >= 0
+        order = sorted(np.flatnonzero(keep).tolist(), key=lambda j: (-gv[j], gi[j]))[:10]
+        return gi[order], gv[order]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    launches0 = tvbx.launch_count()
+    sampler = start_clock_sampler(0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        top_i, top_v = step()
+    torch.cuda.synchronize(dev)
+    el = (time.perf_counter() - t0) / args.steps
+    clocks = stop_clock_sampler(sampler)
+    launches = (tvbx.launch_count() - launches0) / args.steps
+    rs = float(Pt) * N * S
+    line = {"metric": T4_METRIC, "value": rs / el, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * el, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Table 4 grid: 262144 sets (g8 x b_e8 x w_noise4 x speed4 x tau_w4 x a_e4 x "
+                                   f"cF 2x2x2x2), 68 regions, {args.t4_seconds} s (dt 0.1 ms) per set, as 4 sweeps "
+                                   "of 65536 sets; FC bf16x3 + FCD + summary + fitness top-10 + Table 2 metrics",
+                       "n_sets": Pt, "n_regions": N, "n_steps": S,
+                       "l2": "inputs larger than L2"},
+            "clocks": clocks, "gpu_launches": launches,
+            "grid_search": {"fittest_sets": [int(i) for i in top_i], "fitness": [float(v) for v in top_v]},
+            "sync_fraction": float(np.mean(chi >= 0.5)), "mean_pli_median": float(np.nanmedian(pli)),
+            "roofline": None, "cpu_baseline": None,
+            "note": "simulation roofline and CPU baseline: see the sweep workload (same kernels)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # Uneven batch: 20 sweeps of 68/84/192/360 regions x speeds 1-16 m/s, grids
 # 8x8 - 64x64 (g x b_e), durations (1, 2, 5, 10, 20) s x --batch-scale.
 BATCH_METRIC = "region-steps/s on 1 GB300, uneven batch of sweeps (batched vs plain)"
@@ -1021,11 +1119,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep", "fc", "batch", "surrogate", "analysis"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "fc", "batch", "surrogate", "analysis", "table4"],
+                    default="sweep",
                     help="sweep: the paper-scale sweep (default); fc: the FC stage alone on 32,768 "
                          "series of 68 regions x 5,000 samples")
     ap.add_argument("--fc-precision", choices=["fp32", "bf16", "bf16x3", "tf32", "tf32x3"], default="bf16x3")
     ap.add_argument("--batch-scale", type=float, default=0.25, help="duration scale of the uneven batch")
+    ap.add_argument("--t4-seconds", type=float, default=1.0, help="biological seconds per set of the Table 4 grid")
     ap.add_argument("--sur-epochs", type=int, default=60)
     ap.add_argument("--sur-rounds", type=int, default=3)
     ap.add_argument("--sur-finetune-epochs", type=int, default=15)
@@ -1036,6 +1136,8 @@ def main():
         return run_surrogate_engine(args)
     if args.workload == "analysis":
         return run_analysis_engine(args)
+    if args.workload == "table4":
+        return run_table4_engine(args)
     if args.workload == "fc":
         return run_fc_reference(args) if args.impl == "reference" else run_fc_engine(args)
     if args.impl == "reference":

@@ -46,6 +46,13 @@ def connectome(n_regions: int, seed: int | None = None, density: float = 0.3,
 SMALL_SWEEP_AXES = [("g", [0.0, 0.1, 0.2, 0.3]), ("b_e", [0.0, 30.0, 60.0, 120.0])]
 PAPER_SCALE_AXES = [("g", (0.0, 0.9, 16)), ("b_e", (0.0, 120.0, 16)),
                     ("E_L_i", (-80.0, -60.0, 16)), ("tau_w_e", (100.0, 1000.0, 8))]
+# The paper's vast exploration (Table 4): ten axes, 8 x 8 x 4^4 x 2^4 =
+# 262,144 parameter sets (ranges and resolutions as printed; c_F in kHz).
+TABLE4_AXES = [("g", (0.1, 0.9, 8)), ("b_e", (0.0, 100.0, 8)), ("w_noise", (1e-9, 1e-4, 4)),
+               ("speed", (1.0, 7.0, 4)), ("tau_w_e", (250.0, 750.0, 4)), ("a_e", (-10.0, 20.0, 4)),
+               ("cF_ee", (0.3e-3, 0.5e-3, 2)), ("cF_ei", (0.0, 0.5e-3, 2)), ("cF_ie", (0.3e-3, 0.5e-3, 2)),
+               ("cF_ii", (0.0, 0.5e-3, 2))]
+
 SMALL_SWEEP = dict(n_regions=68, axes=SMALL_SWEEP_AXES, speed=4.0, dt=0.1, n_steps=10_000,
                    tavg_steps=10, seed=1)
 PAPER_SCALE_SWEEP = dict(n_regions=68, axes=PAPER_SCALE_AXES, speed=4.0, dt=0.1,

@@ -150,6 +150,26 @@ def test_zero_delays_and_uncoupled_regions(tvbx, oracle, conn):
     assert np.array_equal(full[:, :1], lone)
 
 
+def test_table4_ten_axis_sweep(tvbx, oracle, conn):
+    """The ten axes of the paper's vast exploration (Table 4) at their
+    range ends: 1,024 sets in one sweep (four speed groups), expanded in grid
+    order; 48 of them against the oracle (spec tolerances on the
+    well-conditioned sets), and each of them equal to the same point run in a
+    sweep of the 48 explicit points (which also checks the grid order)."""
+    W, L = conn
+    axes = [(name, [lo, hi]) for name, (lo, hi, _) in synth.TABLE4_AXES]
+    pts = oracle.expand_grid(axes)
+    assert pts.shape == (1024, 12)
+    full = _gpu(tvbx, W, L, 3000, 10, axes=axes, seed=6)
+    rng = np.random.default_rng(4)
+    pick = np.sort(rng.choice(1024, 48, replace=False))
+    sub = _gpu(tvbx, W, L, 3000, 10, points=pts[pick], seed=6)
+    assert np.array_equal(full.series()[pick], sub.series(), equal_nan=True)
+    ref = oracle.simulate(oracle.make_model(), W, L, pts[pick], DT, 3000, 10, 6)
+    pert = oracle.simulate(oracle.make_model(PERTURBATION), W, L, pts[pick], DT, 3000, 10, 6)
+    _compare_sweep(sub, ref, oracle, label_frac=0.9, pert=pert)
+
+
 def test_shard_invariance(tvbx, conn):
     W, L = conn
     pts = np.array(synth_points(12))
