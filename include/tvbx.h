@@ -491,6 +491,51 @@ tvbx_status tvbx_top_k(const float* values, int64_t n, int32_t k, int64_t* idx_o
 tvbx_status tvbx_series_analysis(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
                                  double dt_ms, float* out, int32_t* n_used, void* cuda_stream);
 
+/* ---- BOLD signal and phFCD -------------------------------------------------
+ * Sec. "Output": a Balloon-Windkessel kernel (Stephan et al. 2007) gives BOLD
+ * series for comparison with fMRI, and the phase functional connectivity
+ * dynamics (phFCD) of those series is computed for comparison.
+ *
+ * tvbx_bold: forward Euler of the Balloon-Windkessel model (Friston et al.
+ * 2000; Stephan et al. 2007), time in seconds, drive z = the E rate in kHz:
+ *   ds/dt = z - kappa s - gamma (f - 1),  df/dt = s,
+ *   tau dv/dt = f - v^(1/alpha),
+ *   tau dq/dt = f E(f)/E0 - v^(1/alpha) q / v,  E(f) = 1 - (1 - E0)^(1/f),
+ *   y = V0 (k1 (1 - q) + k2 (1 - q/v) + k3 (1 - v)),
+ *   k1 = 4.3 theta0 E0 TE, k2 = eps r0 E0 TE, k3 = 1 - eps;
+ * one step per rate sample (dt_ms), one BOLD value after every `decim`
+ * steps. series: DEVICE [n_samples][n_regions][n_sets] (the engine's layout,
+ * e.g. a stretch of rates the caller keeps); bold_out: DEVICE
+ * [n_samples / decim][n_regions][n_sets]; state: DEVICE [4][n_regions]
+ * [n_sets] = (s, f - 1, v - 1, q - 1), nullable; with reset_state = 1 (or no
+ * state) the integration starts at rest, otherwise from *state, and the final
+ * state is written back, so long runs can be fed in pieces. params NULL =
+ * tvbx_bold_defaults (kappa 0.65 /s, gamma 0.41 /s, tau 0.98 s, alpha 0.32,
+ * E0 0.34, V0 0.02, theta0 40.3 /s, r0 25 /s, TE 0.04 s, eps 1).
+ *
+ * tvbx_phfcd: for each set, the last T'' samples of each region's BOLD
+ * series (T'' the largest number <= min(n_tr, 8192) whose prime factors are
+ * 2, 3 and 5), mean removed; the band-limited analytic signal (DFT bins
+ * 0 < i < T''/2 with i / (T'' tr_s) in [f_lo_hz, f_hi_hz] doubled, all
+ * others 0, inverse DFT); `discard` samples dropped at each end, T' =
+ * T'' - 2 discard kept (returned in *n_used, host, nullable); phases theta
+ * (0 where the signal is 0); dFC_kj(t) = cos(theta_k - theta_j); output
+ * out[p][e] = cosine similarity of the upper triangles (k < j) of dFC(t1)
+ * and dFC(t2) for every t1 < t2, e = t1 T' - t1 (t1 + 1) / 2 + t2 - t1 - 1.
+ * bold: DEVICE [n_tr][n_regions][n_sets]; out: DEVICE [n_sets][T'(T'-1)/2].
+ * 2 <= n_regions <= 4096 (the phase tiles must fit in shared memory).
+ * Both calls are asynchronous on cuda_stream (NULL = legacy default stream). */
+typedef struct {
+    double kappa, gamma, tau, alpha, E0, V0, theta0, r0, TE, eps;
+} tvbx_bold_params;
+tvbx_status tvbx_bold_defaults(tvbx_bold_params* out);
+tvbx_status tvbx_bold(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples, double dt_ms,
+                      int32_t decim, const tvbx_bold_params* params, float* state, int32_t reset_state,
+                      float* bold_out, void* cuda_stream);
+tvbx_status tvbx_phfcd(const float* bold, int32_t n_regions, int64_t n_sets, int64_t n_tr, double tr_s,
+                       double f_lo_hz, double f_hi_hz, int32_t discard, float* out, int32_t* n_used,
+                       void* cuda_stream);
+
 /* ---- Surrogate network ---------------------------------------------------
  * The paper has no surrogate model; it motivates guided exploration of the
  * parameter space (Sec. "Discussion"). This is the learned form of the

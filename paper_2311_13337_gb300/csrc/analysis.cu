@@ -425,6 +425,139 @@ an_finalize_kernel(const float* __restrict__ psd, const int* __restrict__ ud, co
     }
 }
 
+// ---------------------------------------------------------------------------
+// phFCD (Sec. "Output": the phase functional connectivity dynamics of the
+// BOLD series; Deco et al. 2017): phases of the band-limited analytic
+// signals, phase-coherence matrices dFC_kj(t) = cos(theta_k - theta_j), and
+// the cosine similarity of their upper triangles for every t1 < t2. With unit
+// phasors u_k(t), the dot product of two triangles is
+//   ((|sum_k u_k(t1) u_k(t2)|^2 - N) + (|sum_k u_k(t1) conj u_k(t2)|^2 - N)) / 4,
+// so a pair of times costs two complex sums over the regions.
+// ---------------------------------------------------------------------------
+constexpr int PF_TILE = 64;
+constexpr int PF_THREADS = 256;
+
+// One CTA per (set in batch, region): unit phasors of the band-limited
+// analytic signal of the region's BOLD series, U[b][t][k] for the T' kept
+// samples.
+__global__ void __launch_bounds__(AN_THREADS)
+an_phase_kernel(const float* __restrict__ bold, int N, int64_t P, int64_t Tb, FftPlan plan,
+                const float2* __restrict__ tw, int band_lo, int band_hi, int discard, int64_t p0,
+                float2* __restrict__ U)
+{
+    extern __shared__ float2 an_smem[];
+    __shared__ double red_d[AN_THREADS / 32];
+    const int n = plan.n, Tp = n - 2 * discard;
+    float2* b0 = an_smem;
+    float2* b1 = an_smem + n;
+    const int b = blockIdx.x / N, k = blockIdx.x - b * N;
+    const int64_t NP = (int64_t)N * P;
+    const float* col = bold + (Tb - n) * NP + (int64_t)k * P + p0 + b;
+    double s = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const float x = col[(int64_t)t * NP];
+        b0[t] = make_float2(x, 0.0f);
+        s += (double)x;
+    }
+    const float mean = (float)(block_sum(s, red_d) / (double)n);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) b0[t].x -= mean;
+    __syncthreads();
+    float2* X = fft(b0, b1, plan, tw, false);
+    float2* other = X == b0 ? b1 : b0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float h = (i >= band_lo && i <= band_hi) ? 2.0f : 0.0f;
+        X[i] = make_float2(h * X[i].x, h * X[i].y);
+    }
+    __syncthreads();
+    float2* z = fft(X, other, plan, tw, true);
+    float2* Ub = U + (int64_t)b * Tp * N;
+    for (int t = threadIdx.x; t < Tp; t += blockDim.x) {
+        const float2 v = z[t + discard];
+        const float r = hypotf(v.x, v.y);
+        Ub[(int64_t)t * N + k] = r > 0.0f ? make_float2(v.x / r, v.y / r) : make_float2(1.0f, 0.0f);
+    }
+}
+
+// One CTA per (tile pair ta <= tc of 64 x 64 times, set in batch). Tiles are
+// stored region-major in shared memory; thread (m, q) owns times
+// ta*64 + q + 16 i and tc*64 + m + 16 j (i, j < 4), so a half-warp reads 16
+// consecutive 8-byte phasors.
+__global__ void __launch_bounds__(PF_THREADS)
+an_phfcd_kernel(const float2* __restrict__ U, int N, int Tp, int64_t p0, int64_t M2, float* __restrict__ out)
+{
+    extern __shared__ float2 pf_smem[];
+    float2* Ua = pf_smem;                       // [N][64]
+    float2* Uc = pf_smem + (size_t)N * PF_TILE;  // [N][64]
+    __shared__ float nrm_a[PF_TILE], nrm_c[PF_TILE];
+    const int nt = (Tp + PF_TILE - 1) / PF_TILE;
+    int ta = 0, rem = blockIdx.x;
+    while (rem >= nt - ta) { rem -= nt - ta; ++ta; }
+    const int tc = ta + rem;
+    const int b = blockIdx.y;
+    const float2* Ub = U + (int64_t)b * Tp * N;
+    for (int i = threadIdx.x; i < PF_TILE * N; i += blockDim.x) {
+        const int r = i / N, k = i - r * N;
+        const int t1 = ta * PF_TILE + r, t2 = tc * PF_TILE + r;
+        Ua[k * PF_TILE + r] = t1 < Tp ? Ub[(int64_t)t1 * N + k] : make_float2(0.0f, 0.0f);
+        Uc[k * PF_TILE + r] = t2 < Tp ? Ub[(int64_t)t2 * N + k] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    // |V(t)| from S = sum_k u_k^2: |V|^2 = ((|S|^2 - N) + N^2 - N) / 4
+    if (threadIdx.x < 2 * PF_TILE) {
+        const int r = threadIdx.x & (PF_TILE - 1);
+        const float2* T = threadIdx.x < PF_TILE ? Ua : Uc;
+        float sx = 0.0f, sy = 0.0f;
+        for (int k = 0; k < N; ++k) {
+            const float2 u = T[k * PF_TILE + r];
+            sx += u.x * u.x - u.y * u.y;
+            sy += 2.0f * u.x * u.y;
+        }
+        const float fN = (float)N;
+        const float v2 = 0.25f * (fmaf(sx, sx, sy * sy) - fN + fN * fN - fN);
+        (threadIdx.x < PF_TILE ? nrm_a : nrm_c)[r] = sqrtf(fmaxf(v2, 0.0f));
+    }
+    __syncthreads();
+    const int q = threadIdx.x >> 4, m = threadIdx.x & 15;
+    float ax[4][4], ay[4][4], bx[4][4], by[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ax[i][j] = ay[i][j] = bx[i][j] = by[i][j] = 0.0f;
+    for (int k = 0; k < N; ++k) {
+        float2 ua[4], uc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ua[i] = Ua[k * PF_TILE + q + 16 * i];
+            uc[i] = Uc[k * PF_TILE + m + 16 * i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                // A += ua uc, B += ua conj(uc)
+                ax[i][j] = fmaf(ua[i].x, uc[j].x, fmaf(-ua[i].y, uc[j].y, ax[i][j]));
+                ay[i][j] = fmaf(ua[i].x, uc[j].y, fmaf(ua[i].y, uc[j].x, ay[i][j]));
+                bx[i][j] = fmaf(ua[i].x, uc[j].x, fmaf(ua[i].y, uc[j].y, bx[i][j]));
+                by[i][j] = fmaf(ua[i].y, uc[j].x, fmaf(-ua[i].x, uc[j].y, by[i][j]));
+            }
+    }
+    const float fN = (float)N;
+    float* o = out + (p0 + b) * M2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int ra = q + 16 * i, rc = m + 16 * j;
+            const int t1 = ta * PF_TILE + ra, t2 = tc * PF_TILE + rc;
+            if (t1 < t2 && t2 < Tp) {
+                const float dot = 0.25f * ((fmaf(ax[i][j], ax[i][j], ay[i][j] * ay[i][j]) - fN) +
+                                           (fmaf(bx[i][j], bx[i][j], by[i][j] * by[i][j]) - fN));
+                const int64_t e = (int64_t)t1 * Tp - (int64_t)t1 * (t1 + 1) / 2 + (t2 - t1 - 1);
+                o[e] = dot / (nrm_a[ra] * nrm_c[rc]);
+            }
+        }
+}
+
 int smooth_length(int64_t n)
 {
     for (int64_t m = std::min<int64_t>(n, AN_MAX_T); m > 0; --m) {
@@ -557,5 +690,65 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
         ACK(cudaGetLastError(), "analysis finalize");
     }
     if (n_used) *n_used = n;
+    return TVBX_OK;
+}
+
+extern "C" tvbx_status tvbx_phfcd(const float* bold, int32_t n_regions, int64_t n_sets, int64_t n_tr, double tr_s,
+                                  double f_lo_hz, double f_hi_hz, int32_t discard, float* out, int32_t* n_used,
+                                  void* cuda_stream)
+{
+    const int N = n_regions;
+    const int64_t P = n_sets;
+    if (!bold || !out) return report_error(TVBX_E_INVALID_ARG, "NULL bold or out");
+    if (N < 2 || N > 4096 || P < 1 || n_tr < 2 || discard < 0)
+        return report_error(TVBX_E_INVALID_ARG, "need 2 <= n_regions <= 4096, n_sets >= 1, n_tr >= 2, discard >= 0");
+    if (!(tr_s > 0.0) || !std::isfinite(tr_s) || !(f_lo_hz <= f_hi_hz))
+        return report_error(TVBX_E_INVALID_ARG, "need tr_s > 0 and f_lo_hz <= f_hi_hz");
+    const int n = smooth_length(n_tr);
+    FftPlan plan;
+    if (n < 2 || !make_plan(n, plan)) return report_error(TVBX_E_INVALID_ARG, "no transform length for %lld samples", (long long)n_tr);
+    const int Tp = n - 2 * discard;
+    if (Tp < 2) return report_error(TVBX_E_INVALID_ARG, "fewer than 2 samples left after discarding %d at each end", discard);
+    int band_lo = n, band_hi = -1;   // empty unless a bin 0 < i < n/2 has its frequency in the band
+    for (int i = 1; 2 * i < n; ++i) {
+        const double f = (double)i / ((double)n * tr_s);
+        if (f >= f_lo_hz && f <= f_hi_hz) {
+            band_lo = std::min(band_lo, i);
+            band_hi = std::max(band_hi, i);
+        }
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int64_t per_set = (int64_t)Tp * N * 8;
+    const int64_t B = std::max<int64_t>(1, std::min<int64_t>(P, ((int64_t)1 << 30) / std::max<int64_t>(per_set, 1)));
+    std::vector<float2> htw(n);
+    for (int e = 0; e < n; ++e) {
+        const double ang = -2.0 * 3.14159265358979323846 * (double)e / (double)n;
+        htw[e] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    AnScratch scr(s);
+    float2 *tw, *U;
+    ACK(scr.get(&tw, n), "phFCD twiddles");
+    ACK(scr.get(&U, (size_t)B * Tp * N), "phFCD phasors");
+    ACK(cudaMemcpyAsync(tw, htw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s), "phFCD twiddles");
+    const size_t smem_phase = sizeof(float2) * 2 * (size_t)n;
+    ACK(cudaFuncSetAttribute(an_phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phase),
+        "phFCD shared memory");
+    const size_t smem_pf = sizeof(float2) * 2 * (size_t)N * PF_TILE;
+    if (smem_pf > 200 * 1024) return report_error(TVBX_E_INVALID_ARG, "too many regions for the phFCD tiles");
+    ACK(cudaFuncSetAttribute(an_phfcd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pf),
+        "phFCD shared memory");
+    const int nt = (Tp + PF_TILE - 1) / PF_TILE;
+    const int64_t M2 = (int64_t)Tp * (Tp - 1) / 2;
+    for (int64_t p0 = 0; p0 < P; p0 += B) {
+        const int64_t nb = std::min<int64_t>(B, P - p0);
+        note_launch(2);
+        an_phase_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_phase, s>>>(bold, N, P, n_tr, plan, tw, band_lo,
+                                                                          band_hi, discard, p0, U);
+        ACK(cudaGetLastError(), "phFCD phases");
+        an_phfcd_kernel<<<dim3((unsigned)(nt * (nt + 1) / 2), (unsigned)nb), PF_THREADS, smem_pf, s>>>(U, N, Tp, p0,
+                                                                                                       M2, out);
+        ACK(cudaGetLastError(), "phFCD");
+    }
+    if (n_used) *n_used = Tp;
     return TVBX_OK;
 }

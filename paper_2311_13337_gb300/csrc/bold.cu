@@ -1,0 +1,139 @@
+// Balloon-Windkessel BOLD signal of the simulated excitatory rates
+// (arXiv 2311.13337, Sec. "Output": a Balloon-Windkessel kernel, Stephan et
+// al. 2007, turns the simulated activity into BOLD series for comparison with
+// fMRI).
+//
+// Model (Friston et al. 2000; Stephan et al. 2007), drive z = E rate in kHz,
+// time in seconds:
+//   ds/dt = z - kappa s - gamma (f - 1),  df/dt = s,
+//   tau dv/dt = f - v^(1/alpha),
+//   tau dq/dt = f E(f) / E0 - v^(1/alpha) q / v,  E(f) = 1 - (1 - E0)^(1/f),
+//   y = V0 (k1 (1 - q) + k2 (1 - q/v) + k3 (1 - v)).
+// One thread per (region, set) integrates forward Euler with the step of the
+// rate samples. The state is kept as deviations from rest (f - 1, v - 1,
+// q - 1) and the powers are written with log1p / expm1, so FP32 resolves the
+// small excursions a drive of a few Hz causes (about 1e-3 of the resting
+// values) instead of rounding them against 1, and a zero drive keeps the
+// resting state exactly.
+//
+// Layouts: series [T][N][P] (the engine's layout: consecutive threads read
+// consecutive sets), BOLD [T / decim][N][P], state [4][N][P] = s, f - 1,
+// v - 1, q - 1.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "internal.h"
+#include "tvbx.h"
+
+namespace tvbx {
+namespace {
+
+struct BoldDev {
+    float kappa, gamma, inv_tau, inv_alpha, r_E0, lnE, V0, k1, k2, k3, dt;   // r_E0 = (1 - E0) / E0
+};
+
+__global__ void bold_kernel(const float* __restrict__ series, int64_t NP, int64_t T, int decim, BoldDev c,
+                            float* __restrict__ state, int reset, float* __restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= NP) return;
+    float s = 0.0f, ft = 0.0f, vt = 0.0f, qt = 0.0f;
+    if (state && !reset) {
+        s = state[i];
+        ft = state[NP + i];
+        vt = state[2 * NP + i];
+        qt = state[3 * NP + i];
+    }
+    int phase = 0;
+    int64_t o = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        const float z = __ldg(series + t * NP + i);
+        const float f = 1.0f + ft;
+        const float lv = log1pf(vt);
+        const float vpa_m1 = expm1f(lv * c.inv_alpha);                        // v^(1/alpha) - 1
+        // f E(f) / E0 - 1 = ft - (1 + ft) r_E0 expm1(-ln(1 - E0) ft / f), since
+        // (1 - E0)^(1/f) = (1 - E0) exp(-ln(1 - E0) ft / f): exactly 0 at rest
+        const float fE_m1 = fmaf(-f * c.r_E0, expm1f(-c.lnE * ft / f), ft);
+        const float vq_m1 = fmaf(expm1f((c.inv_alpha - 1.0f) * lv), 1.0f + qt, qt);   // v^(1/alpha - 1) q - 1
+        const float ds = z - c.kappa * s - c.gamma * ft;
+        const float nft = fmaf(c.dt, s, ft);
+        const float nvt = fmaf(c.dt * c.inv_tau, ft - vpa_m1, vt);
+        const float nqt = fmaf(c.dt * c.inv_tau, fE_m1 - vq_m1, qt);
+        s = fmaf(c.dt, ds, s);
+        ft = nft;
+        vt = nvt;
+        qt = nqt;
+        if (++phase == decim) {
+            phase = 0;
+            // 1 - q = -qt, 1 - q / v = (vt - qt) / (1 + vt), 1 - v = -vt
+            out[o * NP + i] = c.V0 * (c.k3 * -vt + fmaf(c.k1, -qt, c.k2 * (vt - qt) / (1.0f + vt)));
+            ++o;
+        }
+    }
+    if (state) {
+        state[i] = s;
+        state[NP + i] = ft;
+        state[2 * NP + i] = vt;
+        state[3 * NP + i] = qt;
+    }
+}
+
+}  // namespace
+}  // namespace tvbx
+
+using namespace tvbx;
+
+extern "C" tvbx_status tvbx_bold_defaults(tvbx_bold_params* out)
+{
+    if (!out) return report_error(TVBX_E_INVALID_ARG, "NULL out");
+    out->kappa = 0.65;
+    out->gamma = 0.41;
+    out->tau = 0.98;
+    out->alpha = 0.32;
+    out->E0 = 0.34;
+    out->V0 = 0.02;
+    out->theta0 = 40.3;
+    out->r0 = 25.0;
+    out->TE = 0.04;
+    out->eps = 1.0;
+    return TVBX_OK;
+}
+
+extern "C" tvbx_status tvbx_bold(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
+                                 double dt_ms, int32_t decim, const tvbx_bold_params* params, float* state,
+                                 int32_t reset_state, float* bold_out, void* cuda_stream)
+{
+    if (!series || !bold_out) return report_error(TVBX_E_INVALID_ARG, "NULL series or bold_out");
+    if (n_regions < 1 || n_sets < 1 || n_samples < 0 || decim < 1)
+        return report_error(TVBX_E_INVALID_ARG, "need n_regions >= 1, n_sets >= 1, n_samples >= 0, decim >= 1");
+    if (!(dt_ms > 0.0) || !std::isfinite(dt_ms)) return report_error(TVBX_E_INVALID_ARG, "dt_ms must be > 0");
+    tvbx_bold_params p;
+    if (params) p = *params;
+    else tvbx_bold_defaults(&p);
+    if (!(p.tau > 0.0) || !(p.alpha > 0.0) || !(p.E0 > 0.0 && p.E0 < 1.0))
+        return report_error(TVBX_E_INVALID_ARG, "need tau > 0, alpha > 0, 0 < E0 < 1");
+    BoldDev c;
+    c.kappa = (float)p.kappa;
+    c.gamma = (float)p.gamma;
+    c.inv_tau = (float)(1.0 / p.tau);
+    c.inv_alpha = (float)(1.0 / p.alpha);
+    c.r_E0 = (float)((1.0 - p.E0) / p.E0);
+    c.lnE = (float)std::log1p(-p.E0);
+    c.V0 = (float)p.V0;
+    c.k1 = (float)(4.3 * p.theta0 * p.E0 * p.TE);
+    c.k2 = (float)(p.eps * p.r0 * p.E0 * p.TE);
+    c.k3 = (float)(1.0 - p.eps);
+    c.dt = (float)(dt_ms * 1e-3);
+    const int64_t NP = (int64_t)n_regions * n_sets;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    note_launch();
+    bold_kernel<<<(unsigned)((NP + 255) / 256), 256, 0, s>>>(series, NP, n_samples, decim, c, state, reset_state,
+                                                            bold_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return report_error(TVBX_E_CUDA, "BOLD: %s", cudaGetErrorString(e));
+    return TVBX_OK;
+}

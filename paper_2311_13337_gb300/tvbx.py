@@ -91,7 +91,7 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_surrogate_predict", "tvbx_surrogate_propose", "tvbx_surrogate_params", "tvbx_surrogate_gradients",
            "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project", "tvbx_batch_create", "tvbx_batch_tune",
            "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy", "tvbx_fc_fitness", "tvbx_top_k",
-           "tvbx_series_analysis")
+           "tvbx_series_analysis", "tvbx_bold_defaults", "tvbx_bold", "tvbx_phfcd")
 
 
 def library_path() -> str:
@@ -150,6 +150,10 @@ def load(build_if_missing: bool = False):
     L.tvbx_fc_fitness.argtypes = [fp, i64, i32, fp, i32, fp, vp]
     L.tvbx_top_k.argtypes = [fp, i64, i32, fp, fp, vp]
     L.tvbx_series_analysis.argtypes = [fp, i32, i64, i64, ctypes.c_double, fp, ctypes.POINTER(i32), vp]
+    L.tvbx_bold_defaults.argtypes = [ctypes.POINTER(BoldParams)]
+    L.tvbx_bold.argtypes = [fp, i32, i64, i64, ctypes.c_double, i32, ctypes.POINTER(BoldParams), fp, i32, fp, vp]
+    L.tvbx_phfcd.argtypes = [fp, i32, i64, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, fp,
+                             ctypes.POINTER(i32), vp]
     L.tvbx_transfer_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.tvbx_profile_enable.argtypes = [vp, i32]
     L.tvbx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -562,7 +566,7 @@ def series_analysis(series, dt_ms, out=None, stream=None):
     used = ctypes.c_int32(0)
     _check(load().tvbx_series_analysis(ctypes.c_void_p(x.data_ptr()), N, P, T, float(dt_ms),
                                        ctypes.c_void_p(out.data_ptr()), ctypes.byref(used), _stream_ptr(stream)),
-           "tvbx_series_analysis")
+           "tvbx_series_analysis", "tvbx_bold_defaults", "tvbx_bold", "tvbx_phfcd")
     return out, used.value
 
 
@@ -581,6 +585,60 @@ def sweep_analysis(sw, dt_ms, transient_samples=0, batch_sets=4096, stream=None)
         series_range(sw.h, p0, m, int(transient_samples), nt, buf[:m])
         _, used = series_analysis(buf[:m], dt_ms, out=out[p0:p0 + m], stream=stream)
     return out, used
+
+
+class BoldParams(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("kappa", "gamma", "tau", "alpha", "E0", "V0", "theta0", "r0", "TE",
+                                               "eps")]
+
+
+def bold_defaults() -> dict:
+    p = BoldParams()
+    _check(load().tvbx_bold_defaults(ctypes.byref(p)), "tvbx_bold_defaults")
+    return {k: getattr(p, k) for k, _ in BoldParams._fields_}
+
+
+def bold(series, dt_ms, decim, params=None, state=None, reset_state=True, stream=None):
+    """Balloon-Windkessel BOLD (tvbx_bold) of CUDA rates [T][N][P] (kHz):
+    a CUDA tensor [T // decim][N][P]; `state` (CUDA [4][N][P]) is read unless
+    reset_state and written back."""
+    import torch
+    x = series.contiguous()
+    T, N, P = x.shape
+    out = torch.empty((T // int(decim), N, P), dtype=torch.float32, device=x.device)
+    pp = None
+    if params is not None:
+        pp = ctypes.byref(BoldParams(**params))
+    st = ctypes.c_void_p(state.data_ptr()) if state is not None else None
+    _check(load().tvbx_bold(ctypes.c_void_p(x.data_ptr()), N, P, T, float(dt_ms), int(decim), pp, st,
+                            1 if reset_state else 0, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "tvbx_bold")
+    return out
+
+
+def phfcd(bold_series, tr_s, f_lo_hz=0.008, f_hi_hz=0.08, discard=0, stream=None):
+    """phFCD (tvbx_phfcd) of CUDA BOLD series [T][N][P]: (CUDA tensor
+    [P][T'(T'-1)/2], T')."""
+    import torch
+    x = bold_series.contiguous()
+    T, N, P = x.shape
+    n = T
+    # T'' (largest 2-3-5-smooth length <= min(T, 8192)) decides the output size
+    for m in range(min(T, 8192), 0, -1):
+        r = m
+        for f in (2, 3, 5):
+            while r % f == 0:
+                r //= f
+        if r == 1:
+            n = m
+            break
+    Tp = n - 2 * int(discard)
+    out = torch.empty((P, max(Tp * (Tp - 1) // 2, 1)), dtype=torch.float32, device=x.device)
+    used = ctypes.c_int32(0)
+    _check(load().tvbx_phfcd(ctypes.c_void_p(x.data_ptr()), N, P, T, float(tr_s), float(f_lo_hz), float(f_hi_hz),
+                             int(discard), ctypes.c_void_p(out.data_ptr()), ctypes.byref(used), _stream_ptr(stream)),
+           "tvbx_phfcd")
+    return out, used.value
 
 
 class Surrogate:

@@ -114,3 +114,8 @@ def test_binding_has_every_function_its_callers_use():
         used |= set(re.findall(r"\btvbx\.([A-Za-z_][A-Za-z_0-9]*)", open(os.path.join(root, f)).read()))
     missing = sorted(n for n in used if not hasattr(tvbx, n))
     assert not missing, missing
+
+
+def test_bold_defaults_match_the_oracle(lib):
+    from oracle import bold as B
+    assert lib.bold_defaults() == B.BW_PARAMS
