@@ -566,7 +566,7 @@ def series_analysis(series, dt_ms, out=None, stream=None):
     used = ctypes.c_int32(0)
     _check(load().tvbx_series_analysis(ctypes.c_void_p(x.data_ptr()), N, P, T, float(dt_ms),
                                        ctypes.c_void_p(out.data_ptr()), ctypes.byref(used), _stream_ptr(stream)),
-           "tvbx_series_analysis", "tvbx_bold_defaults", "tvbx_bold", "tvbx_phfcd")
+           "tvbx_series_analysis")
     return out, used.value
 
 

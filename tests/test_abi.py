@@ -119,3 +119,13 @@ def test_binding_has_every_function_its_callers_use():
 def test_bold_defaults_match_the_oracle(lib):
     from oracle import bold as B
     assert lib.bold_defaults() == B.BW_PARAMS
+
+
+def test_every_status_check_in_the_binding_names_one_call():
+    """Each _check(status, where) in the binding passes exactly two arguments
+    (a malformed call would only fail when that entry point runs on a GPU)."""
+    import ast
+    src = open(os.path.join(ROOT, "paper_2311_13337_gb300", "tvbx.py")).read()
+    calls = [n for n in ast.walk(ast.parse(src))
+             if isinstance(n, ast.Call) and getattr(n.func, "id", None) == "_check"]
+    assert calls and all(len(c.args) == 2 and not c.keywords for c in calls)
