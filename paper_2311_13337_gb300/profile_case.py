@@ -3,6 +3,7 @@
   python -m paper_2311_13337_gb300.profile_case --sets 8192 --n-steps 1000 --chunk 500 [--fc]
   python -m paper_2311_13337_gb300.profile_case --fc-series --sets 4096 --samples 5000 --fc-precision bf16x3
   python -m paper_2311_13337_gb300.profile_case --analysis --sets 4096 --samples 5000
+  python -m paper_2311_13337_gb300.profile_case --bold --sets 8192 --samples 10000
 
 Takes the first `--sets` sets of the 32,768-set grid (68 regions, v 4 m/s),
 integrates `--n-steps` steps in launches of `--chunk` steps and optionally
@@ -10,7 +11,9 @@ runs the FC/FCD pass, then prints the wall time. With --fc-series, runs
 only the FC stage (tvbx_fc_series, FCD 1000/500 unless --no-fcd) on
 synthetic rate-like series of `--sets` x 68 regions x `--samples`. With
 --analysis, runs only the Table 2 metrics (tvbx_series_analysis) on such
-series in the [sets][regions][samples] layout. Sized so
+series in the [sets][regions][samples] layout. With --bold, runs the
+Balloon-Windkessel kernel on such rates (TR 1 s) and the phFCD of 300 TRs.
+Sized so
 that a profiler can capture single launches on a few GB of device memory.
 """
 from __future__ import annotations
@@ -39,7 +42,10 @@ def main():
     ap.add_argument("--no-fcd", action="store_true")
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--analysis", action="store_true")
+    ap.add_argument("--bold", action="store_true")
     args = ap.parse_args()
+    if args.bold:
+        return bold_case(args)
     if args.fc_series:
         return fc_series_case(args)
     if args.analysis:
@@ -93,6 +99,24 @@ def fc_series_case(args):
         tvbx.fc_series(X, N, P, T, precision=prec, fc_out=fc, fcd_out=fcd if w else None, fcd_window=w,
                        fcd_step=s)
         print(f"fc series {P} x {N} x {T} {args.fc_precision}: {time.time() - t0:.4f} s")
+
+
+def bold_case(args):
+    import torch
+
+    from paper_2311_13337_gb300 import build, synth, tvbx
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    P, N, T = args.sets, 68, args.samples
+    X = synth.rate_series_device(torch, dev, P, N, T, seed=5)
+    Y = torch.randn((300, N, P), device=dev)
+    for i in range(args.repeat):
+        t0 = time.time()
+        tvbx.bold(X, 1.0, 1000)
+        tvbx.phfcd(Y, 1.0, 0.008, 0.08, 9)
+        torch.cuda.synchronize()
+        print(f"bold {P} x {N} x {T} + phfcd 300: {time.time() - t0:.4f} s")
 
 
 def analysis_case(args):
