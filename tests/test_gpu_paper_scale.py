@@ -9,7 +9,7 @@ About a third of the sets pass through the clamp of E and I at 0 or 0.2 kHz;
 there the FP64 trajectory moves far under the 1e-7 perturbation, so the
 engine is held to that spread. On the well-conditioned sets (no clamp,
 divergence or non-finite event, and a relative sensitivity below 1e-5 over
-the compared window) the benchmark spec's tolerances apply: trajectories
+the compared window) the parity tolerances apply: trajectories
 within 1e-3 over the first 200 ms, mean rates within 1%, FC within 0.05, and
 the synchrony label on >= 99% of the finite sets."""
 import numpy as np
@@ -50,7 +50,7 @@ def test_paper_scale_sweep_sampled(oracle):
 
     # well-conditioned sets (no clamp, divergence or non-finite event, and an
     # FP64 trajectory that the persistent 1e-7 perturbation moves by < 1e-5):
-    # spec tolerances
+    # parity tolerances
     wc = conditioned_sets(st, ref["status"]) & stable_sets(ref["E"], pert["E"])
     assert wc.sum() >= 100
     err = rel_err(E[wc], ref["E"][wc, :, :200])

@@ -71,7 +71,7 @@ def test_first_steps_every_state_variable(tvbx, oracle, conn, n_steps):
 
 
 def _compare_sweep(tvbx_sw, ref, oracle, traj_samples=200, label_frac=1.0, pert=None):
-    """Spec tolerances on the well-conditioned sets (no clamp, divergence
+    """Parity tolerances on the well-conditioned sets (no clamp, divergence
     or non-finite event on either side, and, given a perturbed oracle run, an
     FP64 trajectory that is stable under it); labels on every finite set."""
     E = tvbx_sw.series()
@@ -153,7 +153,7 @@ def test_zero_delays_and_uncoupled_regions(tvbx, oracle, conn):
 def test_table4_ten_axis_sweep(tvbx, oracle, conn):
     """The ten axes of the paper's vast exploration (Table 4) at their
     range ends: 1,024 sets in one sweep (four speed groups), expanded in grid
-    order; 48 of them against the oracle (spec tolerances on the
+    order; 48 of them against the oracle (parity tolerances on the
     well-conditioned sets), and each of them equal to the same point run in a
     sweep of the 48 explicit points (which also checks the grid order)."""
     W, L = conn
