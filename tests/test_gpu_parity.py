@@ -248,6 +248,20 @@ def test_invalid_run_arguments(tvbx, conn):
     assert e.value.code == -1
 
 
+def test_oversized_sweep_reports_out_of_memory(tvbx, conn):
+    """16.8 million sets at 1 m/s need a ring of about 9 TB: the run reports
+    TVBX_E_OOM (an allocation that fails, nothing launched), and the device
+    stays usable for the next sweep."""
+    W, L = conn
+    big = tvbx.Sweep(W, L, axes=[("g", (0.0, 0.9, 4096)), ("b_e", (0.0, 120.0, 4096)), ("speed", [1.0])])
+    with pytest.raises(tvbx.TvbxError) as e:
+        big.run(dt_ms=DT, n_steps=100, tavg_steps=10)
+    assert e.value.code == -2
+    big.close()
+    ok = _gpu(tvbx, W, L, 200, 10, axes=[("g", [0.2])], seed=1)
+    assert np.all(np.isfinite(ok.series()))
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(tvbx, conn):
     """The TMA-copy kernel's waits are bounded: withholding one step's copies
     (a flag that no copy satisfies) makes the wait expire; the run reports
