@@ -128,6 +128,26 @@ def ncu_traffic_per_region_step():
     return d.get("dram_bytes_per_region_step")
 
 
+def fc_kernel_source_hash() -> str:
+    """Hash of the sources the tensor-core FC kernel is built from."""
+    h = hashlib.sha256()
+    for f in ("fc_tc.cu", "ptx_async.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2311_13337_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_fc_traffic_per_set():
+    """DRAM bytes per set (68 regions x 5,000 samples, bf16x3) of the FC kernel
+    from the committed ncu summary, if taken on the current kernel source."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "fc_tc_traffic.json")))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_sha256_16") != fc_kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_set")
+
+
 def algorithmic_bytes_per_region_step(W, tavg_steps):
     """Coupling gather (4 B per nonzero weight of the row) + ring write (4 B)
     + series write (4 B per tavg_steps steps)."""
@@ -578,8 +598,9 @@ def run_fc_engine(args):
         peak = peaks.get("hbm_gbs") if peaks else 6800.0
         alg_bytes = 4.0 * units + 4.0 * P * (N * N + nw * nw + 2)
         achieved = alg_bytes / (dev_ms * 1e-3) / 1e9
+        tr_set = ncu_fc_traffic_per_set() if args.fc_precision == "bf16x3" else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "fc_tc_kernel (" + args.fc_precision + ")",
+                    "traffic": tr_set * P if tr_set else None, "kernel": "fc_tc_kernel (" + args.fc_precision + ")",
                     "peak_source": "measured" if peaks else "fallback",
                     "timed": "whole FC stage per step (shift, tensor-core moments, finalize, FCD), CUDA events",
                     "algorithmic_bytes_per_step": alg_bytes, "avg_step_device_ms": dev_ms}

@@ -140,6 +140,10 @@ typedef struct {
                                  stays usable). Other kernels ignore it. */
 } tvbx_run_cfg;
 #define TVBX_KERNEL_AUTO     0 /* fastest kernel that fits the sweep */
+#define TVBX_KERNEL_DIRECT 100 /* register tiles for connectomes too large for the
+                                  prefetch buffer (up to 768 regions): 4 sets of
+                                  one region per thread, 16-byte ring gathers;
+                                  results bit-identical to TVBX_KERNEL_GENERAL */
 #define TVBX_KERNEL_GENERAL  1 /* any size: state in shared memory, direct gathers */
 #define TVBX_KERNEL_PREFETCH 2 /* + v: next-step gather prefetched into shared
                                   memory; CTA of 16 or 32 sets; cp.async into one
@@ -367,13 +371,18 @@ tvbx_status tvbx_batch_create(tvbx_sweep* const* jobs, const tvbx_run_cfg* cfgs,
                               tvbx_batch** out);
 
 /* Autotuner: builds and times (two graph launches each, CUDA events) the
- * batch with each candidate tiling -- threads per CTA in {128, 256, 512}
- * (regions per thread = ceil(N pb / threads)) and a shared-memory budget in
- * {64, 100, 200} KB, which sets each job's sets per CTA pb in {32, 16, 8}
- * (the widest whose state fits) and the CTAs per SM -- on runs shortened to
- * trial_steps steps per job, keeps the fastest and rebuilds the full batch
- * with it. threads_out, smem_kb_out: the choice; trial_ms [n_trials] (host,
- * nullable; 6 entries, INFINITY where a candidate does not fit). */
+ * batch with each candidate tiling and keeps the fastest, rebuilding the full
+ * batch with it. Candidates, in this order: six of the general body --
+ * threads per CTA and shared-memory budget (256, 100 KB), (512, 100 KB),
+ * (256, 200 KB), (512, 200 KB), (128, 64 KB), (256, 64 KB); the budget sets
+ * each job's sets per CTA pb in {32, 16, 8} (the widest whose state fits) --
+ * then two of the register-tile body (threads 512 and 768: each job with
+ * N <= threads gets pb = 4 floor(threads / N) sets per CTA, 4 sets of one
+ * region per thread; larger jobs keep the general body with a 200 KB budget).
+ * Runs are shortened to trial_steps steps per job. threads_out, smem_kb_out:
+ * the choice (smem_kb_out is the general body's budget); trial_ms [n_trials]
+ * (host, nullable; 8 entries, INFINITY where a candidate does not fit).
+ * Every candidate gives the same results bit for bit. */
 tvbx_status tvbx_batch_tune(tvbx_batch* b, int64_t trial_steps, int32_t* threads_out, int32_t* smem_kb_out,
                             float* trial_ms, int32_t* n_trials);
 

@@ -492,8 +492,8 @@ tvbx_status tvbx_sweep_info(const tvbx_sweep* h, int64_t* n_sets, int32_t* n_reg
 // Everything a run needs before its first simulation launch: argument
 // checks, delay groups, internal set order, kernel and tile choice, device
 // buffers and uploads; with device_init also the state and ring
-// initialisation on stream s. general_pb > 0 forces the general kernel with
-// that tile width (used by batches).
+// initialisation on stream s. general_pb > 0 forces the general kernel (or,
+// with direct_body, the register-tile body) with that tile width (batches).
 struct RunPlan {
     SimArgs a;
     int variant = -1;
@@ -507,7 +507,7 @@ struct RunPlan {
 };
 
 static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_t s, int general_pb,
-                               bool device_init, RunPlan& plan)
+                               bool device_init, RunPlan& plan, bool direct_body = false)
 {
     if (!(c.dt_ms > 0.0) || !isfinite(c.dt_ms)) return fail(TVBX_E_INVALID_ARG, "dt_ms must be > 0");
     if (c.n_steps < 0 || c.n_steps > ((int64_t)1 << 32) - 2)
@@ -554,16 +554,23 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     // gather buffer fits, else the general kernel
     int nnz_max = 0;
     for (const Group& g : groups) nnz_max = std::max(nnz_max, (int)g.col_dly.size());
-    if (c.kernel < TVBX_KERNEL_AUTO || c.kernel >= TVBX_KERNEL_PREFETCH + sim_fast_variants())
+    if (c.kernel != TVBX_KERNEL_DIRECT &&
+        (c.kernel < TVBX_KERNEL_AUTO || c.kernel >= TVBX_KERNEL_PREFETCH + sim_fast_variants()))
         return fail(TVBX_E_INVALID_ARG, "unknown kernel %d", c.kernel);
     if (c.withhold_step < 0) return fail(TVBX_E_INVALID_ARG, "withhold_step must be >= 0");
-    int variant = -1;   // prefetch variant, -1 = general kernel
+    int variant = -1;   // prefetch variant, -1 = general kernel, -2 = register-tile kernel
     if (general_pb > 0) {
-        // batch: general kernel with the batch's tile width
+        // batch: the batch's body and tile width
+        if (direct_body) variant = -2;
     } else if (c.kernel == TVBX_KERNEL_AUTO) {
-        // preference order from measurement on the 32,768-set, 68-region sweep
+        // preference order from measurement on the 32,768-set, 68-region sweep;
+        // connectomes too large for the prefetch buffer take the register tiles
         for (int v : {1, 0, 2, 3})
             if (sim_fast_fits(v, N, nnz_max)) { variant = v; break; }
+        if (variant < 0 && sim_direct_pb(N) > 0) variant = -2;
+    } else if (c.kernel == TVBX_KERNEL_DIRECT) {
+        if (sim_direct_pb(N) == 0) return fail(TVBX_E_UNSUPPORTED, "register-tile kernel: too many regions (%d)", N);
+        variant = -2;
     } else if (c.kernel != TVBX_KERNEL_GENERAL) {
         variant = c.kernel - TVBX_KERNEL_PREFETCH;
         if (!sim_fast_fits(variant, N, nnz_max))
@@ -573,9 +580,12 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     int pb = 16;
     if (general_pb > 0) {
         pb = general_pb;
-        if (sim_smem_bytes(N, pb) > 227 * 1024) return fail(TVBX_E_UNSUPPORTED, "n_regions %d too large", N);
+        if (!direct_body && sim_smem_bytes(N, pb) > 227 * 1024)
+            return fail(TVBX_E_UNSUPPORTED, "n_regions %d too large", N);
     } else if (variant >= 0) {
         pb = sim_fast_pb(variant);
+    } else if (variant == -2) {
+        pb = sim_direct_pb(N);
     } else {
         while (pb > 8 && sim_smem_bytes(N, pb) > 200 * 1024) pb /= 2;
         if (sim_smem_bytes(N, pb) > 200 * 1024) return fail(TVBX_E_UNSUPPORTED, "n_regions %d too large", N);
@@ -737,6 +747,7 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
             CK(cudaEventRecord(h->ev[h->ev_used], s), "profiling event");
         }
         if (variant >= 0) CK(launch_sim_fast(a, variant, plan.n_tiles, plan.nnz_max, s), "simulation chunk");
+        else if (variant == -2) CK(launch_sim_direct(a, plan.n_tiles, plan.pb, s), "simulation chunk");
         else CK(launch_sim_chunk(a, plan.n_tiles, plan.pb, s), "simulation chunk");
         if (h->profiling) {
             CK(cudaEventRecord(h->ev[h->ev_used + 1], s), "profiling event");
@@ -1105,7 +1116,9 @@ tvbx_status tvbx_last_kernel(const tvbx_sweep* h, int32_t* kernel, int32_t* sets
 {
     if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
     if (!h->ran) return fail(TVBX_E_BAD_STATE, "tvbx_last_kernel before tvbx_run");
-    if (kernel) *kernel = h->variant < 0 ? TVBX_KERNEL_GENERAL : TVBX_KERNEL_PREFETCH + h->variant;
+    if (kernel)
+        *kernel = h->variant == -2 ? TVBX_KERNEL_DIRECT
+                                   : (h->variant < 0 ? TVBX_KERNEL_GENERAL : TVBX_KERNEL_PREFETCH + h->variant);
     if (sets_per_tile) *sets_per_tile = h->pb;
     return TVBX_OK;
 }
@@ -1165,6 +1178,8 @@ struct tvbx_batch {
     cudaStream_t stream = nullptr;
     int32_t threads = 512;
     size_t smem_budget = 200 * 1024;
+    bool direct = false;                // register-tile bodies where a job fits
+    bool only_direct = false;           // every job on register tiles
     DevBuf d_jobs, d_items, d_head, d_ou;
     int32_t n_items = 0, grid = 0;
     cudaGraph_t graph = nullptr;
@@ -1219,14 +1234,14 @@ tvbx_status batch_adopt_jobs(tvbx_batch* b)
     return TVBX_OK;
 }
 
-tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t trial_steps)
+tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t trial_steps, bool direct)
 {
     b->drop_graph();
     if (tvbx_status st = batch_adopt_jobs(b)) return st;
     const size_t nj = b->jobs.size();
     std::vector<RunPlan> plans(nj);
     std::vector<tvbx_run_cfg> run_cfgs(b->cfgs);
-    std::vector<int> pbs(nj);
+    std::vector<int> pbs(nj), dirs(nj);
     size_t smem = 0;
     int64_t ou_floats = 0;
     std::vector<int64_t> ou_off(nj, -1);
@@ -1237,13 +1252,17 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
             c.transient_samples = 0;
         }
         if (c.n_steps > INT32_MAX) return fail(TVBX_E_INVALID_ARG, "batch job %zu: n_steps must be < 2^31", j);
-        const int pb = batch_pb(b->jobs[j]->N, budget, threads);
+        const int N = b->jobs[j]->N;
+        // register tiles: as many 4-set quads per region as the CTA has threads for
+        const bool dj = direct && N <= threads;
+        const int pb = dj ? 4 * (threads / N) : batch_pb(N, budget, threads);
         if (!pb) return fail(TVBX_E_UNSUPPORTED, "batch job %zu: %d regions do not fit %zu bytes of shared memory", j,
-                             b->jobs[j]->N, budget);
+                             N, budget);
         pbs[j] = pb;
-        smem = std::max(smem, sim_smem_bytes(b->jobs[j]->N, pb));
+        dirs[j] = dj ? 1 : 0;
+        smem = std::max(smem, dj ? sizeof(float) * 11 * (size_t)pb : sim_smem_bytes(N, pb));
         c.chunk_steps = 0;
-        tvbx_status st = prepare_run(b->jobs[j], c, b->stream, pb, false, plans[j]);
+        tvbx_status st = prepare_run(b->jobs[j], c, b->stream, pb, false, plans[j], dj);
         if (st != TVBX_OK) return st;
         if (!c.noise_per_set) {
             ou_off[j] = ou_floats;
@@ -1259,7 +1278,7 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
         a.n0 = 0;
         a.n_chunk = (int32_t)run_cfgs[j].n_steps;
         a.ou_table = ou_off[j] >= 0 ? b->d_ou.as<float>() + ou_off[j] : nullptr;
-        jobs[j] = BatchJob{a, pbs[j]};
+        jobs[j] = BatchJob{a, pbs[j], dirs[j]};
         const int N = b->jobs[j]->N;
         for (int32_t t = 0; t < plans[j].n_tiles; ++t) {
             const double per_step = (double)N * 40.0 + (double)plans[j].tile_nnz[t];   // TF work + gathers
@@ -1281,11 +1300,13 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev), "device");
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
-    const int per_sm = sim_batch_ctas_per_sm(threads, smem);
+    b->only_direct = std::all_of(dirs.begin(), dirs.end(), [](int d) { return d != 0; });
+    const int per_sm = sim_batch_ctas_per_sm(threads, smem, b->only_direct);
     if (per_sm < 1) return fail(TVBX_E_UNSUPPORTED, "batch kernel does not fit %d threads / %zu bytes", threads, smem);
     b->grid = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (int64_t)items.size()));
     b->threads = threads;
     b->smem_budget = budget;
+    b->direct = direct;
     CK(cudaStreamSynchronize(b->stream), "batch upload");
 
     // capture the device work of one run
@@ -1314,7 +1335,7 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
     if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_head.ptr, 0, sizeof(int32_t), b->stream);
     if (ce == cudaSuccess && b->n_items > 0) {
         ce = launch_sim_batch(b->d_jobs.as<BatchJob>(), b->d_items.as<BatchItem>(), b->n_items,
-                              b->d_head.as<int32_t>(), b->grid, threads, smem, b->stream);
+                              b->d_head.as<int32_t>(), b->grid, threads, smem, b->only_direct, b->stream);
         ++kernels;
     }
     cudaGraph_t g = nullptr;
@@ -1371,18 +1392,21 @@ tvbx_status tvbx_batch_tune(tvbx_batch* b, int64_t trial_steps, int32_t* threads
 {
     if (!b) return fail(TVBX_E_INVALID_ARG, "NULL batch");
     if (trial_steps < 1) return fail(TVBX_E_INVALID_ARG, "trial_steps must be >= 1");
-    struct Cand { int32_t threads; size_t budget; };
-    const Cand cands[] = {{256, 100 * 1024}, {512, 100 * 1024}, {256, 200 * 1024}, {512, 200 * 1024},
-                          {128, 64 * 1024}, {256, 64 * 1024}};
+    // general body under shared-memory budgets, and register tiles (general
+    // body only for jobs with more regions than threads)
+    struct Cand { int32_t threads; size_t budget; bool direct; };
+    const Cand cands[] = {{256, 100 * 1024, false}, {512, 100 * 1024, false}, {256, 200 * 1024, false},
+                          {512, 200 * 1024, false}, {128, 64 * 1024, false},  {256, 64 * 1024, false},
+                          {512, 200 * 1024, true},  {768, 200 * 1024, true}};
     float best = INFINITY;
-    Cand win{0, 0};
+    Cand win{0, 0, false};
     int32_t k = 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
     for (const Cand& c : cands) {
         float ms = INFINITY;
-        if (batch_build(b, c.threads, c.budget, trial_steps) == TVBX_OK) {
+        if (batch_build(b, c.threads, c.budget, trial_steps, c.direct) == TVBX_OK) {
             cudaError_t e = cudaGraphLaunch(b->exec, b->stream);   // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
             if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
@@ -1406,7 +1430,7 @@ tvbx_status tvbx_batch_tune(tvbx_batch* b, int64_t trial_steps, int32_t* threads
     cudaEventDestroy(e1);
     if (!(best < INFINITY)) return fail(TVBX_E_UNSUPPORTED, "no batch configuration fits every job");
     if (n_trials) *n_trials = k;
-    tvbx_status st = batch_build(b, win.threads, win.budget, 0);
+    tvbx_status st = batch_build(b, win.threads, win.budget, 0, win.direct);
     if (st != TVBX_OK) return st;
     if (threads_out) *threads_out = win.threads;
     if (smem_kb_out) *smem_kb_out = (int32_t)(win.budget / 1024);
@@ -1421,7 +1445,7 @@ tvbx_status tvbx_batch_run(tvbx_batch* b)
     for (size_t j = 0; j < b->jobs.size() && !stale; ++j) stale = b->jobs[j]->gen != b->gens[j];
     for (size_t j = 0; j < b->jobs.size() && !stale; ++j) stale = b->cfgs_run[j].n_steps != b->cfgs[j].n_steps;
     if (stale) {
-        tvbx_status st = batch_build(b, b->threads, b->smem_budget, 0);
+        tvbx_status st = batch_build(b, b->threads, b->smem_budget, 0, b->direct);
         if (st != TVBX_OK) return st;
     }
     CK(cudaGraphLaunch(b->exec, b->stream), "batch launch");

@@ -120,14 +120,19 @@ size_t sim_smem_bytes(int N, int pb);
 // n_chunk = n_steps, OU table for every step); pb = its tile width.
 struct BatchJob {
     SimArgs a;
-    int32_t pb;
+    int32_t pb;       // tile width of the job
+    int32_t direct;   // 1: register-tile body (N pb / 4 <= blockDim), 0: general body
 };
 struct BatchItem {
     int32_t job, tile;
 };
+// Register-tile kernel for large connectomes: tile width for N regions (0 if
+// N is too large), and the launch of one chunk.
+int sim_direct_pb(int N);
+cudaError_t launch_sim_direct(const SimArgs& a, int32_t n_tiles, int32_t pb, cudaStream_t s);
 cudaError_t launch_sim_batch(const BatchJob* jobs, const BatchItem* items, int32_t n_items, int32_t* head,
-                             int32_t grid, int32_t threads, size_t smem, cudaStream_t s);
-int sim_batch_ctas_per_sm(int32_t threads, size_t smem);
+                             int32_t grid, int32_t threads, size_t smem, bool only_direct, cudaStream_t s);
+int sim_batch_ctas_per_sm(int32_t threads, size_t smem, bool only_direct);
 
 struct FcArgs {
     const float* series;       // [T][N][P]

@@ -9,6 +9,7 @@
 
 #include "internal.h"
 #include "model_device.cuh"
+#include "tile_common.cuh"
 
 namespace tvbx {
 
@@ -186,12 +187,82 @@ sim_chunk_kernel(const __grid_constant__ SimArgs a)
     chunk_body<PB>(a, a.tiles[blockIdx.x], PB, st);
 }
 
+// ---------------------------------------------------------------------------
+// Register-tile body for connectomes whose delayed rows do not fit a
+// shared-memory prefetch buffer. Thread (k, quad) keeps 4 adjacent sets of
+// region k in registers for the whole chunk; the coupling reads each delayed
+// value of its 4 sets with one 16-byte load from the ring (the CSR rows through
+// the read-only cache) and sums in CSR order, like the general body, so the
+// results are bit-identical to it. One CTA barrier per step (after the ring
+// writes of E(n+1)). pb: sets per tile, a multiple of 4, with N pb / 4 <=
+// blockDim; s_prm: shared memory [11][pb].
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ void direct_body(const SimArgs& a, const TileDev& tile, int pb, float* s_prm)
+{
+    constexpr int SPT = 4;
+    const GroupDev grp = a.groups[tile.group];
+    const int N = a.N;
+    const int nq = pb / SPT;
+    stage_set_params<0>(a, tile, grp, s_prm, pb);
+    const int kk = threadIdx.x / nq;   // >= N: an idle thread (it still takes the barriers)
+    ThreadSlot ts;
+    ts.qt = (threadIdx.x - kk * nq) * SPT;
+    ts.kr = kk;
+    ts.kstride = N;
+    ts.col0 = grp.p_base + tile.q0;
+    ThreadPairs<SPT, 1> tp;
+    load_pairs<SPT, 1>(a, tile, ts, tp);
+    __syncthreads();
+
+    const int H = grp.H;
+    const int64_t slot_stride = (int64_t)N * grp.stride;
+    float* ring_cols = grp.ring + tile.q0;
+    // a quad whose first set exists reads 16 bytes inside the ring row (the
+    // row stride is a multiple of 32 sets and quads start at multiples of 4)
+    const bool reads = kk < N && tp.act[0];
+    const int e0 = reads ? __ldg(grp.row_ptr + kk) : 0, e1 = reads ? __ldg(grp.row_ptr + kk + 1) : 0;
+    for (int step = 0; step < a.n_chunk; ++step) {
+        const int64_t n = a.n0 + step;
+        const int slot_n = (int)(n % H);
+        const int slot_w = slot_n + 1 == H ? 0 : slot_n + 1;
+        float cpl[SPT] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+        for (int e = e0; e < e1; ++e) {
+            const uint32_t cd = __ldg(grp.col_dly + e);
+            const float w = __ldg(grp.w + e);
+            int sl = slot_n - (int)(cd >> 16);
+            sl += sl < 0 ? H : 0;
+            const float4 v = *reinterpret_cast<const float4*>(ring_cols + sl * slot_stride +
+                                                               (int64_t)(cd & 0xffffu) * grp.stride + ts.qt);
+            cpl[0] = fmaf(w, v.x, cpl[0]);
+            cpl[1] = fmaf(w, v.y, cpl[1]);
+            cpl[2] = fmaf(w, v.z, cpl[2]);
+            cpl[3] = fmaf(w, v.w, cpl[3]);
+        }
+        advance_pairs<0, SPT, 1>(a, ts, s_prm, tp, cpl, n, step, ring_cols + slot_w * slot_stride, grp.stride, pb);
+        __syncthreads();
+    }
+    store_pairs<SPT, 1>(a, ts, tp);
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+sim_direct_kernel(const __grid_constant__ SimArgs a, int32_t pb)
+{
+    extern __shared__ float s_prm[];   // [11][pb]
+    direct_body(a, a.tiles[blockIdx.x], pb, s_prm);
+}
+
 // Persistent kernel of a batch of sweeps (any region counts, durations and
 // delay horizons): each CTA takes work items (job, tile) from a global
 // counter, most expensive first, and integrates the tile over the job's
 // whole duration (the job's SimArgs have n0 = 0, n_chunk = n_steps and an OU
-// table for all steps). The tile width pb is per job.
-__global__ void __launch_bounds__(512)
+// table for all steps). The tile width pb and the body (register tiles or the
+// general body) are per job; ONLY_DIRECT instances (every job on register
+// tiles) leave the general body out, which keeps its registers off the
+// direct body's budget.
+template <int MAXT, bool ONLY_DIRECT>
+__global__ void __launch_bounds__(MAXT)
 sim_batch_kernel(const BatchJob* __restrict__ jobs, const BatchItem* __restrict__ items, int32_t n_items,
                  int32_t* __restrict__ head)
 {
@@ -209,7 +280,8 @@ sim_batch_kernel(const BatchJob* __restrict__ jobs, const BatchItem* __restrict_
         uint32_t* dst = reinterpret_cast<uint32_t*>(&s_job);
         for (int w = threadIdx.x; w < (int)(sizeof(BatchJob) / 4); w += blockDim.x) dst[w] = src[w];
         __syncthreads();
-        chunk_body<0>(s_job.a, s_job.a.tiles[bi.tile], s_job.pb, st);
+        if (ONLY_DIRECT || s_job.direct) direct_body(s_job.a, s_job.a.tiles[bi.tile], s_job.pb, st);
+        else chunk_body<0>(s_job.a, s_job.a.tiles[bi.tile], s_job.pb, st);
         __syncthreads();
     }
 }
@@ -297,22 +369,53 @@ cudaError_t launch_sim_chunk(const SimArgs& a, int32_t n_tiles, int32_t pb, cuda
     }
 }
 
-cudaError_t launch_sim_batch(const BatchJob* jobs, const BatchItem* items, int32_t n_items, int32_t* head,
-                             int32_t grid, int32_t threads, size_t smem, cudaStream_t s)
+int sim_direct_pb(int N)
 {
-    cudaError_t e = cudaFuncSetAttribute(sim_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // at most 384 threads (151 registers, no spills) where an 8- or 16-set
+    // tile allows; otherwise 8 sets (full 32-byte ring sectors) on up to 768
+    // threads, then 4
+    for (int pb : {16, 8, 4})
+        if ((int64_t)N * (pb / 4) <= 768) return pb;
+    return 0;
+}
+
+cudaError_t launch_sim_direct(const SimArgs& a, int32_t n_tiles, int32_t pb, cudaStream_t s)
+{
+    if (n_tiles <= 0 || a.n_chunk <= 0) return cudaSuccess;
+    if (pb % 4 != 0 || pb < 4 || (int64_t)a.N * (pb / 4) > 768) return cudaErrorInvalidValue;
+    const int threads = (a.N * (pb / 4) + 31) / 32 * 32;
+    const size_t smem = sizeof(float) * 11 * (size_t)pb;
     note_launch();
-    sim_batch_kernel<<<grid, threads, smem, s>>>(jobs, items, n_items, head);
+    if (threads <= 384) sim_direct_kernel<384><<<n_tiles, threads, smem, s>>>(a, pb);
+    else sim_direct_kernel<768><<<n_tiles, threads, smem, s>>>(a, pb);
     return cudaGetLastError();
 }
 
-int sim_batch_ctas_per_sm(int32_t threads, size_t smem)
+static auto batch_kernel(int32_t threads, bool only_direct)
 {
+    if (only_direct) return threads <= 512 ? sim_batch_kernel<512, true> : sim_batch_kernel<768, true>;
+    return threads <= 512 ? sim_batch_kernel<512, false> : sim_batch_kernel<768, false>;
+}
+
+cudaError_t launch_sim_batch(const BatchJob* jobs, const BatchItem* items, int32_t n_items, int32_t* head,
+                             int32_t grid, int32_t threads, size_t smem, bool only_direct, cudaStream_t s)
+{
+    if (threads > 768) return cudaErrorInvalidValue;
+    auto kern = batch_kernel(threads, only_direct);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    kern<<<grid, threads, smem, s>>>(jobs, items, n_items, head);
+    return cudaGetLastError();
+}
+
+int sim_batch_ctas_per_sm(int32_t threads, size_t smem, bool only_direct)
+{
+    if (threads > 768) return 0;
+    auto kern = batch_kernel(threads, only_direct);
     int n = 0;
-    if (cudaFuncSetAttribute(sim_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sim_batch_kernel, threads, smem) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
     return n;
 }
 

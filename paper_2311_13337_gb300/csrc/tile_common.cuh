@@ -41,16 +41,18 @@ struct ThreadSlot {
     int64_t col0; // internal index of set 0 of the tile
 };
 
-// Stage the tile's set parameters into shared memory s_prm[11][PB].
+// Stage the tile's set parameters into shared memory s_prm[11][PB] (PB = 0:
+// the runtime width pb_rt).
 template <int PB>
 static __device__ __forceinline__ void stage_set_params(const SimArgs& a, const TileDev& tile, const GroupDev& grp,
-                                                        float* s_prm)
+                                                        float* s_prm, int pb_rt = 0)
 {
-    for (int q = threadIdx.x; q < PB; q += blockDim.x) {
+    const int pbs = PB > 0 ? PB : pb_rt;
+    for (int q = threadIdx.x; q < pbs; q += blockDim.x) {
         SetParams v{};
         if (q < tile.nq) v = load_set_params(a.prm, a.P, grp.p_base + tile.q0 + q);
         const float* f = reinterpret_cast<const float*>(&v);
-        for (int c = 0; c < 11; ++c) s_prm[c * PB + q] = f[c];
+        for (int c = 0; c < 11; ++c) s_prm[c * pbs + q] = f[c];
     }
 }
 
@@ -159,12 +161,14 @@ static __device__ __forceinline__ void coupling_sums(const ThreadSlot& ts, int N
 }
 
 // One Euler step of the thread's pairs, the ring write of E(n+1) and the
-// temporal average. ring_slot_w points at slot (n+1) mod H, column 0 of the tile.
+// temporal average. ring_slot_w points at slot (n+1) mod H, column 0 of the
+// tile; s_prm is [11][PB] (PB = 0: the runtime width pb_rt).
 template <int PB, int SPT, int RPT>
 static __device__ __forceinline__ void advance_pairs(const SimArgs& a, const ThreadSlot& ts, const float* s_prm,
                                                      ThreadPairs<SPT, RPT>& tp, const float* cpl, int64_t n,
-                                                     int step, float* ring_slot_w, int64_t row_stride)
+                                                     int step, float* ring_slot_w, int64_t row_stride, int pb_rt = 0)
 {
+    const int pbs = PB > 0 ? PB : pb_rt;
     const DevModel& m = a.m;
     const int N = a.N;
     const int64_t NP = (int64_t)N * a.P;
@@ -182,7 +186,7 @@ static __device__ __forceinline__ void advance_pairs(const SimArgs& a, const Thr
             SetParams spv;
             float* f = reinterpret_cast<float*>(&spv);
 #pragma unroll
-            for (int c = 0; c < 11; ++c) f[c] = s_prm[c * PB + ts.qt + s];
+            for (int c = 0; c < 11; ++c) f[c] = s_prm[c * pbs + ts.qt + s];
             euler_step(m, spv, tp.x[i], cpl[i], OU, tp.flags[s]);
             if (a.noise_per_set) {
                 const float xi = std_normal(a.seed, (uint32_t)n, (uint32_t)k, tp.pn[s]);

@@ -263,7 +263,7 @@ def sweep_info(h) -> tuple[int, int, int]:
     return p.value, n.value, t.value
 
 
-KERNEL_AUTO, KERNEL_GENERAL, KERNEL_PREFETCH = 0, 1, 2
+KERNEL_AUTO, KERNEL_GENERAL, KERNEL_PREFETCH, KERNEL_DIRECT = 0, 1, 2, 100
 N_PREFETCH_VARIANTS = 8
 
 
@@ -382,7 +382,7 @@ def transfer_function(pop: int, x_e, x_i, W, E_L, C=None, model: Model | None = 
     return out
 
 
-KERNEL_NAMES = {KERNEL_GENERAL: "sim_chunk_kernel"}
+KERNEL_NAMES = {KERNEL_GENERAL: "sim_chunk_kernel", KERNEL_DIRECT: "sim_direct_kernel"}
 KERNEL_NAMES.update({KERNEL_PREFETCH + v: ("sim_bulk_kernel" if v in (4, 5) else "sim_fast_kernel") + f" (variant {v})"
                      for v in range(N_PREFETCH_VARIANTS)})
 

@@ -248,6 +248,33 @@ def test_invalid_run_arguments(tvbx, conn):
     assert e.value.code == -1
 
 
+@pytest.mark.parametrize("N", [192, 360])
+def test_register_tile_kernel_equals_general_kernel(tvbx, N):
+    """The register-tile kernel for large connectomes sums the coupling in
+    the general kernel's order: bit-identical series, state and status on 42
+    sets (ragged tiles), three speeds, per-set noise and a clamping set."""
+    W, L = synth.connectome(N)
+    rng = np.random.default_rng(N)
+    m = tvbx.make_model()
+    pts = np.tile(np.array([m.defaults[i] for i in range(tvbx.N_AXES)]), (42, 1))
+    pts[:, tvbx.AXES.index("g")] = rng.uniform(0.0, 0.8, 42)
+    pts[:, tvbx.AXES.index("b_e")] = rng.uniform(0.0, 120.0, 42)
+    pts[:, tvbx.AXES.index("speed")] = rng.choice([2.0, 4.0, 7.0], 42)
+    pts[5, tvbx.AXES.index("g")] = 40.0
+    out = []
+    for kern in (tvbx.KERNEL_GENERAL, tvbx.KERNEL_DIRECT):
+        sw = tvbx.Sweep(W, L, points=pts)
+        sw.run(dt_ms=DT, n_steps=1500, tavg_steps=10, seed=3, noise_per_set=True, kernel=kern)
+        assert tvbx.last_kernel(sw.h)[0] == kern
+        out.append((sw.series(), sw.state(), sw.summary()["status"]))
+        sw.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b, equal_nan=True)
+    auto = tvbx.Sweep(W, L, points=pts[:8])
+    auto.run(dt_ms=DT, n_steps=20, tavg_steps=10)
+    assert tvbx.last_kernel(auto.h)[0] == tvbx.KERNEL_DIRECT
+
+
 def test_oversized_sweep_reports_out_of_memory(tvbx, conn):
     """16.8 million sets at 1 m/s need a ring of about 9 TB: the run reports
     TVBX_E_OOM (an allocation that fails, nothing launched), and the device
