@@ -371,10 +371,8 @@ cudaError_t launch_sim_chunk(const SimArgs& a, int32_t n_tiles, int32_t pb, cuda
 
 int sim_direct_pb(int N)
 {
-    // at most 384 threads (151 registers, no spills) where an 8- or 16-set
-    // tile allows; otherwise 8 sets (full 32-byte ring sectors) on up to 768
-    // threads, then 4
-    for (int pb : {16, 8, 4})
+    // the widest tile that fits 768 threads (wider tiles measured faster)
+    for (int pb : {32, 16, 8, 4})
         if ((int64_t)N * (pb / 4) <= 768) return pb;
     return 0;
 }
