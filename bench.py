@@ -108,9 +108,9 @@ def stop_clock_sampler(proc):
 
 
 def kernel_source_hash() -> str:
-    """Hash of every source the simulation kernels are built from."""
+    """Hash of every source the prefetching simulation kernel is built from."""
     h = hashlib.sha256()
-    for f in ("sim.cu", "sim_fast.cu", "tile_common.cuh", "model_device.cuh", "internal.h", "ptx_async.cuh"):
+    for f in ("sim_fast.cu", "tile_common.cuh", "model_device.cuh", "internal.h", "ptx_async.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2311_13337_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
