@@ -12,10 +12,12 @@
 // sets, B * N * T' complex floats):
 //  * an_series_kernel, one CTA per (set, region): the FP64 mean of the row;
 //    UP / DOWN runs against that mean (rounded to FP32); the forward DFT of
-//    the mean-removed row (Stockham autosort, radices 2, 3, 4, 5, in shared
-//    memory; twiddles from a host FP64 table); the periodogram on the PSD
-//    band; the analytic signal (one-sided spectrum doubled) by the inverse
-//    DFT, written to scratch;
+//    the mean-removed row (in place in one shared-memory buffer: the row is
+//    stored digit-reversed and transformed by decimation-in-time stages of
+//    radix 2, 3, 4, 5; twiddles from a host FP64 table); the periodogram on
+//    the PSD band; the analytic signal (one-sided spectrum doubled) by the
+//    inverse DFT (decimation in frequency, in place, read back through the
+//    digit reversal), written to scratch;
 //  * an_pli_kernel, one CTA per set: time tiles of the N analytic signals in
 //    shared memory; a thread owns a 4 x 4 block of region pairs and counts
 //    sign(Im(z_k conj(z_j))) by comparing the two rounded products, so
@@ -49,7 +51,9 @@ struct FftPlan {
     int n;
     int n_stages;
     int radix[AN_MAX_STAGES];
-    uint32_t magic[AN_MAX_STAGES];   // ceil(2^32 / L1) of the stage (0 for L1 = 1): idx / L1 = umulhi(idx, magic)
+    // stage s (radix[s], DIT or DIF) has L1 = radix[0] ... radix[s-1]:
+    // magic[s] = ceil(2^32 / L1) (0 for L1 = 1), so idx / L1 = umulhi(idx, magic)
+    uint32_t magic[AN_MAX_STAGES];
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -66,90 +70,130 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e, 
     return w;
 }
 
-// One Stockham stage of radix R: in viewed as [n/(L1 R)][L1], out as
-// [n/(L1 R)][L1 R]; out[a][b1 + L1 b2] = sum_q w_R^{b2 q} w_L^{b1 q} in[a + Rr q][b1]
-// with L = L1 R, Rr = n / L, w_m = exp(-+2 pi i / m). The R-point transforms
-// use the symmetric forms (cos and sin of 2 pi / 3 and 2 pi k / 5).
+// R-point DFT v_k = sum_q w_R^{k q} u_q with w_R = exp(sg 2 pi i / R), in the
+// symmetric forms (cos and sin of 2 pi / 3 and 2 pi k / 5).
 template <int R>
-__device__ void fft_stage(const float2* in, float2* out, int n, int L1, uint32_t magic, const float2* __restrict__ tw,
-                          bool inv)
+__device__ __forceinline__ void butterfly(const float2 (&u)[R], float2 (&v)[R], float sg)
 {
-    const int L = L1 * R, Rr = n / L, m = n / R;
-    const int nl = n / L;
-    const float sg = inv ? 1.0f : -1.0f;   // sign of the exponent
-    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
-        const int a = magic ? (int)__umulhi((uint32_t)idx, magic) : idx;
-        const int b1 = idx - a * L1;
-        float2 u[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const float2 y = in[(a + Rr * q) * L1 + b1];
-            u[q] = (q == 0 || b1 == 0) ? y : cmul(y, twiddle(tw, nl * b1 * q, inv));
-        }
-        float2* o = out + a * L + b1;
-        if constexpr (R == 2) {
-            o[0] = cadd(u[0], u[1]);
-            o[L1] = csub(u[0], u[1]);
-        } else if constexpr (R == 4) {
-            const float2 s02 = cadd(u[0], u[2]), d02 = csub(u[0], u[2]);
-            const float2 s13 = cadd(u[1], u[3]), d13 = csub(u[1], u[3]);
-            // (sg i) d13
-            const float2 jd13 = make_float2(-sg * d13.y, sg * d13.x);
-            o[0] = cadd(s02, s13);
-            o[L1] = cadd(d02, jd13);
-            o[2 * L1] = csub(s02, s13);
-            o[3 * L1] = csub(d02, jd13);
-        } else if constexpr (R == 3) {
-            constexpr float S3 = 0.86602540378443865f;   // sin(2 pi / 3); cos(2 pi / 3) = -1/2
-            const float2 t1 = cadd(u[1], u[2]), t2 = csub(u[1], u[2]);
-            const float2 a0 = make_float2(fmaf(-0.5f, t1.x, u[0].x), fmaf(-0.5f, t1.y, u[0].y));
-            const float bx = sg * S3 * t2.x, by = sg * S3 * t2.y;   // (sg S3) t2, times i below
-            o[0] = cadd(u[0], t1);
-            o[L1] = make_float2(a0.x - by, a0.y + bx);
-            o[2 * L1] = make_float2(a0.x + by, a0.y - bx);
-        } else {
-            // cos and sin of 2 pi / 5 and 4 pi / 5
-            constexpr float C1 = 0.30901699437494742f, C2 = -0.80901699437494742f;
-            constexpr float S1 = 0.95105651629515357f, S2 = 0.58778525229247313f;
-            const float2 t1 = cadd(u[1], u[4]), t2 = cadd(u[2], u[3]);
-            const float2 t3 = csub(u[1], u[4]), t4 = csub(u[2], u[3]);
-            const float2 a1 = make_float2(fmaf(C1, t1.x, fmaf(C2, t2.x, u[0].x)), fmaf(C1, t1.y, fmaf(C2, t2.y, u[0].y)));
-            const float2 a2 = make_float2(fmaf(C2, t1.x, fmaf(C1, t2.x, u[0].x)), fmaf(C2, t1.y, fmaf(C1, t2.y, u[0].y)));
-            // b1 = sg (S1 t3 + S2 t4), b2 = sg (S2 t3 - S1 t4); outputs a -+ ... with i b
-            const float b1x = sg * fmaf(S1, t3.x, S2 * t4.x), b1y = sg * fmaf(S1, t3.y, S2 * t4.y);
-            const float b2x = sg * fmaf(S2, t3.x, -S1 * t4.x), b2y = sg * fmaf(S2, t3.y, -S1 * t4.y);
-            o[0] = make_float2(u[0].x + t1.x + t2.x, u[0].y + t1.y + t2.y);
-            o[L1] = make_float2(a1.x - b1y, a1.y + b1x);       // a1 + i b1
-            o[4 * L1] = make_float2(a1.x + b1y, a1.y - b1x);   // a1 - i b1
-            o[2 * L1] = make_float2(a2.x - b2y, a2.y + b2x);   // a2 + i b2
-            o[3 * L1] = make_float2(a2.x + b2y, a2.y - b2x);   // a2 - i b2
-        }
+    if constexpr (R == 2) {
+        v[0] = cadd(u[0], u[1]);
+        v[1] = csub(u[0], u[1]);
+    } else if constexpr (R == 4) {
+        const float2 s02 = cadd(u[0], u[2]), d02 = csub(u[0], u[2]);
+        const float2 s13 = cadd(u[1], u[3]), d13 = csub(u[1], u[3]);
+        const float2 jd13 = make_float2(-sg * d13.y, sg * d13.x);   // (sg i) d13
+        v[0] = cadd(s02, s13);
+        v[1] = cadd(d02, jd13);
+        v[2] = csub(s02, s13);
+        v[3] = csub(d02, jd13);
+    } else if constexpr (R == 3) {
+        constexpr float S3 = 0.86602540378443865f;   // sin(2 pi / 3); cos(2 pi / 3) = -1/2
+        const float2 t1 = cadd(u[1], u[2]), t2 = csub(u[1], u[2]);
+        const float2 a0 = make_float2(fmaf(-0.5f, t1.x, u[0].x), fmaf(-0.5f, t1.y, u[0].y));
+        const float bx = sg * S3 * t2.x, by = sg * S3 * t2.y;   // (sg S3) t2, times i below
+        v[0] = cadd(u[0], t1);
+        v[1] = make_float2(a0.x - by, a0.y + bx);
+        v[2] = make_float2(a0.x + by, a0.y - bx);
+    } else {
+        constexpr float C1 = 0.30901699437494742f, C2 = -0.80901699437494742f;
+        constexpr float S1 = 0.95105651629515357f, S2 = 0.58778525229247313f;
+        const float2 t1 = cadd(u[1], u[4]), t2 = cadd(u[2], u[3]);
+        const float2 t3 = csub(u[1], u[4]), t4 = csub(u[2], u[3]);
+        const float2 a1 = make_float2(fmaf(C1, t1.x, fmaf(C2, t2.x, u[0].x)), fmaf(C1, t1.y, fmaf(C2, t2.y, u[0].y)));
+        const float2 a2 = make_float2(fmaf(C2, t1.x, fmaf(C1, t2.x, u[0].x)), fmaf(C2, t1.y, fmaf(C1, t2.y, u[0].y)));
+        // b1 = sg (S1 t3 + S2 t4), b2 = sg (S2 t3 - S1 t4)
+        const float b1x = sg * fmaf(S1, t3.x, S2 * t4.x), b1y = sg * fmaf(S1, t3.y, S2 * t4.y);
+        const float b2x = sg * fmaf(S2, t3.x, -S1 * t4.x), b2y = sg * fmaf(S2, t3.y, -S1 * t4.y);
+        v[0] = make_float2(u[0].x + t1.x + t2.x, u[0].y + t1.y + t2.y);
+        v[1] = make_float2(a1.x - b1y, a1.y + b1x);   // a1 + i b1
+        v[4] = make_float2(a1.x + b1y, a1.y - b1x);   // a1 - i b1
+        v[2] = make_float2(a2.x - b2y, a2.y + b2x);   // a2 + i b2
+        v[3] = make_float2(a2.x + b2y, a2.y - b2x);   // a2 - i b2
     }
 }
 
-// Full transform of buf[0] (length n) using buf[1] as the other stage buffer;
-// returns the buffer holding the result.
-__device__ float2* fft(float2* b0, float2* b1, const FftPlan& plan, const float2* __restrict__ tw, bool inv)
+// In-place decimation-in-time stage of radix R on a (length n, input in
+// digit-reversed order): butterfly j of a block of span L = L1 R combines
+// a[blk L + j + q L1], twiddled by w_L^{j q} before the R-point DFT.
+template <int R>
+__device__ void dit_stage(float2* a, int n, int L1, uint32_t magic, const float2* __restrict__ tw, bool inv)
 {
-    float2* in = b0;
-    float2* out = b1;
+    const int L = L1 * R, nl = n / L, m = n / R;
+    const float sg = inv ? 1.0f : -1.0f;
+    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+        const int blk = magic ? (int)__umulhi((uint32_t)idx, magic) : idx;   // idx / L1
+        const int j = idx - blk * L1;
+        float2* p = a + blk * L + j;
+        float2 u[R], v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float2 y = p[q * L1];
+            u[q] = (q == 0 || j == 0) ? y : cmul(y, twiddle(tw, nl * j * q, inv));
+        }
+        butterfly<R>(u, v, sg);
+#pragma unroll
+        for (int k = 0; k < R; ++k) p[k * L1] = v[k];
+    }
+}
+
+// In-place decimation-in-frequency stage of radix R (natural-order input,
+// span L = L1 R): the R-point DFT of a[blk L + j + q L1], each output k then
+// twiddled by w_L^{j k}; after all stages the result is digit-reversed.
+template <int R>
+__device__ void dif_stage(float2* a, int n, int L1, uint32_t magic, const float2* __restrict__ tw, bool inv)
+{
+    const int L = L1 * R, nl = n / L, m = n / R;
+    const float sg = inv ? 1.0f : -1.0f;
+    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+        const int blk = magic ? (int)__umulhi((uint32_t)idx, magic) : idx;   // idx / L1
+        const int j = idx - blk * L1;
+        float2* p = a + blk * L + j;
+        float2 u[R], v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) u[q] = p[q * L1];
+        butterfly<R>(u, v, sg);
+#pragma unroll
+        for (int k = 0; k < R; ++k) p[k * L1] = (k == 0 || j == 0) ? v[k] : cmul(v[k], twiddle(tw, nl * j * k, inv));
+    }
+}
+
+// Forward transform in place: a holds the input in digit-reversed order
+// (a[perm[t]] = x[t]) and ends in natural order.
+__device__ void fft_dit(float2* a, const FftPlan& plan, const float2* __restrict__ tw, bool inv)
+{
     int L1 = 1;
     for (int s = 0; s < plan.n_stages; ++s) {
         const int r = plan.radix[s];
         const uint32_t mg = plan.magic[s];
         switch (r) {
-        case 2: fft_stage<2>(in, out, plan.n, L1, mg, tw, inv); break;
-        case 3: fft_stage<3>(in, out, plan.n, L1, mg, tw, inv); break;
-        case 4: fft_stage<4>(in, out, plan.n, L1, mg, tw, inv); break;
-        default: fft_stage<5>(in, out, plan.n, L1, mg, tw, inv); break;
+        case 2: dit_stage<2>(a, plan.n, L1, mg, tw, inv); break;
+        case 3: dit_stage<3>(a, plan.n, L1, mg, tw, inv); break;
+        case 4: dit_stage<4>(a, plan.n, L1, mg, tw, inv); break;
+        default: dit_stage<5>(a, plan.n, L1, mg, tw, inv); break;
         }
         __syncthreads();
         L1 *= r;
-        float2* t = in;
-        in = out;
-        out = t;
     }
-    return in;
+}
+
+// Transform in place from natural order to digit-reversed order (result t at
+// a[perm[t]]): the stages in reverse radix order.
+__device__ void fft_dif(float2* a, const FftPlan& plan, const float2* __restrict__ tw, bool inv)
+{
+    int L = plan.n;
+    for (int s = plan.n_stages - 1; s >= 0; --s) {
+        const int r = plan.radix[s];
+        const int L1 = L / r;
+        const uint32_t mg = plan.magic[s];
+        switch (r) {
+        case 2: dif_stage<2>(a, plan.n, L1, mg, tw, inv); break;
+        case 3: dif_stage<3>(a, plan.n, L1, mg, tw, inv); break;
+        case 4: dif_stage<4>(a, plan.n, L1, mg, tw, inv); break;
+        default: dif_stage<5>(a, plan.n, L1, mg, tw, inv); break;
+        }
+        __syncthreads();
+        L = L1;
+    }
 }
 
 template <class T>
@@ -165,25 +209,27 @@ __device__ __forceinline__ T block_sum(T v, T* red)
     return s;
 }
 
-// One CTA per (set in batch, region).
+// One CTA per (set in batch, region). The row is held once in shared memory
+// in digit-reversed order (a[perm[t]] = x_t), transformed in place forward
+// (DIT, natural-order spectrum) and back (DIF, digit-reversed analytic
+// signal).
 __global__ void __launch_bounds__(AN_THREADS)
 an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan plan, const float2* __restrict__ tw,
-                 int band_lo, int band_n, float psd_scale, int64_t p0, float* __restrict__ psd_out,
-                 int* __restrict__ ud_out, float2* __restrict__ z_out)
+                 const int* __restrict__ perm, int band_lo, int band_n, float psd_scale, int64_t p0,
+                 float* __restrict__ psd_out, int* __restrict__ ud_out, float2* __restrict__ z_out)
 {
     extern __shared__ float2 an_smem[];
     __shared__ double red_d[AN_THREADS / 32];
     __shared__ int chunk_first[AN_THREADS], chunk_last[AN_THREADS];
     __shared__ int red_i[4][AN_THREADS / 32];
     const int n = plan.n;
-    float2* b0 = an_smem;
-    float2* b1 = an_smem + n;
+    float2* a = an_smem;
     const int b = blockIdx.x / N, k = blockIdx.x - b * N;
     const float* row = series + ((p0 + b) * (int64_t)N + k) * T + (T - n);
     double s = 0.0;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const float x = row[t];
-        b0[t] = make_float2(x, 0.0f);
+        a[__ldg(perm + t)] = make_float2(x, 0.0f);
         s += (double)x;
     }
     const float theta = (float)(block_sum(s, red_d) / (double)n);
@@ -193,8 +239,10 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int c0 = threadIdx.x * per, c1 = min(n, c0 + per);
     int first = -1, last = -1, nu = 0, su = 0, nd = 0, sd = 0;
-    for (int t = max(c0, 1); t < c1; ++t) {
-        const bool up = b0[t].x > theta, was = b0[t - 1].x > theta;
+    const int tb = max(c0, 1);
+    bool was = tb < c1 ? a[__ldg(perm + tb - 1)].x > theta : false;   // the state at tb - 1
+    for (int t = tb; t < c1; ++t) {
+        const bool up = a[__ldg(perm + t)].x > theta;
         if (up != was) {
             if (last >= 0) {   // complete run [last, t) in state `was`
                 if (was) { ++nu; su += t - last; } else { ++nd; sd += t - last; }
@@ -202,6 +250,7 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
             if (first < 0) first = t;
             last = t;
         }
+        was = up;
     }
     chunk_first[threadIdx.x] = first;
     chunk_last[threadIdx.x] = last;
@@ -216,7 +265,7 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
             if (chunk_first[c] < 0) continue;
             if (prev >= 0) {
                 const int t = chunk_first[c];
-                if (b0[prev].x > theta) { ++nu; su += t - prev; } else { ++nd; sd += t - prev; }
+                if (a[__ldg(perm + prev)].x > theta) { ++nu; su += t - prev; } else { ++nd; sd += t - prev; }
             }
             prev = chunk_last[c];
         }
@@ -225,30 +274,29 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
     }
     __syncthreads();   // thread 0 read the raw row above
     // mean-removed row
-    for (int t = threadIdx.x; t < n; t += blockDim.x) b0[t].x -= theta;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) a[t].x -= theta;
     __syncthreads();
-    float2* X = fft(b0, b1, plan, tw, false);
-    float2* other = X == b0 ? b1 : b0;
+    fft_dit(a, plan, tw, false);
     float* pr = psd_out + ((int64_t)b * N + k) * band_n;
     for (int i = threadIdx.x; i < band_n; i += blockDim.x) {
-        const float2 v = X[band_lo + i];
+        const float2 v = a[band_lo + i];
         pr[i] = psd_scale * fmaf(v.x, v.x, v.y * v.y);
     }
-    __syncthreads();   // the band is read before X is overwritten
+    __syncthreads();   // the band is read before the spectrum is overwritten
     // analytic signal: spectrum times h (h_0 = 1, h_i = 2 below n/2, h_{n/2} = 1, 0 above)
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         float h = 0.0f;
         if (i == 0 || 2 * i == n) h = 1.0f;
         else if (2 * i < n) h = 2.0f;
-        const float2 v = X[i];
-        X[i] = make_float2(h * v.x, h * v.y);
+        const float2 v = a[i];
+        a[i] = make_float2(h * v.x, h * v.y);
     }
     __syncthreads();
-    float2* z = fft(X, other, plan, tw, true);
+    fft_dif(a, plan, tw, true);
     const float inv_n = 1.0f / (float)n;
     float2* zr = z_out + ((int64_t)b * N + k) * n;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const float2 v = z[t];
+        const float2 v = a[__ldg(perm + t)];
         zr[t] = make_float2(v.x * inv_n, v.y * inv_n);
     }
 }
@@ -442,37 +490,35 @@ constexpr int PF_THREADS = 256;
 // samples.
 __global__ void __launch_bounds__(AN_THREADS)
 an_phase_kernel(const float* __restrict__ bold, int N, int64_t P, int64_t Tb, FftPlan plan,
-                const float2* __restrict__ tw, int band_lo, int band_hi, int discard, int64_t p0,
-                float2* __restrict__ U)
+                const float2* __restrict__ tw, const int* __restrict__ perm, int band_lo, int band_hi, int discard,
+                int64_t p0, float2* __restrict__ U)
 {
     extern __shared__ float2 an_smem[];
     __shared__ double red_d[AN_THREADS / 32];
     const int n = plan.n, Tp = n - 2 * discard;
-    float2* b0 = an_smem;
-    float2* b1 = an_smem + n;
+    float2* a = an_smem;   // the series in digit-reversed order, transformed in place
     const int b = blockIdx.x / N, k = blockIdx.x - b * N;
     const int64_t NP = (int64_t)N * P;
     const float* col = bold + (Tb - n) * NP + (int64_t)k * P + p0 + b;
     double s = 0.0;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
         const float x = col[(int64_t)t * NP];
-        b0[t] = make_float2(x, 0.0f);
+        a[__ldg(perm + t)] = make_float2(x, 0.0f);
         s += (double)x;
     }
     const float mean = (float)(block_sum(s, red_d) / (double)n);
-    for (int t = threadIdx.x; t < n; t += blockDim.x) b0[t].x -= mean;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) a[t].x -= mean;
     __syncthreads();
-    float2* X = fft(b0, b1, plan, tw, false);
-    float2* other = X == b0 ? b1 : b0;
+    fft_dit(a, plan, tw, false);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float h = (i >= band_lo && i <= band_hi) ? 2.0f : 0.0f;
-        X[i] = make_float2(h * X[i].x, h * X[i].y);
+        a[i] = make_float2(h * a[i].x, h * a[i].y);
     }
     __syncthreads();
-    float2* z = fft(X, other, plan, tw, true);
+    fft_dif(a, plan, tw, true);
     float2* Ub = U + (int64_t)b * Tp * N;
     for (int t = threadIdx.x; t < Tp; t += blockDim.x) {
-        const float2 v = z[t + discard];
+        const float2 v = a[__ldg(perm + t + discard)];
         const float r = hypotf(v.x, v.y);
         Ub[(int64_t)t * N + k] = r > 0.0f ? make_float2(v.x / r, v.y / r) : make_float2(1.0f, 0.0f);
     }
@@ -592,6 +638,34 @@ bool make_plan(int n, FftPlan& p)
     return true;
 }
 
+// Digit reversal of the plan: the decimation-in-time stages (radix[0] first)
+// take x_t at position perm[t], and the decimation-in-frequency stages leave
+// output t at perm[t]. With t = sum_k d_k W_k in the number system whose
+// least significant digit has radix radix[m-1] (W_0 = 1, W_{k+1} = W_k
+// radix[m-1-k]), perm[t] = sum_k d_{m-1-k} V_k with V_0 = 1,
+// V_{k+1} = V_k radix[k].
+std::vector<int> digit_reversal(const FftPlan& p)
+{
+    const int m = p.n_stages;
+    std::vector<int> perm(p.n);
+    for (int t = 0; t < p.n; ++t) {
+        int d[AN_MAX_STAGES];
+        int rem = t;
+        for (int k = 0; k < m; ++k) {
+            const int r = p.radix[m - 1 - k];
+            d[k] = rem % r;
+            rem /= r;
+        }
+        int v = 0, w = 1;
+        for (int k = 0; k < m; ++k) {
+            v += d[m - 1 - k] * w;
+            w *= p.radix[k];
+        }
+        perm[t] = v;
+    }
+    return perm;
+}
+
 #define ACK(call, what)                                                                              \
     do {                                                                                             \
         cudaError_t e_ = (call);                                                                     \
@@ -660,12 +734,16 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
     float *psd, *pli;
     int* ud;
     ACK(scr.get(&tw, n), "analysis twiddles");
+    int* perm;
+    ACK(scr.get(&perm, n), "analysis digit reversal");
+    const std::vector<int> hperm = digit_reversal(plan);
+    ACK(cudaMemcpyAsync(perm, hperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s), "analysis digit reversal");
     ACK(scr.get(&z, (size_t)B * N * n), "analysis signals");
     ACK(scr.get(&psd, (size_t)B * N * std::max(band_n, 1)), "analysis PSD");
     ACK(scr.get(&pli, (size_t)B), "analysis PLI");
     ACK(scr.get(&ud, (size_t)B * N * 4), "analysis UP/DOWN");
     ACK(cudaMemcpyAsync(tw, htw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s), "analysis twiddles");
-    const size_t smem_series = sizeof(float2) * 2 * (size_t)n;
+    const size_t smem_series = sizeof(float2) * (size_t)n;
     ACK(cudaFuncSetAttribute(an_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_series),
         "analysis shared memory");
     const size_t smem_pli = sizeof(float) * 2 * (size_t)((N + 3) / 4 * 4) * PLI_TS;
@@ -680,7 +758,7 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
     for (int64_t p0 = 0; p0 < P; p0 += B) {
         const int64_t nb = std::min<int64_t>(B, P - p0);
         note_launch(3);
-        an_series_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_series, s>>>(series, N, T, plan, tw, band_lo,
+        an_series_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_series, s>>>(series, N, T, plan, tw, perm, band_lo,
                                                                            band_n, psd_scale, p0, psd, ud, z);
         ACK(cudaGetLastError(), "analysis series");
         an_pli_kernel<<<(unsigned)nb, PLI_THREADS, smem_pli, s>>>(z, N, n, pli);
@@ -728,9 +806,13 @@ extern "C" tvbx_status tvbx_phfcd(const float* bold, int32_t n_regions, int64_t 
     AnScratch scr(s);
     float2 *tw, *U;
     ACK(scr.get(&tw, n), "phFCD twiddles");
+    int* perm;
+    ACK(scr.get(&perm, n), "phFCD digit reversal");
+    const std::vector<int> hperm = digit_reversal(plan);
+    ACK(cudaMemcpyAsync(perm, hperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s), "phFCD digit reversal");
     ACK(scr.get(&U, (size_t)B * Tp * N), "phFCD phasors");
     ACK(cudaMemcpyAsync(tw, htw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s), "phFCD twiddles");
-    const size_t smem_phase = sizeof(float2) * 2 * (size_t)n;
+    const size_t smem_phase = sizeof(float2) * (size_t)n;
     ACK(cudaFuncSetAttribute(an_phase_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_phase),
         "phFCD shared memory");
     const size_t smem_pf = sizeof(float2) * 2 * (size_t)N * PF_TILE;
@@ -742,7 +824,7 @@ extern "C" tvbx_status tvbx_phfcd(const float* bold, int32_t n_regions, int64_t 
     for (int64_t p0 = 0; p0 < P; p0 += B) {
         const int64_t nb = std::min<int64_t>(B, P - p0);
         note_launch(2);
-        an_phase_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_phase, s>>>(bold, N, P, n_tr, plan, tw, band_lo,
+        an_phase_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_phase, s>>>(bold, N, P, n_tr, plan, tw, perm, band_lo,
                                                                           band_hi, discard, p0, U);
         ACK(cudaGetLastError(), "phFCD phases");
         an_phfcd_kernel<<<dim3((unsigned)(nt * (nt + 1) / 2), (unsigned)nb), PF_THREADS, smem_pf, s>>>(U, N, Tp, p0,
