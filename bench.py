@@ -829,6 +829,64 @@ def run_bold_engine(args):
 
 
 # ---------------------------------------------------------------------------
+# Refit of the Table 1 polynomial: 768 (nu_e, nu_i, W) points x 128 AdEx cells
+# with Poisson inputs, 5 s each at dt 0.05 ms, then the least-squares fit of
+# the effective thresholds (regular-spiking cell).
+TF_METRIC = "cell-steps/s on 1 GB300 (single-cell AdEx simulations for the Table 1 refit)"
+
+
+def run_tffit_engine(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2311_13337_gb300 import tvbx
+    cell = tvbx.cell_defaults(0)
+    g = np.linspace(0.001, 0.03, 16)
+    nu_e, nu_i, W = np.meshgrid(g, g, [0.0, 50.0, 100.0], indexing="ij")
+    nu_e, nu_i, W = nu_e.ravel(), nu_i.ravel(), W.ravel()
+    n_cells, T_ms, tr_ms, dt = 128, 5000.0, 200.0, 0.05
+    EL = np.full(nu_e.size, cell["EL"])
+
+    def step():
+        r = tvbx.cell_rates(cell, nu_e, nu_i, W, n_cells=n_cells, T_ms=T_ms, transient_ms=tr_ms, dt_ms=dt, seed=1)
+        return r, tvbx.tf_fit(nu_e, nu_i, W, EL, r)
+
+    for _ in range(args.warmup):
+        step()
+    launches0 = tvbx.launch_count()
+    sampler = start_clock_sampler(0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rates, (P, used) = step()
+    el = (time.perf_counter() - t0) / args.steps
+    clocks = stop_clock_sampler(sampler)
+    units = float(nu_e.size) * n_cells * (T_ms / dt)
+    m = tvbx.make_model()
+    base = None
+    if not args.no_cpu_baseline:
+        from oracle import adex_cell as A
+        t0 = time.time()
+        A.simulate_cells(A.CELL_RS, nu_e[:32], nu_i[:32], W[:32], 8, 500.0, 0.0, dt, 1)
+        cel = time.time() - t0
+        base = {"value": 32 * 8 * (500.0 / dt) / cel, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                "sample": f"32 points x 8 cells x 0.5 s (FP64 numpy); {cel:.1f} s"}
+    line = {"metric": TF_METRIC, "value": units / el, "unit": "cell-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * el, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "768 points (nu_e 16 x nu_i 16 in 1-30 Hz, W in {0, 50, 100} pA) x 128 "
+                                   "regular-spiking AdEx cells x 5 s at dt 0.05 ms, then the Table 1 least-squares "
+                                   "fit", "n_points": int(nu_e.size), "n_cells": n_cells},
+            "clocks": clocks, "gpu_launches": (tvbx.launch_count() - launches0) / args.steps,
+            "fit": {"points_used": used, "P_fitted_mV": [float(x) for x in P],
+                    "P_table1_RS_mV": [float(x) for x in m.P_e]},
+            "roofline": None, "cpu_baseline": base,
+            "note": "compute-bound cell integration (an exponential per step); see DESIGN for the roofline reading"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # The paper's vast exploration (Table 4): the full 10-axis grid of 262,144
 # parameter sets on the 68-region connectome, run as four sweeps of 65,536
 # sets (one per conduction speed), each followed by FC (bf16x3), FCD, the
@@ -1233,7 +1291,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep", "fc", "batch", "surrogate", "analysis", "table4", "bold"],
+    ap.add_argument("--workload", choices=["sweep", "fc", "batch", "surrogate", "analysis", "table4", "bold", "tffit"],
                     default="sweep",
                     help="sweep: the paper-scale sweep (default); fc: the FC stage alone on 32,768 "
                          "series of 68 regions x 5,000 samples")
@@ -1254,6 +1312,8 @@ def main():
         return run_table4_engine(args)
     if args.workload == "bold":
         return run_bold_engine(args)
+    if args.workload == "tffit":
+        return run_tffit_engine(args)
     if args.workload == "fc":
         return run_fc_reference(args) if args.impl == "reference" else run_fc_engine(args)
     if args.impl == "reference":

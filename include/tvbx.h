@@ -545,6 +545,49 @@ tvbx_status tvbx_phfcd(const float* bold, int32_t n_regions, int64_t n_sets, int
                        double f_lo_hz, double f_hi_hz, int32_t discard, float* out, int32_t* n_used,
                        void* cuda_stream);
 
+/* ---- Refit of the transfer-function polynomial ------------------------------
+ * Sec. "Transfer Function": the template's effective threshold is the
+ * second-order polynomial of Table 1 in the normalised mu_V, sigma_V,
+ * tau_V^N, fitted to simulations of single AdEx neurons (Zerlaut et al.
+ * 2018). These calls redo that fit on the GPU.
+ *
+ * tvbx_cell_rates: output rates (kHz, host rate_khz_out [n_points]) of
+ * n_cells independent cells at each point (input rates nu_e_khz, nu_i_khz per
+ * input synapse, constant current -W_pA; host arrays [n_points]). Each cell
+ * is an adaptive exponential integrate-and-fire neuron
+ *   C dV/dt = g_L (E_L - V) + g_L Delta exp((V - V_T) / Delta)
+ *             + g_e (E_e - V) + g_i (E_i - V) - W,
+ * spike at V >= V_T + 5 Delta (reset to V_reset, refractory t_ref), with
+ * exponential conductances (time constants tau_e, tau_i) that jump by Q_e,
+ * Q_i per input spike; forward Euler with step dt_ms; per step the input
+ * counts are Poisson with means K_e nu_e dt and K_i nu_i dt, drawn from words
+ * 0 and 1 of Philox4x32-10 (counter (step, cell index, 0, 0), key = seed,
+ * cell index = point n_cells + c) by comparison with the integer thresholds
+ * floor(P(N <= k) 2^32), k < 32. Spikes after transient_ms count. Runs on
+ * the legacy default stream and returns when the rates are on the host.
+ * tvbx_cell_defaults: regular-spiking (pop 0) or fast-spiking (pop 1) cell
+ * (C 200 pF, g_L 10 nS, E_L -64 mV, V_T -50 mV, Delta 2 or 0.5 mV, V_reset
+ * -65 mV, t_ref 5 ms, Q_e 1.5 nS, Q_i 5 nS, tau_e = tau_i = 5 ms, E_e 0,
+ * E_i -80 mV, K_e 400, K_i 100).
+ *
+ * tvbx_tf_fit: host computation (no device use). For each point with a rate F
+ * in (0, 1 / (2 tau_V)): the template's mu_V, sigma_V, tau_V, tau_V^N (FP64,
+ * model m, leak E_L[p], current W_pA[p]) and the effective threshold
+ * mu_V + sqrt(2) sigma_V erfcinv(2 tau_V F); P_out[10] = least-squares
+ * coefficients (mV, Table 1 column order) of the threshold polynomial;
+ * *n_used = points used (nullable). Fewer than 10 usable points:
+ * TVBX_E_NUMERIC. */
+typedef struct {
+    double C, gL, EL, VT, Delta, Vreset, t_ref, Qe, Qi, tau_e, tau_i, Ee, Ei, Ke, Ki;
+} tvbx_cell_params;
+tvbx_status tvbx_cell_defaults(int32_t pop, tvbx_cell_params* out);
+tvbx_status tvbx_cell_rates(const tvbx_cell_params* cell, int64_t n_points, const double* nu_e_khz,
+                            const double* nu_i_khz, const double* W_pA, int32_t n_cells, double T_ms,
+                            double transient_ms, double dt_ms, uint64_t seed, double* rate_khz_out);
+tvbx_status tvbx_tf_fit(const tvbx_model* m, int64_t n_points, const double* nu_e_khz, const double* nu_i_khz,
+                        const double* W_pA, const double* E_L, const double* rate_khz, double P_out[10],
+                        int32_t* n_used);
+
 /* ---- Surrogate network ---------------------------------------------------
  * The paper has no surrogate model; it motivates guided exploration of the
  * parameter space (Sec. "Discussion"). This is the learned form of the

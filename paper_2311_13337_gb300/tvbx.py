@@ -91,7 +91,8 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_surrogate_predict", "tvbx_surrogate_propose", "tvbx_surrogate_params", "tvbx_surrogate_gradients",
            "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project", "tvbx_batch_create", "tvbx_batch_tune",
            "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy", "tvbx_fc_fitness", "tvbx_top_k",
-           "tvbx_series_analysis", "tvbx_bold_defaults", "tvbx_bold", "tvbx_phfcd")
+           "tvbx_series_analysis", "tvbx_bold_defaults", "tvbx_bold", "tvbx_phfcd",
+           "tvbx_cell_defaults", "tvbx_cell_rates", "tvbx_tf_fit")
 
 
 def library_path() -> str:
@@ -151,6 +152,10 @@ def load(build_if_missing: bool = False):
     L.tvbx_top_k.argtypes = [fp, i64, i32, fp, fp, vp]
     L.tvbx_series_analysis.argtypes = [fp, i32, i64, i64, ctypes.c_double, fp, ctypes.POINTER(i32), vp]
     L.tvbx_bold_defaults.argtypes = [ctypes.POINTER(BoldParams)]
+    L.tvbx_cell_defaults.argtypes = [i32, ctypes.POINTER(CellParams)]
+    L.tvbx_cell_rates.argtypes = [ctypes.POINTER(CellParams), i64, dp, dp, dp, i32, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_uint64, dp]
+    L.tvbx_tf_fit.argtypes = [ctypes.POINTER(Model), i64, dp, dp, dp, dp, dp, dp, ctypes.POINTER(i32)]
     L.tvbx_bold.argtypes = [fp, i32, i64, i64, ctypes.c_double, i32, ctypes.POINTER(BoldParams), fp, i32, fp, vp]
     L.tvbx_phfcd.argtypes = [fp, i32, i64, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, fp,
                              ctypes.POINTER(i32), vp]
@@ -639,6 +644,41 @@ def phfcd(bold_series, tr_s, f_lo_hz=0.008, f_hi_hz=0.08, discard=0, stream=None
                              int(discard), ctypes.c_void_p(out.data_ptr()), ctypes.byref(used), _stream_ptr(stream)),
            "tvbx_phfcd")
     return out, used.value
+
+
+class CellParams(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("C", "gL", "EL", "VT", "Delta", "Vreset", "t_ref", "Qe", "Qi", "tau_e",
+                                               "tau_i", "Ee", "Ei", "Ke", "Ki")]
+
+
+def cell_defaults(pop: int = 0) -> dict:
+    """Regular-spiking (0) or fast-spiking (1) AdEx cell (tvbx_cell_defaults)."""
+    p = CellParams()
+    _check(load().tvbx_cell_defaults(int(pop), ctypes.byref(p)), "tvbx_cell_defaults")
+    return {k: getattr(p, k) for k, _ in CellParams._fields_}
+
+
+def cell_rates(cell: dict, nu_e_khz, nu_i_khz, W_pA, n_cells=16, T_ms=5000.0, transient_ms=200.0, dt_ms=0.05,
+               seed=1) -> np.ndarray:
+    """Output rates (kHz) of single AdEx cells with Poisson inputs (tvbx_cell_rates)."""
+    arrs = [np.ascontiguousarray(np.atleast_1d(a), dtype=np.float64) for a in (nu_e_khz, nu_i_khz, W_pA)]
+    out = np.zeros(arrs[0].size)
+    _check(load().tvbx_cell_rates(ctypes.byref(CellParams(**cell)), arrs[0].size, _dptr(arrs[0]), _dptr(arrs[1]),
+                                  _dptr(arrs[2]), int(n_cells), float(T_ms), float(transient_ms), float(dt_ms),
+                                  int(seed), _dptr(out)), "tvbx_cell_rates")
+    return out
+
+
+def tf_fit(nu_e_khz, nu_i_khz, W_pA, E_L, rate_khz, model: Model | None = None):
+    """Table 1 coefficients fitted to measured rates (tvbx_tf_fit): (P[10], points used)."""
+    m = model if model is not None else make_model()
+    arrs = [np.ascontiguousarray(np.atleast_1d(a), dtype=np.float64) for a in (nu_e_khz, nu_i_khz, W_pA, E_L,
+                                                                               rate_khz)]
+    P = np.zeros(10)
+    used = ctypes.c_int32(0)
+    _check(load().tvbx_tf_fit(ctypes.byref(m), arrs[0].size, *[_dptr(a) for a in arrs], _dptr(P), ctypes.byref(used)),
+           "tvbx_tf_fit")
+    return P, used.value
 
 
 class Surrogate:

@@ -129,3 +129,37 @@ def test_every_status_check_in_the_binding_names_one_call():
     calls = [n for n in ast.walk(ast.parse(src))
              if isinstance(n, ast.Call) and getattr(n.func, "id", None) == "_check"]
     assert calls and all(len(c.args) == 2 and not c.keywords for c in calls)
+
+
+def test_tf_fit_on_the_host_equals_the_oracle_fit(lib, oracle):
+    """tvbx_tf_fit is host arithmetic (no device use): on rates produced by the
+    template itself it returns the Table 1 coefficients, and on rates from
+    another polynomial it equals the oracle's inversion and least squares."""
+    from oracle import adex_cell as A
+    m_e = lib.make_model()
+    om = oracle.make_model()
+    rng = np.random.default_rng(5)
+    nu_e, nu_i, W, EL, F, aux_all = [], [], [], [], [], []
+    for _ in range(300):
+        x_e, x_i, w = rng.uniform(0.002, 0.03), rng.uniform(0.002, 0.03), rng.uniform(0, 100)
+        jet, aux = oracle.tf_eval(om, "e", -64.0, x_e, x_i, w)
+        if 0 < jet[0] < 1 / (2 * aux[4]):
+            nu_e.append(x_e); nu_i.append(x_i); W.append(w); EL.append(-64.0); F.append(jet[0]); aux_all.append(aux)
+    P, used = lib.tf_fit(nu_e, nu_i, W, EL, F, model=m_e)
+    assert used == len(F) >= 40
+    assert np.allclose(P, list(om.P_e), atol=1e-5)
+    # perturbed rates: the two fits agree
+    Fp = np.array(F) * rng.uniform(0.8, 1.25, len(F))
+    keep = Fp < 1 / (2 * np.array([a[4] for a in aux_all]))
+    P2, used2 = lib.tf_fit(np.array(nu_e)[keep], np.array(nu_i)[keep], np.array(W)[keep], np.array(EL)[keep], Fp[keep],
+                           model=m_e)
+    vth = [A.effective_threshold(a[1], a[3], a[4], f) for a, f in zip(np.array(aux_all)[keep], Fp[keep])]
+    Po = A.fit_polynomial([a[1] for a in np.array(aux_all)[keep]], [a[3] for a in np.array(aux_all)[keep]],
+                          [a[5] for a in np.array(aux_all)[keep]], vth,
+                          (om.mu0, om.dmu0, om.sig0, om.dsig0, om.tau0, om.dtau0))
+    assert used2 == keep.sum() and np.allclose(P2, Po, rtol=1e-8, atol=1e-8)
+
+
+def test_cell_defaults_match_the_oracle(lib):
+    from oracle import adex_cell as A
+    assert lib.cell_defaults(0) == A.CELL_RS and lib.cell_defaults(1) == A.CELL_FS
