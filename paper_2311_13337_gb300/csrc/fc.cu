@@ -8,7 +8,10 @@
 //   s_b[k]    = sum_{t in block b} (x_k(t) - m_k),
 // with the shift m_k = the running mean kept by the simulation, or a given
 // shift (any shift is exact; a close one avoids cancellation). The covariance over a union of
-// blocks of length L is sum G_b - (sum s_b)(sum s_b)^T / L.
+// blocks of length L is sum G_b - (sum s_b)(sum s_b)^T / L. The tensor-core
+// producer leaves G_b unsymmetric in its split forms, so the readers take
+// (G_b + G_b^T) / 2 for each pair (k, j), which also makes the FC exactly
+// symmetric.
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -134,72 +137,6 @@ fc_moments_kernel(const __grid_constant__ FcArgs a, int32_t Npad, int32_t Tt, in
             }
         }
         __syncthreads();
-    }
-}
-
-// Per set: covariance over all blocks, Pearson FC, chi and mean off-diagonal FC.
-__global__ void fc_finalize_kernel(const __grid_constant__ FcArgs a)
-{
-    extern __shared__ float sm[];   // cov [N][N] + sdev [N] + red[64]
-    const int N = a.N;
-    const int p = blockIdx.x;
-    const int64_t Tn = a.t_end - a.t_begin;
-    float* cov = sm;
-    float* sd = sm + N * N;
-    float* red = sd + N;
-    const int64_t stride_b = (int64_t)N * N + N;
-    const float* B = a.blocks + (int64_t)p * a.n_blocks * stride_b;
-    const float invT = Tn > 0 ? 1.0f / (float)Tn : 0.0f;
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-        const int k = i / N, j = i - k * N;
-        float g = 0.0f, sk = 0.0f, sj = 0.0f;
-        for (int b = 0; b < a.n_blocks; ++b) {
-            g += 0.5f * (B[b * stride_b + i] + B[b * stride_b + (int64_t)j * N + k]);
-            sk += B[b * stride_b + (int64_t)N * N + k];
-            sj += B[b * stride_b + (int64_t)N * N + j];
-        }
-        cov[i] = g - sk * sj * invT;
-    }
-    __syncthreads();
-    bool zero = false;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const float v = cov[k * N + k];
-        sd[k] = v > 0.0f ? sqrtf(v) : 0.0f;
-    }
-    __syncthreads();
-    // chi^2 = (sum_kj cov / N^2) / (sum_k cov_kk / N); mean off-diagonal FC
-    float s_all = 0.0f, s_diag = 0.0f, s_fc = 0.0f;
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-        const int k = i / N, j = i - k * N;
-        s_all += cov[i];
-        float f;
-        if (k == j) {
-            s_diag += cov[i];
-            f = 1.0f;
-            if (!(sd[k] > 0.0f)) zero = true;
-        } else {
-            const float d = sd[k] * sd[j];
-            f = d > 0.0f ? cov[i] / d : 0.0f;
-            s_fc += f;
-        }
-        if (a.fc) a.fc[(int64_t)p * N * N + i] = f;
-    }
-    // block reduction of the three sums
-    for (int o = 16; o > 0; o >>= 1) {
-        s_all += __shfl_xor_sync(0xffffffffu, s_all, o);
-        s_diag += __shfl_xor_sync(0xffffffffu, s_diag, o);
-        s_fc += __shfl_xor_sync(0xffffffffu, s_fc, o);
-    }
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (lane == 0) { red[warp] = s_all; red[16 + warp] = s_diag; red[32 + warp] = s_fc; }
-    if (zero) atomicOr(a.status + p, TVBX_SET_ZERO_VAR);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float A = 0.0f, D = 0.0f, Fs = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) { A += red[w]; D += red[16 + w]; Fs += red[32 + w]; }
-        const float num = A / ((float)N * (float)N), den = D / (float)N;
-        a.chi[p] = den > 0.0f ? sqrtf(fmaxf(num / den, 0.0f)) : 0.0f;
-        a.mean_fc[p] = N > 1 ? Fs / ((float)N * (float)(N - 1)) : 0.0f;
     }
 }
 
@@ -331,17 +268,6 @@ cudaError_t launch_fc_moments(const FcArgs& a, cudaStream_t s)
     dim3 grid((a.P + FC_SETS - 1) / FC_SETS, chunks);
     note_launch();
     fc_moments_kernel<<<grid, FC_THREADS, smem, s>>>(a, Npad, Tt, tasks_per_set, per_chunk);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fc_finalize(const FcArgs& a, cudaStream_t s)
-{
-    cudaError_t e;
-    const size_t smem2 = sizeof(float) * ((size_t)a.N * a.N + a.N + 64);
-    e = cudaFuncSetAttribute(fc_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    fc_finalize_kernel<<<a.P, 512, smem2, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -558,9 +484,10 @@ cudaError_t launch_fc_reduce(const FcArgs& a, int32_t m, int32_t nw, int64_t Lw,
 {
     const size_t smem = fc_reduce_smem(a.N, a.n_blocks, nw);
     if (smem > 200 * 1024) {
-        // too large for shared memory: the two-kernel form
+        // window vectors too large for shared memory: the FC pass without
+        // windows, then the FCD with the vectors in global scratch
         cudaError_t e = launch_fc_finalize(a, s);
-        if (e != cudaSuccess || nw == 0) return e;
+        if (e != cudaSuccess) return e;
         return launch_fcd(a.blocks, a.P, a.N, a.n_blocks, m, nw, Lw, vec_scratch, fcd, s);
     }
     if (a.n_blocks <= FCR_MAXB) {
@@ -574,6 +501,13 @@ cudaError_t launch_fc_reduce(const FcArgs& a, int32_t m, int32_t nw, int64_t Lw,
         }
     }
     return launch_reduce_mw<0>(a, m, nw, Lw, fcd, smem, s);
+}
+
+cudaError_t launch_fc_finalize(const FcArgs& a, cudaStream_t s)
+{
+    const size_t smem = fc_reduce_smem(a.N, a.n_blocks, 0);
+    return a.n_blocks <= FCR_MAXB ? launch_reduce_mw<1>(a, 0, 0, 0, nullptr, smem, s)
+                                  : launch_reduce_mw<0>(a, 0, 0, 0, nullptr, smem, s);
 }
 
 size_t fc_reduce_needs_vec_scratch(int N, int nb, int nw) { return fc_reduce_smem(N, nb, nw) > 200 * 1024; }

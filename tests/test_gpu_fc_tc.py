@@ -90,6 +90,7 @@ def test_fc_series_matches_oracle(tvbx, torch, oracle, prec, N, P, T, kind):
     err = np.abs(g["fc"] - ref).max()
     assert err <= TOL[prec], f"precision {prec}: max |FC error| {err:.3g}"
     assert np.all(np.diagonal(g["fc"], axis1=1, axis2=2) == 1.0)
+    assert np.array_equal(g["fc"], np.transpose(g["fc"], (0, 2, 1)))   # one entry of each pair serves both
     rchi = oracle.chi(x)
     assert np.abs(g["chi"] - rchi).max() <= 10 * TOL[prec] * max(1.0, rchi.max())
     assert np.abs(g["mean_fc"] - oracle.mean_offdiag(ref)).max() <= TOL[prec]
@@ -105,6 +106,20 @@ def test_fcd_series_matches_oracle(tvbx, torch, oracle, prec):
     assert g["fcd"].shape == ref.shape
     assert np.abs(g["fcd"] - ref).max() <= min(FC_ATOL, 20 * TOL[prec])
     assert np.abs(g["fc"] - oracle.fc_pearson(x)).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize("N", [200, 360])
+def test_fc_and_fcd_beyond_shared_memory(tvbx, torch, oracle, N):
+    """Three FCD windows of 200 or 360 regions: the window vectors (3 x
+    19,900 or 3 x 64,620 floats) do not fit in shared memory, so the FC and
+    the FCD take the two-kernel form with the vectors in global scratch."""
+    x = _series(3, N, 300, seed=17, kind="gauss")
+    g = _run(tvbx, torch, x, 0, fcd_window=100, fcd_step=100)
+    assert g["n_windows"] == 3
+    assert np.abs(g["fc"] - oracle.fc_pearson(x)).max() <= TOL[0]
+    assert np.array_equal(g["fc"], np.transpose(g["fc"], (0, 2, 1)))
+    assert np.abs(g["fcd"] - oracle.fcd(x, 100, 100)).max() <= FC_ATOL
+    assert np.abs(g["mean_fc"] - oracle.mean_offdiag(oracle.fc_pearson(x))).max() <= TOL[0]
 
 
 def test_zero_variance_rows(tvbx, torch, oracle):
