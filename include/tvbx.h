@@ -226,6 +226,40 @@ tvbx_status tvbx_sweep_info(const tvbx_sweep* h, int64_t* n_sets, int32_t* n_reg
  * transient_samples >= T), TVBX_E_OOM, TVBX_E_CUDA. */
 tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream);
 
+/* Continue the trajectory of h for n_steps more steps (Eq. 1-5 as in
+ * tvbx_run) from the step where the last tvbx_run, tvbx_run_continue or
+ * tvbx_restore left it, with the same dt, averaging, noise and seed. The
+ * state, the delay ring buffers, the OU processes and the status bits carry
+ * over, and the noise is keyed by the global step (counter-based Philox), so
+ * tvbx_run of n1 steps followed by tvbx_run_continue of n2 steps follows the
+ * same trajectory, bit for bit, as one tvbx_run of n1 + n2 steps. The series
+ * [P][N][n_steps / tavg_steps] and the running sums behind the means, FC and
+ * chi then cover the new samples only; transient_samples of them are left
+ * out of the means. Asynchronous on cuda_stream like tvbx_run.
+ * Errors: TVBX_E_BAD_STATE without a preceding run on h (a batch run does
+ * not count) or when the steps so far are not a multiple of tavg_steps;
+ * TVBX_E_INVALID_ARG for n_steps < 0, transient_samples out of range, or a
+ * total of 2^32 - 1 steps or more; TVBX_E_OOM, TVBX_E_CUDA. */
+tvbx_status tvbx_run_continue(tvbx_sweep* h, int64_t n_steps, int32_t transient_samples, void* cuda_stream);
+
+/* Checkpoint / restore of a trajectory (no counterpart in the paper, whose
+ * runs write observables only). A checkpoint is a host byte buffer holding
+ * the state [14][N][P], the status words, the delay ring buffers, the OU
+ * state, the step count and the run settings, tagged with a fingerprint of
+ * the sweep's connectome, points and constants.
+ *   tvbx_checkpoint_size: *bytes = the buffer size needed.
+ *   tvbx_checkpoint: synchronises h's stream and copies into host_buf
+ *     (caller-owned, at least that many bytes).
+ *   tvbx_restore: loads a checkpoint into h, a sweep created with the same
+ *     connectome, points and constants (any handle, e.g. in a new process);
+ *     synchronous. tvbx_run_continue on h then resumes bit for bit.
+ * Errors: TVBX_E_BAD_STATE (checkpoint before any run), TVBX_E_INVALID_ARG
+ * (NULL, short buffer, not a checkpoint, another sweep's checkpoint),
+ * TVBX_E_OOM, TVBX_E_CUDA. */
+tvbx_status tvbx_checkpoint_size(const tvbx_sweep* h, uint64_t* bytes);
+tvbx_status tvbx_checkpoint(tvbx_sweep* h, void* host_buf, uint64_t bytes);
+tvbx_status tvbx_restore(tvbx_sweep* h, const void* host_buf, uint64_t bytes);
+
 /* Per-set summary of the last run, each output [n_sets] (any may be NULL):
  * mean E and I rates (Hz) over samples after the transient and regions,
  * the synchrony index chi = sqrt(Var_t(mean_k E_k) / mean_k Var_t(E_k)),

@@ -212,6 +212,9 @@ struct tvbx_sweep {
     int32_t pb = 16;
     int32_t variant = -1;           // simulation kernel of the last run
     uint64_t gen = 0;               // incremented by every run preparation
+    int64_t steps_done = 0;         // steps integrated since the initial state
+    bool resumable = false;         // state, ring and OU state hold step steps_done
+    int64_t ring_floats = 0;        // size of the ring allocation in use
 
     DevBuf d_prm, d_ext, d_state, d_status, d_ring, d_series, d_ou_table, d_ou_state;
     DevBuf d_csr_row, d_csr_cd, d_csr_w, d_groups, d_tiles;
@@ -506,12 +509,15 @@ struct RunPlan {
     std::vector<int64_t> tile_nnz;   // weights per row of the tile's group (cost model)
 };
 
+// n_base > 0: the run continues a trajectory at global step n_base (state,
+// ring buffers and OU state are kept; the series and the running sums start
+// afresh for the new samples).
 static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_t s, int general_pb,
-                               bool device_init, RunPlan& plan, bool direct_body = false)
+                               bool device_init, RunPlan& plan, bool direct_body = false, int64_t n_base = 0)
 {
     if (!(c.dt_ms > 0.0) || !isfinite(c.dt_ms)) return fail(TVBX_E_INVALID_ARG, "dt_ms must be > 0");
-    if (c.n_steps < 0 || c.n_steps > ((int64_t)1 << 32) - 2)
-        return fail(TVBX_E_INVALID_ARG, "n_steps must be in [0, 2^32 - 1)");
+    if (c.n_steps < 0 || n_base + c.n_steps > ((int64_t)1 << 32) - 2)
+        return fail(TVBX_E_INVALID_ARG, "steps so far plus n_steps must be in [0, 2^32 - 1)");
     if (c.tavg_steps < 1) return fail(TVBX_E_INVALID_ARG, "tavg_steps must be >= 1");
     if (c.chunk_steps < 0 || (c.chunk_steps > 0 && c.chunk_steps % c.tavg_steps != 0))
         return fail(TVBX_E_INVALID_ARG, "chunk_steps must be 0 or a positive multiple of tavg_steps");
@@ -522,6 +528,7 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     h->stream = s;
     h->ran = false;
     h->fc_valid = false;
+    h->resumable = false;
     h->gen += 1;
 
     std::vector<Group> groups;
@@ -660,8 +667,9 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     CK(cudaMemcpyAsync(h->d_groups.ptr, gdev.data(), sizeof(GroupDev) * gdev.size(), cudaMemcpyHostToDevice, s), "upload");
     if (!tiles.empty())
         CK(cudaMemcpyAsync(h->d_tiles.ptr, tiles.data(), sizeof(TileDev) * tiles.size(), cudaMemcpyHostToDevice, s), "upload");
-    CK(cudaMemsetAsync(h->d_ou_state.ptr, 0, sizeof(float) * N, s), "OU state");
+    if (n_base == 0) CK(cudaMemsetAsync(h->d_ou_state.ptr, 0, sizeof(float) * N, s), "OU state");
     CK(cudaMemsetAsync(h->d_error.ptr, 0, sizeof(uint32_t), s), "error word");
+    h->ring_floats = ring_floats;
 
     // chunking: keep each launch around 4-8 thousand steps
     int64_t chunk = c.chunk_steps > 0 ? c.chunk_steps : 0;
@@ -694,6 +702,20 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     a.noise_per_set = c.noise_per_set ? 1 : 0;
     a.seed = c.seed;
     a.p_offset = c.p_offset;
+    if (n_base > 0) {
+        // the kernels index samples by the global step, t = (n + 1) / ts - 1:
+        // shift the window [t_base, t_base + T) onto the series buffer (the
+        // address is formed in integers; every write lands inside the buffer)
+        const int64_t t_base = n_base / c.tavg_steps;
+        a.series = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(h->d_series.ptr) -
+                                            (uintptr_t)(sizeof(float) * (size_t)t_base * N * P));
+        a.T = t_base + T;
+        a.transient = t_base + c.transient_samples;
+        // running sums (means, FC shift) cover the new samples only
+        CK(cudaMemsetAsync(h->d_state.as<float>() + (size_t)SV_SUM_E * N * P, 0,
+                           sizeof(float) * (size_t)(SV_CMP_I - SV_SUM_E + 1) * N * P, s),
+           "running sums");
+    }
 
     if (device_init) {
         CK(launch_init_state(a, s), "init state");
@@ -711,30 +733,30 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     return TVBX_OK;
 }
 
-// Mark a handle's run as complete (results may be read).
-static void finish_run(tvbx_sweep* h, const tvbx_run_cfg& c)
+// Mark a handle's run as complete (results may be read). steps_before: the
+// global step the run started at; resumable: the state may be continued.
+static void finish_run(tvbx_sweep* h, const tvbx_run_cfg& c, int64_t steps_before = 0, bool resumable = false)
 {
     h->cfg = c;
     h->T = c.n_steps / c.tavg_steps;
     h->ran = true;
+    h->steps_done = steps_before + c.n_steps;
+    h->resumable = resumable;
 }
 
-tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
+// Enqueue the chunked launches of a prepared run over global steps
+// [n_base, n_base + c.n_steps).
+static tvbx_status run_chunks(tvbx_sweep* h, const tvbx_run_cfg& c, const RunPlan& plan, int64_t n_base,
+                              cudaStream_t s)
 {
-    if (!h || !cfg) return fail(TVBX_E_INVALID_ARG, "NULL handle or cfg");
-    const tvbx_run_cfg c = *cfg;
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    RunPlan plan;
-    tvbx_status st = prepare_run(h, c, s, 0, true, plan);
-    if (st != TVBX_OK) return st;
     SimArgs a = plan.a;
     const int N = h->N;
     const int64_t P = h->P;
     const int64_t chunk = plan.chunk;
     const int variant = plan.variant;
-    for (int64_t n0 = 0; n0 < c.n_steps; n0 += chunk) {
+    for (int64_t n0 = n_base; n0 < n_base + c.n_steps; n0 += chunk) {
         a.n0 = n0;
-        a.n_chunk = (int32_t)std::min<int64_t>(chunk, c.n_steps - n0);
+        a.n_chunk = (int32_t)std::min<int64_t>(chunk, n_base + c.n_steps - n0);
         if (!c.noise_per_set)
             CK(launch_ou_table(a.m, h->d_ou_table.as<float>(), h->d_ou_state.as<float>(), N, n0, a.n_chunk, c.seed, s),
                "OU table");
@@ -755,7 +777,190 @@ tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
             h->prof_region_steps += (double)P * N * a.n_chunk;
         }
     }
-    finish_run(h, c);
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_run(tvbx_sweep* h, const tvbx_run_cfg* cfg, void* cuda_stream)
+{
+    if (!h || !cfg) return fail(TVBX_E_INVALID_ARG, "NULL handle or cfg");
+    const tvbx_run_cfg c = *cfg;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    RunPlan plan;
+    tvbx_status st = prepare_run(h, c, s, 0, true, plan);
+    if (st != TVBX_OK) return st;
+    if ((st = run_chunks(h, c, plan, 0, s)) != TVBX_OK) return st;
+    finish_run(h, c, 0, true);
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_run_continue(tvbx_sweep* h, int64_t n_steps, int32_t transient_samples, void* cuda_stream)
+{
+    if (!h) return fail(TVBX_E_INVALID_ARG, "NULL handle");
+    if (!h->resumable) return fail(TVBX_E_BAD_STATE, "tvbx_run_continue needs a completed tvbx_run, "
+                                                     "tvbx_run_continue or tvbx_restore on this handle");
+    tvbx_run_cfg c = h->cfg;
+    if (h->steps_done % c.tavg_steps != 0)
+        return fail(TVBX_E_BAD_STATE, "the steps so far (%lld) are not a multiple of tavg_steps (%d)",
+                    (long long)h->steps_done, c.tavg_steps);
+    if (n_steps < 0) return fail(TVBX_E_INVALID_ARG, "n_steps must be >= 0");
+    c.n_steps = n_steps;
+    c.transient_samples = transient_samples;
+    const int64_t n_base = h->steps_done;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    RunPlan plan;
+    tvbx_status st = prepare_run(h, c, s, 0, false, plan, false, n_base);
+    if (st != TVBX_OK) return st;
+    if ((st = run_chunks(h, c, plan, n_base, s)) != TVBX_OK) return st;
+    finish_run(h, c, n_base, true);
+    return TVBX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint / restore
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char CKPT_MAGIC[8] = {'T', 'V', 'B', 'X', 'C', 'K', 'P', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    uint64_t fingerprint;     // of the sweep's connectome, points and constants
+    int64_t n_regions;
+    int64_t n_sets;
+    int64_t steps_done;
+    int64_t ring_floats;
+    double dt_ms;
+    int64_t tavg_steps;
+    int64_t noise_per_set;
+    uint64_t seed;
+    int64_t p_offset;
+    int64_t chunk_steps;
+    int64_t kernel;
+};
+
+// FNV-1a over the bytes of the definition of a sweep (all fields are doubles
+// or integers without padding)
+uint64_t sweep_fingerprint(const tvbx_sweep* h)
+{
+    uint64_t x = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) x = (x ^ b[i]) * 1099511628211ull;
+    };
+    const int64_t dims[2] = {h->N, h->P};
+    mix(dims, sizeof dims);
+    mix(h->W.data(), sizeof(double) * h->W.size());
+    mix(h->L.data(), sizeof(double) * h->L.size());
+    mix(h->prm.data(), sizeof(double) * h->prm.size());
+    mix(&h->model, sizeof h->model);
+    return x;
+}
+
+size_t ckpt_bytes(int64_t N, int64_t P, int64_t ring_floats)
+{
+    return sizeof(CkptHeader) + sizeof(float) * ((size_t)SV_COUNT * N * P + (size_t)ring_floats + (size_t)N) +
+           sizeof(uint32_t) * (size_t)P;
+}
+
+}  // namespace
+
+tvbx_status tvbx_checkpoint_size(const tvbx_sweep* h, uint64_t* bytes)
+{
+    if (!h || !bytes) return fail(TVBX_E_INVALID_ARG, "NULL handle or bytes");
+    if (!h->resumable) return fail(TVBX_E_BAD_STATE, "nothing to checkpoint: no completed run on this handle");
+    *bytes = ckpt_bytes(h->N, h->P, h->ring_floats);
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_checkpoint(tvbx_sweep* h, void* host_buf, uint64_t bytes)
+{
+    if (!h || !host_buf) return fail(TVBX_E_INVALID_ARG, "NULL handle or buffer");
+    if (!h->resumable) return fail(TVBX_E_BAD_STATE, "nothing to checkpoint: no completed run on this handle");
+    const int64_t N = h->N, P = h->P;
+    const size_t need = ckpt_bytes(N, P, h->ring_floats);
+    if (bytes < need) return fail(TVBX_E_INVALID_ARG, "checkpoint buffer holds %llu bytes, needs %zu",
+                                  (unsigned long long)bytes, need);
+    CK(cudaStreamSynchronize(h->stream), "checkpoint");
+    if (tvbx_status e = check_device_error(h)) return e;
+    CkptHeader hd;
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, CKPT_MAGIC, sizeof hd.magic);
+    hd.fingerprint = sweep_fingerprint(h);
+    hd.n_regions = N;
+    hd.n_sets = P;
+    hd.steps_done = h->steps_done;
+    hd.ring_floats = h->ring_floats;
+    hd.dt_ms = h->cfg.dt_ms;
+    hd.tavg_steps = h->cfg.tavg_steps;
+    hd.noise_per_set = h->cfg.noise_per_set;
+    hd.seed = h->cfg.seed;
+    hd.p_offset = h->cfg.p_offset;
+    hd.chunk_steps = h->cfg.chunk_steps;
+    hd.kernel = h->cfg.kernel;
+    unsigned char* out = static_cast<unsigned char*>(host_buf);
+    memcpy(out, &hd, sizeof hd);
+    size_t off = sizeof hd;
+    const size_t b_state = sizeof(float) * (size_t)SV_COUNT * N * P;
+    const size_t b_status = sizeof(uint32_t) * (size_t)P;
+    const size_t b_ring = sizeof(float) * (size_t)h->ring_floats;
+    const size_t b_ou = sizeof(float) * (size_t)N;
+    CK(cudaMemcpy(out + off, h->d_state.ptr, b_state, cudaMemcpyDeviceToHost), "checkpoint state");
+    off += b_state;
+    CK(cudaMemcpy(out + off, h->d_status.ptr, b_status, cudaMemcpyDeviceToHost), "checkpoint status");
+    off += b_status;
+    if (b_ring) CK(cudaMemcpy(out + off, h->d_ring.ptr, b_ring, cudaMemcpyDeviceToHost), "checkpoint ring");
+    off += b_ring;
+    CK(cudaMemcpy(out + off, h->d_ou_state.ptr, b_ou, cudaMemcpyDeviceToHost), "checkpoint OU state");
+    h->d2h += need - sizeof hd;
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_restore(tvbx_sweep* h, const void* host_buf, uint64_t bytes)
+{
+    if (!h || !host_buf) return fail(TVBX_E_INVALID_ARG, "NULL handle or buffer");
+    if (bytes < sizeof(CkptHeader)) return fail(TVBX_E_INVALID_ARG, "checkpoint too short");
+    CkptHeader hd;
+    memcpy(&hd, host_buf, sizeof hd);
+    if (memcmp(hd.magic, CKPT_MAGIC, sizeof hd.magic) != 0) return fail(TVBX_E_INVALID_ARG, "not a tvbx checkpoint");
+    if (hd.n_regions != h->N || hd.n_sets != h->P || hd.fingerprint != sweep_fingerprint(h))
+        return fail(TVBX_E_INVALID_ARG, "checkpoint of a different sweep (connectome, points or constants differ)");
+    if (hd.ring_floats < 0 || hd.steps_done < 0 || bytes < ckpt_bytes(h->N, h->P, hd.ring_floats))
+        return fail(TVBX_E_INVALID_ARG, "checkpoint truncated");
+    tvbx_run_cfg c;
+    memset(&c, 0, sizeof c);
+    c.dt_ms = hd.dt_ms;
+    c.n_steps = 0;
+    c.tavg_steps = (int32_t)hd.tavg_steps;
+    c.noise_per_set = (int32_t)hd.noise_per_set;
+    c.seed = hd.seed;
+    c.p_offset = hd.p_offset;
+    c.chunk_steps = (int32_t)hd.chunk_steps;
+    c.kernel = (int32_t)hd.kernel;
+    // lay out the buffers as the checkpointed run did, then fill them
+    RunPlan plan;
+    tvbx_status st = prepare_run(h, c, h->stream, 0, false, plan);
+    if (st != TVBX_OK) return st;
+    if (h->ring_floats != hd.ring_floats) return fail(TVBX_E_INVALID_ARG, "checkpoint ring layout differs");
+    const int64_t N = h->N, P = h->P;
+    const unsigned char* in = static_cast<const unsigned char*>(host_buf) + sizeof hd;
+    const size_t b_state = sizeof(float) * (size_t)SV_COUNT * N * P;
+    const size_t b_status = sizeof(uint32_t) * (size_t)P;
+    const size_t b_ring = sizeof(float) * (size_t)hd.ring_floats;
+    const size_t b_ou = sizeof(float) * (size_t)N;
+    CK(cudaStreamSynchronize(h->stream), "restore");
+    CK(cudaMemcpy(h->d_state.ptr, in, b_state, cudaMemcpyHostToDevice), "restore state");
+    in += b_state;
+    CK(cudaMemcpy(h->d_status.ptr, in, b_status, cudaMemcpyHostToDevice), "restore status");
+    in += b_status;
+    if (b_ring) CK(cudaMemcpy(h->d_ring.ptr, in, b_ring, cudaMemcpyHostToDevice), "restore ring");
+    in += b_ring;
+    CK(cudaMemcpy(h->d_ou_state.ptr, in, b_ou, cudaMemcpyHostToDevice), "restore OU state");
+    h->h2d += b_state + b_status + b_ring + b_ou;
+    h->cfg = c;
+    h->T = 0;
+    h->ran = false;
+    h->steps_done = hd.steps_done;
+    h->resumable = true;
     return TVBX_OK;
 }
 

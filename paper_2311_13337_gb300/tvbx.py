@@ -92,7 +92,8 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project", "tvbx_batch_create", "tvbx_batch_tune",
            "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy", "tvbx_fc_fitness", "tvbx_top_k",
            "tvbx_series_analysis", "tvbx_bold_defaults", "tvbx_bold", "tvbx_phfcd",
-           "tvbx_cell_defaults", "tvbx_cell_rates", "tvbx_tf_fit")
+           "tvbx_cell_defaults", "tvbx_cell_rates", "tvbx_tf_fit", "tvbx_run_continue", "tvbx_checkpoint_size",
+           "tvbx_checkpoint", "tvbx_restore")
 
 
 def library_path() -> str:
@@ -119,6 +120,10 @@ def load(build_if_missing: bool = False):
     L.tvbx_sweep_create_points.argtypes = [dp, dp, i32, i64, dp, ctypes.POINTER(Model), ctypes.POINTER(vp)]
     L.tvbx_sweep_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.tvbx_run.argtypes = [vp, ctypes.POINTER(RunCfg), vp]
+    L.tvbx_run_continue.argtypes = [vp, i64, i32, vp]
+    L.tvbx_checkpoint_size.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    L.tvbx_checkpoint.argtypes = [vp, vp, ctypes.c_uint64]
+    L.tvbx_restore.argtypes = [vp, vp, ctypes.c_uint64]
     L.tvbx_summary.argtypes = [vp, i32, fp, fp, fp, fp, fp]
     L.tvbx_series.argtypes = [vp, i32, fp]
     L.tvbx_series_range.argtypes = [vp, i64, i64, i64, i64, i32, fp]
@@ -290,6 +295,28 @@ def run(h, dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False
     _check(load().tvbx_run(h, ctypes.byref(cfg), sp), "tvbx_run")
 
 
+def run_continue(h, n_steps, transient_samples=0, stream=None):
+    """Continue the last run for n_steps more steps (tvbx_run_continue)."""
+    _check(load().tvbx_run_continue(h, int(n_steps), int(transient_samples), _stream_ptr(stream)),
+           "tvbx_run_continue")
+
+
+def checkpoint(h) -> np.ndarray:
+    """The trajectory's checkpoint as a host uint8 array (tvbx_checkpoint)."""
+    n = ctypes.c_uint64()
+    _check(load().tvbx_checkpoint_size(h, ctypes.byref(n)), "tvbx_checkpoint_size")
+    buf = np.zeros(n.value, dtype=np.uint8)
+    _check(load().tvbx_checkpoint(h, ctypes.c_void_p(buf.ctypes.data), n.value), "tvbx_checkpoint")
+    return buf
+
+
+def restore(h, buf):
+    """Load a checkpoint made by checkpoint() (tvbx_restore)."""
+    b = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if not isinstance(buf, np.ndarray) else buf,
+                             dtype=np.uint8)
+    _check(load().tvbx_restore(h, ctypes.c_void_p(b.ctypes.data), b.size), "tvbx_restore")
+
+
 def summary(h, mean_e_hz=None, mean_i_hz=None, chi=None, mean_fc=None, status=None):
     outs = [mean_e_hz, mean_i_hz, chi, mean_fc, status]
     kinds = {k for _, k in (_out_ptr(o) for o in outs) if k is not None}
@@ -436,6 +463,18 @@ class Sweep:
     def run(self, **kw):
         run(self.h, **kw)
         self._transient = int(kw.get("transient_samples", 0))
+        return self
+
+    def run_continue(self, n_steps, transient_samples=0, stream=None):
+        run_continue(self.h, n_steps, transient_samples, stream)
+        self._transient = int(transient_samples)
+        return self
+
+    def checkpoint(self) -> np.ndarray:
+        return checkpoint(self.h)
+
+    def restore(self, buf):
+        restore(self.h, buf)
         return self
 
     @property

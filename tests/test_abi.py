@@ -89,6 +89,17 @@ def test_fitness_and_top_k_reject_bad_arguments_before_device_use(lib):
     assert L.tvbx_top_k(one, 10, 1025, one, one, None) == -1
 
 
+def test_resume_entry_points_reject_bad_arguments_before_device_use(lib):
+    L = lib.load()
+    one = ctypes.c_void_p(16)   # never dereferenced
+    n = ctypes.c_uint64()
+    assert L.tvbx_run_continue(None, 10, 0, None) == -1
+    assert L.tvbx_checkpoint_size(None, ctypes.byref(n)) == -1
+    assert L.tvbx_checkpoint(None, one, 100) == -1
+    assert L.tvbx_restore(None, one, 100) == -1
+    assert L.tvbx_restore(one, None, 100) == -1
+
+
 def test_no_cpu_fallback_without_a_device(lib):
     import torch
     if torch.cuda.is_available():
