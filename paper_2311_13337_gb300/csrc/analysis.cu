@@ -220,7 +220,8 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
 {
     extern __shared__ float2 an_smem[];
     __shared__ double red_d[AN_THREADS / 32];
-    __shared__ int chunk_first[AN_THREADS], chunk_last[AN_THREADS];
+    __shared__ int chunk_last[AN_THREADS];
+    __shared__ int warp_last[AN_THREADS / 32];
     __shared__ int red_i[4][AN_THREADS / 32];
     const int n = plan.n;
     float2* a = an_smem;
@@ -252,27 +253,41 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
         }
         was = up;
     }
-    chunk_first[threadIdx.x] = first;
+    // the run that ends at this chunk's first transition starts at the last
+    // transition of the nearest preceding chunk that has one: an exclusive
+    // max-scan over the chunks finds it
     chunk_last[threadIdx.x] = last;
-    nu = block_sum(nu, red_i[0]);
-    su = block_sum(su, red_i[1]);
-    nd = block_sum(nd, red_i[2]);
-    sd = block_sum(sd, red_i[3]);
-    if (threadIdx.x == 0) {
-        // runs that cross chunk boundaries, in chunk order
-        int prev = -1;
-        for (int c = 0; c < (int)blockDim.x; ++c) {
-            if (chunk_first[c] < 0) continue;
-            if (prev >= 0) {
-                const int t = chunk_first[c];
-                if (a[__ldg(perm + prev)].x > theta) { ++nu; su += t - prev; } else { ++nd; sd += t - prev; }
-            }
-            prev = chunk_last[c];
-        }
-        int* u = ud_out + ((int64_t)b * N + k) * 4;
-        u[0] = nu; u[1] = su; u[2] = nd; u[3] = sd;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int pv = first >= 0 ? (int)threadIdx.x : -1;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pv, o);
+        if (lane >= o) pv = max(pv, v);
     }
-    __syncthreads();   // thread 0 read the raw row above
+    if (lane == 31) warp_last[warp] = pv;
+    __syncthreads();
+    int prev_chunk = __shfl_up_sync(0xffffffffu, pv, 1);
+    if (lane == 0) prev_chunk = -1;
+    for (int w = 0; w < warp; ++w) prev_chunk = max(prev_chunk, warp_last[w]);
+    if (first >= 0 && prev_chunk >= 0) {
+        const int prev = chunk_last[prev_chunk];
+        if (a[__ldg(perm + prev)].x > theta) { ++nu; su += first - prev; } else { ++nd; sd += first - prev; }
+    }
+    // the four counts summed over the CTA in one pass (thread 0 writes them)
+    for (int o = 16; o > 0; o >>= 1) {
+        nu += __shfl_xor_sync(0xffffffffu, nu, o);
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        nd += __shfl_xor_sync(0xffffffffu, nd, o);
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    }
+    if (lane == 0) { red_i[0][warp] = nu; red_i[1][warp] = su; red_i[2][warp] = nd; red_i[3][warp] = sd; }
+    __syncthreads();   // also: the raw row was read above
+    if (threadIdx.x == 0) {
+        int tot[4] = {0, 0, 0, 0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            for (int c = 0; c < 4; ++c) tot[c] += red_i[c][w];
+        int* u = ud_out + ((int64_t)b * N + k) * 4;
+        u[0] = tot[0]; u[1] = tot[1]; u[2] = tot[2]; u[3] = tot[3];
+    }
     // mean-removed row
     for (int t = threadIdx.x; t < n; t += blockDim.x) a[t].x -= theta;
     __syncthreads();
@@ -721,9 +736,24 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
     }
     const int band_n = band_lo < 0 ? 0 : band_hi - band_lo + 1;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // batch of sets: analytic signals of B sets at most ~1 GiB
+    // batch of sets: analytic signals of B sets in at most ~2 GiB, B a whole
+    // number of waves of the phase-lag kernel (one CTA per set) when the
+    // budget allows, so no SM runs more of its CTAs than another
     const int64_t per_set = (int64_t)N * n * 8;
-    const int64_t B = std::max<int64_t>(1, std::min<int64_t>(P, ((int64_t)1 << 30) / std::max<int64_t>(per_set, 1)));
+    int64_t B = std::max<int64_t>(1, std::min<int64_t>(P, ((int64_t)1 << 31) / std::max<int64_t>(per_set, 1)));
+    const size_t smem_pli = sizeof(float) * 2 * (size_t)((N + 3) / 4 * 4) * PLI_TS;
+    if (smem_pli > 200 * 1024) return report_error(TVBX_E_INVALID_ARG, "too many regions for the PLI tile");
+    ACK(cudaFuncSetAttribute(an_pli_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pli),
+        "analysis shared memory");
+    {
+        int dev = 0, sms = 0, per_sm = 0;
+        ACK(cudaGetDevice(&dev), "device");
+        ACK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
+        ACK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, an_pli_kernel, PLI_THREADS, smem_pli),
+            "occupancy");
+        const int64_t wave = (int64_t)sms * std::max(per_sm, 1);
+        if (B < P && B >= wave) B = B / wave * wave;
+    }
     std::vector<float2> htw(n);
     for (int e = 0; e < n; ++e) {
         const double ang = -2.0 * 3.14159265358979323846 * (double)e / (double)n;
@@ -745,10 +775,6 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
     ACK(cudaMemcpyAsync(tw, htw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s), "analysis twiddles");
     const size_t smem_series = sizeof(float2) * (size_t)n;
     ACK(cudaFuncSetAttribute(an_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_series),
-        "analysis shared memory");
-    const size_t smem_pli = sizeof(float) * 2 * (size_t)((N + 3) / 4 * 4) * PLI_TS;
-    if (smem_pli > 200 * 1024) return report_error(TVBX_E_INVALID_ARG, "too many regions for the PLI tile");
-    ACK(cudaFuncSetAttribute(an_pli_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pli),
         "analysis shared memory");
     const size_t smem_fin = sizeof(float) * (size_t)std::max(band_n, 1);
     ACK(cudaFuncSetAttribute(an_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fin),
