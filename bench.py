@@ -805,7 +805,7 @@ def run_bold_engine(args):
                 "traffic": None, "kernel": "bold_kernel + an_phase_kernel + an_phfcd_kernel",
                 "peak_source": "measured" if peaks else "fallback",
                 "algorithmic_bytes_per_step": alg, "avg_step_device_ms": dev_ms,
-                "note": "the BOLD kernel is bound by its four transcendental functions per sample, not by the "
+                "note": "the BOLD kernel is bound by its three transcendental functions per sample, not by the "
                         "4 bytes it reads"}
     base = None
     if not args.no_cpu_baseline:

@@ -53,12 +53,14 @@ __global__ void bold_kernel(const float* __restrict__ series, int64_t NP, int64_
     for (int64_t t = 0; t < T; ++t) {
         const float z = __ldg(series + t * NP + i);
         const float f = 1.0f + ft;
-        const float lv = log1pf(vt);
-        const float vpa_m1 = expm1f(lv * c.inv_alpha);                        // v^(1/alpha) - 1
+        const float vpa_m1 = expm1f(log1pf(vt) * c.inv_alpha);                // v^(1/alpha) - 1
         // f E(f) / E0 - 1 = ft - (1 + ft) r_E0 expm1(-ln(1 - E0) ft / f), since
         // (1 - E0)^(1/f) = (1 - E0) exp(-ln(1 - E0) ft / f): exactly 0 at rest
-        const float fE_m1 = fmaf(-f * c.r_E0, expm1f(-c.lnE * ft / f), ft);
-        const float vq_m1 = fmaf(expm1f((c.inv_alpha - 1.0f) * lv), 1.0f + qt, qt);   // v^(1/alpha - 1) q - 1
+        // (the argument of expm1 to 2 ulp)
+        const float fE_m1 = fmaf(-f * c.r_E0, expm1f(__fdividef(-c.lnE * ft, f)), ft);
+        // v^(1/alpha - 1) q - 1, with v^(1/alpha - 1) - 1 = (v^(1/alpha) - v) / v
+        // = (vpa_m1 - vt) / (1 + vt) (no cancellation: vpa_m1 is about vt / alpha)
+        const float vq_m1 = fmaf((vpa_m1 - vt) * __frcp_rn(1.0f + vt), 1.0f + qt, qt);
         const float ds = z - c.kappa * s - c.gamma * ft;
         const float nft = fmaf(c.dt, s, ft);
         const float nvt = fmaf(c.dt * c.inv_tau, ft - vpa_m1, vt);
