@@ -525,12 +525,17 @@ tvbx_status tvbx_top_k(const float* values, int64_t n, int32_t k, int64_t* idx_o
 #define TVBX_AN_DOWN_SAMPLES 10
 #define TVBX_AN_COUNT        11
 
-/* series: DEVICE [n_sets][n_regions][n_samples] FP32 rates in kHz (the
- * layout tvbx_series_range writes), sample interval dt_ms; out: DEVICE
+/* series: DEVICE or HOST [n_sets][n_regions][n_samples] FP32 rates in kHz
+ * (the layout tvbx_series_range writes), sample interval dt_ms; out: DEVICE
  * [n_sets][TVBX_AN_COUNT], caller-owned; n_used: host, nullable. 1 <=
- * n_regions <= 4096, n_samples >= 2. Asynchronous on cuda_stream (NULL =
- * legacy default stream); scratch (the analytic signals of up to 1 GiB of
- * sets at a time) comes from the stream-ordered allocator. */
+ * n_regions <= 4096, n_samples >= 2. Sets are analysed in batches (the
+ * analytic signals of up to 2 GiB of sets, whole waves of the phase-lag
+ * kernel). A host series is uploaded batch by batch on a second stream into
+ * two staging buffers, so the upload of one batch overlaps the analysis of
+ * the previous one when the host memory is pinned (pageable memory works but
+ * does not overlap); it must stay valid until cuda_stream has completed.
+ * Asynchronous on cuda_stream (NULL = legacy default stream); scratch comes
+ * from the stream-ordered allocator. */
 tvbx_status tvbx_series_analysis(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
                                  double dt_ms, float* out, int32_t* n_used, void* cuda_stream);
 

@@ -708,6 +708,31 @@ struct AnScratch {
     }
 };
 
+// Copy stream and events of a host-input analysis (released when the call
+// returns; work still queued completes first).
+struct HostPipe {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // start, ready[2], free[2]
+    ~HostPipe()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
+// Whether p is ordinary host memory (pageable or pinned) rather than memory
+// a kernel can read.
+bool is_host_pointer(const void* p)
+{
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    return pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered;
+}
+
 }  // namespace
 }  // namespace tvbx
 
@@ -781,12 +806,40 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
         "analysis shared memory");
     const float psd_scale = (float)(2.0 * dt_s / (double)n * 1e6);   // kHz^2 -> Hz^2, one-sided
     const double df = 1.0 / ((double)n * dt_s);
-    for (int64_t p0 = 0; p0 < P; p0 += B) {
+    // host input: batch b + 1 is copied on a second stream into one of two
+    // staging buffers while batch b is analysed on s
+    const bool host_in = is_host_pointer(series);
+    HostPipe hp;
+    float* stage[2] = {nullptr, nullptr};
+    if (host_in) {
+        ACK(scr.get(&stage[0], (size_t)B * N * T), "analysis staging");
+        ACK(scr.get(&stage[1], (size_t)B * N * T), "analysis staging");
+        ACK(cudaStreamCreateWithFlags(&hp.cs, cudaStreamNonBlocking), "analysis copy stream");
+        for (cudaEvent_t& e : hp.ev) ACK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "analysis events");
+        ACK(cudaEventRecord(hp.ev[0], s), "analysis events");   // the staging buffers exist
+        ACK(cudaStreamWaitEvent(hp.cs, hp.ev[0], 0), "analysis events");
+    }
+    int64_t batch = 0;
+    for (int64_t p0 = 0; p0 < P; p0 += B, ++batch) {
         const int64_t nb = std::min<int64_t>(B, P - p0);
+        const float* in = series;
+        int64_t in_p0 = p0;
+        const int slot = (int)(batch & 1);
+        if (host_in) {
+            if (batch >= 2) ACK(cudaStreamWaitEvent(hp.cs, hp.ev[3 + slot], 0), "analysis events");
+            ACK(cudaMemcpyAsync(stage[slot], series + p0 * N * T, sizeof(float) * (size_t)(nb * N * T),
+                                cudaMemcpyHostToDevice, hp.cs),
+                "analysis series upload");
+            ACK(cudaEventRecord(hp.ev[1 + slot], hp.cs), "analysis events");
+            ACK(cudaStreamWaitEvent(s, hp.ev[1 + slot], 0), "analysis events");
+            in = stage[slot];
+            in_p0 = 0;
+        }
         note_launch(3);
-        an_series_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_series, s>>>(series, N, T, plan, tw, perm, band_lo,
-                                                                           band_n, psd_scale, p0, psd, ud, z);
+        an_series_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_series, s>>>(in, N, T, plan, tw, perm, band_lo,
+                                                                           band_n, psd_scale, in_p0, psd, ud, z);
         ACK(cudaGetLastError(), "analysis series");
+        if (host_in) ACK(cudaEventRecord(hp.ev[3 + slot], s), "analysis events");   // the slot was read
         an_pli_kernel<<<(unsigned)nb, PLI_THREADS, smem_pli, s>>>(z, N, n, pli);
         ACK(cudaGetLastError(), "analysis PLI");
         an_finalize_kernel<<<(unsigned)nb, AN_THREADS, smem_fin, s>>>(psd, ud, pli, N, band_lo, band_n, df, dt_ms,

@@ -600,13 +600,14 @@ AN_FIELDS = ("mean_pli", "psd_fmax", "psd_ampmax", "psd_a", "psd_b", "up_ms", "d
 
 
 def series_analysis(series, dt_ms, out=None, stream=None):
-    """Table 2 metrics (tvbx_series_analysis) of CUDA series [P][N][T] (kHz):
-    (CUDA tensor [P][len(AN_FIELDS)], samples used)."""
+    """Table 2 metrics (tvbx_series_analysis) of series [P][N][T] (kHz), a
+    CUDA tensor or a host tensor (pinned host memory overlaps its upload
+    with the analysis): (CUDA tensor [P][len(AN_FIELDS)], samples used)."""
     import torch
     x = series.contiguous()
     P, N, T = x.shape
     if out is None:
-        out = torch.empty((P, len(AN_FIELDS)), dtype=torch.float32, device=x.device)
+        out = torch.empty((P, len(AN_FIELDS)), dtype=torch.float32, device=x.device if x.is_cuda else "cuda")
     used = ctypes.c_int32(0)
     _check(load().tvbx_series_analysis(ctypes.c_void_p(x.data_ptr()), N, P, T, float(dt_ms),
                                        ctypes.c_void_p(out.data_ptr()), ctypes.byref(used), _stream_ptr(stream)),

@@ -108,3 +108,22 @@ def test_metrics_of_a_sweep(tvbx, oracle):
     sw.close()
     fin = np.all(np.isfinite(X), axis=(1, 2))
     _check(out.cpu().numpy()[fin], X[fin], 1.0, used)
+
+
+def test_host_series_equal_device_series_over_several_batches(tvbx):
+    """A pinned and a pageable host series give the device series' metrics bit
+    for bit; 1,100 sets of 64 x 8,192 samples take three batches, so the two
+    staging buffers are each reused."""
+    import torch
+    P, N, T = 1100, 64, 8192
+    g = torch.Generator().manual_seed(4)
+    base = 5e-3 + 1e-3 * torch.rand((P, N, 1), generator=g)
+    X = (base + 1e-3 * torch.randn((P, N, T), generator=g)).to(torch.float32)
+    X[:, :, ::97] += 2e-3                                  # some structure for the PSD and the runs
+    ref, used = tvbx.series_analysis(X.cuda(), 1.0)
+    ref = ref.cpu().numpy()
+    assert used == 8192
+    for host in (X.pin_memory(), X):
+        got, _ = tvbx.series_analysis(host, 1.0)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(got.cpu().numpy(), ref)
