@@ -252,7 +252,9 @@ tvbx_status tvbx_run_continue(tvbx_sweep* h, int64_t n_steps, int32_t transient_
  *     (caller-owned, at least that many bytes).
  *   tvbx_restore: loads a checkpoint into h, a sweep created with the same
  *     connectome, points and constants (any handle, e.g. in a new process);
- *     synchronous. tvbx_run_continue on h then resumes bit for bit.
+ *     synchronous: it first waits for all work on the device, then fills h
+ *     through the default stream. tvbx_run_continue on h then resumes bit
+ *     for bit.
  * Errors: TVBX_E_BAD_STATE (checkpoint before any run), TVBX_E_INVALID_ARG
  * (NULL, short buffer, not a checkpoint, another sweep's checkpoint),
  * TVBX_E_OOM, TVBX_E_CUDA. */

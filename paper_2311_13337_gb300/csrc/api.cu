@@ -936,9 +936,12 @@ tvbx_status tvbx_restore(tvbx_sweep* h, const void* host_buf, uint64_t bytes)
     c.p_offset = hd.p_offset;
     c.chunk_steps = (int32_t)hd.chunk_steps;
     c.kernel = (int32_t)hd.kernel;
-    // lay out the buffers as the checkpointed run did, then fill them
+    // lay out the buffers as the checkpointed run did, then fill them; the
+    // handle's earlier stream may no longer exist, so the device is drained
+    // and the default stream used
+    CK(cudaDeviceSynchronize(), "restore");
     RunPlan plan;
-    tvbx_status st = prepare_run(h, c, h->stream, 0, false, plan);
+    tvbx_status st = prepare_run(h, c, nullptr, 0, false, plan);
     if (st != TVBX_OK) return st;
     if (h->ring_floats != hd.ring_floats) return fail(TVBX_E_INVALID_ARG, "checkpoint ring layout differs");
     const int64_t N = h->N, P = h->P;
@@ -947,7 +950,7 @@ tvbx_status tvbx_restore(tvbx_sweep* h, const void* host_buf, uint64_t bytes)
     const size_t b_status = sizeof(uint32_t) * (size_t)P;
     const size_t b_ring = sizeof(float) * (size_t)hd.ring_floats;
     const size_t b_ou = sizeof(float) * (size_t)N;
-    CK(cudaStreamSynchronize(h->stream), "restore");
+    CK(cudaStreamSynchronize(nullptr), "restore");
     CK(cudaMemcpy(h->d_state.ptr, in, b_state, cudaMemcpyHostToDevice), "restore state");
     in += b_state;
     CK(cudaMemcpy(h->d_status.ptr, in, b_status, cudaMemcpyHostToDevice), "restore status");
