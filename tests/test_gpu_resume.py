@@ -95,6 +95,8 @@ def test_checkpoint_restores_into_a_new_handle(tvbx, oracle, conn):
     with pytest.raises(tvbx.TvbxError) as e:
         b.series()                       # nothing integrated on b yet
     assert e.value.code == -6
+    b.run_continue(0)                    # an empty stretch changes nothing
+    assert b.n_samples == 0
     b.run_continue(3000)
     assert np.array_equal(b.series(), a.series(), equal_nan=True)
     assert np.array_equal(b.state(), a.state(), equal_nan=True)
