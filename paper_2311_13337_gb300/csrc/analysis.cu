@@ -14,7 +14,9 @@
 //    UP / DOWN runs against that mean (rounded to FP32); the forward DFT of
 //    the mean-removed row (in place in one shared-memory buffer: the row is
 //    stored digit-reversed and transformed by decimation-in-time stages of
-//    radix 2, 3, 4, 5; twiddles from a host FP64 table); the periodogram on
+//    radix 2, 3, 4, 5; twiddles from a host FP64 table; for even T' as a
+//    complex transform of length T'/2 of the sample pairs, untangled into the
+//    spectrum of the real row); the periodogram on
 //    the PSD band; the analytic signal (one-sided spectrum doubled) by the
 //    inverse DFT (decimation in frequency, in place, read back through the
 //    digit reversal), written to scratch;
@@ -116,7 +118,8 @@ __device__ __forceinline__ void butterfly(const float2 (&u)[R], float2 (&v)[R], 
 // digit-reversed order): butterfly j of a block of span L = L1 R combines
 // a[blk L + j + q L1], twiddled by w_L^{j q} before the R-point DFT.
 template <int R>
-__device__ void dit_stage(float2* a, int n, int L1, uint32_t magic, const float2* __restrict__ tw, bool inv)
+__device__ void dit_stage(float2* a, int n, int L1, uint32_t magic, const float2* __restrict__ tw, bool inv,
+                          int tws)
 {
     const int L = L1 * R, nl = n / L, m = n / R;
     const float sg = inv ? 1.0f : -1.0f;
@@ -128,7 +131,7 @@ __device__ void dit_stage(float2* a, int n, int L1, uint32_t magic, const float2
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const float2 y = p[q * L1];
-            u[q] = (q == 0 || j == 0) ? y : cmul(y, twiddle(tw, nl * j * q, inv));
+            u[q] = (q == 0 || j == 0) ? y : cmul(y, twiddle(tw, tws * nl * j * q, inv));
         }
         butterfly<R>(u, v, sg);
 #pragma unroll
@@ -158,18 +161,19 @@ __device__ void dif_stage(float2* a, int n, int L1, uint32_t magic, const float2
 }
 
 // Forward transform in place: a holds the input in digit-reversed order
-// (a[perm[t]] = x[t]) and ends in natural order.
-__device__ void fft_dit(float2* a, const FftPlan& plan, const float2* __restrict__ tw, bool inv)
+// (a[perm[t]] = x[t]) and ends in natural order. tw holds the twiddles of a
+// transform tws times longer than the plan's (every tws-th one is used).
+__device__ void fft_dit(float2* a, const FftPlan& plan, const float2* __restrict__ tw, bool inv, int tws = 1)
 {
     int L1 = 1;
     for (int s = 0; s < plan.n_stages; ++s) {
         const int r = plan.radix[s];
         const uint32_t mg = plan.magic[s];
         switch (r) {
-        case 2: dit_stage<2>(a, plan.n, L1, mg, tw, inv); break;
-        case 3: dit_stage<3>(a, plan.n, L1, mg, tw, inv); break;
-        case 4: dit_stage<4>(a, plan.n, L1, mg, tw, inv); break;
-        default: dit_stage<5>(a, plan.n, L1, mg, tw, inv); break;
+        case 2: dit_stage<2>(a, plan.n, L1, mg, tw, inv, tws); break;
+        case 3: dit_stage<3>(a, plan.n, L1, mg, tw, inv, tws); break;
+        case 4: dit_stage<4>(a, plan.n, L1, mg, tw, inv, tws); break;
+        default: dit_stage<5>(a, plan.n, L1, mg, tw, inv, tws); break;
         }
         __syncthreads();
         L1 *= r;
@@ -213,27 +217,53 @@ __device__ __forceinline__ T block_sum(T v, T* red)
 // in digit-reversed order (a[perm[t]] = x_t), transformed in place forward
 // (DIT, natural-order spectrum) and back (DIF, digit-reversed analytic
 // signal).
+//
+// HALF (n even): the real row goes through a complex transform of length
+// M = n / 2, z_m = x_2m + i x_2m+1 stored digit-reversed for the half plan
+// (a[perm_h[m]] = z_m); with E, O the transforms of the even and odd samples,
+// E_k = (Z_k + conj Z_{M-k}) / 2, O_k = -i (Z_k - conj Z_{M-k}) / 2, and
+// X_k = E_k + w^k O_k, X_{M-k} = conj(E_k - w^k O_k), X_M = E_0 - O_0
+// (w = exp(-2 pi i / n)); the spectrum is untangled in place, pair by pair.
+template <bool HALF>
 __global__ void __launch_bounds__(AN_THREADS)
-an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan plan, const float2* __restrict__ tw,
-                 const int* __restrict__ perm, int band_lo, int band_n, float psd_scale, int64_t p0,
-                 float* __restrict__ psd_out, int* __restrict__ ud_out, float2* __restrict__ z_out)
+an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan plan, FftPlan plan_h,
+                 const float2* __restrict__ tw, const int* __restrict__ perm, const int* __restrict__ perm_h,
+                 int band_lo, int band_n, float psd_scale, int64_t p0, float* __restrict__ psd_out,
+                 int* __restrict__ ud_out, float2* __restrict__ z_out)
 {
     extern __shared__ float2 an_smem[];
     __shared__ double red_d[AN_THREADS / 32];
     __shared__ int chunk_last[AN_THREADS];
     __shared__ int warp_last[AN_THREADS / 32];
     __shared__ int red_i[4][AN_THREADS / 32];
-    const int n = plan.n;
+    const int n = plan.n, M = n / 2;
     float2* a = an_smem;
     const int b = blockIdx.x / N, k = blockIdx.x - b * N;
     const float* row = series + ((p0 + b) * (int64_t)N + k) * T + (T - n);
     double s = 0.0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const float x = row[t];
-        a[__ldg(perm + t)] = make_float2(x, 0.0f);
-        s += (double)x;
+    if constexpr (HALF) {
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            const float x0 = row[2 * m], x1 = row[2 * m + 1];
+            a[__ldg(perm_h + m)] = make_float2(x0, x1);
+            s += (double)x0 + (double)x1;
+        }
+    } else {
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const float x = row[t];
+            a[__ldg(perm + t)] = make_float2(x, 0.0f);
+            s += (double)x;
+        }
     }
     const float theta = (float)(block_sum(s, red_d) / (double)n);
+    // sample t of the raw row
+    auto raw = [&](int t) -> float {
+        if constexpr (HALF) {
+            const float2 v = a[__ldg(perm_h + (t >> 1))];
+            return (t & 1) ? v.y : v.x;
+        } else {
+            return a[__ldg(perm + t)].x;
+        }
+    };
 
     // UP / DOWN: runs between consecutive transitions (a transition at t >= 1
     // where the state differs from t - 1); thread c scans [c0, c1)
@@ -241,9 +271,9 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
     const int c0 = threadIdx.x * per, c1 = min(n, c0 + per);
     int first = -1, last = -1, nu = 0, su = 0, nd = 0, sd = 0;
     const int tb = max(c0, 1);
-    bool was = tb < c1 ? a[__ldg(perm + tb - 1)].x > theta : false;   // the state at tb - 1
+    bool was = tb < c1 ? raw(tb - 1) > theta : false;   // the state at tb - 1
     for (int t = tb; t < c1; ++t) {
-        const bool up = a[__ldg(perm + t)].x > theta;
+        const bool up = raw(t) > theta;
         if (up != was) {
             if (last >= 0) {   // complete run [last, t) in state `was`
                 if (was) { ++nu; su += t - last; } else { ++nd; sd += t - last; }
@@ -270,7 +300,7 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
     for (int w = 0; w < warp; ++w) prev_chunk = max(prev_chunk, warp_last[w]);
     if (first >= 0 && prev_chunk >= 0) {
         const int prev = chunk_last[prev_chunk];
-        if (a[__ldg(perm + prev)].x > theta) { ++nu; su += first - prev; } else { ++nd; sd += first - prev; }
+        if (raw(prev) > theta) { ++nu; su += first - prev; } else { ++nd; sd += first - prev; }
     }
     // the four counts summed over the CTA in one pass (thread 0 writes them)
     for (int o = 16; o > 0; o >>= 1) {
@@ -288,25 +318,54 @@ an_series_kernel(const float* __restrict__ series, int N, int64_t T, FftPlan pla
         int* u = ud_out + ((int64_t)b * N + k) * 4;
         u[0] = tot[0]; u[1] = tot[1]; u[2] = tot[2]; u[3] = tot[3];
     }
-    // mean-removed row
-    for (int t = threadIdx.x; t < n; t += blockDim.x) a[t].x -= theta;
-    __syncthreads();
-    fft_dit(a, plan, tw, false);
     float* pr = psd_out + ((int64_t)b * N + k) * band_n;
-    for (int i = threadIdx.x; i < band_n; i += blockDim.x) {
-        const float2 v = a[band_lo + i];
-        pr[i] = psd_scale * fmaf(v.x, v.x, v.y * v.y);
+    if constexpr (HALF) {
+        for (int i = threadIdx.x; i < M; i += blockDim.x) a[i] = make_float2(a[i].x - theta, a[i].y - theta);
+        __syncthreads();
+        fft_dit(a, plan_h, tw, false, 2);
+        // untangle pairs (i, M - i); periodogram of the band bins; analytic
+        // weights h_0 = h_M = 1, h_i = 2 for 0 < i < M, 0 above M
+        for (int i = threadIdx.x; i <= M / 2; i += blockDim.x) {
+            if (i == 0) {
+                const float2 z0 = a[0];
+                a[0] = make_float2(z0.x + z0.y, 0.0f);
+                a[M] = make_float2(z0.x - z0.y, 0.0f);
+                continue;
+            }
+            const float2 zk = a[i], zm = a[M - i];
+            const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));   // (Z_i + conj Z_{M-i}) / 2
+            const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));  // -i (Z_i - conj Z_{M-i}) / 2
+            const float2 t = cmul(__ldg(tw + i), o);
+            const float2 xk = cadd(e, t);
+            const float2 xm = make_float2(e.x - t.x, t.y - e.y);                         // conj(e - t)
+            if (i >= band_lo && i < band_lo + band_n) pr[i - band_lo] = psd_scale * fmaf(xk.x, xk.x, xk.y * xk.y);
+            if (M - i != i && M - i >= band_lo && M - i < band_lo + band_n)
+                pr[M - i - band_lo] = psd_scale * fmaf(xm.x, xm.x, xm.y * xm.y);
+            a[i] = make_float2(2.0f * xk.x, 2.0f * xk.y);
+            a[M - i] = make_float2(2.0f * xm.x, 2.0f * xm.y);
+        }
+        for (int i = M + 1 + threadIdx.x; i < n; i += blockDim.x) a[i] = make_float2(0.0f, 0.0f);
+        __syncthreads();
+    } else {
+        // mean-removed row
+        for (int t = threadIdx.x; t < n; t += blockDim.x) a[t].x -= theta;
+        __syncthreads();
+        fft_dit(a, plan, tw, false);
+        for (int i = threadIdx.x; i < band_n; i += blockDim.x) {
+            const float2 v = a[band_lo + i];
+            pr[i] = psd_scale * fmaf(v.x, v.x, v.y * v.y);
+        }
+        __syncthreads();   // the band is read before the spectrum is overwritten
+        // analytic signal: spectrum times h (h_0 = 1, h_i = 2 below n/2, h_{n/2} = 1, 0 above)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            float h = 0.0f;
+            if (i == 0 || 2 * i == n) h = 1.0f;
+            else if (2 * i < n) h = 2.0f;
+            const float2 v = a[i];
+            a[i] = make_float2(h * v.x, h * v.y);
+        }
+        __syncthreads();
     }
-    __syncthreads();   // the band is read before the spectrum is overwritten
-    // analytic signal: spectrum times h (h_0 = 1, h_i = 2 below n/2, h_{n/2} = 1, 0 above)
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        float h = 0.0f;
-        if (i == 0 || 2 * i == n) h = 1.0f;
-        else if (2 * i < n) h = 2.0f;
-        const float2 v = a[i];
-        a[i] = make_float2(h * v.x, h * v.y);
-    }
-    __syncthreads();
     fft_dif(a, plan, tw, true);
     const float inv_n = 1.0f / (float)n;
     float2* zr = z_out + ((int64_t)b * N + k) * n;
@@ -793,13 +852,24 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
     ACK(scr.get(&perm, n), "analysis digit reversal");
     const std::vector<int> hperm = digit_reversal(plan);
     ACK(cudaMemcpyAsync(perm, hperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s), "analysis digit reversal");
+    // even lengths: the forward transform as a complex one of half the length
+    FftPlan plan_h = plan;
+    const bool half = n % 2 == 0 && n >= 4 && make_plan(n / 2, plan_h);
+    int* perm_h = perm;
+    if (half) {
+        ACK(scr.get(&perm_h, n / 2), "analysis digit reversal");
+        const std::vector<int> hperm_h = digit_reversal(plan_h);
+        ACK(cudaMemcpyAsync(perm_h, hperm_h.data(), sizeof(int) * (n / 2), cudaMemcpyHostToDevice, s),
+            "analysis digit reversal");
+    }
     ACK(scr.get(&z, (size_t)B * N * n), "analysis signals");
     ACK(scr.get(&psd, (size_t)B * N * std::max(band_n, 1)), "analysis PSD");
     ACK(scr.get(&pli, (size_t)B), "analysis PLI");
     ACK(scr.get(&ud, (size_t)B * N * 4), "analysis UP/DOWN");
     ACK(cudaMemcpyAsync(tw, htw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s), "analysis twiddles");
     const size_t smem_series = sizeof(float2) * (size_t)n;
-    ACK(cudaFuncSetAttribute(an_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_series),
+    auto series_kernel = half ? an_series_kernel<true> : an_series_kernel<false>;
+    ACK(cudaFuncSetAttribute(series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_series),
         "analysis shared memory");
     const size_t smem_fin = sizeof(float) * (size_t)std::max(band_n, 1);
     ACK(cudaFuncSetAttribute(an_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fin),
@@ -836,8 +906,9 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
             in_p0 = 0;
         }
         note_launch(3);
-        an_series_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_series, s>>>(in, N, T, plan, tw, perm, band_lo,
-                                                                           band_n, psd_scale, in_p0, psd, ud, z);
+        series_kernel<<<(unsigned)(nb * N), AN_THREADS, smem_series, s>>>(in, N, T, plan, plan_h, tw, perm, perm_h,
+                                                                        band_lo, band_n, psd_scale, in_p0, psd,
+                                                                        ud, z);
         ACK(cudaGetLastError(), "analysis series");
         if (host_in) ACK(cudaEventRecord(hp.ev[3 + slot], s), "analysis events");   // the slot was read
         an_pli_kernel<<<(unsigned)nb, PLI_THREADS, smem_pli, s>>>(z, N, n, pli);
