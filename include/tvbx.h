@@ -530,7 +530,8 @@ tvbx_status tvbx_top_k(const float* values, int64_t n, int32_t k, int64_t* idx_o
 /* series: DEVICE or HOST [n_sets][n_regions][n_samples] FP32 rates in kHz
  * (the layout tvbx_series_range writes), sample interval dt_ms; out: DEVICE
  * [n_sets][TVBX_AN_COUNT], caller-owned; n_used: host, nullable. 1 <=
- * n_regions <= 4096, n_samples >= 2. Sets are analysed in batches (the
+ * n_regions <= 752 (the phase-lag tiles of all regions must fit in shared
+ * memory), n_samples >= 2. Sets are analysed in batches (the
  * analytic signals of up to 2 GiB of sets, whole waves of the phase-lag
  * kernel). A host series is uploaded batch by batch on a second stream into
  * two staging buffers, so the upload of one batch overlaps the analysis of
@@ -573,7 +574,8 @@ tvbx_status tvbx_series_analysis(const float* series, int32_t n_regions, int64_t
  * out[p][e] = cosine similarity of the upper triangles (k < j) of dFC(t1)
  * and dFC(t2) for every t1 < t2, e = t1 T' - t1 (t1 + 1) / 2 + t2 - t1 - 1.
  * bold: DEVICE [n_tr][n_regions][n_sets]; out: DEVICE [n_sets][T'(T'-1)/2].
- * 2 <= n_regions <= 4096 (the phase tiles must fit in shared memory).
+ * 2 <= n_regions <= 200 (two 64-sample phase tiles of all regions must fit
+ * in shared memory).
  * Both calls are asynchronous on cuda_stream (NULL = legacy default stream). */
 typedef struct {
     double kappa, gamma, tau, alpha, E0, V0, theta0, r0, TE, eps;

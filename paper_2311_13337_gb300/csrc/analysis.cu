@@ -45,8 +45,10 @@ namespace {
 constexpr int AN_MAX_T = 8192;
 constexpr int AN_MAX_STAGES = 16;
 constexpr int AN_THREADS = 256;
-constexpr int PLI_TT = 32;          // samples per time tile of the PLI kernel
-constexpr int PLI_TS = PLI_TT + 2; // padded row stride of a tile plane (floats)
+// samples per time tile of the PLI kernel: TT (64, or 32 when the tiles of
+// many regions would not fit); padded row stride of a tile plane TT + 2 floats
+constexpr int PLI_TT_MAX = 64;
+constexpr int PLI_TT_MIN = 32;
 constexpr int PLI_THREADS = 256;
 
 struct FftPlan {
@@ -398,9 +400,11 @@ __device__ __forceinline__ int sign_diff2(uint64_t p, uint64_t q)
 // fastest, so one 8-byte load gives two consecutive samples and the packed
 // two-lane FP32 products handle two samples of a pair per instruction (each
 // lane rounds like the scalar product).
+template <int PLI_TT>
 __global__ void __launch_bounds__(PLI_THREADS)
 an_pli_kernel(const float2* __restrict__ z_all, int N, int n, float* __restrict__ pli_out)
 {
+    constexpr int PLI_TS = PLI_TT + 2;
     // planes [2][(r mod 4) * NB + r / 4][PLI_TS]: the rows a half-warp reads
     // together (4 apart in r) are adjacent, and the stride (2 mod 32 words)
     // puts their 8-byte pieces in distinct banks
@@ -803,7 +807,8 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
     const int N = n_regions;
     const int64_t P = n_sets, T = n_samples;
     if (!series || !out) return report_error(TVBX_E_INVALID_ARG, "NULL series or out");
-    if (N < 1 || N > 4096 || P < 1 || T < 2) return report_error(TVBX_E_INVALID_ARG, "need 1 <= n_regions <= 4096, n_sets >= 1, n_samples >= 2");
+    if (N < 1 || N > 752 || P < 1 || T < 2)
+        return report_error(TVBX_E_INVALID_ARG, "need 1 <= n_regions <= 752, n_sets >= 1, n_samples >= 2");
     if (!(dt_ms > 0.0) || !std::isfinite(dt_ms)) return report_error(TVBX_E_INVALID_ARG, "dt_ms must be > 0");
     const int n = smooth_length(T);
     FftPlan plan;
@@ -825,15 +830,18 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
     // budget allows, so no SM runs more of its CTAs than another
     const int64_t per_set = (int64_t)N * n * 8;
     int64_t B = std::max<int64_t>(1, std::min<int64_t>(P, ((int64_t)1 << 31) / std::max<int64_t>(per_set, 1)));
-    const size_t smem_pli = sizeof(float) * 2 * (size_t)((N + 3) / 4 * 4) * PLI_TS;
+    const size_t pli_row = sizeof(float) * 2 * (size_t)((N + 3) / 4 * 4);
+    const bool wide_tiles = pli_row * (PLI_TT_MAX + 2) <= 64 * 1024;
+    const size_t smem_pli = pli_row * (size_t)((wide_tiles ? PLI_TT_MAX : PLI_TT_MIN) + 2);
     if (smem_pli > 200 * 1024) return report_error(TVBX_E_INVALID_ARG, "too many regions for the PLI tile");
-    ACK(cudaFuncSetAttribute(an_pli_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pli),
+    auto pli_kernel = wide_tiles ? an_pli_kernel<PLI_TT_MAX> : an_pli_kernel<PLI_TT_MIN>;
+    ACK(cudaFuncSetAttribute(pli_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pli),
         "analysis shared memory");
     {
         int dev = 0, sms = 0, per_sm = 0;
         ACK(cudaGetDevice(&dev), "device");
         ACK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
-        ACK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, an_pli_kernel, PLI_THREADS, smem_pli),
+        ACK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pli_kernel, PLI_THREADS, smem_pli),
             "occupancy");
         const int64_t wave = (int64_t)sms * std::max(per_sm, 1);
         if (B < P && B >= wave) B = B / wave * wave;
@@ -911,7 +919,7 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
                                                                         ud, z);
         ACK(cudaGetLastError(), "analysis series");
         if (host_in) ACK(cudaEventRecord(hp.ev[3 + slot], s), "analysis events");   // the slot was read
-        an_pli_kernel<<<(unsigned)nb, PLI_THREADS, smem_pli, s>>>(z, N, n, pli);
+        pli_kernel<<<(unsigned)nb, PLI_THREADS, smem_pli, s>>>(z, N, n, pli);
         ACK(cudaGetLastError(), "analysis PLI");
         an_finalize_kernel<<<(unsigned)nb, AN_THREADS, smem_fin, s>>>(psd, ud, pli, N, band_lo, band_n, df, dt_ms,
                                                                        p0, out);
@@ -928,8 +936,8 @@ extern "C" tvbx_status tvbx_phfcd(const float* bold, int32_t n_regions, int64_t 
     const int N = n_regions;
     const int64_t P = n_sets;
     if (!bold || !out) return report_error(TVBX_E_INVALID_ARG, "NULL bold or out");
-    if (N < 2 || N > 4096 || P < 1 || n_tr < 2 || discard < 0)
-        return report_error(TVBX_E_INVALID_ARG, "need 2 <= n_regions <= 4096, n_sets >= 1, n_tr >= 2, discard >= 0");
+    if (N < 2 || N > 200 || P < 1 || n_tr < 2 || discard < 0)
+        return report_error(TVBX_E_INVALID_ARG, "need 2 <= n_regions <= 200, n_sets >= 1, n_tr >= 2, discard >= 0");
     if (!(tr_s > 0.0) || !std::isfinite(tr_s) || !(f_lo_hz <= f_hi_hz))
         return report_error(TVBX_E_INVALID_ARG, "need tr_s > 0 and f_lo_hz <= f_hi_hz");
     const int n = smooth_length(n_tr);

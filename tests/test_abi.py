@@ -89,6 +89,15 @@ def test_fitness_and_top_k_reject_bad_arguments_before_device_use(lib):
     assert L.tvbx_top_k(one, 10, 1025, one, one, None) == -1
 
 
+def test_analysis_region_limits_are_checked_before_device_use(lib):
+    L = lib.load()
+    one = ctypes.c_void_p(16)   # never dereferenced
+    assert L.tvbx_series_analysis(one, 753, 1, 100, 1.0, one, None, None) == -1 and "752" in lib.last_error()
+    assert L.tvbx_series_analysis(one, 0, 1, 100, 1.0, one, None, None) == -1
+    assert L.tvbx_phfcd(one, 201, 1, 100, 2.0, 0.008, 0.08, 0, one, None, None) == -1 and "200" in lib.last_error()
+    assert L.tvbx_phfcd(one, 1, 1, 100, 2.0, 0.008, 0.08, 0, one, None, None) == -1
+
+
 def test_resume_entry_points_reject_bad_arguments_before_device_use(lib):
     L = lib.load()
     one = ctypes.c_void_p(16)   # never dereferenced
