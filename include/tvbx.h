@@ -184,6 +184,25 @@ const char* tvbx_version(void);
  * the next failing call on the same thread. */
 const char* tvbx_last_error(void);
 
+/* Device memory of the handles (sweeps, batches, surrogates; no counterpart
+ * in the paper). By default it comes from cudaMalloc / cudaFree.
+ * tvbx_set_allocator installs a caller's pair instead, for example a
+ * framework's caching allocator so that the engine and the framework share
+ * one pool. The pair is process-wide and serves allocations made after the
+ * call; each buffer is released through the pair that allocated it, after a
+ * device synchronisation (a caching allocator may hand a freed block out at
+ * once while queued work still uses it). alloc(bytes, ctx) returns a device
+ * pointer aligned to at least 256 bytes, or NULL on failure (reported as
+ * TVBX_E_OOM); free(ptr, ctx) releases it. Both NULL restore the default.
+ * The scratch of the stateless calls (tvbx_fc_series, tvbx_series_analysis,
+ * tvbx_phfcd, tvbx_fc_fitness, tvbx_top_k) comes from CUDA's stream-ordered
+ * allocator, tvbx_cell_rates uses cudaMalloc for its call, and
+ * tvbx_fc_noalloc allocates nothing. Errors: TVBX_E_INVALID_ARG when only one
+ * of the pair is given. */
+typedef void* (*tvbx_alloc_fn)(uint64_t bytes, void* ctx);
+typedef void (*tvbx_free_fn)(void* ptr, void* ctx);
+tvbx_status tvbx_set_allocator(tvbx_alloc_fn alloc, tvbx_free_fn free_fn, void* ctx);
+
 /* Fill *out with the engine's default model constants and axis defaults.
  * Needs no GPU. */
 tvbx_status tvbx_model_defaults(tvbx_model* out);

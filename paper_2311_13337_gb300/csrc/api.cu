@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "alloc.h"
 #include "internal.h"
 #include "tvbx.h"
 
@@ -71,24 +72,28 @@ tvbx_status cuda_fail(cudaError_t e, const char* what)
     } while (0)
 
 // A device allocation owned by a sweep handle; grows on demand.
+// A handle's device buffer, from the allocator in force when it grew
+// (tvbx_set_allocator) and released through the same one.
 struct DevBuf {
     void* ptr = nullptr;
     size_t bytes = 0;
+    DevAllocator how;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
     cudaError_t ensure(size_t n)
     {
         if (n <= bytes && ptr) return cudaSuccess;
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        bytes = 0;
+        release();
         if (n == 0) return cudaSuccess;
-        cudaError_t e = cudaMalloc(&ptr, n);
+        cudaError_t e = dev_alloc(&ptr, n, &how);
         if (e == cudaSuccess) bytes = n;
-        else (void)cudaGetLastError();
         return e;
     }
     void release()
     {
-        if (ptr) cudaFree(ptr);
+        dev_free(ptr, how);
         ptr = nullptr;
         bytes = 0;
     }

@@ -26,6 +26,7 @@
 #include <numeric>
 #include <vector>
 
+#include "alloc.h"
 #include "internal.h"
 #include "gemm_simt.cuh"
 #include "model_device.cuh"
@@ -251,22 +252,31 @@ __global__ void mlp_score_kernel(const float* __restrict__ mean, const float* __
     score[c] = r == r ? r : -INFINITY;
 }
 
+// Device array from the allocator in force when it grew (tvbx_set_allocator),
+// released through the same one.
 template <class T> struct Buf {
     T* p = nullptr;
     size_t n = 0;
+    DevAllocator how;
+    Buf() = default;
+    Buf(const Buf&) = delete;
+    Buf& operator=(const Buf&) = delete;
+    ~Buf() { release(); }
     cudaError_t ensure(size_t count)
     {
         if (count <= n && p) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = 0;
-        cudaError_t e = cudaMalloc(&p, sizeof(T) * (count ? count : 1));
-        if (e == cudaSuccess) n = count;
+        release();
+        void* q = nullptr;
+        cudaError_t e = dev_alloc(&q, sizeof(T) * (count ? count : 1), &how);
+        if (e == cudaSuccess) {
+            p = static_cast<T*>(q);
+            n = count;
+        }
         return e;
     }
     void release()
     {
-        if (p) cudaFree(p);
+        dev_free(p, how);
         p = nullptr;
         n = 0;
     }

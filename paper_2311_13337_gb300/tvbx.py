@@ -93,7 +93,12 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy", "tvbx_fc_fitness", "tvbx_top_k",
            "tvbx_series_analysis", "tvbx_bold_defaults", "tvbx_bold", "tvbx_phfcd",
            "tvbx_cell_defaults", "tvbx_cell_rates", "tvbx_tf_fit", "tvbx_run_continue", "tvbx_checkpoint_size",
-           "tvbx_checkpoint", "tvbx_restore")
+           "tvbx_checkpoint", "tvbx_restore", "tvbx_set_allocator")
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = None   # the installed callbacks, kept alive while installed
 
 
 def library_path() -> str:
@@ -121,6 +126,7 @@ def load(build_if_missing: bool = False):
     L.tvbx_sweep_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.tvbx_run.argtypes = [vp, ctypes.POINTER(RunCfg), vp]
     L.tvbx_run_continue.argtypes = [vp, i64, i32, vp]
+    L.tvbx_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
     L.tvbx_checkpoint_size.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     L.tvbx_checkpoint.argtypes = [vp, vp, ctypes.c_uint64]
     L.tvbx_restore.argtypes = [vp, vp, ctypes.c_uint64]
@@ -293,6 +299,40 @@ def run(h, dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(load().tvbx_run(h, ctypes.byref(cfg), sp), "tvbx_run")
+
+
+def set_allocator(alloc=None, free=None):
+    """Install alloc(bytes) -> device pointer (int, 0 on failure) and
+    free(pointer) for the handles' device memory (tvbx_set_allocator); no
+    arguments restore cudaMalloc / cudaFree."""
+    global _allocator_refs
+    if alloc is None and free is None:
+        _check(load().tvbx_set_allocator(ALLOC_FN(), FREE_FN(), None), "tvbx_set_allocator")
+        _allocator_refs = None
+        return
+
+    def _a(n, ctx):
+        try:
+            return int(alloc(int(n))) or None
+        except Exception:
+            return None
+
+    def _f(p, ctx):
+        free(int(p))
+
+    refs = (ALLOC_FN(_a), FREE_FN(_f))
+    _check(load().tvbx_set_allocator(refs[0], refs[1], None), "tvbx_set_allocator")
+    _allocator_refs = refs
+
+
+def use_torch_allocator(enable=True):
+    """Take the handles' device memory from PyTorch's caching allocator (on
+    the current device), so the engine and PyTorch share one pool."""
+    if not enable:
+        set_allocator()
+        return
+    import torch
+    set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n), torch.cuda.caching_allocator_delete)
 
 
 def run_continue(h, n_steps, transient_samples=0, stream=None):

@@ -89,6 +89,16 @@ def test_fitness_and_top_k_reject_bad_arguments_before_device_use(lib):
     assert L.tvbx_top_k(one, 10, 1025, one, one, None) == -1
 
 
+def test_allocator_hook_takes_both_functions_or_neither(lib):
+    L = lib.load()
+    alloc = lib.ALLOC_FN(lambda n, ctx: None)
+    free = lib.FREE_FN(lambda p, ctx: None)
+    assert L.tvbx_set_allocator(alloc, lib.FREE_FN(), None) == -1 and "both" in lib.last_error()
+    assert L.tvbx_set_allocator(lib.ALLOC_FN(), free, None) == -1
+    assert L.tvbx_set_allocator(alloc, free, None) == 0
+    assert L.tvbx_set_allocator(lib.ALLOC_FN(), lib.FREE_FN(), None) == 0   # default again
+
+
 def test_analysis_region_limits_are_checked_before_device_use(lib):
     L = lib.load()
     one = ctypes.c_void_p(16)   # never dereferenced
