@@ -10,6 +10,7 @@ import pytest
 
 import test_oracle_dynamics as TD
 import test_oracle_rng as TR
+import test_oracle_regimes as TG
 import test_oracle_tf as TT
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -42,6 +43,10 @@ MUTANTS = [
     ("tavg_not_averaged", "serE[(size_t)k * T_out + t] = accE[k] / ts;",
      "serE[(size_t)k * T_out + t] = accE[k];", ["brute"]),
     ("coupling_missing_g", "c[k] = g * s;", "c[k] = s;", ["brute"]),
+    ("rate_missing_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
+     "jet F = j_div(j_erfc(arg), tV);", ["fixed_point_190hz"]),
+    ("rate_extra_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
+     "jet F = j_div(j_erfc(arg), j_scale(tV, 4.0));", ["fixed_point_190hz"]),
 ]
 
 
@@ -81,6 +86,8 @@ def _pin(name, O, aten):
         TR.test_ou_stationary_law(O)
     elif name == "philox":
         TR.test_philox_matches_aten(O, aten)
+    elif name == "fixed_point_190hz":
+        TG.test_pathological_fixed_point_near_190_hz(O)
     else:
         raise KeyError(name)
 
