@@ -772,12 +772,25 @@ struct AnScratch {
 };
 
 // Copy stream and events of a host-input analysis (released when the call
-// returns; work still queued completes first).
+// returns; work still queued completes first). Before the release, the
+// compute stream s waits for everything queued on the copy stream, so the
+// staging buffers, freed on s afterwards, outlive every copy into them even
+// when the call returns early on an error.
 struct HostPipe {
+    cudaStream_t s = nullptr;
     cudaStream_t cs = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // start, ready[2], free[2]
     ~HostPipe()
     {
+        if (cs) {
+            cudaEvent_t done = nullptr;
+            if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+                if (cudaEventRecord(done, cs) == cudaSuccess) cudaStreamWaitEvent(s, done, 0);
+                cudaEventDestroy(done);
+            } else {
+                cudaStreamSynchronize(cs);
+            }
+        }
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
         if (cs) cudaStreamDestroy(cs);
@@ -888,6 +901,7 @@ extern "C" tvbx_status tvbx_series_analysis(const float* series, int32_t n_regio
     // staging buffers while batch b is analysed on s
     const bool host_in = is_host_pointer(series);
     HostPipe hp;
+    hp.s = s;
     float* stage[2] = {nullptr, nullptr};
     if (host_in) {
         ACK(scr.get(&stage[0], (size_t)B * N * T), "analysis staging");
