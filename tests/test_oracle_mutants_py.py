@@ -1,5 +1,6 @@
 """Mutation check of the pins of the Python oracles (oracle/analysis.py,
-oracle/bold.py, oracle/adex_cell.py): a plausible mistake planted in a
+oracle/bold.py, oracle/adex_cell.py and the analysis half of
+oracle/oracle.py): a plausible mistake planted in a
 temporary copy of a module's source (never in the source itself) must make
 at least one of the named pins fail. The mutant module is loaded under the
 oracle package (so its relative imports resolve) and swapped in for the pin
@@ -17,6 +18,8 @@ T2 = "test_oracle_table2"
 FIT = "test_oracle_fitness"
 BW = "test_oracle_bold"
 CELL = "test_oracle_adex_cell"
+AN = "test_oracle_analysis"
+DYN = "test_oracle_dynamics"
 # the name under which each pin module refers to the oracle module it pins
 ALIAS = {T2: "A", FIT: "A", BW: "B", CELL: "A"}
 
@@ -72,6 +75,23 @@ MUTANTS = [
      [(CELL, "test_fit_recovers_table1_from_template_rates")]),
     ("adex_cell", "basis_columns_swapped", "V * S, V * Z, S * Z]", "V * Z, V * S, S * Z]",
      [(CELL, "test_fit_recovers_table1_from_template_rates")]),
+    # the analysis half of oracle/oracle.py; its pins take the module as their oracle argument
+    ("oracle", "fc_not_centred", "Xc = X - X.mean(axis=-1, keepdims=True)", "Xc = X",
+     [(AN, "test_fc_matches_corrcoef")]),
+    ("oracle", "fc_diagonal_of_silent_rows", "    fc[..., idx, idx] = 1.0\n", "",
+     [(AN, "test_fc_invariances_and_degenerate_rows")]),
+    ("oracle", "fcd_last_window_dropped", "starts = list(range(0, T - window + 1, step))",
+     "starts = list(range(0, T - window, step))", [(AN, "test_fcd_matches_window_loop")]),
+    ("oracle", "chi_without_root", "    return np.sqrt(r)", "    return r", [(AN, "test_chi_special_cases")]),
+    ("oracle", "chi_variance_of_regions", "num = X.mean(axis=-2).var(axis=-1)", "num = X.var(axis=-2).mean(axis=-1)",
+     [(AN, "test_chi_special_cases")]),
+    ("oracle", "mean_fc_with_diagonal", "mask = ~np.eye(n, dtype=bool)", "mask = np.ones((n, n), dtype=bool)",
+     [(AN, "test_summary_fields")]),
+    ("oracle", "summary_keeps_transient", "    Et = E[..., transient:]", "    Et = E", [(AN, "test_summary_fields")]),
+    ("oracle", "grid_linspace_open_end", "vals = [lo + (hi - lo) * q / (n - 1) if n > 1 else lo for q in range(n)]",
+     "vals = [lo + (hi - lo) * q / n if n > 1 else lo for q in range(n)]", [(DYN, "test_grid_expansion_order")]),
+    ("oracle", "grid_first_axis_fastest", "for combo in itertools.product(*value_lists):",
+     "for combo in (c[::-1] for c in itertools.product(*value_lists[::-1])):", [(DYN, "test_grid_expansion_order")]),
 ]
 
 
@@ -86,6 +106,9 @@ def _load_mutant(tmp_path, module, original, planted):
     mod = importlib.util.module_from_spec(spec)
     mod.__package__ = "oracle"
     spec.loader.exec_module(mod)
+    if module == "oracle":   # the copy keeps using the real C source and library
+        real = importlib.import_module("oracle.oracle")
+        mod._SRC, mod._LIB_DIR, mod._LIB = real._SRC, real._LIB_DIR, real._LIB
     return mod
 
 
@@ -96,22 +119,26 @@ def test_python_pins_catch_planted_mistake(tmp_path, monkeypatch, oracle, module
     for pin_module, fn in pins:
         T = importlib.import_module(pin_module)
         with monkeypatch.context() as m:
-            m.setattr(T, ALIAS[pin_module], mutant)
+            if pin_module in ALIAS:
+                m.setattr(T, ALIAS[pin_module], mutant)
             f = getattr(T, fn)
+            arg = mutant if module == "oracle" else oracle
             try:
-                f(oracle) if "oracle" in inspect.signature(f).parameters else f()
+                f(arg) if "oracle" in inspect.signature(f).parameters else f()
             except (AssertionError, ValueError, FloatingPointError, IndexError, ZeroDivisionError):
                 caught.append(fn)
     assert caught, f"mutant {name} of oracle/{module}.py survived {[p[1] for p in pins]}"
 
 
-@pytest.mark.parametrize("module", ["analysis", "bold", "adex_cell"])
+@pytest.mark.parametrize("module", ["analysis", "bold", "adex_cell", "oracle"])
 def test_unmutated_copy_passes_every_pin(tmp_path, monkeypatch, oracle, module):
     """Control: the same harness with nothing planted catches nothing."""
     copy = _load_mutant(tmp_path, module, None, None)
     for pin_module, fn in sorted({p for m in MUTANTS if m[0] == module for p in m[4]}):
         T = importlib.import_module(pin_module)
         with monkeypatch.context() as m:
-            m.setattr(T, ALIAS[pin_module], copy)
+            if pin_module in ALIAS:
+                m.setattr(T, ALIAS[pin_module], copy)
             f = getattr(T, fn)
-            f(oracle) if "oracle" in inspect.signature(f).parameters else f()
+            arg = copy if module == "oracle" else oracle
+            f(arg) if "oracle" in inspect.signature(f).parameters else f()
