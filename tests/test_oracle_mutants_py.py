@@ -1,5 +1,5 @@
 """Mutation check of the pins of the Python oracles (oracle/analysis.py,
-oracle/bold.py, oracle/adex_cell.py and the analysis half of
+oracle/bold.py, oracle/adex_cell.py, oracle/mlp.py and the analysis half of
 oracle/oracle.py): a plausible mistake planted in a
 temporary copy of a module's source (never in the source itself) must make
 at least one of the named pins fail. The mutant module is loaded under the
@@ -19,9 +19,10 @@ FIT = "test_oracle_fitness"
 BW = "test_oracle_bold"
 CELL = "test_oracle_adex_cell"
 AN = "test_oracle_analysis"
+MLP = "test_oracle_mlp"
 DYN = "test_oracle_dynamics"
 # the name under which each pin module refers to the oracle module it pins
-ALIAS = {T2: "A", FIT: "A", BW: "B", CELL: "A"}
+ALIAS = {T2: "A", FIT: "A", BW: "B", CELL: "A", MLP: "M"}
 
 # (oracle module, mutant name, original text, planted text, pins expected to catch it)
 MUTANTS = [
@@ -75,6 +76,25 @@ MUTANTS = [
      [(CELL, "test_fit_recovers_table1_from_template_rates")]),
     ("adex_cell", "basis_columns_swapped", "V * S, V * Z, S * Z]", "V * Z, V * S, S * Z]",
      [(CELL, "test_fit_recovers_table1_from_template_rates")]),
+    ("mlp", "bf16_truncates", "r = ((f + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)",
+     "r = (f >> np.uint64(16)) << np.uint64(16)", [(MLP, "test_bf16_rounding_known_values")]),
+    ("mlp", "bf16_ties_away", "r = ((f + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)",
+     "r = ((f + np.uint64(0x8000)) >> np.uint64(16)) << np.uint64(16)", [(MLP, "test_bf16_rounding_known_values")]),
+    ("mlp", "relu_gate_on_wrong_layer", "dz = da * (a_prev > 0.0)", "dz = da",
+     [(MLP, "test_gradients_match_central_differences")]),
+    ("mlp", "mse_gradient_factor", "dz = 2.0 * diff / (B * O)", "dz = diff / (B * O)",
+     [(MLP, "test_gradients_match_central_differences")]),
+    ("mlp", "bias_gradient_not_summed", "grads[l] = (dz.T @ a_prev, dz.sum(axis=0))",
+     "grads[l] = (dz.T @ a_prev, dz.mean(axis=0))", [(MLP, "test_gradients_match_central_differences")]),
+    ("mlp", "adamw_decays_biases", "(b, gb, 0.0)", "(b, gb, wd)", [(MLP, "test_adamw_matches_torch")]),
+    ("mlp", "adamw_no_bias_correction", "p = p - lr * (m / bc1) / (np.sqrt(v / bc2) + eps)",
+     "p = p - lr * m / (np.sqrt(v) + eps)", [(MLP, "test_adamw_matches_torch")]),
+    ("mlp", "adamw_coupled_decay", "p = p * (1.0 - lr * decay)", "g = g + decay * p",
+     [(MLP, "test_adamw_matches_torch")]),
+    ("mlp", "standardisation_sample_sd", "sd = Y.std(axis=0)", "sd = Y.std(axis=0, ddof=1)",
+     [(MLP, "test_standardisation_and_normalisation")]),
+    ("mlp", "pca_smallest_components", "order = np.argsort(w)[::-1][:n_comp]", "order = np.argsort(w)[:n_comp]",
+     [(MLP, "test_pca_recovers_a_planted_subspace")]),
     # the analysis half of oracle/oracle.py; its pins take the module as their oracle argument
     ("oracle", "fc_not_centred", "Xc = X - X.mean(axis=-1, keepdims=True)", "Xc = X",
      [(AN, "test_fc_matches_corrcoef")]),
@@ -130,7 +150,7 @@ def test_python_pins_catch_planted_mistake(tmp_path, monkeypatch, oracle, module
     assert caught, f"mutant {name} of oracle/{module}.py survived {[p[1] for p in pins]}"
 
 
-@pytest.mark.parametrize("module", ["analysis", "bold", "adex_cell", "oracle"])
+@pytest.mark.parametrize("module", ["analysis", "bold", "adex_cell", "mlp", "oracle"])
 def test_unmutated_copy_passes_every_pin(tmp_path, monkeypatch, oracle, module):
     """Control: the same harness with nothing planted catches nothing."""
     copy = _load_mutant(tmp_path, module, None, None)
