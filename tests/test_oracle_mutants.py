@@ -43,6 +43,11 @@ MUTANTS = [
     ("tavg_not_averaged", "serE[(size_t)k * T_out + t] = accE[k] / ts;",
      "serE[(size_t)k * T_out + t] = accE[k];", ["brute"]),
     ("coupling_missing_g", "c[k] = g * s;", "c[k] = s;", ["brute"]),
+    ("box_muller_sine", "return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);",
+     "return sqrt(-2.0 * log(u1)) * sin(2.0 * M_PI * u2);", ["box_muller"]),
+    ("box_muller_u1_offset", "double u1 = ((double)x[0] + 1.0) / two32;", "double u1 = ((double)x[0] + 0.5) / two32;",
+     ["box_muller"]),
+    ("noise_stream_ignores_set", "noise_per_set ? p_global : 0u", "0u", ["brute"]),
     ("rate_missing_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
      "jet F = j_div(j_erfc(arg), tV);", ["fixed_point_190hz"]),
     ("rate_extra_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
@@ -86,6 +91,8 @@ def _pin(name, O, aten):
         TR.test_ou_stationary_law(O)
     elif name == "philox":
         TR.test_philox_matches_aten(O, aten)
+    elif name == "box_muller":
+        TR.test_normals_follow_box_muller_on_aten_words(O, aten)
     elif name == "fixed_point_190hz":
         TG.test_pathological_fixed_point_near_190_hz(O)
     else:

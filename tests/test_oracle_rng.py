@@ -50,6 +50,20 @@ def test_philox_matches_aten(oracle, aten_philox):
     assert np.array_equal(got, ref)
 
 
+def test_normals_follow_box_muller_on_aten_words(oracle, aten_philox):
+    """Each normal is Box-Muller of the first two Philox words of counter
+    (step, region, set, 0) under key = seed, u1 = (x0 + 1) 2^-32, u2 = x1 2^-32,
+    sqrt(-2 ln u1) cos(2 pi u2); the words come from the ATen engine."""
+    cases = [(seed, n, k, p) for seed in (1, 7, 2**40 + 3) for n in (0, 1, 49999) for k in (0, 67) for p in (0, 5)]
+    rows = [[seed & 0xFFFFFFFF, seed >> 32, n, k, p, 0] for seed, n, k, p in cases]
+    words = aten_philox(rows)
+    for (seed, n, k, p), w in zip(cases, words):
+        u1 = (float(w[0]) + 1.0) / 2.0 ** 32
+        u2 = float(w[1]) / 2.0 ** 32
+        want = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+        assert oracle.normal(seed, n, k, p) == pytest.approx(want, rel=1e-13, abs=1e-15)
+
+
 def test_philox_counter_sensitivity(oracle):
     """Every bit of counter and key changes the output (avalanche sanity)."""
     base = oracle.philox([5, 6, 7, 8], [9, 10])
