@@ -205,3 +205,20 @@ def test_table1_sign_reading(oracle, connectome68):
     assert diverged.all()
     assert (good["status"] & oracle.ST_NONFINITE).sum() == 0
     assert np.all(np.abs(good["state"][:, 2:5, :]) < 1e-3)
+
+
+def test_clamp_bounds_and_flags(oracle):
+    """E and I are clamped to [E_min, E_max] after each step, and the set's
+    status records which bound was hit: a start above E_max comes back at
+    E_max exactly with CLAMP_HI, a start below E_min at E_min with CLAMP_LO,
+    a start inside leaves the status clear."""
+    W, L = _small_connectome(3, 5)
+    prm = oracle.expand_grid([("g", [0.2])])
+    for E0, bit, bound in ((0.35, oracle.ST_CLAMP_HI, "E_max"), (-0.05, oracle.ST_CLAMP_LO, "E_min")):
+        m = oracle.make_model({"E0": E0, "I0": E0})
+        r = oracle.simulate(m, W, L, prm, 0.1, 1, 1, 1)
+        assert r["status"][0] & bit and not r["status"][0] & (oracle.ST_CLAMP_HI + oracle.ST_CLAMP_LO - bit)
+        assert np.all(r["state"][0, 0] == getattr(m, bound)) and np.all(r["state"][0, 1] == getattr(m, bound))
+    m = oracle.make_model({"E0": 0.01, "I0": 0.01})
+    r = oracle.simulate(m, W, L, prm, 0.1, 1, 1, 1)
+    assert r["status"][0] == 0 and np.all(r["state"][0, 0] < m.E_max) and np.all(r["state"][0, 0] > m.E_min)

@@ -48,6 +48,10 @@ MUTANTS = [
     ("box_muller_u1_offset", "double u1 = ((double)x[0] + 1.0) / two32;", "double u1 = ((double)x[0] + 0.5) / two32;",
      ["box_muller"]),
     ("noise_stream_ignores_set", "noise_per_set ? p_global : 0u", "0u", ["brute"]),
+    ("clamp_hi_dropped", "if (En > m->E_max) { En = m->E_max; status |= OR_ST_CLAMP_HI; }",
+     "if (En > m->E_max) { status |= OR_ST_CLAMP_HI; }", ["clamp"]),
+    ("clamp_lo_flagged_hi", "if (In < m->E_min) { In = m->E_min; status |= OR_ST_CLAMP_LO; }",
+     "if (In < m->E_min) { In = m->E_min; status |= OR_ST_CLAMP_HI; }", ["clamp"]),
     ("rate_missing_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
      "jet F = j_div(j_erfc(arg), tV);", ["fixed_point_190hz"]),
     ("rate_extra_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
@@ -91,6 +95,8 @@ def _pin(name, O, aten):
         TR.test_ou_stationary_law(O)
     elif name == "philox":
         TR.test_philox_matches_aten(O, aten)
+    elif name == "clamp":
+        TD.test_clamp_bounds_and_flags(O)
     elif name == "box_muller":
         TR.test_normals_follow_box_muller_on_aten_words(O, aten)
     elif name == "fixed_point_190hz":
