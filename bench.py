@@ -1091,7 +1091,7 @@ def run_batch_engine(args):
 # ---------------------------------------------------------------------------
 # Surrogate-guided exploration: an ensemble MLP (5 -> 256 x 3 -> 24) trained
 # on the paper-scale sweep's outputs (+ a speed-augmented set) maps the
-# sync/async boundary of a (g, b_e) slice; the simulator judges proposals.
+# sync/async boundary of a (g, b_e) slice; the simulator checks the proposals.
 SUR_METRIC = "speedup of the time-to-map of a regime boundary on 1 GB300 (surrogate-guided vs plain dense sweep)"
 REGIME_HZ = 50.0
 SUR_IN = ("g", "b_e", "tau_w_e", "E_L_i", "speed")
@@ -1222,7 +1222,7 @@ def run_surrogate_engine(args):
     ig = np.rint(np.linspace(0, cs - 1, side)).astype(int)
     err_coarse = float(np.mean(lab_c[np.ix_(ig, ig)].ravel() != truth))
 
-    # surrogate-guided: predict the map, then rounds of proposals judged by the simulator
+    # surrogate-guided: predict the map, then batches of proposals checked by the simulator
     rounds = []
     t0 = time.perf_counter()
     lab = sur.predict(X_map)[:, 0] >= REGIME_HZ
