@@ -63,7 +63,7 @@ def _brute_force(oracle, m, W, L, prm_row, S, ts, seed, noise_per_set, p_global,
     Wad = np.zeros((N, 2))
     ou = np.zeros(N)
     acc = np.zeros((N, 2))
-    ser = []
+    ser, ser_i = [], []
     sq = np.sqrt(DT)
     for n in range(S):
         if coupling_dense:
@@ -100,10 +100,11 @@ def _brute_force(oracle, m, W, L, prm_row, S, ts, seed, noise_per_set, p_global,
         hist.append(newE)
         if (n + 1) % ts == 0:
             ser.append(acc[:, 0] / ts)
+            ser_i.append(acc[:, 1] / ts)
             acc[:] = 0.0
     state = np.array([nu[:, 0], nu[:, 1], [c_[0, 0] for c_ in C], [c_[0, 1] for c_ in C],
                       [c_[1, 1] for c_ in C], Wad[:, 0], Wad[:, 1], ou])
-    return np.array(ser).T, state
+    return np.array(ser).T, state, np.array(ser_i).T
 
 
 def _small_connectome(N, seed, zero_lengths=False, w_hi=0.3):
@@ -119,28 +120,37 @@ def _small_connectome(N, seed, zero_lengths=False, w_hi=0.3):
     return W, L
 
 
-@pytest.mark.parametrize("N,noise_per_set,zero_lengths,w_hi,rtol",
-                         [(2, False, False, 0.3, 1e-10), (3, True, False, 0.3, 1e-10),
-                          (4, False, False, 0.3, 1e-10), (3, False, True, 0.3, 1e-10),
-                          (2, False, False, 1.0, 1e-7)])
-def test_brute_force_small_networks(oracle, N, noise_per_set, zero_lengths, w_hi, rtol):
+# constants away from their defaults, so that terms that vanish at the
+# defaults (the inhibitory adaptation, c_F{e,i} and c_F{i,i}, I0 = E0) count
+NONDEFAULT = {"E0": 1.5e-3, "I0": 4e-3, "b_i": 5.0, "a_i": 0.5, "tau_w_i": 200.0}
+
+
+@pytest.mark.parametrize("N,noise_per_set,zero_lengths,w_hi,rtol,nondefault",
+                         [(2, False, False, 0.3, 1e-10, False), (3, True, False, 0.3, 1e-10, False),
+                          (4, False, False, 0.3, 1e-10, False), (3, False, True, 0.3, 1e-10, False),
+                          (2, False, False, 1.0, 1e-7, False), (3, True, False, 0.3, 1e-10, True)])
+def test_brute_force_small_networks(oracle, N, noise_per_set, zero_lengths, w_hi, rtol, nondefault):
     """Smooth cases agree to rounding; the strongly coupled case (w_hi = 1)
     drives regions into the 0.2 kHz clamp, where the stiff jump amplifies the
-    rounding-order difference between the two formulations."""
-    m = oracle.make_model()
+    rounding-order difference between the two formulations. The non-default
+    case moves the constants and inputs whose terms vanish at the defaults."""
+    m = oracle.make_model(NONDEFAULT if nondefault else None)
     W, L = _small_connectome(N, 10 + N, zero_lengths, w_hi)
     g, E_L_e, wn = (0.2, -62.0, 1e-3) if w_hi < 1.0 else (0.35, -60.0, 2e-3)
-    prm = oracle.expand_grid([("g", [g]), ("b_e", [40.0]), ("a_e", [1.5]), ("w_noise", [wn]),
-                              ("E_L_e", [E_L_e])])
+    axes = [("g", [g]), ("b_e", [40.0]), ("a_e", [1.5]), ("w_noise", [wn]), ("E_L_e", [E_L_e])]
+    if nondefault:
+        axes += [("cF_ei", [0.2e-3]), ("cF_ii", [0.1e-3]), ("E_L_i", [-66.0])]
+    prm = oracle.expand_grid(axes)
     S, ts, seed, p_off = 240, 4, 99, 7
     r = oracle.simulate(m, W, L, prm, DT, S, ts, seed, noise_per_set=noise_per_set, p_offset=p_off)
-    ser, state = _brute_force(oracle, m, W, L, prm[0], S, ts, seed, noise_per_set, p_off,
-                              coupling_dense=zero_lengths)
+    ser, state, ser_i = _brute_force(oracle, m, W, L, prm[0], S, ts, seed, noise_per_set, p_off,
+                                     coupling_dense=zero_lengths)
     if w_hi < 1.0:
         assert not r["status"][0] & (oracle.ST_NONFINITE | oracle.ST_CLAMP_HI)
     else:
         assert r["status"][0] & oracle.ST_CLAMP_HI
     assert np.allclose(r["E"][0], ser, rtol=rtol, atol=1e-15)
+    assert np.allclose(r["I"][0], ser_i, rtol=rtol, atol=1e-15)
     assert np.allclose(r["state"][0], state, rtol=10 * rtol, atol=1e-15)
 
 
@@ -222,3 +232,15 @@ def test_clamp_bounds_and_flags(oracle):
     m = oracle.make_model({"E0": 0.01, "I0": 0.01})
     r = oracle.simulate(m, W, L, prm, 0.1, 1, 1, 1)
     assert r["status"][0] == 0 and np.all(r["state"][0, 0] < m.E_max) and np.all(r["state"][0, 0] > m.E_min)
+
+
+def test_status_bits_for_divergence_and_nonfinite_parameters(oracle):
+    """DIVERGED when a covariance passes C_div (here set below the first
+    step's covariance), NONFINITE for a set with a non-finite parameter (from
+    the start, whatever its trajectory), neither for a plain set."""
+    W, L = _small_connectome(3, 5)
+    prm = oracle.expand_grid([("g", [0.2, float("nan")])])
+    r = oracle.simulate(oracle.make_model(), W, L, prm, DT, 20, 1, 1)
+    assert r["status"][0] == 0 and r["status"][1] & oracle.ST_NONFINITE
+    r = oracle.simulate(oracle.make_model({"C_div": 1e-12}), W, L, prm[:1], DT, 20, 1, 1)
+    assert r["status"][0] & oracle.ST_DIVERGED and not r["status"][0] & oracle.ST_NONFINITE

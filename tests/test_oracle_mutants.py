@@ -52,6 +52,14 @@ MUTANTS = [
      "if (En > m->E_max) { status |= OR_ST_CLAMP_HI; }", ["clamp"]),
     ("clamp_lo_flagged_hi", "if (In < m->E_min) { In = m->E_min; status |= OR_ST_CLAMP_LO; }",
      "if (In < m->E_min) { In = m->E_min; status |= OR_ST_CLAMP_HI; }", ["clamp"]),
+    ("diverged_flag_never", "                status |= OR_ST_DIVERGED;", "                ;", ["status"]),
+    ("nonfinite_parameter_ignored", "if (!isfinite(prm[a])) status |= OR_ST_NONFINITE;",
+     "if (0) status |= OR_ST_NONFINITE;", ["status"]),
+    ("initial_I_from_E0", "E[k] = m->E0; I[k] = m->I0;", "E[k] = m->E0; I[k] = m->E0;", ["brute_nondefault"]),
+    ("tavg_I_from_E", "accE[k] += En; accI[k] += In;", "accE[k] += En; accI[k] += En;", ["brute"]),
+    ("inhibitory_adaptation_sign", "m->b_i * Ik + m->a_i", "-m->b_i * Ik + m->a_i", ["brute_nondefault"]),
+    ("cF_ei_read_as_cF_ii", "jet Fe = or_tf_jet(m, m->P_e, E_L_e, exc + cF_ee, Ik + cF_ei, We[k], &ae);",
+     "jet Fe = or_tf_jet(m, m->P_e, E_L_e, exc + cF_ee, Ik + cF_ii, We[k], &ae);", ["brute_nondefault"]),
     ("rate_missing_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
      "jet F = j_div(j_erfc(arg), tV);", ["fixed_point_190hz"]),
     ("rate_extra_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
@@ -89,8 +97,12 @@ def _pin(name, O, aten):
     elif name == "fixed_point":
         TD.test_fixed_point_satisfies_eq1_eq2_eq3(O)
     elif name == "brute":
-        for case in [(3, True, False, 0.3, 1e-10), (3, False, True, 0.3, 1e-10)]:
+        for case in [(3, True, False, 0.3, 1e-10, False), (3, False, True, 0.3, 1e-10, False)]:
             TD.test_brute_force_small_networks(O, *case)
+    elif name == "brute_nondefault":
+        TD.test_brute_force_small_networks(O, 3, True, False, 0.3, 1e-10, True)
+    elif name == "status":
+        TD.test_status_bits_for_divergence_and_nonfinite_parameters(O)
     elif name == "ou":
         TR.test_ou_stationary_law(O)
     elif name == "philox":
