@@ -122,7 +122,7 @@ def _small_connectome(N, seed, zero_lengths=False, w_hi=0.3):
 
 # constants away from their defaults, so that terms that vanish at the
 # defaults (the inhibitory adaptation, c_F{e,i} and c_F{i,i}, I0 = E0) count
-NONDEFAULT = {"E0": 1.5e-3, "I0": 4e-3, "b_i": 5.0, "a_i": 0.5, "tau_w_i": 200.0}
+NONDEFAULT = {"E0": 1.5e-3, "I0": 4e-3, "b_i": 5.0, "a_i": 0.5, "tau_w_i": 200.0, "mu_OU": 0.3}
 
 
 @pytest.mark.parametrize("N,noise_per_set,zero_lengths,w_hi,rtol,nondefault",

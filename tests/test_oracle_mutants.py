@@ -60,6 +60,8 @@ MUTANTS = [
     ("inhibitory_adaptation_sign", "m->b_i * Ik + m->a_i", "-m->b_i * Ik + m->a_i", ["brute_nondefault"]),
     ("cF_ei_read_as_cF_ii", "jet Fe = or_tf_jet(m, m->P_e, E_L_e, exc + cF_ee, Ik + cF_ei, We[k], &ae);",
      "jet Fe = or_tf_jet(m, m->P_e, E_L_e, exc + cF_ee, Ik + cF_ii, We[k], &ae);", ["brute_nondefault"]),
+    ("ou_mean_ignored", "OU[k] = OU[k] + dt / m->tau_OU * (m->mu_OU - OU[k])", "OU[k] = OU[k] + dt / m->tau_OU * (0.0 - OU[k])",
+     ["brute_nondefault"]),
     ("rate_missing_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
      "jet F = j_div(j_erfc(arg), tV);", ["fixed_point_190hz"]),
     ("rate_extra_half", "jet F = j_div(j_erfc(arg), j_scale(tV, 2.0));",
