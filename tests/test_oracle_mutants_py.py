@@ -48,6 +48,14 @@ MUTANTS = [
      "                r //= f\n        if r == 1:\n            return m",
      "        for f in (2, 3, 5, 7):\n            while r % f == 0:\n                r //= f\n        if r == 1:\n"
      "            return m", [(T2, "test_smooth_length")]),
+    ("analysis", "peak_ties_to_higher_frequency", "        if P[i] > P[best]:", "        if P[i] >= P[best]:",
+     [(T2, "test_peak_ties_and_band_edges")]),
+    ("analysis", "peak_band_upper_edge_open", "    m = (f >= band[0]) & (f <= band[1])\n    if not m.any():",
+     "    m = (f >= band[0]) & (f < band[1])\n    if not m.any():", [(T2, "test_peak_ties_and_band_edges")]),
+    ("analysis", "fit_band_lower_edge_open", "    m = (f >= band[0]) & (f <= band[1])\n    if m.sum() < 2",
+     "    m = (f > band[0]) & (f <= band[1])\n    if m.sum() < 2", [(T2, "test_peak_ties_and_band_edges")]),
+    ("analysis", "up_down_threshold_in_fp64", "theta = np.float32(np.asarray(row, dtype=np.float64).mean())",
+     "theta = np.asarray(row, dtype=np.float64).mean()", [(T2, "test_up_down_threshold_is_the_fp32_mean")]),
     ("analysis", "fitness_includes_diagonal", "iu = np.triu_indices(n, k=1)", "iu = np.triu_indices(n, k=0)",
      [(FIT, "test_fitness_matches_corrcoef_on_the_triangles")]),
     ("analysis", "pearson_not_centred", "yc = y - y.mean()", "yc = y",

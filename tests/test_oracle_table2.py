@@ -126,3 +126,31 @@ def test_up_down_against_hand_counted_runs():
     # a constant or a monotone row has no complete run
     assert A.up_down(np.full((1, 10), 0.3, dtype=np.float32), 1.0)[2:] == (0, 0, 0, 0)
     assert A.up_down(np.arange(10, dtype=np.float32)[None], 1.0)[2:] == (0, 0, 0, 0)
+
+
+def test_peak_ties_and_band_edges():
+    """The PSD peak takes the lowest of equal maxima and includes the band's
+    upper edge (100 Hz); the power-law fit includes the lower edge (1 Hz):
+    its coefficients equal numpy's least-squares line through every band bin."""
+    f = np.array([0.5, 1.0, 2.0, 4.0, 50.0, 100.0, 150.0])
+    fmax, amax = A.psd_peak(f, np.array([9.0, 1.0, 5.0, 5.0, 2.0, 1.0, 9.0]))
+    assert (fmax, amax) == (2.0, 5.0)
+    fmax, amax = A.psd_peak(f, np.array([9.0, 1.0, 2.0, 3.0, 4.0, 8.0, 9.0]))
+    assert (fmax, amax) == (100.0, 8.0)
+    P = np.array([7.0, 10.0, 1.0, 0.25, 1e-3, 3e-4, 1.0])
+    a, b = A.psd_fit(f, P)
+    band = (f >= 1.0) & (f <= 100.0)
+    slope, icpt = np.polyfit(np.log10(f[band]), np.log10(P[band]), 1)
+    assert a == pytest.approx(-slope, rel=1e-12) and b == pytest.approx(10.0 ** icpt, rel=1e-12)
+
+
+def test_up_down_threshold_is_the_fp32_mean():
+    """A row of four 1s and six c = 1 + 2^-23 (the next FP32 value): its FP64
+    mean, 1 + 0.6 * 2^-23, rounds to c in FP32, so no sample lies above the
+    threshold and there is no transition (against the FP64 mean every c would
+    be UP and the row would hold complete runs)."""
+    c = np.float32(1.0) + np.float32(2.0 ** -23)
+    row = np.array([1, 1, c, c, c, 1, 1, c, c, c], dtype=np.float32)
+    assert np.float32(row.astype(np.float64).mean()) == c
+    mu, md, nu, su, nd, sd = A.up_down(row[None, :], 1.0)
+    assert (nu, su, nd, sd) == (0, 0, 0, 0) and np.isnan(mu) and np.isnan(md)
