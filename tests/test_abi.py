@@ -193,3 +193,35 @@ def test_tf_fit_on_the_host_equals_the_oracle_fit(lib, oracle):
 def test_cell_defaults_match_the_oracle(lib):
     from oracle import adex_cell as A
     assert lib.cell_defaults(0) == A.CELL_RS and lib.cell_defaults(1) == A.CELL_FS
+
+
+def _declared_arities():
+    """Number of parameters of every function include/tvbx.h declares
+    ((void) counts as none)."""
+    out = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"typedef[^;]*;", "", text)   # function-pointer typedefs are not functions
+        for name, params in re.findall(r"\b(tvbx_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text, flags=re.S):
+            p = params.strip()
+            out[name] = 0 if p in ("", "void") else p.count(",") + 1
+    return out
+
+
+def test_binding_argtypes_match_the_declarations(lib):
+    """Every function the binding gives argtypes takes as many arguments as
+    its C declaration, so a parameter added on one side only is caught here."""
+    L = lib.load()
+    arities = _declared_arities()
+    assert sorted(arities) == _declared_functions()
+    checked = 0
+    for name, n in arities.items():
+        fn = getattr(L, name)
+        if fn.argtypes is None:
+            continue
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+        checked += 1
+    assert checked >= len(arities) - 3   # all but the argument-less ones
