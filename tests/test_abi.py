@@ -225,3 +225,36 @@ def test_binding_argtypes_match_the_declarations(lib):
         assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
         checked += 1
     assert checked >= len(arities) - 3   # all but the argument-less ones
+
+
+STRUCTS = {"Model": "tvbx_model", "AxisSpec": "tvbx_axis_spec", "Grid": "tvbx_grid", "RunCfg": "tvbx_run_cfg",
+           "FcCfg": "tvbx_fc_cfg", "SurrogateCfg": "tvbx_surrogate_cfg", "BoldParams": "tvbx_bold_params",
+           "CellParams": "tvbx_cell_params"}
+
+
+def test_binding_structures_have_the_c_layout(lib, tmp_path):
+    """Size and every field offset of the binding's ctypes structures equal
+    those the C compiler gives the declarations of include/tvbx.h."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "tvbx.h"', "int main(void) {"]
+    for py, c in STRUCTS.items():
+        lines.append(f'printf("{py} size %zu\\n", sizeof({c}));')
+        for field, _ in getattr(lib, py)._fields_:
+            lines.append(f'printf("{py} {field} %zu\\n", offsetof({c}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    n = 0
+    for line in filter(None, out):
+        py, field, value = line.split()
+        S = getattr(lib, py)
+        want = ctypes.sizeof(S) if field == "size" else getattr(S, field).offset
+        assert int(value) == want, (py, field, int(value), want)
+        n += 1
+    assert n == sum(len(getattr(lib, py)._fields_) + 1 for py in STRUCTS)
