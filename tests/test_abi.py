@@ -258,3 +258,18 @@ def test_binding_structures_have_the_c_layout(lib, tmp_path):
         assert int(value) == want, (py, field, int(value), want)
         n += 1
     assert n == sum(len(getattr(lib, py)._fields_) + 1 for py in STRUCTS)
+
+
+@pytest.mark.parametrize("compiler,std,suffix", [("gcc", "-std=c99", ".c"), ("g++", "-std=c++17", ".cpp")])
+def test_header_compiles_as_plain_c_and_cpp(tmp_path, compiler, std, suffix):
+    """include/tvbx.h is a C header: pedantic C99 and C++17 (C linkage) both
+    compile it without a warning."""
+    import shutil
+    import subprocess
+    if shutil.which(compiler) is None:
+        pytest.skip(f"no {compiler}")
+    src = tmp_path / ("probe" + suffix)
+    src.write_text('#include "tvbx.h"\nint main(void) { tvbx_run_cfg c; (void)c; return 0; }\n')
+    r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(src), "-o", str(tmp_path / "probe.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
