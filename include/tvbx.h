@@ -152,7 +152,17 @@ typedef struct {
                                   3: 16 sets, 2 x 2; TMA bulk copies into two
                                   buffers: 4: 16 sets, 2 x 1; 5: 16 sets, 1 x 2;
                                   cp.async, 8 sets, two CTAs per SM: 6: 2 x 1;
-                                  7: 1 x 2 */
+                                  7: 1 x 2; two sets per thread in packed
+                                  FP32x2 arithmetic, TMA bulk copies into two
+                                  buffers (only for tau_e == tau_i, else
+                                  TVBX_E_UNSUPPORTED): 8: 12 sets, 2 x 1;
+                                  9: 16 sets, 2 x 1; 10: 8 sets, 2 x 1;
+                                  11: 16 sets, 2 x 2; TMA bulk copies into
+                                  one buffer, one CTA barrier per step:
+                                  12: 32 sets, 4 x 1; 13: 16 sets, 2 x 1;
+                                  14: 32 sets, 2 x 2; cp.async into two
+                                  buffers, one barrier per step: 15: 16
+                                  sets, 2 x 1; 16: 16 sets, 1 x 2 */
 
 /* FC settings (Sec. "Output": FC from the covariance of the series,
  * Eq. 6 Pearson; FCD over sliding windows). */
@@ -344,8 +354,11 @@ tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_set
  * W = W_e), 1 = inhibitory (FS row). Inputs x_e, x_i (total input rates,
  * kHz), W (pA), E_L (mV), each [n]; C [n][3] = (C_ee, C_ei, C_ii) (kHz^2,
  * nullable). out [n][8] = F, dF/dx_e, dF/dx_i, d2F/dx_e2, d2F/dx_e dx_i,
- * d2F/dx_i2, mu_V (mV), and sum_ij C_ij d2F/dx_i dx_j as the integrator
- * computes it for Eq. 1 (contracted second-order jets; 0 when C is NULL).
+ * d2F/dx_i2, mu_V (mV), and sum_ij C_ij d2F/dx_i dx_j for Eq. 1 (0 when C is
+ * NULL). F, the gradient, mu_V and the contracted term come from the code the
+ * integrator runs (for tau_e == tau_i the reduced form of the template, else
+ * the template itself, both with contracted second-order jets); the three
+ * Hessian entries come from full second-order jets of the template.
  * All arrays live in memory of kind `mem`. model NULL = defaults. Synchronous. */
 tvbx_status tvbx_transfer_function(const tvbx_model* model, int32_t pop, int64_t n, int32_t mem,
                                    const float* x_e, const float* x_i, const float* W,
@@ -389,13 +402,19 @@ tvbx_status tvbx_profile_read(tvbx_sweep* h, double* sim_ms, int64_t* sim_launch
  * until the process exits; a call needs n_sets * (n_regions^2 + n_regions)
  * floats of it, so n_sets <= 1,787 at 68 regions. Larger requests, more than
  * 90 regions, NULL buffers or non-positive sizes return TVBX_E_INVALID_ARG
- * with the limit in tvbx_last_error(). The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress with that device current);
- * make that first call before any stream capture. Every call shares the array:
- * calls that overlap on the GPU (other streams, other threads) race and
- * corrupt each other's results; serialise them. Each call writes every
- * scratch entry it reads, so nothing needs clearing between calls. No
- * cudaMalloc, cudaFree or allocating library routine is called. */
+ * with the limit in tvbx_last_error(). The moments are taken about the first
+ * sample plus the mean deviation from it over up to 64 evenly spaced samples
+ * (exactly the value of a constant row) and summed with compensation
+ * (FP32 sums of 32-sample tiles, Kahan-added). The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress with that device
+ * current); make that first call before any stream capture. Later calls made
+ * outside stream capture look the address up again, so a cudaDeviceReset
+ * between calls is harmless; a call under capture uses the address of the
+ * last call outside it, so do not reset the device between those. Every call
+ * shares the array: calls that overlap on the GPU (other streams, other
+ * threads) race and corrupt each other's results; serialise them. Each call
+ * writes every scratch entry it reads, so nothing needs clearing between
+ * calls. No cudaMalloc, cudaFree or allocating library routine is called. */
 tvbx_status tvbx_fc_noalloc(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,
                             float* fc_out, float* chi, float* mean_fc, void* cuda_stream);
 

@@ -24,6 +24,11 @@ OBJ_DIR = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]
+# The integrator's translation units: no multiply-add contraction anywhere in
+# the compiler, so that one set per thread and two sets in a packed register
+# pair round every operation identically (the code writes each intended
+# fused multiply-add explicitly).
+FILE_FLAGS = {"sim.cu": ["-fmad=false"], "sim_fast.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -38,8 +43,10 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [
-        os.path.abspath(__file__)]
+    """Every file the library is built from: sources, headers (.h and .cuh) and
+    this script."""
+    return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+        glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:
@@ -59,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list | None =
 
     def compile_one(src):
         obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *flags, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

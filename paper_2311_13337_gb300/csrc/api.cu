@@ -157,6 +157,30 @@ DevModel to_device_model(const tvbx_model& m, double dt)
     d.ou_b = (float)(m.sigma_OU * sqrt(dt) / m.tau_OU);
     d.ou_mu = (float)m.mu_OU;
     d.dt = (float)dt;
+    // reduced transfer function (tau_e == tau_i): constants of the algebra in
+    // model_device.cuh, computed in double and rounded once
+    d.reduced = m.tau_e == m.tau_i ? 1 : 0;
+    const double qe = m.Q_e * m.tau_e, qi = m.Q_i * m.tau_i, dE = m.E_e - m.E_i;
+    const double be = qi * dE, bi = -qe * dE, v1 = 1.0 / m.dmu0, s1 = 1.0 / m.dsig0, z1 = m.g_L / m.dtau0;
+    d.tau = (float)m.tau_e;
+    d.ke = (float)(qe * qe); d.ki = (float)(qi * qi);
+    d.dE = (float)dE;
+    d.be = (float)be; d.bi = (float)bi; d.two_be = (float)(2.0 * be); d.two_bi = (float)(2.0 * bi);
+    d.gLEe = (float)(m.g_L * m.E_e);
+    d.v0 = (float)((m.E_e - m.mu0) * v1); d.v1 = (float)v1;
+    d.v1qe = (float)(v1 * qe); d.v1qi = (float)(v1 * qi); d.v1be = (float)(v1 * be); d.two_v1 = (float)(2.0 * v1);
+    d.s0 = (float)(m.sig0 * s1); d.s1 = (float)s1; d.s1h = (float)(0.5 * s1); d.s1q = (float)(0.25 * s1);
+    d.z0 = (float)((m.tau_e * m.g_L / m.C_m - m.tau0) / m.dtau0); d.z1 = (float)z1;
+    d.z1sq = (float)(z1 * z1); d.two_z1 = (float)(2.0 * z1);
+    d.sq_e = (float)(2.0 * qe * qe * be * be); d.sq_i = (float)(2.0 * qi * qi * bi * bi);
+    // d = theta - mu_V with mu_V = mu0 + dmu0 V, over sqrt(2)
+    const double rs2 = 1.0 / sqrt(2.0);
+    for (int i = 0; i < 10; ++i) {
+        const double ce = m.P_e[i] - (i == 0 ? m.mu0 : 0.0) - (i == 1 ? m.dmu0 : 0.0);
+        const double ci = m.P_i[i] - (i == 0 ? m.mu0 : 0.0) - (i == 1 ? m.dmu0 : 0.0);
+        d.cp_e[i] = (float)(ce * rs2);
+        d.cp_i[i] = (float)(ci * rs2);
+    }
     return d;
 }
 
@@ -360,9 +384,10 @@ tvbx_status create_common(const double* weights, const double* tract_mm, int32_t
     return TVBX_OK;
 }
 
-// Ring row stride: a group's sets rounded up to a multiple of 32 floats, so
-// that every tile's row segment starts on a 16-byte (indeed 128-byte) boundary.
-int64_t ring_stride(size_t sets) { return ((int64_t)sets + 31) / 32 * 32; }
+// Ring row stride: a group's sets rounded up to a multiple of 96 floats, so
+// that every tile of 8, 12, 16 or 32 sets lies inside the row and its row
+// segment starts on a 16-byte boundary (the alignment TMA bulk copies need).
+int64_t ring_stride(size_t sets) { return ((int64_t)sets + 95) / 96 * 96; }
 
 // Build the speed groups for dt: delays, CSR and ring depth per distinct speed.
 tvbx_status build_groups(tvbx_sweep* h, double dt, std::vector<Group>& groups)
@@ -575,16 +600,21 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
         // batch: the batch's body and tile width
         if (direct_body) variant = -2;
     } else if (c.kernel == TVBX_KERNEL_AUTO) {
-        // preference order from measurement on the 32,768-set, 68-region sweep;
-        // connectomes too large for the prefetch buffer take the register tiles
-        for (int v : {1, 0, 2, 3})
-            if (sim_fast_fits(v, N, nnz_max)) { variant = v; break; }
+        // preference order from measurement on the 32,768-set, 68-region sweep
+        // (the packed kernels, slower there, need the reduced transfer
+        // function, tau_e == tau_i); connectomes too large for the prefetch
+        // buffer take the register tiles
+        const bool reduced = h->model.tau_e == h->model.tau_i;
+        for (int v : {15, 0, 1, 2, 3, 9, 8})
+            if ((reduced || !sim_fast_packed(v)) && sim_fast_fits(v, N, nnz_max)) { variant = v; break; }
         if (variant < 0 && sim_direct_pb(N) > 0) variant = -2;
     } else if (c.kernel == TVBX_KERNEL_DIRECT) {
         if (sim_direct_pb(N) == 0) return fail(TVBX_E_UNSUPPORTED, "register-tile kernel: too many regions (%d)", N);
         variant = -2;
     } else if (c.kernel != TVBX_KERNEL_GENERAL) {
         variant = c.kernel - TVBX_KERNEL_PREFETCH;
+        if (sim_fast_packed(variant) && h->model.tau_e != h->model.tau_i)
+            return fail(TVBX_E_UNSUPPORTED, "packed kernel %d needs tau_e == tau_i", c.kernel);
         if (!sim_fast_fits(variant, N, nnz_max))
             return fail(TVBX_E_UNSUPPORTED, "prefetch kernel %d does not fit %d regions / %d weights", c.kernel, N,
                         nnz_max);
@@ -825,7 +855,7 @@ tvbx_status tvbx_run_continue(tvbx_sweep* h, int64_t n_steps, int32_t transient_
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr char CKPT_MAGIC[8] = {'T', 'V', 'B', 'X', 'C', 'K', 'P', '1'};
+constexpr char CKPT_MAGIC[8] = {'T', 'V', 'B', 'X', 'C', 'K', 'P', '2'};   // 2: the state holds the W carries
 
 struct CkptHeader {
     char magic[8];

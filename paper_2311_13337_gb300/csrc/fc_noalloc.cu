@@ -10,8 +10,8 @@
 // that loads it.
 //
 // The scratch is a file-scope __device__ array. Its address in host code is a
-// host-side stand-in, so the device address is obtained once per device with
-// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// host-side stand-in, so the device address is obtained with
+// cudaGetSymbolAddress (with the device current) and passed to the kernels.
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -34,16 +34,24 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 float* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set up on the
-// first call per device).
-cudaError_t scratch_address(float** out)
+// Device address of the scratch array on the current device. The first call
+// on a device looks it up; every later call made outside stream capture
+// looks it up again (cheap), so the address stays valid when the device has
+// been reset and the module reloaded since. Under capture the cached address
+// is used.
+cudaError_t scratch_address(cudaStream_t s, float** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();   // the query's own error is not the call's
+        cs = cudaStreamCaptureStatusActive;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_fc_noalloc_scratch);
         if (e != cudaSuccess) return e;
@@ -55,12 +63,24 @@ cudaError_t scratch_address(float** out)
 
 }  // namespace
 
-// Per set: shift m_k = x_k(0) (any shift is exact), then the upper triangle
-// of G[k][j] = sum_t (x_k - m_k)(x_j - m_j) and s[k] = sum_t (x_k - m_k) into
-// scratch [P][N*N + N] (both triangles written). One CTA of 512 threads per
+// Per set: shift m_k = x_k(0) plus the mean of x_k - x_k(0) over up to 64
+// evenly spaced samples (any shift is exact; one near the mean keeps the
+// centred sums small, and a constant row gets exactly zero variance), then the
+// upper triangle of G[k][j] = sum_t (x_k - m_k)(x_j - m_j) and
+// s[k] = sum_t (x_k - m_k) into scratch [P][N*N + N] (both triangles
+// written). The sums are compensated: each 32-sample tile is summed in FP32
+// and the tile sums are added with a Kahan carry. One CTA of 512 threads per
 // set, up to 8 (k <= j) pairs per thread; the series is [T][N][P].
 constexpr int NOALLOC_THREADS = 512;
 constexpr int NOALLOC_PAIRS = 8;
+
+static __device__ __forceinline__ void noalloc_kahan(float& s, float& c, float v)
+{
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
 
 __global__ void __launch_bounds__(NOALLOC_THREADS)
 fc_noalloc_moments_kernel(const float* __restrict__ X, int32_t N, int64_t P, int64_t T, float* __restrict__ scratch)
@@ -71,9 +91,16 @@ fc_noalloc_moments_kernel(const float* __restrict__ X, int32_t N, int64_t P, int
     float* tile = sh + N;
     const int64_t NP = (int64_t)N * P;
     const int n_tri = N * (N + 1) / 2;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) shift[k] = X[(int64_t)k * P + p];
+    const int ns = (int)(T < 64 ? T : 64);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        // x(0) plus the mean deviation from it: exactly x(0) for a constant row
+        const float x0 = X[(int64_t)k * P + p];
+        float m = 0.0f;
+        for (int i = 0; i < ns; ++i) m += X[(i * T / ns) * NP + (int64_t)k * P + p] - x0;
+        shift[k] = x0 + m / (float)ns;
+    }
     int pk[NOALLOC_PAIRS], pj[NOALLOC_PAIRS];
-    float acc[NOALLOC_PAIRS];
+    float acc[NOALLOC_PAIRS], cmp[NOALLOC_PAIRS];
 #pragma unroll
     for (int c = 0; c < NOALLOC_PAIRS; ++c) {
         int r = threadIdx.x + c * NOALLOC_THREADS, k = 0;
@@ -85,8 +112,9 @@ fc_noalloc_moments_kernel(const float* __restrict__ X, int32_t N, int64_t P, int
             pk[c] = pj[c] = -1;
         }
         acc[c] = 0.0f;
+        cmp[c] = 0.0f;
     }
-    float rs = 0.0f;
+    float rs = 0.0f, rc = 0.0f;
     __syncthreads();
     for (int64_t t0 = 0; t0 < T; t0 += 32) {
         const int len = (int)(T - t0 < 32 ? T - t0 : 32);
@@ -95,12 +123,19 @@ fc_noalloc_moments_kernel(const float* __restrict__ X, int32_t N, int64_t P, int
             tile[i] = X[(t0 + tt) * NP + (int64_t)k * P + p] - shift[k];
         }
         __syncthreads();
+        float part[NOALLOC_PAIRS];
+#pragma unroll
+        for (int c = 0; c < NOALLOC_PAIRS; ++c) part[c] = 0.0f;
+        float prs = 0.0f;
         for (int tt = 0; tt < len; ++tt) {
 #pragma unroll
             for (int c = 0; c < NOALLOC_PAIRS; ++c)
-                if (pk[c] >= 0) acc[c] = fmaf(tile[tt * N + pk[c]], tile[tt * N + pj[c]], acc[c]);
-            if (threadIdx.x < N) rs += tile[tt * N + threadIdx.x];
+                if (pk[c] >= 0) part[c] = fmaf(tile[tt * N + pk[c]], tile[tt * N + pj[c]], part[c]);
+            if (threadIdx.x < N) prs += tile[tt * N + threadIdx.x];
         }
+#pragma unroll
+        for (int c = 0; c < NOALLOC_PAIRS; ++c) noalloc_kahan(acc[c], cmp[c], part[c]);
+        noalloc_kahan(rs, rc, prs);
         __syncthreads();
     }
     float* out = scratch + p * (int64_t)(N * N + N);
@@ -184,10 +219,10 @@ extern "C" tvbx_status tvbx_fc_noalloc(const float* series, int32_t n_regions, i
                                  "floats; split the sets into calls of at most %lld",
                                  (long long)need, (long long)FC_NOALLOC_FLOATS,
                                  (long long)(FC_NOALLOC_FLOATS / ((int64_t)n_regions * n_regions + n_regions)));
-    float* scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
-    if (e != cudaSuccess) return report_error(TVBX_E_CUDA, "scratch address: %s", cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    float* scratch = nullptr;
+    cudaError_t e = scratch_address(s, &scratch);
+    if (e != cudaSuccess) return report_error(TVBX_E_CUDA, "scratch address: %s", cudaGetErrorString(e));
     const size_t sm1 = sizeof(float) * ((size_t)n_regions + 32 * (size_t)n_regions);
     note_launch();
     fc_noalloc_moments_kernel<<<(unsigned)n_sets, NOALLOC_THREADS, sm1, s>>>(series, n_regions, n_sets, n_samples, scratch);

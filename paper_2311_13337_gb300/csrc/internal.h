@@ -17,10 +17,11 @@ tvbx_status report_error(tvbx_status code, const char* fmt, ...);
 
 // Number of per-(set, region) state words kept across steps and chunks:
 // E, I, C_ee, C_ei, C_ii, W_e, W_i, OU, then the temporal-average accumulators
-// of E and I, then compensated running sums (sum, carry) of the E and I samples.
+// of E and I, then compensated running sums (sum, carry) of the E and I
+// samples, then the carries of the compensated Euler updates of W_e and W_i.
 enum {
     SV_E = 0, SV_I, SV_CEE, SV_CEI, SV_CII, SV_WE, SV_WI, SV_OU,
-    SV_ACC_E, SV_ACC_I, SV_SUM_E, SV_CMP_E, SV_SUM_I, SV_CMP_I, SV_COUNT
+    SV_ACC_E, SV_ACC_I, SV_SUM_E, SV_CMP_E, SV_SUM_I, SV_CMP_I, SV_CWE, SV_CWI, SV_COUNT
 };
 
 // Model constants prepared for the device (FP32, with derived quantities).
@@ -41,6 +42,19 @@ struct DevModel {
     // OU (Eq. 4) by Euler-Maruyama: OU' = OU + ou_a (mu - OU) + ou_b xi
     float ou_a, ou_b, ou_mu;
     float dt;
+    // Reduced transfer function (model_device.cuh), used when tau_e == tau_i
+    int32_t reduced;         // 1: tau_e == tau_i
+    float tau;               // the common synaptic time constant
+    float ke, ki;            // qe^2, qi^2
+    float dE;                // E_e - E_i
+    float be, bi;            // qi dE, -qe dE
+    float two_be, two_bi;
+    float gLEe;              // g_L E_e
+    float v0, v1, v1qe, v1qi, v1be, two_v1;   // V = v0 - v1 a_e / mu_G
+    float s0, s1, s1h, s1q;  // S = s1 sigma_V - s0, s1 / 2, s1 / 4
+    float z0, z1, z1sq, two_z1;               // Z = z0 + z1 / mu_G
+    float sq_e, sq_i;        // 2 ke be^2, 2 ki bi^2
+    float cp_e[10], cp_i[10];  // (V_thre - mu_V) / sqrt(2) as a polynomial in (V, S, Z)
 };
 
 // One speed group: sets sharing a delay matrix and a ring buffer.
@@ -110,6 +124,7 @@ cudaError_t launch_tf_eval(const DevModel& m, int pop, int64_t n, const float* x
 cudaError_t launch_sim_fast(const SimArgs& a, int variant, int32_t n_tiles, int nnz_max, cudaStream_t s);
 bool sim_fast_fits(int variant, int N, int nnz_max);
 int sim_fast_pb(int variant);
+bool sim_fast_packed(int variant);   // FP32x2 kernel (needs tau_e == tau_i)
 int sim_fast_variants();
 size_t sim_fast_smem_bytes(int variant, int N, int nnz);
 int sim_threads(int N, int pb);

@@ -114,7 +114,7 @@ static __device__ __forceinline__ void chunk_body(const SimArgs& a, const TileDe
         sp = load_set_params(a.prm, P, p);
         pn = (uint32_t)(a.p_offset + a.ext_index[p]);
     }
-    uint32_t flags = 0u;
+    Track<float> trk = track_init<float>();
     const int64_t slot_stride = (int64_t)N * grp.stride;
     const float inv_ts = 1.0f / (float)a.ts;
 
@@ -137,10 +137,11 @@ static __device__ __forceinline__ void chunk_body(const SimArgs& a, const TileDe
                     acc = fmaf(__ldg(grp.w + e), grp.ring[sl * slot_stride + (int64_t)j * grp.stride + qg], acc);
                 }
                 float* sk = st + k * pb + q;
-                PairState x{sk[SV_E * npairs], sk[SV_I * npairs], sk[SV_CEE * npairs], sk[SV_CEI * npairs],
-                            sk[SV_CII * npairs], sk[SV_WE * npairs], sk[SV_WI * npairs]};
+                PairState x{sk[SV_E * npairs],   sk[SV_I * npairs],  sk[SV_CEE * npairs],
+                            sk[SV_CEI * npairs], sk[SV_CII * npairs], sk[SV_WE * npairs],
+                            sk[SV_WI * npairs],  sk[SV_CWE * npairs], sk[SV_CWI * npairs]};
                 const float OU = a.noise_per_set ? sk[SV_OU * npairs] : a.ou_table[(int64_t)s * N + k];
-                euler_step(m, sp, x, acc, OU, flags);
+                pair_step(m, sp, x, acc, OU, trk);
                 if (a.noise_per_set) {
                     const float xi = std_normal(a.seed, (uint32_t)n, (uint32_t)k, pn);
                     sk[SV_OU * npairs] = fmaf(m.ou_a, m.ou_mu - OU, fmaf(m.ou_b, xi, OU));
@@ -148,6 +149,7 @@ static __device__ __forceinline__ void chunk_body(const SimArgs& a, const TileDe
                 sk[SV_E * npairs] = x.E; sk[SV_I * npairs] = x.I;
                 sk[SV_CEE * npairs] = x.Cee; sk[SV_CEI * npairs] = x.Cei; sk[SV_CII * npairs] = x.Cii;
                 sk[SV_WE * npairs] = x.We; sk[SV_WI * npairs] = x.Wi;
+                sk[SV_CWE * npairs] = x.cWe; sk[SV_CWI * npairs] = x.cWi;
                 grp.ring[slot_w * slot_stride + (int64_t)k * grp.stride + qg] = x.E;
 
                 // temporal average: block mean of ts consecutive post-step states
@@ -176,6 +178,7 @@ static __device__ __forceinline__ void chunk_body(const SimArgs& a, const TileDe
         const int v = i / npairs, rem = i - v * npairs, k = rem / pb, qq = rem - k * pb;
         if (qq < tile.nq) a.state[((int64_t)v * N + k) * P + grp.p_base + tile.q0 + qq] = st[i];
     }
+    const uint32_t flags = track_flags(m, trk, 0);
     if (active && flags) atomicOr(a.status + p, flags);
 }
 
@@ -296,13 +299,17 @@ __global__ void tf_eval_kernel(DevModel m, int pop, int64_t n, const float* __re
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        // F, its gradient, mu_V and the contracted term from the integrator's
+        // code; the Hessian from the full second-order jets
         const float* P = pop == 0 ? m.P_e : m.P_i;
         float F[6], muV;
         transfer_x(m, P, E_L[i], W[i], x_e[i], x_i[i], F, muV);
-        for (int c = 0; c < 6; ++c) out[i * 8 + c] = F[c];
+        for (int c = 3; c < 6; ++c) out[i * 8 + c] = F[c];
+        float L[4];
+        transfer_integrator(m, pop, E_L[i], W[i], x_e[i], x_i[i], C ? C[3 * i] : 0.0f, C ? C[3 * i + 1] : 0.0f,
+                            C ? C[3 * i + 2] : 0.0f, L, muV);
+        for (int c = 0; c < 3; ++c) out[i * 8 + c] = L[c];
         out[i * 8 + 6] = muV;
-        float L[4] = {0.f, 0.f, 0.f, 0.f};
-        if (C) transfer_x_lap(m, P, E_L[i], W[i], x_e[i], x_i[i], C[3 * i], C[3 * i + 1], C[3 * i + 2], L, muV);
         out[i * 8 + 7] = L[3];
     }
 }

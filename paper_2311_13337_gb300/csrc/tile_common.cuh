@@ -30,7 +30,7 @@ struct ThreadPairs {
     float ou[SPT * RPT], accE[SPT * RPT], accI[SPT * RPT];
     uint32_t pn[SPT];     // noise counter of each set (per-set noise)
     bool act[SPT];        // set exists in the tile
-    uint32_t flags[SPT];  // status bits gathered during the chunk
+    Track<float> trk[SPT];  // status events gathered during the chunk
 };
 
 // Tile geometry of the calling thread.
@@ -66,7 +66,7 @@ static __device__ __forceinline__ void load_pairs(const SimArgs& a, const TileDe
     for (int s = 0; s < SPT; ++s) {
         tp.act[s] = ts.qt + s < tile.nq;
         tp.pn[s] = tp.act[s] ? (uint32_t)(a.p_offset + a.ext_index[ts.col0 + ts.qt + s]) : 0u;
-        tp.flags[s] = 0u;
+        tp.trk[s] = track_init<float>();
     }
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
@@ -76,14 +76,14 @@ static __device__ __forceinline__ void load_pairs(const SimArgs& a, const TileDe
             const int i = r * SPT + s;
             if (tp.act[s] && k < N) {
                 const int64_t o = (int64_t)k * a.P + ts.col0 + ts.qt + s;
-                tp.x[i] = PairState{a.state[SV_E * NP + o], a.state[SV_I * NP + o], a.state[SV_CEE * NP + o],
+                tp.x[i] = PairState{a.state[SV_E * NP + o],   a.state[SV_I * NP + o],   a.state[SV_CEE * NP + o],
                                     a.state[SV_CEI * NP + o], a.state[SV_CII * NP + o], a.state[SV_WE * NP + o],
-                                    a.state[SV_WI * NP + o]};
+                                    a.state[SV_WI * NP + o],  a.state[SV_CWE * NP + o], a.state[SV_CWI * NP + o]};
                 tp.ou[i] = a.state[SV_OU * NP + o];
                 tp.accE[i] = a.state[SV_ACC_E * NP + o];
                 tp.accI[i] = a.state[SV_ACC_I * NP + o];
             } else {
-                tp.x[i] = PairState{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                tp.x[i] = PairState{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 tp.ou[i] = tp.accE[i] = tp.accI[i] = 0.0f;
             }
         }
@@ -111,6 +111,8 @@ static __device__ __forceinline__ void store_pairs(const SimArgs& a, const Threa
                 a.state[SV_CII * NP + o] = tp.x[i].Cii;
                 a.state[SV_WE * NP + o] = tp.x[i].We;
                 a.state[SV_WI * NP + o] = tp.x[i].Wi;
+                a.state[SV_CWE * NP + o] = tp.x[i].cWe;
+                a.state[SV_CWI * NP + o] = tp.x[i].cWi;
                 a.state[SV_OU * NP + o] = tp.ou[i];
                 a.state[SV_ACC_E * NP + o] = tp.accE[i];
                 a.state[SV_ACC_I * NP + o] = tp.accI[i];
@@ -118,8 +120,10 @@ static __device__ __forceinline__ void store_pairs(const SimArgs& a, const Threa
         }
     }
 #pragma unroll
-    for (int s = 0; s < SPT; ++s)
-        if (tp.act[s] && tp.flags[s]) atomicOr(a.status + ts.col0 + ts.qt + s, tp.flags[s]);
+    for (int s = 0; s < SPT; ++s) {
+        const uint32_t f = track_flags(a.m, tp.trk[s], 0);
+        if (tp.act[s] && f) atomicOr(a.status + ts.col0 + ts.qt + s, f);
+    }
 }
 
 // Coupling sums sum_j u_kj E_j(n - d_kj) of the thread's pairs: delayed
@@ -160,6 +164,15 @@ static __device__ __forceinline__ void coupling_sums(const ThreadSlot& ts, int N
     }
 }
 
+// OU value of one set advanced by one step with its own normal (per-set
+// noise), out of line to keep it off the integration's register budget.
+static __device__ __noinline__ float ou_advance(const DevModel& m, uint64_t seed, uint32_t n, uint32_t k, uint32_t p,
+                                                float OU)
+{
+    const float xi = std_normal(seed, n, k, p);
+    return fmaf(m.ou_a, m.ou_mu - OU, fmaf(m.ou_b, xi, OU));
+}
+
 // One Euler step of the thread's pairs, the ring write of E(n+1) and the
 // temporal average. ring_slot_w points at slot (n+1) mod H, column 0 of the
 // tile; s_prm is [11][PB] (PB = 0: the runtime width pb_rt).
@@ -178,20 +191,19 @@ static __device__ __forceinline__ void advance_pairs(const SimArgs& a, const Thr
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int k = ts.kr + r * ts.kstride;
+        // the shared OU value of region k at this step (one load for the thread's sets)
+        const float ou_k = (!a.noise_per_set && k < N) ? a.ou_table[(int64_t)step * N + k] : 0.0f;
 #pragma unroll
         for (int s = 0; s < SPT; ++s) {
             const int i = r * SPT + s;
             if (!(tp.act[s] && k < N)) continue;
-            const float OU = a.noise_per_set ? tp.ou[i] : a.ou_table[(int64_t)step * N + k];
+            const float OU = a.noise_per_set ? tp.ou[i] : ou_k;
             SetParams spv;
             float* f = reinterpret_cast<float*>(&spv);
 #pragma unroll
             for (int c = 0; c < 11; ++c) f[c] = s_prm[c * pbs + ts.qt + s];
-            euler_step(m, spv, tp.x[i], cpl[i], OU, tp.flags[s]);
-            if (a.noise_per_set) {
-                const float xi = std_normal(a.seed, (uint32_t)n, (uint32_t)k, tp.pn[s]);
-                tp.ou[i] = fmaf(m.ou_a, m.ou_mu - OU, fmaf(m.ou_b, xi, OU));
-            }
+            pair_step(m, spv, tp.x[i], cpl[i], OU, tp.trk[s]);
+            if (a.noise_per_set) tp.ou[i] = ou_advance(m, a.seed, (uint32_t)n, (uint32_t)k, tp.pn[s], OU);
             ring_slot_w[(int64_t)k * row_stride + ts.qt + s] = tp.x[i].E;
             tp.accE[i] += tp.x[i].E;
             tp.accI[i] += tp.x[i].I;

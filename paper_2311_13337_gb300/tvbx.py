@@ -280,7 +280,8 @@ def sweep_info(h) -> tuple[int, int, int]:
 
 
 KERNEL_AUTO, KERNEL_GENERAL, KERNEL_PREFETCH, KERNEL_DIRECT = 0, 1, 2, 100
-N_PREFETCH_VARIANTS = 8
+N_PREFETCH_VARIANTS = 17
+PACKED_VARIANTS = (8, 9, 10, 11)   # FP32x2 kernels: need tau_e == tau_i
 
 
 def _run_cfg(dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
@@ -398,19 +399,37 @@ def fc(h, fc_out=None, fcd_out=None, fcd_window=0, fcd_step=0, precision=FC_FP32
 def fc_noalloc(series, n_regions: int, n_sets: int, n_samples: int, fc_out, chi=None, mean_fc=None, stream=None):
     """FC with no device allocation (scratch in a fixed array reserved by the
     library). series: CUDA tensor [n_samples][n_regions][n_sets]; outputs are
-    CUDA tensors. Calls that overlap on the GPU race; see tvbx.h."""
+    CUDA tensors. Calls that overlap on the GPU race; see tvbx.h.
+
+    Every buffer must be a contiguous float32 tensor on the current CUDA
+    device holding at least the elements the sizes imply (series
+    n_samples * n_regions * n_sets, fc_out n_sets * n_regions^2, chi and
+    mean_fc n_sets); anything else raises ValueError before the library is
+    called, so a wrong buffer never reaches a kernel."""
+    import torch
     sp = None
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    n_regions, n_sets, n_samples = int(n_regions), int(n_sets), int(n_samples)
+    need = {"series": n_samples * n_regions * n_sets, "fc_out": n_sets * n_regions * n_regions,
+            "chi": n_sets, "mean_fc": n_sets}
     args = []
-    for x in (series, fc_out, chi, mean_fc):
+    for name, x in (("series", series), ("fc_out", fc_out), ("chi", chi), ("mean_fc", mean_fc)):
         if x is None:
+            if name in ("series", "fc_out"):
+                raise ValueError(f"tvbx_fc_noalloc: {name} is required")
             args.append(None)
-        else:
-            ptr, mem = _out_ptr(x)
-            if mem != MEM_DEVICE:
-                raise ValueError("tvbx_fc_noalloc takes device buffers only")
-            args.append(ptr)
+            continue
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise ValueError("tvbx_fc_noalloc takes device buffers only (CUDA tensors)")
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError(f"tvbx_fc_noalloc: {name} must be a contiguous float32 tensor")
+        if x.device.index != torch.cuda.current_device():
+            raise ValueError(f"tvbx_fc_noalloc: {name} is on cuda:{x.device.index}, "
+                             f"the current device is cuda:{torch.cuda.current_device()}")
+        if x.numel() < need[name]:
+            raise ValueError(f"tvbx_fc_noalloc: {name} holds {x.numel()} elements, the sizes need {need[name]}")
+        args.append(ctypes.c_void_p(x.data_ptr()))
     _check(load().tvbx_fc_noalloc(args[0], int(n_regions), int(n_sets), int(n_samples), args[1], args[2], args[3],
                                   sp), "tvbx_fc_noalloc")
 
@@ -455,7 +474,8 @@ def transfer_function(pop: int, x_e, x_i, W, E_L, C=None, model: Model | None = 
 
 
 KERNEL_NAMES = {KERNEL_GENERAL: "sim_chunk_kernel", KERNEL_DIRECT: "sim_direct_kernel"}
-KERNEL_NAMES.update({KERNEL_PREFETCH + v: ("sim_bulk_kernel" if v in (4, 5) else "sim_fast_kernel") + f" (variant {v})"
+KERNEL_NAMES.update({KERNEL_PREFETCH + v: ("sim_pack_kernel" if v in PACKED_VARIANTS else "sim_tma_kernel" if 12 <= v <= 14 else
+                                          "sim_bulk_kernel" if v in (4, 5) else "sim_fast_kernel") + f" (variant {v})"
                      for v in range(N_PREFETCH_VARIANTS)})
 
 

@@ -64,3 +64,33 @@ def stable_sets(ref_E, pert_E, samples=200, rtol=1e-5):
     engine can be held to 1e-3."""
     d = rel_err(pert_E[..., :samples], ref_E[..., :samples])
     return d.reshape(d.shape[0], -1).max(axis=1) <= rtol
+
+
+THETA_SYNC = 0.5
+
+
+def label_disagreements(chi_gpu, chi_ref, chi_pert, finite, theta=THETA_SYNC):
+    """Synchrony labels (chi >= theta) of the engine against the oracle on the
+    finite sets. A disagreement is attributed to the threshold when the
+    oracle's own chi is closer to theta than the spread between the oracle
+    and its 1e-7-perturbed run (the label is not determined at float32
+    resolution there). Returns (finite sets, disagreements, attributed)."""
+    chi_gpu, chi_ref = np.asarray(chi_gpu, np.float64), np.asarray(chi_ref, np.float64)
+    fin = np.asarray(finite, bool)
+    dis = fin & ((chi_gpu >= theta) != (chi_ref >= theta))
+    if chi_pert is None:
+        near = np.zeros_like(dis)
+    else:
+        near = np.abs(chi_ref - theta) <= np.abs(chi_ref - np.asarray(chi_pert, np.float64))
+    return int(fin.sum()), int(dis.sum()), int((dis & near).sum())
+
+
+def assert_labels(chi_gpu, chi_ref, chi_pert, finite, min_frac=0.99):
+    """The labels agree on at least min_frac of the finite sets, and every
+    disagreement is attributed to the threshold (see label_disagreements)."""
+    n, d, a = label_disagreements(chi_gpu, chi_ref, chi_pert, finite)
+    msg = f"labels: {n} finite sets, {d} disagreements, {a} within the oracle's own spread of theta"
+    print(msg)
+    assert d == a, msg
+    assert n == 0 or (n - d) / n >= min_frac, msg
+    return n, d, a

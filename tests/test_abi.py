@@ -273,3 +273,22 @@ def test_header_compiles_as_plain_c_and_cpp(tmp_path, compiler, std, suffix):
     r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
                         "-c", str(src), "-o", str(tmp_path / "probe.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_header_edits_make_the_library_stale(lib):
+    """Every header of the engine, the device headers (.cuh) included, is a
+    build dependency: a header newer than the library makes up_to_date()
+    false, so the next build recompiles."""
+    from paper_2311_13337_gb300 import build
+    assert build.up_to_date()
+    headers = [d for d in build._deps() if d.endswith((".cuh", ".h"))]
+    assert any(h.endswith("model_device.cuh") for h in headers)
+    t_lib = os.path.getmtime(build.LIB)
+    for h in headers:
+        st = os.stat(h)
+        try:
+            os.utime(h, (st.st_atime, t_lib + 10.0))
+            assert not build.up_to_date(), h
+        finally:
+            os.utime(h, (st.st_atime, st.st_mtime))
+    assert build.up_to_date()

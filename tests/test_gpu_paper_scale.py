@@ -1,7 +1,7 @@
 """Parity at the paper-scale workload: g(16) x b_e(16) x E_L_i(16) x
 tau_w_e(8) = 32,768 sets, 68 regions, 5 s (50,000 steps), run on the GPU in
-the configuration the benchmark times. 256 seeded random sets are integrated
-one by one by the FP64 oracle, twice: as given, and with every rate update
+the configuration the benchmark times. 1,024 seeded random sets are
+integrated one by one by the FP64 oracle, twice: as given, and with every rate update
 perturbed by a relative 1e-7 (float32 resolution; the time constant T scaled
 by 1 + 1e-7) to measure how sensitive each set is by itself.
 
@@ -10,12 +10,17 @@ there the FP64 trajectory moves far under the 1e-7 perturbation, so the
 engine is held to that spread. On the well-conditioned sets (no clamp,
 divergence or non-finite event, and a relative sensitivity below 1e-5 over
 the compared window) the parity tolerances apply: trajectories
-within 1e-3 over the first 200 ms, mean rates within 1%, FC within 0.05, and
-the synchrony label on >= 99% of the finite sets."""
+within 1e-3 over the first 200 ms, and, where the oracle's own perturbed run
+leaves them within a tenth of the tolerance, mean rates within 1% and FC
+within 0.05 over the whole 5 s; and
+the synchrony label on >= 99% of the finite sets, every disagreement within
+the oracle's own spread of the threshold (|chi - 0.5| below the change of chi
+under the perturbation)."""
 import numpy as np
 import pytest
 
-from gpu_common import (BAD, FC_ATOL, PERTURBATION, RATE_RTOL, TRAJ_RTOL, conditioned_sets, rel_err, require_gpu,
+from gpu_common import (BAD, FC_ATOL, PERTURBATION, RATE_RTOL, TRAJ_RTOL, assert_labels, conditioned_sets, rel_err,
+                        require_gpu,
                         stable_sets, well_conditioned)
 from paper_2311_13337_gb300 import synth
 
@@ -34,7 +39,7 @@ def test_paper_scale_sweep_sampled(oracle):
     fc = sw.fc()
 
     rng = np.random.default_rng(2024)
-    idx = np.sort(rng.choice(P, 256, replace=False))
+    idx = np.sort(rng.choice(P, 1024, replace=False))
     E = np.stack([sw.series_window(int(p), 1, 0, 200)[0] for p in idx])
     prm = oracle.expand_grid(cfg["axes"])[idx]
     args = (W, L, prm, cfg["dt"], cfg["n_steps"], cfg["tavg_steps"], cfg["seed"])
@@ -52,14 +57,23 @@ def test_paper_scale_sweep_sampled(oracle):
     # FP64 trajectory that the persistent 1e-7 perturbation moves by < 1e-5):
     # parity tolerances
     wc = conditioned_sets(st, ref["status"]) & stable_sets(ref["E"], pert["E"])
-    assert wc.sum() >= 100
+    assert wc.sum() >= 300
     err = rel_err(E[wc], ref["E"][wc, :, :200])
     where = np.unravel_index(err.argmax(), err.shape)
     assert err.max() <= TRAJ_RTOL, \
         f"trajectory error {err.max():.3g} at set {idx[np.where(wc)[0][where[0]]]} region {where[1]} sample {where[2]}"
+    # quantities over the whole 5 s (mean rates, FC) on the sets where they
+    # are determined at float32 resolution: the oracle's own perturbed run
+    # moves them by less than a tenth of the tolerance (a set can stay stable
+    # over the first 200 ms and turn chaotic later)
     for key in ("mean_e_hz", "mean_i_hz"):
-        assert np.all(np.abs(s[key][idx][wc] - rs[key][wc]) <= RATE_RTOL * np.abs(rs[key][wc]) + 1e-6), key
+        det = wc & (np.abs(rp[key] - rs[key]) <= 0.1 * RATE_RTOL * np.abs(rs[key]) + 1e-6)
+        assert det.sum() >= 0.5 * wc.sum(), (key, det.sum(), wc.sum())
+        err = np.abs(s[key][idx][det] - rs[key][det])
+        assert np.all(err <= RATE_RTOL * np.abs(rs[key][det]) + 1e-6), (key, (err / np.abs(rs[key][det])).max())
     good = wc & well_conditioned(ref["E"])
+    good &= np.abs(rp["fc"] - rs["fc"]).max(axis=(1, 2)) <= 0.1 * FC_ATOL
+    assert good.sum() >= 100
     assert np.abs(fc[idx][good] - rs["fc"][good]).max() <= FC_ATOL
 
     # every finite set: rate agreement at least as good as the oracle's own
@@ -68,5 +82,4 @@ def test_paper_scale_sweep_sampled(oracle):
     within_g = np.abs(s["mean_e_hz"][idx][ok] - rs["mean_e_hz"][ok]) <= RATE_RTOL * np.abs(rs["mean_e_hz"][ok]) + 1e-6
     within_p = np.abs(rp["mean_e_hz"][ok] - rs["mean_e_hz"][ok]) <= RATE_RTOL * np.abs(rs["mean_e_hz"][ok]) + 1e-6
     assert within_g.mean() >= within_p.mean() - 0.05
-    agree = (s["chi"][idx][ok] >= 0.5) == rs["sync"][ok]
-    assert agree.mean() >= 0.99
+    assert_labels(s["chi"][idx], rs["chi"], rp["chi"], ok, 0.99)

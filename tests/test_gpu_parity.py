@@ -9,7 +9,7 @@ delays, g = 0, shard invariance, non-finite parameters, and edge cases."""
 import numpy as np
 import pytest
 
-from gpu_common import (BAD, FC_ATOL, PERTURBATION, RATE_RTOL, TRAJ_RTOL, conditioned_sets, rel_err,
+from gpu_common import (BAD, FC_ATOL, PERTURBATION, RATE_RTOL, TRAJ_RTOL, assert_labels, conditioned_sets, rel_err,
                         require_gpu, stable_sets, well_conditioned)
 from paper_2311_13337_gb300 import synth
 
@@ -70,7 +70,7 @@ def test_first_steps_every_state_variable(tvbx, oracle, conn, n_steps):
         assert np.all(np.abs(st[:, v] - ref[:, v]) <= 1e-4 * np.abs(ref[:, v]) + 1e-6 * scale), v
 
 
-def _compare_sweep(tvbx_sw, ref, oracle, traj_samples=200, label_frac=1.0, pert=None):
+def _compare_sweep(tvbx_sw, ref, oracle, traj_samples=200, label_frac=0.99, pert=None):
     """Parity tolerances on the well-conditioned sets (no clamp, divergence
     or non-finite event on either side, and, given a perturbed oracle run, an
     FP64 trajectory that is stable under it); labels on every finite set."""
@@ -91,8 +91,11 @@ def _compare_sweep(tvbx_sw, ref, oracle, traj_samples=200, label_frac=1.0, pert=
         if good.any():
             assert np.abs(fc[good] - rs["fc"][good]).max() <= FC_ATOL
     fin = ((s["status"] & BAD) == 0) & ((ref["status"] & BAD) == 0)
-    agree = (s["chi"][fin] >= 0.5) == rs["sync"][fin]
-    assert agree.mean() >= label_frac
+    chi_pert = None
+    if pert is not None:
+        fin &= (pert["status"] & BAD) == 0
+        chi_pert = oracle.summary(pert["E"], pert["I"])["chi"]
+    assert_labels(s["chi"], rs["chi"], chi_pert, fin, label_frac)
     return E, s, fc, rs, wc
 
 
@@ -122,9 +125,11 @@ def test_rich_dynamics_noise_speeds_ragged(tvbx, oracle, conn):
     ref = oracle.simulate(oracle.make_model(), W, L, pts, DT, 8000, 10, 5, noise_per_set=True, p_offset=3)
     pert = oracle.simulate(oracle.make_model(PERTURBATION), W, L, pts, DT, 8000, 10, 5,
                            noise_per_set=True, p_offset=3)
-    E, s, fc, rs, wc = _compare_sweep(sw, ref, oracle, label_frac=15 / 17, pert=pert)
+    E, s, fc, rs, wc = _compare_sweep(sw, ref, oracle, pert=pert)
     assert wc.sum() >= 3
-    # all kernels agree (general vs prefetch variants, where they fit)
+    # all kernels agree: every prefetch variant (one set per thread or two in
+    # packed FP32x2 registers, cp.async or TMA copies) bit for bit with the
+    # automatic choice; the general kernel within 1e-5
     base = E
     for kern in [tvbx.KERNEL_GENERAL] + [tvbx.KERNEL_PREFETCH + v for v in range(tvbx.N_PREFETCH_VARIANTS)]:
         try:
@@ -132,7 +137,10 @@ def test_rich_dynamics_noise_speeds_ragged(tvbx, oracle, conn):
         except tvbx.TvbxError as e:
             assert e.code == -7   # variant does not fit this sweep
             continue
-        assert np.allclose(sw.series(), base, rtol=1e-5, atol=1e-9, equal_nan=True), kern
+        if kern == tvbx.KERNEL_GENERAL:
+            assert np.allclose(sw.series(), base, rtol=1e-5, atol=1e-9, equal_nan=True), kern
+        else:
+            assert np.array_equal(sw.series(), base, equal_nan=True), kern
 
 
 def test_zero_delays_and_uncoupled_regions(tvbx, oracle, conn):
@@ -167,7 +175,7 @@ def test_table4_ten_axis_sweep(tvbx, oracle, conn):
     assert np.array_equal(full.series()[pick], sub.series(), equal_nan=True)
     ref = oracle.simulate(oracle.make_model(), W, L, pts[pick], DT, 3000, 10, 6)
     pert = oracle.simulate(oracle.make_model(PERTURBATION), W, L, pts[pick], DT, 3000, 10, 6)
-    _compare_sweep(sub, ref, oracle, label_frac=0.9, pert=pert)
+    _compare_sweep(sub, ref, oracle, pert=pert)
 
 
 def test_shard_invariance(tvbx, conn):
