@@ -586,6 +586,9 @@ static cudaError_t launch_fast(const SimArgs& a, int variant, int32_t n_tiles, i
     else kern = sim_fast_kernel<PB, SPT, RPT, MAXT, MINB, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // all of the unified L1 as shared memory, so that MINB CTAs fit on an SM
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
     note_launch();
     kern<<<n_tiles, threads, smem, s>>>(a);
     return cudaGetLastError();

@@ -1,9 +1,9 @@
 """Run one sized sweep of the paper-scale grid for profiling.
 
-  python -m paper_2311_13337_gb300.profile_case --sets 8192 --n-steps 1000 --chunk 500 [--fc]
-  python -m paper_2311_13337_gb300.profile_case --fc-series --sets 4096 --samples 5000 --fc-precision bf16x3
-  python -m paper_2311_13337_gb300.profile_case --analysis --sets 4096 --samples 5000
-  python -m paper_2311_13337_gb300.profile_case --bold --sets 8192 --samples 10000
+  python profile_case.py --sets 8192 --n-steps 1000 --chunk 500 [--fc]
+  python profile_case.py --fc-series --sets 4096 --samples 5000 --fc-precision bf16x3
+  python profile_case.py --analysis --sets 4096 --samples 5000
+  python profile_case.py --bold --sets 8192 --samples 10000
 
 Takes the first `--sets` sets of the 32,768-set grid (68 regions, v 4 m/s),
 integrates `--n-steps` steps in launches of `--chunk` steps and optionally
@@ -23,7 +23,7 @@ import os
 import sys
 import time
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -138,7 +138,7 @@ def test_binding_has_every_function_its_callers_use():
     import re
     from paper_2311_13337_gb300 import tvbx
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    files = ["bench.py", "__graft_entry__.py", os.path.join("paper_2311_13337_gb300", "profile_case.py")]
+    files = ["bench.py", "__graft_entry__.py", "profile_case.py"]
     used = set()
     for f in files:
         used |= set(re.findall(r"\btvbx\.([A-Za-z_][A-Za-z_0-9]*)", open(os.path.join(root, f)).read()))
