@@ -29,6 +29,7 @@
 #include "alloc.h"
 #include "internal.h"
 #include "gemm_simt.cuh"
+#include "gemm_tc.cuh"
 #include "model_device.cuh"
 #include "tvbx.h"
 
@@ -303,6 +304,7 @@ struct tvbx_surrogate {
     Buf<float> act, dz0, dz1, tb;        // work buffers
     Buf<float> xin, yin, ymean, yvar, cand, score, cbox;
     Buf<double> loss;
+    Buf<uint32_t> err;                   // device error word of the tensor-core products
     int work_rows = 0;
 };
 
@@ -346,6 +348,22 @@ cudaError_t ensure_work(tvbx_surrogate* s, int rows)
     return cudaSuccess;
 }
 
+// try_wait polls before a tensor-core product's wait gives up (seconds).
+constexpr uint32_t kTcWait = 1u << 26;
+
+// After a stream synchronisation: TVBX_E_TIMEOUT if a bounded wait of a
+// tensor-core product expired since the last check (the word is cleared).
+tvbx_status check_tc_error(tvbx_surrogate* s, const char* what)
+{
+    uint32_t w = 0;
+    SCK(cudaMemcpy(&w, s->err.p, sizeof w, cudaMemcpyDeviceToHost), what);
+    if (w) {
+        SCK(cudaMemset(s->err.p, 0, sizeof w), what);
+        return report_error(TVBX_E_TIMEOUT, "%s: a tensor-core product's bounded wait expired", what);
+    }
+    return TVBX_OK;
+}
+
 // Forward pass of rows already placed in the input activations.
 cudaError_t forward(tvbx_surrogate* s, int rows)
 {
@@ -362,8 +380,8 @@ cudaError_t forward(tvbx_surrogate* s, int rows)
         g.bias = s->p.p + s->b_off[l];
         g.bias_mem = s->n_par;
         g.M = rows; g.N = O; g.K = I;
-        cudaError_t e = (l + 1 < L) ? gemm<float, __nv_bfloat16, EPI_BIAS_RELU>(g, s->E, s->stream)
-                                    : gemm<float, __nv_bfloat16, EPI_BIAS>(g, s->E, s->stream);
+        cudaError_t e = (l + 1 < L) ? gemm_tc<float, __nv_bfloat16, EPI_BIAS_RELU>(g, s->E, s->err.p, kTcWait, s->stream)
+                                    : gemm_tc<float, __nv_bfloat16, EPI_BIAS>(g, s->E, s->err.p, kTcWait, s->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -392,7 +410,7 @@ cudaError_t backward(tvbx_surrogate* s, int rows)
         gw.B = a_prev; gw.sbn = 1; gw.sbk = I; gw.b_mem = (int64_t)rows * I;
         gw.C = s->g.p + s->w_off[l]; gw.ldc = I; gw.c_mem = s->n_par;
         gw.M = O; gw.N = I; gw.K = rows;
-        if ((e = gemm<float, float, EPI_STORE>(gw, s->E, s->stream)) != cudaSuccess) return e;
+        if ((e = gemm_tc<float, float, EPI_STORE>(gw, s->E, s->err.p, kTcWait, s->stream)) != cudaSuccess) return e;
         // db_l
         {
             dim3 grid((O + 31) / 32, s->E);
@@ -408,7 +426,7 @@ cudaError_t backward(tvbx_surrogate* s, int rows)
         gd.C = dzn; gd.ldc = I; gd.c_mem = (int64_t)rows * I;
         gd.mask = a_prev; gd.ldm = I; gd.mask_mem = (int64_t)rows * I;
         gd.M = rows; gd.N = I; gd.K = O;
-        if ((e = gemm<float, __nv_bfloat16, EPI_MASK>(gd, s->E, s->stream)) != cudaSuccess) return e;
+        if ((e = gemm_tc<float, __nv_bfloat16, EPI_MASK>(gd, s->E, s->err.p, kTcWait, s->stream)) != cudaSuccess) return e;
         std::swap(dz, dzn);
     }
     return cudaSuccess;
@@ -493,7 +511,8 @@ tvbx_status tvbx_surrogate_create(const tvbx_surrogate_cfg* cfg, tvbx_surrogate*
     if ((e = s->p.ensure(np)) || (e = s->m1.ensure(np)) || (e = s->m2.ensure(np)) || (e = s->g.ensure(np)) ||
         (e = s->pb.ensure(np)) || (e = s->decay.ensure((size_t)s->n_par)) || (e = s->seg.ensure(seg.size())) ||
         (e = s->lo.ensure(s->n_in)) || (e = s->hi.ensure(s->n_in)) || (e = s->mu.ensure(s->n_out)) ||
-        (e = s->sd.ensure(s->n_out)) || (e = s->loss.ensure(s->E)))
+        (e = s->sd.ensure(s->n_out)) || (e = s->loss.ensure(s->E)) || (e = s->err.ensure(1)) ||
+        (e = cudaMemsetAsync(s->err.p, 0, sizeof(uint32_t), s->stream)))
         return fail_destroy(e, "surrogate parameters");
     std::vector<float> lo(cfg->in_lo, cfg->in_lo + s->n_in), hi(cfg->in_hi, cfg->in_hi + s->n_in);
     std::vector<float> mu(s->n_out, 0.0f), sd(s->n_out, 1.0f);
@@ -591,6 +610,7 @@ tvbx_status tvbx_surrogate_gradients(tvbx_surrogate* s, int32_t member, const fl
                             cudaMemcpyDeviceToHost, s->stream),
             "gradients");
     SCK(cudaStreamSynchronize(s->stream), "gradients");
+    if (tvbx_status st = check_tc_error(s, "gradients")) return st;
     if (loss) *loss = (float)hl[member];
     return TVBX_OK;
 }
@@ -649,6 +669,7 @@ tvbx_status tvbx_surrogate_train(tvbx_surrogate* s, int32_t mem, const float* X,
         }
     }
     SCK(cudaStreamSynchronize(s->stream), "train");
+    if (tvbx_status st = check_tc_error(s, "train")) return st;
     return TVBX_OK;
 }
 
@@ -701,6 +722,7 @@ tvbx_status tvbx_surrogate_predict(tvbx_surrogate* s, int32_t mem, const float* 
             SCK(cudaMemcpyAsync(y_var, dv, sizeof(float) * n * s->n_out, cudaMemcpyDeviceToHost, s->stream), "predict");
     }
     SCK(cudaStreamSynchronize(s->stream), "predict");
+    if (tvbx_status st = check_tc_error(s, "predict")) return st;
     return TVBX_OK;
 }
 
@@ -747,6 +769,7 @@ tvbx_status tvbx_surrogate_propose(tvbx_surrogate* s, int64_t n_candidates, uint
     SCK(cudaMemcpyAsync(score.data(), s->score.p, sizeof(float) * n_candidates, cudaMemcpyDeviceToHost, s->stream),
         "scores");
     SCK(cudaStreamSynchronize(s->stream), "scores");
+    if (tvbx_status st = check_tc_error(s, "propose")) return st;
     std::vector<int64_t> idx((size_t)n_candidates);
     std::iota(idx.begin(), idx.end(), 0);
     auto better = [&](int64_t a, int64_t b) { return score[a] > score[b] || (score[a] == score[b] && a < b); };
