@@ -1090,13 +1090,17 @@ def run_batch_engine(args):
 
 # ---------------------------------------------------------------------------
 # Surrogate-guided exploration: an ensemble MLP (5 -> 256 x 3 -> 24) trained
-# on the paper-scale sweep's outputs (+ a speed-augmented set) maps the
-# sync/async boundary of a (g, b_e) slice; the simulator checks the proposals.
-SUR_METRIC = "speedup of the time-to-map of a regime boundary on 1 GB300 (surrogate-guided vs plain dense sweep)"
+# on the paper-scale sweep's outputs (+ a speed-augmented set) maps regime
+# boundaries of a (g, b_e) slice; the simulator judges every proposal.
+SUR_METRIC = ("speedup of the time-to-map of a regime boundary at >= 99% label agreement on 1 GB300 "
+              "(surrogate-guided vs the cheapest plain sweep that reaches it)")
 REGIME_HZ = 50.0
+SYNC_CHI = 0.5
 SUR_IN = ("g", "b_e", "tau_w_e", "E_L_i", "speed")
 SUR_LO = np.array([0.0, 0.0, 100.0, -80.0, 1.0])
 SUR_HI = np.array([0.9, 120.0, 1000.0, -60.0, 16.0])
+FC_TOL = 0.05          # FC entries within 0.05 absolute count as equal FC
+MAP_TARGET = 0.01      # a map with >= 99% of its points labelled as the dense sweep labels them
 
 
 def run_surrogate_engine(args):
@@ -1105,11 +1109,12 @@ def run_surrogate_engine(args):
     dev = torch.device("cuda", 0)
     import __graft_entry__ as ge
     ge.build()
-    from paper_2311_13337_gb300 import synth, tvbx
+    from paper_2311_13337_gb300 import guided, synth, tvbx
     W, L = synth.connectome(68)
     mdl = tvbx.make_model()
     rng = np.random.Generator(np.random.PCG64(2311))
     steps, N = 50000, 68
+    iu = torch.triu_indices(N, N, 1, device=dev)
     timings = {}
 
     def rows(X):
@@ -1118,16 +1123,18 @@ def run_surrogate_engine(args):
             pts[:, tvbx.AXES.index(name)] = X[:, c]
         return pts
 
-    def simulate(X, want_fc=True):
+    def simulate(X, want_fc=True, seed=1):
         """Summary (and device FC) of 5-s simulations of the rows of X."""
         sw = tvbx.Sweep(W, L, points=rows(np.asarray(X, dtype=np.float64)))
         P = sw.n_sets
-        tvbx.run(sw.h, dt_ms=0.1, n_steps=steps, tavg_steps=10, seed=1)
-        fc = torch.empty((P, N, N), dtype=torch.float32, device=dev)
-        tvbx.fc(sw.h, fc, precision=tvbx.FC_BF16X3)
+        tvbx.run(sw.h, dt_ms=0.1, n_steps=steps, tavg_steps=10, seed=seed)
+        fc = None
+        if want_fc:
+            fc = torch.empty((P, N, N), dtype=torch.float32, device=dev)
+            tvbx.fc(sw.h, fc, precision=tvbx.FC_BF16X3)
         out = sw.summary()
         sw.close()
-        out["fc"] = fc if want_fc else None
+        out["fc"] = fc
         return out
 
     def targets(out, mean, comps):
@@ -1135,150 +1142,228 @@ def run_surrogate_engine(args):
         y = np.column_stack([out["mean_e_hz"], out["mean_i_hz"], out["chi"], out["mean_fc"], coef])
         return y.astype(np.float32)
 
-    # training data: the paper-scale grid (v = 4 m/s) and a speed-augmented random set
+    def timed(fn, *a, **k):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn(*a, **k)
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    # libraries that load on first use (cuBLAS for the FC reconstructions) are loaded before any timing
+    (torch.ones((8, 8), device=dev) @ torch.ones((8, 8), device=dev)).sum().item()
+
+    # one-off 1: training data, the paper-scale grid (v = 4 m/s) and a speed-augmented random set
     g = np.linspace(0.0, 0.9, 16); be = np.linspace(0.0, 120.0, 16)
     eli = np.linspace(-80.0, -60.0, 16); tw = np.linspace(100.0, 1000.0, 8)
     grid = np.array(np.meshgrid(g, be, eli, tw, indexing="ij")).reshape(4, -1).T      # last axis fastest
     X_grid = np.column_stack([grid[:, 0], grid[:, 1], grid[:, 3], grid[:, 2], np.full(len(grid), 4.0)])
     X_aug = SUR_LO + (SUR_HI - SUR_LO) * rng.uniform(size=(8192, 5))
     X_aug[:, 4] = rng.choice([1.0, 2.0, 4.0, 8.0, 16.0], size=8192)
-    t0 = time.perf_counter()
-    d_grid = simulate(X_grid)
-    d_aug = simulate(X_aug)
-    fc_all = torch.cat([d_grid["fc"], d_aug["fc"]])
-    ok = torch.isfinite(fc_all).all(dim=2).all(dim=1).cpu().numpy()
-    mean, comps, _, ev = tvbx.fc_pca(fc_all[torch.as_tensor(ok, device=dev)], n_comp=20, n_iter=40)
-    Y = np.concatenate([targets(d_grid, mean, comps), targets(d_aug, mean, comps)])
+
+    def make_data():
+        (d_grid, d_aug), timings["training_sweeps_s"] = timed(lambda: (simulate(X_grid), simulate(X_aug)))
+        fc_all = torch.cat([d_grid["fc"], d_aug["fc"]])
+        ok = torch.isfinite(fc_all).all(dim=2).all(dim=1).cpu().numpy()
+        (mean, comps, _, ev), timings["fc_pca_s"] = timed(
+            tvbx.fc_pca, fc_all[torch.as_tensor(ok, device=dev)], n_comp=20, n_iter=40)
+        Y, timings["targets_s"] = timed(lambda: np.concatenate([targets(d_grid, mean, comps),
+                                                                 targets(d_aug, mean, comps)]))
+        return ok, mean, comps, ev, Y
+    (ok, mean, comps, ev, Y), timings["training_data_s"] = timed(make_data)
     X = np.concatenate([X_grid, X_aug]).astype(np.float32)
     keep = ok & np.all(np.isfinite(Y), axis=1)
-    # the regime boundary to map: low activity vs the high-activity
-    # (paroxysmal, ~190 Hz) state, label = mean E rate >= REGIME_HZ; the
-    # slice: the (E_L_i, tau_w_e) slice of the grid whose high-activity
-    # fraction over its 16 x 16 (g, b_e) points is closest to 1/2
-    rate_grid = Y[:len(X_grid), 0].reshape(16, 16, 16, 8)           # g, b_e, E_L_i, tau_w_e
-    finite = np.isfinite(rate_grid).mean(axis=(0, 1))
-    frac = np.nanmean(rate_grid >= REGIME_HZ, axis=(0, 1))
-    # slices where the integration stays finite (no divergence) for >= 95% of the points
-    ie, it = np.unravel_index(np.argmin(np.where(finite >= 0.95, np.abs(frac - 0.5), np.inf)), frac.shape)
-    slice_eli, slice_tw, slice_frac = float(eli[ie]), float(tw[it]), float(frac[ie, it])
-    slice_finite = float(finite[ie, it])
-    torch.cuda.synchronize()
-    timings["training_data_s"] = time.perf_counter() - t0
-    del fc_all, d_grid, d_aug
 
+    # one-off 2: training (cosine learning-rate decay, one library call per epoch)
     sur = tvbx.Surrogate(SUR_LO, SUR_HI, 24, n_hidden=256, n_layers=3, n_members=4, seed=7)
-    t0 = time.perf_counter()
-    losses = sur.train(X[keep], Y[keep], epochs=args.sur_epochs, batch=1024, lr=1e-3, weight_decay=1e-4)
-    timings["train_s"] = time.perf_counter() - t0
 
-    # surrogate error on held-out simulations (v = 4 and v != 4 separately)
+    def train():
+        out = []
+        E = args.sur_epochs
+        for e in range(E):
+            lr = 2e-5 + 0.5 * (2e-3 - 2e-5) * (1.0 + np.cos(np.pi * e / max(1, E - 1)))
+            out.append(sur.train(X[keep], Y[keep], epochs=1, batch=1024, lr=float(lr), weight_decay=1e-4,
+                                 keep_scale=e > 0)[0])
+        return out
+    losses, timings["train_s"] = timed(train)
+    one_off = timings["training_data_s"] + timings["train_s"]
+
+    # surrogate error on held-out simulations (v = 4 and v != 4 separately), and the
+    # same simulations with another noise seed: how far the outputs move with the noise alone
     X_te = SUR_LO + (SUR_HI - SUR_LO) * rng.uniform(size=(2048, 5))
     X_te[:1024, 4] = 4.0
     X_te[1024:, 4] = rng.choice([1.0, 2.0, 8.0, 16.0], size=1024)
-    d_te = simulate(X_te)
-    Y_te = targets(d_te, mean, comps)
+    Y_te = targets(simulate(X_te), mean, comps)
+    Y_te2 = targets(simulate(X_te, seed=2), mean, comps)
     P_te = sur.predict(X_te.astype(np.float32))
     sd = np.nanstd(Y[keep], axis=0)
+
+    def rmse(A, B):
+        fin = np.all(np.isfinite(A), axis=1) & np.all(np.isfinite(B), axis=1)
+        r = (A[fin] - B[fin]) / sd
+        return {k: round(float(np.sqrt(np.mean(r[:, s] ** 2))), 4) for k, s in
+                (("mean_e", slice(0, 1)), ("mean_i", slice(1, 2)), ("chi", slice(2, 3)), ("mean_fc", slice(3, 4)),
+                 ("pca", slice(4, 24)))}
     err = {}
     for name, sl in (("v4", slice(0, 1024)), ("v_other", slice(1024, 2048))):
-        fin = np.all(np.isfinite(Y_te[sl]), axis=1)
-        r = (P_te[sl][fin] - Y_te[sl][fin]) / sd
-        err[name] = {"regime_label_agreement": float(np.mean((P_te[sl][fin, 0] >= REGIME_HZ) ==
-                                                            (Y_te[sl][fin, 0] >= REGIME_HZ))),
-                     "rmse_over_sd": {"mean_e": float(np.sqrt(np.mean(r[:, 0] ** 2))),
-                                      "mean_i": float(np.sqrt(np.mean(r[:, 1] ** 2))),
-                                      "chi": float(np.sqrt(np.mean(r[:, 2] ** 2))),
-                                      "mean_fc": float(np.sqrt(np.mean(r[:, 3] ** 2))),
-                                      "pca": float(np.sqrt(np.mean(r[:, 4:] ** 2)))},
-                     "sync_label_agreement": float(np.mean((P_te[sl][fin, 2] >= 0.5) == (Y_te[sl][fin, 2] >= 0.5)))}
+        fin = np.isfinite(Y_te[sl, 0])
+        err[name] = {"rmse_over_sd": rmse(P_te[sl], Y_te[sl]), "noise_seed_rmse_over_sd": rmse(Y_te2[sl], Y_te[sl]),
+                     "regime_label_agreement": float(np.mean((P_te[sl][fin, 0] >= REGIME_HZ) ==
+                                                             (Y_te[sl][fin, 0] >= REGIME_HZ))),
+                     "sync_label_agreement": float(np.mean((P_te[sl][fin, 2] >= SYNC_CHI) ==
+                                                           (Y_te[sl][fin, 2] >= SYNC_CHI)))}
 
-    # the map: sync/async labels on a 128 x 128 (g, b_e) slice at the chosen (tau_w_e, E_L_i), v 4
-    side = 128
+    # the slices to map: the (E_L_i, tau_w_e) slice of the training grid whose labelled
+    # fraction over its finite (g, b_e) points is closest to 1/2 (>= 90% of them finite)
+    Yg = Y[:len(X_grid)]
+    fin4 = np.isfinite(Yg[:, 0]).reshape(16, 16, 16, 8)                  # g, b_e, E_L_i, tau_w_e
+
+    def pick(lab4):
+        nf = fin4.sum(axis=(0, 1))
+        frac = (lab4 & fin4).sum(axis=(0, 1)) / np.maximum(nf, 1)
+        ie, it = np.unravel_index(np.argmin(np.where(nf >= 0.9 * 256, np.abs(frac - 0.5), np.inf)), frac.shape)
+        return float(eli[ie]), float(tw[it]), float(frac[ie, it]), float(nf[ie, it] / 256.0)
+
+    side, B = args.sur_side, 4096
     gg, bb = np.meshgrid(np.linspace(0.0, 0.9, side), np.linspace(0.0, 120.0, side), indexing="ij")
-    X_map = np.column_stack([gg.ravel(), bb.ravel(), np.full(side * side, slice_tw), np.full(side * side, slice_eli),
-                             np.full(side * side, 4.0)]).astype(np.float32)
-    box = (np.array([0.0, 0.0, slice_tw, slice_eli, 4.0]), np.array([0.9, 120.0, slice_tw, slice_eli, 4.0]))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    d_map = simulate(X_map, want_fc=False)
-    truth = d_map["mean_e_hz"] >= REGIME_HZ
-    t_dense = time.perf_counter() - t0
-    map_nan = float(np.mean(~np.isfinite(d_map["mean_e_hz"])))
-    map_status = {str(bit): float(np.mean((d_map["status"] & bit) != 0)) for bit in (1, 2, 4, 8, 16)}
-    # speckle of the dense map: points whose label disagrees with the majority of their 8 neighbours
-    tg = truth.reshape(side, side).astype(np.int32)
-    pad = np.pad(tg, 1, mode="edge")
-    nb = sum(np.roll(np.roll(pad, dx, 0), dy, 1)[1:-1, 1:-1] for dx in (-1, 0, 1) for dy in (-1, 0, 1)) - tg
-    speckle = float(np.mean((nb >= 5) != (tg == 1)))
 
-    # plain coarse sweep with one round's budget (64 x 64), nearest-neighbour map
-    cs = 64
-    cg, cb = np.meshgrid(np.linspace(0.0, 0.9, cs), np.linspace(0.0, 120.0, cs), indexing="ij")
-    X_c = np.column_stack([cg.ravel(), cb.ravel(), np.full(cs * cs, 500.0), np.full(cs * cs, -64.0),
-                           np.full(cs * cs, 4.0)])
-    t0 = time.perf_counter()
-    lab_c = (simulate(X_c, want_fc=False)["mean_e_hz"] >= REGIME_HZ).reshape(cs, cs)
-    t_coarse = time.perf_counter() - t0
-    ig = np.rint(np.linspace(0, cs - 1, side)).astype(int)
-    err_coarse = float(np.mean(lab_c[np.ix_(ig, ig)].ravel() != truth))
+    def map_study(o, thr, s_eli, s_tw):
+        X_map = np.column_stack([gg.ravel(), bb.ravel(), np.full(side * side, s_tw), np.full(side * side, s_eli),
+                                 np.full(side * side, 4.0)]).astype(np.float32)
 
-    # surrogate-guided: predict the map, then batches of proposals checked by the simulator
-    rounds = []
-    t0 = time.perf_counter()
-    lab = sur.predict(X_map)[:, 0] >= REGIME_HZ
-    t_pred = time.perf_counter() - t0
-    rounds.append({"round": 0, "map_error": float(np.mean(lab != truth)), "elapsed_s": t_pred, "simulations": 0})
-    elapsed, n_sims = t_pred, 0
-    Xr, Yr = X[keep], Y[keep]
-    for r in range(1, args.sur_rounds + 1):
-        t0 = time.perf_counter()
-        props, _ = sur.propose(1 << 20, 4096, output=0, threshold=REGIME_HZ, var_weight=1.0, round=r, box=box)
-        d_p = simulate(props)
-        prop_status = {str(bit): float(np.mean((d_p["status"] & bit) != 0)) for bit in (1, 2, 4, 8, 16)}
-        prop_sample = props[:3].tolist()
-        Y_p = targets(d_p, mean, comps)
-        pred_p = sur.predict(props)[:, 0]
-        rate_ok = np.isfinite(Y_p[:, 0])
-        fin = np.all(np.isfinite(Y_p), axis=1)
-        judged = float(np.mean((pred_p[rate_ok] >= REGIME_HZ) == (Y_p[rate_ok, 0] >= REGIME_HZ)))
-        if fin.any():
-            sub = rng.choice(len(Xr), min(len(Xr), 4 * int(fin.sum())), replace=False)
-            Xf = np.concatenate([props[fin], Xr[sub]])
-            Yf = np.concatenate([Y_p[fin], Yr[sub]])
-            sur.train(Xf, Yf, epochs=args.sur_finetune_epochs, batch=512, lr=3e-4, weight_decay=1e-4)
-        lab = sur.predict(X_map)[:, 0] >= REGIME_HZ
-        torch.cuda.synchronize()
-        elapsed += time.perf_counter() - t0
-        n_sims += 4096
-        Xr, Yr = np.concatenate([Xr, props[fin]]), np.concatenate([Yr, Y_p[fin]])
-        rounds.append({"round": r, "map_error": float(np.mean(lab != truth)), "elapsed_s": elapsed,
-                       "simulations": n_sims, "proposal_label_agreement": judged,
-                       "proposals_with_finite_rate": int(rate_ok.sum()), "proposals_all_finite": int(fin.sum()),
-                       "proposal_status_bit_fractions": prop_status, "first_proposals": prop_sample})
-    reach = [x for x in rounds if x["map_error"] <= err_coarse]
-    t_guided = reach[0]["elapsed_s"] if reach else None
-    line = {"metric": SUR_METRIC, "value": (t_dense / t_guided) if t_guided else None, "unit": "x",
-            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1000.0 * (t_guided or elapsed),
+        def value(d):
+            return d["mean_e_hz"] if o == 0 else d["chi"]
+        d_map, t_dense = timed(simulate, X_map)
+        v_true = value(d_map)
+        tfin = np.isfinite(v_true)
+        truth = v_true >= thr
+        V_true = d_map["fc"][:, iu[0], iu[1]]
+        del d_map
+        vt_ok = torch.isfinite(V_true).all(dim=1)
+
+        def label_err(lab):     # over the points whose dense simulation stayed finite
+            return float(np.mean(lab[tfin] != truth[tfin]))
+
+        def fc_err(V):          # over the points whose dense FC is finite
+            d = (V - V_true)[vt_ok]
+            dmax = d.abs().amax(dim=1)
+            fin = torch.isfinite(dmax)
+            return {"within_tol_fraction": float((dmax <= FC_TOL).float().mean()),
+                    "rmse": float(torch.sqrt(torch.mean(d[fin] ** 2)))}
+
+        # the plain method: regular sweeps of the slice, nearest-neighbour maps; the dense one is the truth
+        plain = [{"side": side, "simulations": side * side, "s": t_dense, "label_error": 0.0, "fc": fc_err(V_true)}]
+        for cs in (16, 32, 64, 128, 192):
+            if cs >= side:
+                continue
+            cg, cb = np.meshgrid(np.linspace(0.0, 0.9, cs), np.linspace(0.0, 120.0, cs), indexing="ij")
+            Xc = np.column_stack([cg.ravel(), cb.ravel(), np.full(cs * cs, s_tw), np.full(cs * cs, s_eli),
+                                  np.full(cs * cs, 4.0)])
+            dc, tc = timed(simulate, Xc)
+            vc = value(dc)
+            Vc_all = dc["fc"][:, iu[0], iu[1]]
+            # nearest coarse point whose simulation stayed finite (label; FC)
+            nn_lab = guided.nearest_finite(cs, side, np.isfinite(vc))
+            nn_fc = guided.nearest_finite(cs, side, torch.isfinite(Vc_all).all(dim=1).cpu().numpy())
+            Vc = Vc_all[torch.as_tensor(nn_fc, device=dev)]
+            plain.append({"side": cs, "simulations": cs * cs, "s": tc, "label_error": label_err((vc >= thr)[nn_lab]),
+                          "fc": fc_err(Vc)})
+            del dc, Vc, Vc_all
+        plain.sort(key=lambda p: p["simulations"])
+
+        # the surrogate's map, then rounds of B judged proposals
+        def predict():
+            pm = sur.predict(X_map)
+            idx_all, sc_all = sur.rank(X_map, side * side, o, thr, var_weight=1.0)
+            score = np.empty(side * side, np.float32)
+            score[idx_all] = sc_all
+            return pm, score, mean + torch.as_tensor(pm[:, 4:], device=dev) @ comps
+        (pm, score_all, V_pred), t_pred = timed(predict)
+        lab_pred = pm[:, o] >= thr
+        judged = np.zeros(side * side, bool)
+        lab_sim, sim_ok, contra = judged.copy(), judged.copy(), judged.copy()
+        V_g = V_pred.clone()
+        rounds = [{"round": 0, "simulations": 0, "s": t_pred, "label_error": label_err(lab_pred), "fc": fc_err(V_pred)}]
+        el = t_pred
+        for r in range(1, args.sur_rounds + 1):
+            nb = min(B, int((~judged).sum()))
+            if nb == 0:
+                break
+
+            def one_round():
+                idx = guided.next_proposals(lambda k, ex: sur.rank(X_map, k, o, thr, var_weight=1.0, exclude=ex)[0],
+                                            judged, contra, score_all, nb, side)
+                d = simulate(X_map[idx])
+                v = value(d)
+                judged[idx] = True
+                sim_ok[idx] = np.isfinite(v)
+                lab_sim[idx] = v >= thr
+                contra[idx] = sim_ok[idx] & (lab_sim[idx] != lab_pred[idx])
+                V_g[torch.as_tensor(idx, device=dev)] = d["fc"][:, iu[0], iu[1]]
+                return guided.guided_labels(judged, lab_sim, sim_ok, lab_pred, side), int((~sim_ok[idx]).sum())
+            (lab, n_div), t = timed(one_round)
+            el += t
+            rounds.append({"round": r, "simulations": int(judged.sum()), "s": el, "label_error": label_err(lab),
+                           "fc": fc_err(V_g), "contradicted_predictions": int(contra.sum()),
+                           "proposals_diverged": n_div})
+
+        def t_plain(eps):
+            return min(p["s"] for p in plain if p["label_error"] <= eps)
+
+        def t_guided(eps):
+            return next((x["s"] for x in rounds if x["label_error"] <= eps), None)
+        tg = t_guided(MAP_TARGET)
+        res = {"slice": {"tau_w_e": s_tw, "E_L_i": s_eli, "speed": 4.0, "side": side},
+               "dense_labelled_fraction": float(truth[tfin].mean()), "dense_nonfinite_fraction": float(1 - tfin.mean()),
+               "plain": plain, "guided": rounds,
+               "at_99pct_agreement": {"plain_s": t_plain(MAP_TARGET), "guided_s": tg,
+                                      "speedup_per_map": (t_plain(MAP_TARGET) / tg) if tg else None,
+                                      "speedup_first_map_with_one_off": (t_plain(MAP_TARGET) / (tg + one_off))
+                                      if tg else None,
+                                      "speedup_one_off_over_128_slices": (t_plain(MAP_TARGET) / (tg + one_off / 128))
+                                      if tg else None}}
+        # FC: the guided map's FC (simulated where judged, the surrogate's 20-component
+        # reconstruction elsewhere) against the cheapest plain sweep whose FC map is as good
+        hit = next((x for x in rounds if x["label_error"] <= MAP_TARGET), None)
+        if hit:
+            f_g = hit["fc"]["within_tol_fraction"]
+            better = [p for p in plain if p["fc"]["within_tol_fraction"] >= f_g]
+            tp = min(p["s"] for p in better)
+            cheapest = min(plain, key=lambda p: p["s"])
+            # when even the coarsest plain sweep's FC map is better, the plain method could go
+            # coarser still: the ratio is then an upper bound on the surrogate's speedup
+            res["at_equal_fc_error"] = {"guided_fc_within_tol_fraction": f_g, "plain_s": tp, "guided_s": hit["s"],
+                                        "plain_side": next(p["side"] for p in better if p["s"] == tp),
+                                        "speedup_one_off_over_128_slices": tp / (hit["s"] + one_off / 128),
+                                        "is_upper_bound": bool(cheapest in better)}
+        del V_true, V_g, V_pred
+        return res
+
+    maps = {}
+    for name, o, thr, lab4 in (("regime", 0, REGIME_HZ, Yg[:, 0].reshape(16, 16, 16, 8) >= REGIME_HZ),
+                               ("sync", 2, SYNC_CHI, Yg[:, 2].reshape(16, 16, 16, 8) >= SYNC_CHI)):
+        s_eli, s_tw, frac, finite = pick(lab4)
+        maps[name] = map_study(o, thr, s_eli, s_tw)
+        maps[name]["slice"].update({"label": f"mean E >= {REGIME_HZ} Hz" if o == 0 else f"chi >= {SYNC_CHI}",
+                                    "grid_labelled_fraction": frac, "grid_finite_fraction": finite})
+        torch.cuda.empty_cache()
+    head = maps["sync"]["at_99pct_agreement"]
+    value = head["speedup_one_off_over_128_slices"]
+    t_step = (head["guided_s"] + one_off / 128) if head["guided_s"] else None
+    line = {"metric": SUR_METRIC, "value": value, "unit": "x",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1000.0 * t_step if t_step else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights / f32",
             "data": "synthetic",
-            "config": {"workload": "surrogate 5->256x3->24 (4 members) trained on the 32,768-set paper-scale sweep "
-                                   "(v 4) + 8,192 speed-augmented sets (5 s each); map: 128 x 128 (g, b_e) slice at "
-                                   "v 4 m/s and the (tau_w_e, E_L_i) of the grid closest to half high-activity "
-                                   "among the slices that stay finite for >= 95% of their points; "
-                                   "regime label: mean E rate >= 50 Hz (low activity vs the ~190 Hz state); "
-                                   "target map error = that of a plain 64 x 64 sweep", "training_sets": int(keep.sum()), "epochs": args.sur_epochs,
-                       "rounds": args.sur_rounds, "proposals_per_round": 4096},
-            "map_slice": {"tau_w_e": slice_tw, "E_L_i": slice_eli, "speed": 4.0, "label": f"mean E >= {REGIME_HZ} Hz",
-                          "grid_high_fraction": slice_frac, "grid_finite_fraction": slice_finite,
-                          "dense_high_fraction": float(truth.mean()),
-                          "dense_map_speckle": speckle, "dense_nonfinite_rate_fraction": map_nan,
-                          "dense_status_bit_fractions": map_status},
-            "time_to_map": {"plain_dense_s": t_dense, "plain_dense_simulations": side * side,
-                            "plain_coarse_s": t_coarse, "plain_coarse_map_error": err_coarse,
-                            "guided_s": t_guided, "rounds": rounds},
-            "one_off": {**timings, "final_train_loss": float(losses[-1]),
+            "config": {"workload": f"surrogate 5->256x3->24 (4 members) trained on the 32,768-set paper-scale sweep "
+                                   f"(v 4) + 8,192 speed-augmented sets (5 s each); maps: {side} x {side} (g, b_e) "
+                                   f"slices at v 4 m/s; sync/async boundary chi >= {SYNC_CHI} (headline) and "
+                                   f"activity boundary mean E >= {REGIME_HZ} Hz; rounds of {B} judged proposals; "
+                                   f"value: per map, the one-off cost (training data + training) shared by the 128 "
+                                   f"(E_L_i, tau_w_e) slices of the grid the same surrogate serves",
+                       "training_sets": int(keep.sum()), "epochs": args.sur_epochs, "rounds": args.sur_rounds,
+                       "proposals_per_round": B},
+            "one_off": {**timings, "total_s": one_off, "final_train_loss": float(losses[-1]),
                         "pca_eigenvalues": [float(x) for x in ev[:5]]},
-            "surrogate_error": err}
+            "maps": maps, "surrogate_error": err}
     print(json.dumps(line), flush=True)
     sur.close()
     return 0
@@ -1299,8 +1384,8 @@ def main():
     ap.add_argument("--batch-scale", type=float, default=0.25, help="duration scale of the uneven batch")
     ap.add_argument("--t4-seconds", type=float, default=1.0, help="biological seconds per set of the Table 4 grid")
     ap.add_argument("--sur-epochs", type=int, default=60)
-    ap.add_argument("--sur-rounds", type=int, default=3)
-    ap.add_argument("--sur-finetune-epochs", type=int, default=15)
+    ap.add_argument("--sur-rounds", type=int, default=8)
+    ap.add_argument("--sur-side", type=int, default=256, help="points per axis of the surrogate maps")
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch_engine(args)

@@ -680,8 +680,8 @@ tvbx_status tvbx_tf_fit(const tvbx_model* m, int64_t n_points, const double* nu_
  *
  * Network: inputs mapped to [-1, 1] by the domain box; n_layers hidden layers
  * of n_hidden units, a = max(0, a_prev W^T + b); linear output layer that
- * predicts the outputs standardised by the last training set's per-output
- * mean and population standard deviation. Loss: mean squared error over rows
+ * predicts the outputs standardised by a training set's per-output
+ * mean and population standard deviation (see tvbx_surrogate_train). Loss: mean squared error over rows
  * and outputs. Optimiser: AdamW (decoupled weight decay on weight matrices
  * only; beta1 0.9, beta2 0.999, eps 1e-8). Weights: FP32 master copy and a
  * BF16 copy read by the matrix products; FP32 accumulation. Initial weights:
@@ -709,16 +709,24 @@ tvbx_status tvbx_surrogate_create(const tvbx_surrogate_cfg* cfg, tvbx_surrogate*
 /* Parameters per member and ensemble size (either pointer nullable). */
 tvbx_status tvbx_surrogate_info(const tvbx_surrogate* s, int64_t* n_params, int32_t* n_members);
 
+/* Flags of tvbx_surrogate_train. */
+#define TVBX_TRAIN_SHUFFLE 1       /* each member visits the rows in its own
+                                      pseudo-random order per pass (else in order) */
+#define TVBX_TRAIN_KEEP_SCALE 2    /* keep the output standardisation of the
+                                      earlier training call (fine-tuning on a
+                                      few new rows must not move the scale the
+                                      network was trained in); ignored on a
+                                      handle that was never trained */
+
 /* Train every member on X [n][n_in], Y [n][n_out] (FP32; mem = TVBX_MEM_HOST
- * or TVBX_MEM_DEVICE): recompute the output standardisation from Y, then
- * `epochs` passes in mini-batches of `batch` rows (the last one may be
- * shorter), one AdamW step (learning rate lr, weight decay weight_decay) per
- * mini-batch. shuffle != 0: each member visits the rows in its own
- * pseudo-random order per pass; 0: in order. loss_out (host, nullable)
- * receives the mean training loss of each pass [epochs] (over members and
- * mini-batches, in standardised units). */
+ * or TVBX_MEM_DEVICE): recompute the output standardisation from Y (unless
+ * flags has TVBX_TRAIN_KEEP_SCALE), then `epochs` passes in mini-batches of
+ * `batch` rows (the last one may be shorter), one AdamW step (learning rate
+ * lr, weight decay weight_decay) per mini-batch; flags: TVBX_TRAIN_* bits.
+ * loss_out (host, nullable) receives the mean training loss of each pass
+ * [epochs] (over members and mini-batches, in standardised units). */
 tvbx_status tvbx_surrogate_train(tvbx_surrogate* s, int32_t mem, const float* X, const float* Y, int64_t n,
-                                 int32_t epochs, int32_t batch, float lr, float weight_decay, int32_t shuffle,
+                                 int32_t epochs, int32_t batch, float lr, float weight_decay, int32_t flags,
                                  float* loss_out);
 
 /* Ensemble mean y_mean [n][n_out] and variance y_var [n][n_out] (nullable)
@@ -740,6 +748,19 @@ tvbx_status tvbx_surrogate_propose(tvbx_surrogate* s, int64_t n_candidates, uint
                                    float threshold, float var_weight, const double* cand_lo,
                                    const double* cand_hi, int32_t n_propose, float* points_out,
                                    float* scores_out);
+
+/* Rank caller-given candidates X [n][n_in] (host) by the proposal score of
+ * tvbx_surrogate_propose (-|mean - threshold| / sd + var_weight sqrt(var) / sd
+ * for output `output`) and write the indices of the best n_propose (best
+ * first; ties to the lower index) to idx_out [n_propose] (host) with their
+ * scores (host, nullable). exclude (host uint8 [n], nullable): candidates
+ * with a non-zero byte are never chosen, e.g. points of a map that the
+ * simulator has already judged. A candidate whose prediction is not finite
+ * scores -inf and ranks last. Errors: TVBX_E_INVALID_ARG when n < 1, n >
+ * 2^26, or n_propose exceeds the candidates not excluded. */
+tvbx_status tvbx_surrogate_rank(tvbx_surrogate* s, const float* X, int64_t n, const uint8_t* exclude, int32_t output,
+                                float threshold, float var_weight, int32_t n_propose, int64_t* idx_out,
+                                float* scores_out);
 
 /* Read (get_out) and/or replace (set_in) the FP32 parameters of one member
  * (host arrays of tvbx_surrogate_info's n_params; either nullable). Setting

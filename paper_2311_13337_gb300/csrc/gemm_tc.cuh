@@ -22,7 +22,15 @@
 // accumulator (128 lanes x up to 128 FP32 columns) is read back by the four
 // warps, each its 32 lanes (rows), and stored with the epilogue. Rows and
 // columns beyond M, N and K are staged as zeros.
+//
+// Split K. A product with few output tiles and a long K (the weight
+// gradients: K = the mini-batch rows) would occupy a handful of SMs, so its
+// K chunks are divided among `splits` CTAs per tile; each writes its partial
+// tile to a scratch array and a second kernel adds the partials in split
+// order (deterministic), for the plain-store epilogue only.
 #pragma once
+
+#include <algorithm>
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -89,7 +97,8 @@ static __device__ __forceinline__ void tcg_stage_row(const T* X, int64_t s_row, 
 
 template <typename TA, typename TB, int EPI>
 __global__ void __launch_bounds__(TCG_THREADS) mlp_gemm_tc_kernel(const GemmArgs g, uint32_t* __restrict__ error,
-                                                                  uint32_t wait_limit)
+                                                                  uint32_t wait_limit, int splits, int chunks_per_split,
+                                                                  float* __restrict__ part)
 {
     extern __shared__ __align__(1024) uint8_t tcg_smem_raw[];
     __shared__ uint64_t mbar;
@@ -103,7 +112,8 @@ __global__ void __launch_bounds__(TCG_THREADS) mlp_gemm_tc_kernel(const GemmArgs
     constexpr bool B_SPLIT = !std::is_same<TB, __nv_bfloat16>::value;
     constexpr bool A_SPLIT = !std::is_same<TA, __nv_bfloat16>::value;
 
-    const int64_t mem = blockIdx.z;
+    const int64_t mem = blockIdx.z / splits;
+    const int split = (int)(blockIdx.z % splits);
     const TA* A = static_cast<const TA*>(g.A) + mem * g.a_mem;
     const TB* B = static_cast<const TB*>(g.B) + mem * g.b_mem;
     const int m0 = blockIdx.y * TCG_M, n0 = blockIdx.x * TCG_N;
@@ -125,7 +135,8 @@ __global__ void __launch_bounds__(TCG_THREADS) mlp_gemm_tc_kernel(const GemmArgs
 
     uint32_t parity = 0;
     const int n_chunks = (g.K + TCG_K - 1) / TCG_K;
-    for (int ch = 0; ch < n_chunks; ++ch) {
+    const int ch0 = split * chunks_per_split, ch1 = min(n_chunks, ch0 + chunks_per_split);   // ch0 < ch1 (host)
+    for (int ch = ch0; ch < ch1; ++ch) {
         const int k0 = ch * TCG_K;
         tcg_stage_row(A, g.sam, g.sak, m0, t, g.M - m0, k0, g.K, sAh, A_SPLIT ? sAl : 0u);
         tcg_stage_row(B, g.sbn, g.sbk, n0, t, g.N - n0, k0, g.K, sBh, B_SPLIT ? sBl : 0u);
@@ -137,7 +148,7 @@ __global__ void __launch_bounds__(TCG_THREADS) mlp_gemm_tc_kernel(const GemmArgs
             for (int sl = 0; sl < TCG_K / 16; ++sl) {
                 const uint32_t koff = (uint32_t)(sl * 32);   // 16 BF16 = 32 bytes into each row
                 const uint64_t ah = sw128_desc(sAh + koff), bh = sw128_desc(sBh + koff);
-                tc_mma<0>(tmem, ah, bh, idesc, (ch > 0 || sl > 0) ? 1u : 0u);
+                tc_mma<0>(tmem, ah, bh, idesc, (ch > ch0 || sl > 0) ? 1u : 0u);
                 if (A_SPLIT) tc_mma<0>(tmem, sw128_desc(sAl + koff), bh, idesc, 1u);
                 if (B_SPLIT) tc_mma<0>(tmem, ah, sw128_desc(sBl + koff), idesc, 1u);
             }
@@ -157,6 +168,12 @@ __global__ void __launch_bounds__(TCG_THREADS) mlp_gemm_tc_kernel(const GemmArgs
     const int warp = t >> 5;
     const int m = m0 + t;   // = m0 + 32 warp + lane
     float* C = g.C + mem * g.c_mem;
+    int64_t ldc = g.ldc;
+    if (part) {   // split K: this split's partial tile, [split][member][M][N]
+        const int64_t E = gridDim.z / splits;
+        C = part + ((int64_t)split * E + mem) * (int64_t)g.M * g.N;
+        ldc = g.N;
+    }
     if (!abort_flag) {
         for (int cb = 0; cb * 16 < nvalid; ++cb) {
             float v[16];
@@ -170,7 +187,7 @@ __global__ void __launch_bounds__(TCG_THREADS) mlp_gemm_tc_kernel(const GemmArgs
                     if (EPI == EPI_BIAS || EPI == EPI_BIAS_RELU) x += g.bias[mem * g.bias_mem + n];
                     if (EPI == EPI_BIAS_RELU) x = fmaxf(x, 0.0f);
                     if (EPI == EPI_MASK && !(g.mask[mem * g.mask_mem + (int64_t)m * g.ldm + n] > 0.0f)) x = 0.0f;
-                    C[(int64_t)m * g.ldc + n] = x;
+                    C[(int64_t)m * ldc + n] = x;
                 }
             }
         }
@@ -180,18 +197,50 @@ __global__ void __launch_bounds__(TCG_THREADS) mlp_gemm_tc_kernel(const GemmArgs
     if (t < 32) tmem_dealloc(tmem, (uint32_t)TCG_N);
 }
 
+// C(member) = sum over splits of the partial tiles, in split order.
+__global__ void mlp_splitk_reduce_kernel(const float* __restrict__ part, int splits, int E, int M, int N,
+                                         float* __restrict__ C, int64_t ldc, int64_t c_mem)
+{
+    const int64_t MN = (int64_t)M * N, total = (int64_t)E * MN;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t mem = i / MN, r = i % MN;
+        float acc = 0.0f;
+        for (int sp = 0; sp < splits; ++sp) acc += part[((int64_t)sp * E + mem) * MN + r];
+        C[mem * c_mem + (r / N) * ldc + r % N] = acc;
+    }
+}
+
 // Launch on E members; error: device word that receives TVBX_DEVERR_TIMEOUT
-// when a bounded wait expires (the outputs are then invalid).
+// when a bounded wait expires (the outputs are then invalid). part / part_cap
+// (floats): scratch for split K (plain-store epilogue only; nullptr: none).
 template <typename TA, typename TB, int EPI>
-static inline cudaError_t gemm_tc(const GemmArgs& g, int E, uint32_t* error, uint32_t wait_limit, cudaStream_t s)
+static inline cudaError_t gemm_tc(const GemmArgs& g, int E, uint32_t* error, uint32_t wait_limit, cudaStream_t s,
+                                  float* part = nullptr, size_t part_cap = 0)
 {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
     auto kern = mlp_gemm_tc_kernel<TA, TB, EPI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCG_SMEM);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.N + TCG_N - 1) / TCG_N, (g.M + TCG_M - 1) / TCG_M, E);
+    const int tiles = ((g.N + TCG_N - 1) / TCG_N) * ((g.M + TCG_M - 1) / TCG_M) * E;
+    const int n_chunks = (g.K + TCG_K - 1) / TCG_K;
+    int splits = 1;
+    if (EPI == EPI_STORE && part) {
+        // about two CTAs per SM of the 152, as far as the chunks and the scratch allow
+        splits = std::min(n_chunks, std::max(1, 304 / tiles));
+        const size_t per_split = (size_t)E * g.M * g.N;
+        splits = (int)std::min<size_t>((size_t)splits, part_cap / per_split);
+        splits = std::max(splits, 1);
+    }
+    const int cps = (n_chunks + splits - 1) / splits;
+    splits = (n_chunks + cps - 1) / cps;   // every split owns at least one chunk
+    dim3 grid((g.N + TCG_N - 1) / TCG_N, (g.M + TCG_M - 1) / TCG_M, E * splits);
     note_launch();
-    kern<<<grid, TCG_THREADS, TCG_SMEM, s>>>(g, error, wait_limit);
+    kern<<<grid, TCG_THREADS, TCG_SMEM, s>>>(g, error, wait_limit, splits, cps, splits > 1 ? part : nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess || splits == 1) return e;
+    const int64_t total = (int64_t)E * g.M * g.N;
+    note_launch();
+    mlp_splitk_reduce_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4 * 152), 256, 0, s>>>(
+        part, splits, E, g.M, g.N, g.C, g.ldc, g.c_mem);
     return cudaGetLastError();
 }
 

@@ -295,6 +295,7 @@ struct tvbx_surrogate {
     int64_t n_par = 0;
     uint64_t seed = 0;
     int64_t step = 0;                    // AdamW steps taken
+    bool scaled = false;                 // output standardisation set by a training call
     cudaStream_t stream = nullptr;
     Buf<float> p, m1, m2, g;             // [E][n_par]
     Buf<__nv_bfloat16> pb;               // [E][n_par]
@@ -302,6 +303,7 @@ struct tvbx_surrogate {
     Buf<int64_t> seg;                    // [4 L]
     Buf<float> lo, hi, mu, sd;           // box, output standardisation
     Buf<float> act, dz0, dz1, tb;        // work buffers
+    Buf<float> splitk;                   // split-K partial products
     Buf<float> xin, yin, ymean, yvar, cand, score, cbox;
     Buf<double> loss;
     Buf<uint32_t> err;                   // device error word of the tensor-core products
@@ -344,6 +346,11 @@ cudaError_t ensure_work(tvbx_surrogate* s, int rows)
     if ((e = s->dz0.ensure(widest)) != cudaSuccess) return e;
     if ((e = s->dz1.ensure(widest)) != cudaSuccess) return e;
     if ((e = s->tb.ensure((size_t)s->E * rows * s->n_out)) != cudaSuccess) return e;
+    // split-K partials of the weight gradients: up to 32 splits, at most 64 MB
+    int64_t widest_w = 0;
+    for (size_t l = 0; l + 1 < s->dims.size(); ++l)
+        widest_w = std::max<int64_t>(widest_w, (int64_t)s->dims[l] * s->dims[l + 1]);
+    if ((e = s->splitk.ensure((size_t)std::min<int64_t>(32 * s->E * widest_w, 1ll << 24))) != cudaSuccess) return e;
     s->work_rows = rows;
     return cudaSuccess;
 }
@@ -410,7 +417,9 @@ cudaError_t backward(tvbx_surrogate* s, int rows)
         gw.B = a_prev; gw.sbn = 1; gw.sbk = I; gw.b_mem = (int64_t)rows * I;
         gw.C = s->g.p + s->w_off[l]; gw.ldc = I; gw.c_mem = s->n_par;
         gw.M = O; gw.N = I; gw.K = rows;
-        if ((e = gemm_tc<float, float, EPI_STORE>(gw, s->E, s->err.p, kTcWait, s->stream)) != cudaSuccess) return e;
+        if ((e = gemm_tc<float, float, EPI_STORE>(gw, s->E, s->err.p, kTcWait, s->stream, s->splitk.p, s->splitk.n)) !=
+            cudaSuccess)
+            return e;
         // db_l
         {
             dim3 grid((O + 31) / 32, s->E);
@@ -542,7 +551,7 @@ tvbx_status tvbx_surrogate_destroy(tvbx_surrogate* s)
     if (!s) return TVBX_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (Buf<float>* b : {&s->p, &s->m1, &s->m2, &s->g, &s->lo, &s->hi, &s->mu, &s->sd, &s->act, &s->dz0, &s->dz1,
-                          &s->tb, &s->xin, &s->yin, &s->ymean, &s->yvar, &s->cand, &s->score, &s->cbox})
+                          &s->tb, &s->splitk, &s->xin, &s->yin, &s->ymean, &s->yvar, &s->cand, &s->score, &s->cbox})
         b->release();
     s->pb.release();
     s->decay.release();
@@ -616,9 +625,10 @@ tvbx_status tvbx_surrogate_gradients(tvbx_surrogate* s, int32_t member, const fl
 }
 
 tvbx_status tvbx_surrogate_train(tvbx_surrogate* s, int32_t mem, const float* X, const float* Y, int64_t n,
-                                 int32_t epochs, int32_t batch, float lr, float weight_decay, int32_t shuffle,
+                                 int32_t epochs, int32_t batch, float lr, float weight_decay, int32_t flags,
                                  float* loss_out)
 {
+    const int shuffle = (flags & TVBX_TRAIN_SHUFFLE) ? 1 : 0;
     if (tvbx_status st = check_handle(s)) return st;
     if (mem != TVBX_MEM_HOST && mem != TVBX_MEM_DEVICE) return report_error(TVBX_E_INVALID_ARG, "bad mem");
     if (!X || !Y || n < 1 || n > (1ll << 31) - 1) return report_error(TVBX_E_INVALID_ARG, "need X, Y and 1 <= n < 2^31");
@@ -629,10 +639,13 @@ tvbx_status tvbx_surrogate_train(tvbx_surrogate* s, int32_t mem, const float* X,
     const float *dX, *dY;
     if (tvbx_status st = stage_rows(s, mem, X, (size_t)n * s->n_in, s->xin, &dX)) return st;
     if (tvbx_status st = stage_rows(s, mem, Y, (size_t)n * s->n_out, s->yin, &dY)) return st;
-    // output standardisation from this training set
-    note_launch();
-    mlp_moments_kernel<<<s->n_out, 256, 0, s->stream>>>(dY, n, s->n_out, s->mu.p, s->sd.p);
-    SCK(cudaGetLastError(), "output moments");
+    // output standardisation from this training set, unless an earlier one is kept
+    if (!(flags & TVBX_TRAIN_KEEP_SCALE) || !s->scaled) {
+        note_launch();
+        mlp_moments_kernel<<<s->n_out, 256, 0, s->stream>>>(dY, n, s->n_out, s->mu.p, s->sd.p);
+        SCK(cudaGetLastError(), "output moments");
+        s->scaled = true;
+    }
     const int hb = half_bits_for(n);
     const size_t np = (size_t)s->n_par * s->E;
     const double b1 = 0.9, b2 = 0.999;
@@ -645,7 +658,7 @@ tvbx_status tvbx_surrogate_train(tvbx_surrogate* s, int32_t mem, const float* X,
             const int rows = (int)std::min<int64_t>(batch, n - start);
             note_launch();
             mlp_batch_kernel<<<dim3((rows + 127) / 128, s->E), 128, 0, s->stream>>>(
-                dX, dY, n, s->n_in, s->n_out, start, rows, shuffle ? 1 : 0, hb, key, s->lo.p, s->hi.p, s->mu.p,
+                dX, dY, n, s->n_in, s->n_out, start, rows, shuffle, hb, key, s->lo.p, s->hi.p, s->mu.p,
                 s->sd.p, s->act.p, s->tb.p);
             SCK(cudaGetLastError(), "batch");
             SCK(forward(s, rows), "forward");
@@ -695,6 +708,40 @@ static tvbx_status predict_device(tvbx_surrogate* s, const float* dX, int64_t n,
             var ? var + start * s->n_out : nullptr);
         SCK(cudaGetLastError(), "ensemble");
     }
+    return TVBX_OK;
+}
+
+// Proposal scores of the device candidates dX [n][n_in] (mlp_score_kernel)
+// and the indices of the n_propose best that exclude (host, nullable) leaves
+// open, best first, ties to the lower index. score receives all n scores.
+static tvbx_status score_and_pick(tvbx_surrogate* s, const float* dX, int64_t n, const uint8_t* exclude, int32_t output,
+                                  float threshold, float var_weight, int32_t n_propose, std::vector<float>& score,
+                                  std::vector<int64_t>& idx)
+{
+    SCK(s->ymean.ensure((size_t)n * s->n_out), "candidate predictions");
+    SCK(s->yvar.ensure((size_t)n * s->n_out), "candidate predictions");
+    if (tvbx_status st = predict_device(s, dX, n, s->ymean.p, s->yvar.p)) return st;
+    // scores on the device; the n_propose best on the host
+    SCK(s->score.ensure((size_t)n), "scores");
+    note_launch();
+    mlp_score_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(s->ymean.p, s->yvar.p, n, s->n_out, output,
+                                                                         threshold, var_weight, s->sd.p, s->score.p);
+    SCK(cudaGetLastError(), "scores");
+    score.resize((size_t)n);
+    SCK(cudaMemcpyAsync(score.data(), s->score.p, sizeof(float) * n, cudaMemcpyDeviceToHost, s->stream), "scores");
+    SCK(cudaStreamSynchronize(s->stream), "scores");
+    if (tvbx_status st = check_tc_error(s, "ranking")) return st;
+    idx.clear();
+    idx.reserve((size_t)n);
+    for (int64_t c = 0; c < n; ++c)
+        if (!exclude || !exclude[c]) idx.push_back(c);
+    if ((int64_t)idx.size() < n_propose)
+        return report_error(TVBX_E_INVALID_ARG, "n_propose %d exceeds the %lld candidates not excluded", n_propose,
+                            (long long)idx.size());
+    auto better = [&](int64_t a, int64_t b) { return score[a] > score[b] || (score[a] == score[b] && a < b); };
+    std::nth_element(idx.begin(), idx.begin() + (n_propose - 1), idx.end(), better);
+    std::sort(idx.begin(), idx.begin() + n_propose, better);
+    idx.resize((size_t)n_propose);
     return TVBX_OK;
 }
 
@@ -758,29 +805,39 @@ tvbx_status tvbx_surrogate_propose(tvbx_surrogate* s, int64_t n_candidates, uint
     mlp_candidates_kernel<<<(unsigned)((n_candidates + 255) / 256), 256, 0, s->stream>>>(
         s->cand.p, n_candidates, s->n_in, clo, chi, s->seed, round);
     SCK(cudaGetLastError(), "candidates");
-    if (tvbx_status st = predict_device(s, s->cand.p, n_candidates, s->ymean.p, s->yvar.p)) return st;
-    // scores on the device; the n_propose best (ties by index) on the host
-    SCK(s->score.ensure((size_t)n_candidates), "scores");
-    note_launch();
-    mlp_score_kernel<<<(unsigned)((n_candidates + 255) / 256), 256, 0, s->stream>>>(
-        s->ymean.p, s->yvar.p, n_candidates, s->n_out, output, threshold, var_weight, s->sd.p, s->score.p);
-    SCK(cudaGetLastError(), "scores");
-    std::vector<float> score((size_t)n_candidates);
-    SCK(cudaMemcpyAsync(score.data(), s->score.p, sizeof(float) * n_candidates, cudaMemcpyDeviceToHost, s->stream),
-        "scores");
-    SCK(cudaStreamSynchronize(s->stream), "scores");
-    if (tvbx_status st = check_tc_error(s, "propose")) return st;
-    std::vector<int64_t> idx((size_t)n_candidates);
-    std::iota(idx.begin(), idx.end(), 0);
-    auto better = [&](int64_t a, int64_t b) { return score[a] > score[b] || (score[a] == score[b] && a < b); };
-    std::nth_element(idx.begin(), idx.begin() + (n_propose - 1), idx.end(), better);
-    std::sort(idx.begin(), idx.begin() + n_propose, better);
+    std::vector<float> score;
+    std::vector<int64_t> idx;
+    if (tvbx_status st = score_and_pick(s, s->cand.p, n_candidates, nullptr, output, threshold, var_weight, n_propose,
+                                        score, idx))
+        return st;
     std::vector<float> pts((size_t)n_candidates * s->n_in);
     SCK(cudaMemcpyAsync(pts.data(), s->cand.p, sizeof(float) * pts.size(), cudaMemcpyDeviceToHost, s->stream),
         "candidate points");
     SCK(cudaStreamSynchronize(s->stream), "candidate points");
     for (int32_t r = 0; r < n_propose; ++r) {
         memcpy(points_out + (size_t)r * s->n_in, pts.data() + (size_t)idx[r] * s->n_in, sizeof(float) * s->n_in);
+        if (scores_out) scores_out[r] = score[idx[r]];
+    }
+    return TVBX_OK;
+}
+
+tvbx_status tvbx_surrogate_rank(tvbx_surrogate* s, const float* X, int64_t n, const uint8_t* exclude, int32_t output,
+                                float threshold, float var_weight, int32_t n_propose, int64_t* idx_out,
+                                float* scores_out)
+{
+    if (tvbx_status st = check_handle(s)) return st;
+    if (!X || !idx_out || n < 1 || n > (1ll << 26) || n_propose < 1 || n_propose > n)
+        return report_error(TVBX_E_INVALID_ARG, "need X, idx_out and 1 <= n_propose <= n <= 2^26");
+    if (output < 0 || output >= s->n_out) return report_error(TVBX_E_INVALID_ARG, "output index out of range");
+    const float* dX;
+    if (tvbx_status st = stage_rows(s, TVBX_MEM_HOST, X, (size_t)n * s->n_in, s->cand, &dX)) return st;
+    std::vector<float> score;
+    std::vector<int64_t> idx;
+    if (tvbx_status st =
+            score_and_pick(s, dX, n, exclude, output, threshold, var_weight, n_propose, score, idx))
+        return st;
+    for (int32_t r = 0; r < n_propose; ++r) {
+        idx_out[r] = idx[r];
         if (scores_out) scores_out[r] = score[idx[r]];
     }
     return TVBX_OK;

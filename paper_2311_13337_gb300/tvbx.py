@@ -88,7 +88,7 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_launch_count",
            "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_fc_noalloc", "tvbx_fc_series",
            "tvbx_sweep_destroy", "tvbx_surrogate_create", "tvbx_surrogate_info", "tvbx_surrogate_train",
-           "tvbx_surrogate_predict", "tvbx_surrogate_propose", "tvbx_surrogate_params", "tvbx_surrogate_gradients",
+           "tvbx_surrogate_predict", "tvbx_surrogate_propose", "tvbx_surrogate_rank", "tvbx_surrogate_params", "tvbx_surrogate_gradients",
            "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project", "tvbx_batch_create", "tvbx_batch_tune",
            "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy", "tvbx_fc_fitness", "tvbx_top_k",
            "tvbx_series_analysis", "tvbx_bold_defaults", "tvbx_bold", "tvbx_phfcd",
@@ -148,6 +148,7 @@ def load(build_if_missing: bool = False):
     L.tvbx_surrogate_predict.argtypes = [vp, i32, fp, i64, fp, fp]
     L.tvbx_surrogate_propose.argtypes = [vp, i64, ctypes.c_uint64, i32, ctypes.c_float, ctypes.c_float, dp, dp, i32,
                                          fp, fp]
+    L.tvbx_surrogate_rank.argtypes = [vp, fp, i64, vp, i32, ctypes.c_float, ctypes.c_float, i32, vp, fp]
     L.tvbx_surrogate_params.argtypes = [vp, i32, fp, fp]
     L.tvbx_surrogate_gradients.argtypes = [vp, i32, fp, fp, i64, ctypes.POINTER(ctypes.c_float), fp]
     L.tvbx_surrogate_destroy.argtypes = [vp]
@@ -804,14 +805,16 @@ class Surrogate:
         a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1, cols)
         return ctypes.c_void_p(a.ctypes.data), MEM_HOST, a.shape[0], a
 
-    def train(self, X, Y, epochs=1, batch=1024, lr=1e-3, weight_decay=1e-4, shuffle=True):
+    def train(self, X, Y, epochs=1, batch=1024, lr=1e-3, weight_decay=1e-4, shuffle=True, keep_scale=False):
+        """keep_scale: keep the output standardisation of the earlier
+        training call (fine-tuning) instead of recomputing it from Y."""
         px, mx, n, kx = self._ptr(X, self.n_in)
         py, my, _, ky = self._ptr(Y, self.n_out)
         if mx != my:
             raise ValueError("X and Y must both be host or both be device arrays")
         losses = np.zeros(int(epochs), dtype=np.float32)
         _check(load().tvbx_surrogate_train(self.h, mx, px, py, n, int(epochs), int(batch), float(lr),
-                                           float(weight_decay), int(bool(shuffle)),
+                                           float(weight_decay), (1 if shuffle else 0) | (2 if keep_scale else 0),
                                            ctypes.c_void_p(losses.ctypes.data)), "tvbx_surrogate_train")
         return losses
 
@@ -842,6 +845,27 @@ class Surrogate:
                                              ctypes.c_void_p(pts.ctypes.data), ctypes.c_void_p(sc.ctypes.data)),
                "tvbx_surrogate_propose")
         return pts, sc
+
+    def rank(self, X, n_propose, output, threshold, var_weight=1.0, exclude=None):
+        """Indices (best first) and scores of the n_propose best rows of the
+        host candidates X by the proposal score; rows where exclude (bool
+        [n]) is set are never chosen."""
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        if X.ndim != 2 or X.shape[1] != self.n_in:
+            raise ValueError(f"X must be [n][{self.n_in}]")
+        ex = None
+        if exclude is not None:
+            ex = np.ascontiguousarray(exclude, dtype=np.uint8)
+            if ex.shape != (X.shape[0],):
+                raise ValueError("exclude must have one entry per candidate")
+        idx = np.zeros(int(n_propose), dtype=np.int64)
+        sc = np.zeros(int(n_propose), dtype=np.float32)
+        _check(load().tvbx_surrogate_rank(self.h, ctypes.c_void_p(X.ctypes.data), X.shape[0],
+                                          ctypes.c_void_p(ex.ctypes.data) if ex is not None else None, int(output),
+                                          float(threshold), float(var_weight), int(n_propose),
+                                          ctypes.c_void_p(idx.ctypes.data), ctypes.c_void_p(sc.ctypes.data)),
+               "tvbx_surrogate_rank")
+        return idx, sc
 
     def params(self, member=0) -> np.ndarray:
         out = np.zeros(self.n_params, dtype=np.float32)

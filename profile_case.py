@@ -4,6 +4,7 @@
   python profile_case.py --fc-series --sets 4096 --samples 5000 --fc-precision bf16x3
   python profile_case.py --analysis --sets 4096 --samples 5000
   python profile_case.py --bold --sets 8192 --samples 10000
+  python profile_case.py --surrogate --sets 36864 --epochs 5
 
 Takes the first `--sets` sets of the 32,768-set grid (68 regions, v 4 m/s),
 integrates `--n-steps` steps in launches of `--chunk` steps and optionally
@@ -13,6 +14,9 @@ synthetic rate-like series of `--sets` x 68 regions x `--samples`. With
 --analysis, runs only the Table 2 metrics (tvbx_series_analysis) on such
 series in the [sets][regions][samples] layout. With --bold, runs the
 Balloon-Windkessel kernel on such rates (TR 1 s) and the phFCD of 300 TRs.
+With --surrogate, trains the 4-member 5 -> 256 x 3 -> 24 surrogate for
+`--epochs` passes (batch 1024) on `--sets` synthetic rows and predicts a
+65,536-point map.
 Sized so
 that a profiler can capture single launches on a few GB of device memory.
 """
@@ -43,7 +47,11 @@ def main():
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--analysis", action="store_true")
     ap.add_argument("--bold", action="store_true")
+    ap.add_argument("--surrogate", action="store_true")
+    ap.add_argument("--epochs", type=int, default=5)
     args = ap.parse_args()
+    if args.surrogate:
+        return surrogate_case(args)
     if args.bold:
         return bold_case(args)
     if args.fc_series:
@@ -133,6 +141,34 @@ def analysis_case(args):
         tvbx.series_analysis(X, 1.0)
         torch.cuda.synchronize()
         print(f"analysis {P} x {N} x {T}: {time.time() - t0:.4f} s")
+
+
+def surrogate_case(args):
+    import numpy as np
+    import torch
+
+    from paper_2311_13337_gb300 import build, tvbx
+    build.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(11)
+    lo, hi = np.array([0.0, 0.0, 100.0, -80.0, 1.0]), np.array([0.9, 120.0, 1000.0, -60.0, 16.0])
+    X = (lo + (hi - lo) * rng.uniform(size=(args.sets, 5))).astype(np.float32)
+    u = (X - lo) / (hi - lo)
+    Y = np.column_stack([np.sin(3.0 * u @ rng.normal(size=5) + k) for k in range(24)])
+    Y = (Y + 0.05 * rng.normal(size=Y.shape)).astype(np.float32)
+    sur = tvbx.Surrogate(lo, hi, 24, n_hidden=256, n_layers=3, n_members=4, seed=7)
+    Xm = (lo + (hi - lo) * rng.uniform(size=(65536, 5))).astype(np.float32)
+    for i in range(args.repeat):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        sur.train(X, Y, epochs=args.epochs, batch=1024, lr=1e-3, weight_decay=1e-4)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        sur.predict(Xm)
+        torch.cuda.synchronize()
+        print(f"surrogate {args.sets} rows x {args.epochs} epochs: {t1 - t0:.4f} s; predict 65,536: "
+              f"{time.time() - t1:.4f} s")
+    sur.close()
 
 
 if __name__ == "__main__":

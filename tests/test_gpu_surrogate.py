@@ -13,7 +13,7 @@ import pytest
 
 from gpu_common import require_gpu
 from oracle import mlp as M
-from paper_2311_13337_gb300 import synth
+from paper_2311_13337_gb300 import guided, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -147,6 +147,49 @@ def test_surrogate_of_the_sweep_predicts_and_proposes_near_the_boundary(tvbx, or
     dp = np.nanmean(np.abs(yp - 0.5))
     dr = np.nanmean(np.abs(yr - 0.5))
     assert dp < 0.5 * dr, (dp, dr)
+
+    # ranking of given candidates: the proposal score of the ensemble's mean and
+    # variance, best first, never an excluded point
+    side = 48
+    gg, bb = np.meshgrid(np.linspace(0.0, 0.9, side), np.linspace(0.0, 120.0, side), indexing="ij")
+    X_map = np.column_stack([gg.ravel(), bb.ravel()]).astype(np.float32)
+    m, v = s.predict(X_map, want_var=True)
+    sd = np.float32(np.std(ytr[ok].astype(np.float64)))
+    host = -np.abs(m[:, 0] - 0.5) / sd + 1.0 * np.sqrt(np.maximum(v[:, 0], 0.0)) / sd
+    ex = np.zeros(side * side, bool)
+    ex[::3] = True
+    idx, sc = s.rank(X_map, 200, 0, 0.5, var_weight=1.0, exclude=ex)
+    assert not ex[idx].any() and len(set(idx.tolist())) == 200 and np.all(np.diff(sc) <= 0)
+    np.testing.assert_allclose(sc, host[idx], rtol=1e-4, atol=1e-5)
+    open_pts = np.flatnonzero(~ex)
+    assert sc[-1] >= np.sort(host[open_pts])[::-1][199] - 1e-4
+
+    # guided map of the same slice: rounds of judged proposals improve on the
+    # surrogate's own map, and the simulator's labels at judged points are the
+    # dense sweep's (a set's result does not depend on its slot in a sweep)
+    truth_v = simulate(X_map.astype(np.float64))
+    tfin = np.isfinite(truth_v)
+    truth = truth_v >= 0.5
+    lab_pred = m[:, 0] >= 0.5
+    idx_all, sc_all = s.rank(X_map, side * side, 0, 0.5, var_weight=1.0)
+    score = np.empty(side * side, np.float32)
+    score[idx_all] = sc_all
+    judged = np.zeros(side * side, bool)
+    lab_sim, sim_ok, contra = judged.copy(), judged.copy(), judged.copy()
+    errs = [np.mean(lab_pred[tfin] != truth[tfin])]
+    for r in range(3):
+        idx = guided.next_proposals(lambda k, e: s.rank(X_map, k, 0, 0.5, var_weight=1.0, exclude=e)[0],
+                                    judged, contra, score, 192, side)
+        assert not judged[idx].any() and len(set(idx.tolist())) == 192
+        y = simulate(X_map[idx].astype(np.float64))
+        assert np.array_equal(y, truth_v[idx], equal_nan=True)
+        judged[idx] = True
+        sim_ok[idx] = np.isfinite(y)
+        lab_sim[idx] = y >= 0.5
+        contra[idx] = sim_ok[idx] & (lab_sim[idx] != lab_pred[idx])
+        lab = guided.guided_labels(judged, lab_sim, sim_ok, lab_pred, side)
+        errs.append(np.mean(lab[tfin] != truth[tfin]))
+    assert errs[-1] <= errs[0] and (errs[-1] < errs[0] or errs[0] == 0.0), errs
     s.close()
 
 
