@@ -138,7 +138,24 @@ typedef struct {
                                  and shorten their wait, so the wait expires and the
                                  run reports TVBX_E_TIMEOUT (no fault, the context
                                  stays usable). Other kernels ignore it. */
+    int32_t series_mode;      /* TVBX_SERIES_KEEP (0) or TVBX_SERIES_STREAM */
 } tvbx_run_cfg;
+
+/* Series modes of tvbx_run_cfg.
+ * TVBX_SERIES_KEEP: the whole E series [T][N][P] stays on the device.
+ * TVBX_SERIES_STREAM: only one chunk of samples is kept (chunk_steps, or the
+ *   automatic chunk of about 5,000 steps, divided by tavg_steps). After each
+ *   chunk the library folds its samples after the transient into per-set FC
+ *   moments (Eq. 6: sums of x_k and x_k x_j about a fixed shift, the mean of
+ *   up to 64 samples of the first chunk after the transient; FP32 CUDA-core
+ *   products, summed over chunks in FP32), so the series memory no longer
+ *   grows with the duration. tvbx_fc then returns FC, chi and mean FC from the
+ *   moments (any precision argument; fcd_window must be 0: the FCD needs the
+ *   whole series), and tvbx_series / tvbx_series_range return
+ *   TVBX_E_BAD_STATE. Needs n_regions <= 384. Means, status and the final
+ *   state are those of TVBX_SERIES_KEEP, bit for bit. */
+#define TVBX_SERIES_KEEP 0
+#define TVBX_SERIES_STREAM 1
 #define TVBX_KERNEL_AUTO     0 /* fastest kernel that fits the sweep */
 #define TVBX_KERNEL_DIRECT 100 /* register tiles for connectomes too large for the
                                   prefetch buffer (up to 768 regions): 4 sets of

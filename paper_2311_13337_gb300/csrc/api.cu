@@ -248,13 +248,14 @@ struct tvbx_sweep {
     DevBuf d_prm, d_ext, d_state, d_status, d_ring, d_series, d_ou_table, d_ou_state;
     DevBuf d_csr_row, d_csr_cd, d_csr_w, d_groups, d_tiles;
     DevBuf d_blocks, d_fc, d_chi, d_meanfc, d_vec, d_fcd, d_tmp, d_perm, d_inv, d_mean_e, d_mean_i, d_error;
+    DevBuf d_fcacc, d_shift;        // streamed series: FC moments over the run, fixed shift [N][P]
 
     ~tvbx_sweep()
     {
         DevBuf* all[] = {&d_prm, &d_ext, &d_state, &d_status, &d_ring, &d_series, &d_ou_table,
                          &d_ou_state, &d_csr_row, &d_csr_cd, &d_csr_w, &d_groups, &d_tiles,
                          &d_blocks, &d_fc, &d_chi, &d_meanfc, &d_vec, &d_fcd, &d_tmp, &d_perm,
-                         &d_inv, &d_mean_e, &d_mean_i, &d_error};
+                         &d_inv, &d_mean_e, &d_mean_i, &d_error, &d_fcacc, &d_shift};
         for (DevBuf* b : all) b->release();
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
@@ -555,6 +556,10 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     if (c.transient_samples < 0 || (T > 0 && c.transient_samples >= T))
         return fail(TVBX_E_INVALID_ARG, "transient_samples must be in [0, n_samples)");
     if (c.p_offset < 0) return fail(TVBX_E_INVALID_ARG, "p_offset must be >= 0");
+    if (c.series_mode != TVBX_SERIES_KEEP && c.series_mode != TVBX_SERIES_STREAM)
+        return fail(TVBX_E_INVALID_ARG, "unknown series_mode %d", c.series_mode);
+    if (c.series_mode == TVBX_SERIES_STREAM && h->N > 384)
+        return fail(TVBX_E_UNSUPPORTED, "a streamed series needs n_regions <= 384 (have %d)", h->N);
     h->stream = s;
     h->ran = false;
     h->fc_valid = false;
@@ -656,6 +661,17 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     }
     if (all_cd.empty()) { all_cd.push_back(0); all_w.push_back(0.f); }
 
+    // chunking: keep each launch around 4-8 thousand steps
+    int64_t chunk = c.chunk_steps > 0 ? c.chunk_steps : 0;
+    if (chunk == 0) {
+        chunk = (int64_t)c.tavg_steps * std::max<int64_t>(1, 5000 / c.tavg_steps);
+        if (chunk <= 0) chunk = c.tavg_steps;
+    }
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(c.n_steps, 1));
+    // a streamed series keeps the samples of one chunk (rounded up to whole samples)
+    const int64_t series_T =
+        c.series_mode == TVBX_SERIES_STREAM ? std::min<int64_t>(T, (chunk + c.tavg_steps - 1) / c.tavg_steps) : T;
+
     // device memory
     CK(h->d_prm.ensure(sizeof(float) * prm_soa.size()), "parameters");
     CK(h->d_ext.ensure(sizeof(int64_t) * P), "set index");
@@ -664,7 +680,12 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     CK(h->d_state.ensure(sizeof(float) * (size_t)SV_COUNT * N * P), "state");
     CK(h->d_status.ensure(sizeof(uint32_t) * P), "status");
     CK(h->d_ring.ensure(sizeof(float) * (size_t)std::max<int64_t>(ring_floats, 1)), "ring buffers");
-    CK(h->d_series.ensure(sizeof(float) * (size_t)std::max<int64_t>(T * N * P, 1)), "series");
+    CK(h->d_series.ensure(sizeof(float) * (size_t)std::max<int64_t>(series_T * N * P, 1)), "series");
+    if (c.series_mode == TVBX_SERIES_STREAM) {
+        CK(h->d_fcacc.ensure(sizeof(float) * (size_t)P * ((size_t)N * N + N)), "streamed FC moments");
+        CK(h->d_blocks.ensure(sizeof(float) * (size_t)P * ((size_t)N * N + N)), "FC block moments");
+        CK(h->d_shift.ensure(sizeof(float) * (size_t)N * P), "FC shift");
+    }
     CK(h->d_ou_state.ensure(sizeof(float) * N), "OU state");
     CK(h->d_error.ensure(sizeof(uint32_t)), "error word");
     CK(h->d_csr_row.ensure(sizeof(int32_t) * all_row.size()), "CSR");
@@ -706,13 +727,6 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     CK(cudaMemsetAsync(h->d_error.ptr, 0, sizeof(uint32_t), s), "error word");
     h->ring_floats = ring_floats;
 
-    // chunking: keep each launch around 4-8 thousand steps
-    int64_t chunk = c.chunk_steps > 0 ? c.chunk_steps : 0;
-    if (chunk == 0) {
-        chunk = (int64_t)c.tavg_steps * std::max<int64_t>(1, 5000 / c.tavg_steps);
-        if (chunk <= 0) chunk = c.tavg_steps;
-    }
-    chunk = std::min<int64_t>(chunk, std::max<int64_t>(c.n_steps, 1));
     if (!c.noise_per_set) CK(h->d_ou_table.ensure(sizeof(float) * (size_t)chunk * N), "OU table");
 
     SimArgs a;
@@ -775,8 +789,51 @@ static void finish_run(tvbx_sweep* h, const tvbx_run_cfg& c, int64_t steps_befor
     h->cfg = c;
     h->T = c.n_steps / c.tavg_steps;
     h->ran = true;
+    h->fc_valid = false;   // a relaunched batch graph rewrites the status words, and the FC pass adds to them
     h->steps_done = steps_before + c.n_steps;
     h->resumable = resumable;
+}
+
+// Streamed series: fold the samples after the transient of the chunk of
+// steps [n0, n0 + n_chunk), held in the series buffer from its row 0, into
+// the run's FC moments. The shift of every chunk is the one taken from the
+// first chunk with such samples (shift_set), so that the moments add.
+static tvbx_status stream_fc_chunk(tvbx_sweep* h, const SimArgs& a, int64_t n0, int32_t n_chunk, bool& shift_set,
+                                   cudaStream_t s)
+{
+    const int64_t tc0 = n0 / a.ts, tc1 = (n0 + n_chunk) / a.ts;   // global samples of the chunk
+    const int64_t u0 = std::max<int64_t>(tc0, a.transient);
+    if (u0 >= tc1) return TVBX_OK;
+    const float* buf = h->d_series.as<float>();
+    if (!shift_set) {
+        CK(launch_fc_shift(buf, a.N, a.P, u0 - tc0, tc1 - tc0, h->d_shift.as<float>(), s), "FC shift");
+        shift_set = true;
+    }
+    FcArgs f;
+    memset(&f, 0, sizeof f);
+    f.series = buf;
+    f.shift = h->d_shift.as<float>();
+    f.N = a.N;
+    f.P = a.P;
+    f.t_begin = u0 - tc0;
+    f.t_end = tc1 - tc0;
+    f.n_blocks = 1;
+    f.blocks = h->d_blocks.as<float>();
+    f.status = h->d_status.as<uint32_t>();
+    f.error = h->d_error.as<uint32_t>();
+    f.wait_limit = 1u << 22;
+    CK(launch_fc_moments(f, s), "streamed FC moments");
+    CK(launch_fc_accumulate(f.blocks, h->d_fcacc.as<float>(), (int64_t)a.P * ((int64_t)a.N * a.N + a.N), s),
+       "streamed FC moments");
+    return TVBX_OK;
+}
+
+// The series pointer of a chunk whose first sample t0 goes to row 0 of the
+// buffer (the kernels index samples by the global step; the address is
+// formed in integers and every write lands inside the buffer).
+static float* series_at(void* buf, int64_t t0, int N, int64_t P)
+{
+    return reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(buf) - (uintptr_t)(sizeof(float) * (size_t)t0 * N * P));
 }
 
 // Enqueue the chunked launches of a prepared run over global steps
@@ -789,9 +846,15 @@ static tvbx_status run_chunks(tvbx_sweep* h, const tvbx_run_cfg& c, const RunPla
     const int64_t P = h->P;
     const int64_t chunk = plan.chunk;
     const int variant = plan.variant;
+    const bool streamed = c.series_mode == TVBX_SERIES_STREAM;
+    bool shift_set = false;
+    if (streamed)
+        CK(cudaMemsetAsync(h->d_fcacc.ptr, 0, sizeof(float) * (size_t)P * ((size_t)N * N + N), s),
+           "streamed FC moments");
     for (int64_t n0 = n_base; n0 < n_base + c.n_steps; n0 += chunk) {
         a.n0 = n0;
         a.n_chunk = (int32_t)std::min<int64_t>(chunk, n_base + c.n_steps - n0);
+        if (streamed) a.series = series_at(h->d_series.ptr, n0 / c.tavg_steps, N, P);
         if (!c.noise_per_set)
             CK(launch_ou_table(a.m, h->d_ou_table.as<float>(), h->d_ou_state.as<float>(), N, n0, a.n_chunk, c.seed, s),
                "OU table");
@@ -811,6 +874,8 @@ static tvbx_status run_chunks(tvbx_sweep* h, const tvbx_run_cfg& c, const RunPla
             h->ev_used += 2;
             h->prof_region_steps += (double)P * N * a.n_chunk;
         }
+        if (streamed)
+            if (tvbx_status st = stream_fc_chunk(h, a, n0, a.n_chunk, shift_set, s)) return st;
     }
     return TVBX_OK;
 }
@@ -855,7 +920,7 @@ tvbx_status tvbx_run_continue(tvbx_sweep* h, int64_t n_steps, int32_t transient_
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr char CKPT_MAGIC[8] = {'T', 'V', 'B', 'X', 'C', 'K', 'P', '2'};   // 2: the state holds the W carries
+constexpr char CKPT_MAGIC[8] = {'T', 'V', 'B', 'X', 'C', 'K', 'P', '3'};   // 3: W carries, series mode
 
 struct CkptHeader {
     char magic[8];
@@ -871,6 +936,7 @@ struct CkptHeader {
     int64_t p_offset;
     int64_t chunk_steps;
     int64_t kernel;
+    int64_t series_mode;
 };
 
 // FNV-1a over the bytes of the definition of a sweep (all fields are doubles
@@ -932,6 +998,7 @@ tvbx_status tvbx_checkpoint(tvbx_sweep* h, void* host_buf, uint64_t bytes)
     hd.p_offset = h->cfg.p_offset;
     hd.chunk_steps = h->cfg.chunk_steps;
     hd.kernel = h->cfg.kernel;
+    hd.series_mode = h->cfg.series_mode;
     unsigned char* out = static_cast<unsigned char*>(host_buf);
     memcpy(out, &hd, sizeof hd);
     size_t off = sizeof hd;
@@ -971,6 +1038,7 @@ tvbx_status tvbx_restore(tvbx_sweep* h, const void* host_buf, uint64_t bytes)
     c.p_offset = hd.p_offset;
     c.chunk_steps = (int32_t)hd.chunk_steps;
     c.kernel = (int32_t)hd.kernel;
+    c.series_mode = (int32_t)hd.series_mode;
     // lay out the buffers as the checkpointed run did, then fill them; the
     // handle's earlier stream may no longer exist, so the device is drained
     // and the default stream used
@@ -1021,6 +1089,32 @@ static tvbx_status run_fc(tvbx_sweep* h, int32_t precision, int32_t fcd_window, 
         nw = (int32_t)((Tn - fcd_window) / fcd_step + 1);
     }
     const size_t stride_b = (size_t)N * N + N;
+    if (h->cfg.series_mode == TVBX_SERIES_STREAM) {
+        // the moments were folded chunk by chunk during the run
+        if (fcd_window > 0)
+            return fail(TVBX_E_INVALID_ARG, "the FCD needs the whole series, and the last run streamed it");
+        CK(h->d_fc.ensure(sizeof(float) * (size_t)P * N * N), "FC");
+        CK(h->d_chi.ensure(sizeof(float) * P), "chi");
+        CK(h->d_meanfc.ensure(sizeof(float) * P), "mean FC");
+        FcArgs f;
+        memset(&f, 0, sizeof f);
+        f.N = N;
+        f.P = (int32_t)P;
+        f.t_begin = t0;
+        f.t_end = t1;
+        f.n_blocks = 1;
+        f.blocks = h->d_fcacc.as<float>();
+        f.fc = h->d_fc.as<float>();
+        f.chi = h->d_chi.as<float>();
+        f.mean_fc = h->d_meanfc.as<float>();
+        f.status = h->d_status.as<uint32_t>();
+        f.error = h->d_error.as<uint32_t>();
+        f.wait_limit = 1u << 22;
+        CK(launch_fc_reduce(f, 0, 0, 0, nullptr, nullptr, h->stream), "FC reduction");
+        if (nw_out) *nw_out = 0;
+        h->fc_valid = true;
+        return TVBX_OK;
+    }
     CK(h->d_blocks.ensure(sizeof(float) * (size_t)P * n_blocks * stride_b), "FC block moments");
     CK(h->d_fc.ensure(sizeof(float) * (size_t)P * N * N), "FC");
     CK(h->d_chi.ensure(sizeof(float) * P), "chi");
@@ -1070,13 +1164,16 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
     if (tvbx_status e = check_device_error(h)) return e;
     if (cfg->precision < TVBX_FC_FP32 || cfg->precision > TVBX_FC_TF32X3)
         return fail(TVBX_E_UNSUPPORTED, "FC precision %d", cfg->precision);
-    if (cfg->precision != TVBX_FC_FP32 && !fc_tc_supported(h->N, cfg->precision))
+    if (cfg->precision != TVBX_FC_FP32 && h->cfg.series_mode != TVBX_SERIES_STREAM &&
+        !fc_tc_supported(h->N, cfg->precision))
         return fail(TVBX_E_INVALID_ARG, "tensor-core FC needs n_regions <= 128 (have %d)", h->N);
     if (cfg->fcd_window < 0) return fail(TVBX_E_INVALID_ARG, "fcd_window must be >= 0");
     int32_t nw = 0;
     tvbx_status st = run_fc(h, cfg->precision, cfg->fcd_window, cfg->fcd_step, &nw);
     if (st != TVBX_OK) return st;
-    if (cfg->precision != TVBX_FC_FP32 && (st = check_device_error(h)) != TVBX_OK) return st;
+    if (cfg->precision != TVBX_FC_FP32 && h->cfg.series_mode != TVBX_SERIES_STREAM &&
+        (st = check_device_error(h)) != TVBX_OK)
+        return st;
     if (n_windows) *n_windows = nw;
     if (fc_out) {
         st = export_rows(h, h->d_fc.as<float>(), (int64_t)h->N * h->N, mem, fc_out);
@@ -1266,6 +1363,8 @@ tvbx_status tvbx_series_range(const tvbx_sweep* hc, int64_t set_begin, int64_t s
     if (!h || !out) return fail(TVBX_E_INVALID_ARG, "NULL handle or out");
     if (check_mem(mem)) return TVBX_E_INVALID_ARG;
     if (!h->ran) return fail(TVBX_E_BAD_STATE, "series export before tvbx_run");
+    if (h->cfg.series_mode == TVBX_SERIES_STREAM)
+        return fail(TVBX_E_BAD_STATE, "the last run streamed its series (series_mode): there is none to export");
     if (tvbx_status e = check_device_error(h)) return e;
     if (set_begin < 0 || set_count < 0 || set_begin + set_count > h->P || t_begin < 0 || t_count < 0 ||
         t_begin + t_count > h->T)
@@ -1488,6 +1587,23 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
     size_t smem = 0;
     int64_t ou_floats = 0;
     std::vector<int64_t> ou_off(nj, -1);
+    // streamed series: the batch runs in rounds of S steps, the streamed jobs'
+    // common chunk, and folds each round's samples into their FC moments
+    int64_t S = 0;
+    for (size_t j = 0; j < nj; ++j) {
+        const tvbx_run_cfg& c = b->cfgs[j];
+        if (c.series_mode != TVBX_SERIES_STREAM) continue;
+        const int64_t cj =
+            c.chunk_steps > 0 ? c.chunk_steps : (int64_t)c.tavg_steps * std::max<int64_t>(1, 5000 / c.tavg_steps);
+        if (S == 0) S = cj;
+        if (cj != S)
+            return fail(TVBX_E_INVALID_ARG, "batch job %zu: streamed jobs share one chunk (%lld steps, have %lld)", j,
+                        (long long)S, (long long)cj);
+    }
+    for (size_t j = 0; j < nj && S > 0; ++j)
+        if (S % b->cfgs[j].tavg_steps != 0)
+            return fail(TVBX_E_INVALID_ARG, "batch job %zu: tavg_steps must divide the streamed chunk of %lld steps", j,
+                        (long long)S);
     for (size_t j = 0; j < nj; ++j) {
         tvbx_run_cfg& c = run_cfgs[j];
         if (trial_steps > 0) {   // timing run only: shortened, no transient
@@ -1504,7 +1620,7 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
         pbs[j] = pb;
         dirs[j] = dj ? 1 : 0;
         smem = std::max(smem, dj ? sizeof(float) * 11 * (size_t)pb : sim_smem_bytes(N, pb));
-        c.chunk_steps = 0;
+        c.chunk_steps = c.series_mode == TVBX_SERIES_STREAM ? (int32_t)S : 0;
         tvbx_status st = prepare_run(b->jobs[j], c, b->stream, pb, false, plans[j], dj);
         if (st != TVBX_OK) return st;
         if (!c.noise_per_set) {
@@ -1513,29 +1629,43 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
         }
     }
     CK(b->d_ou.ensure(sizeof(float) * (size_t)std::max<int64_t>(ou_floats, 1)), "batch OU tables");
-    std::vector<BatchJob> jobs(nj);
+    int64_t max_steps = 0;
+    for (size_t j = 0; j < nj; ++j) max_steps = std::max<int64_t>(max_steps, run_cfgs[j].n_steps);
+    const int64_t R = S > 0 ? (max_steps + S - 1) / S : 1;   // rounds
+    const int64_t round_steps = S > 0 ? S : max_steps;
+    std::vector<BatchJob> jobs((size_t)R * nj);               // [round][job]
     struct Cost { double c; int32_t job, tile; };
-    std::vector<Cost> costs;
-    for (size_t j = 0; j < nj; ++j) {
-        SimArgs a = plans[j].a;
-        a.n0 = 0;
-        a.n_chunk = (int32_t)run_cfgs[j].n_steps;
-        a.ou_table = ou_off[j] >= 0 ? b->d_ou.as<float>() + ou_off[j] : nullptr;
-        jobs[j] = BatchJob{a, pbs[j], dirs[j]};
-        const int N = b->jobs[j]->N;
-        for (int32_t t = 0; t < plans[j].n_tiles; ++t) {
-            const double per_step = (double)N * 40.0 + (double)plans[j].tile_nnz[t];   // TF work + gathers
-            costs.push_back(Cost{per_step * (double)run_cfgs[j].n_steps * plans[j].tiles[t].nq, (int32_t)j, t});
+    std::vector<BatchItem> items;
+    std::vector<int64_t> item_off((size_t)R + 1, 0);
+    for (int64_t r = 0; r < R; ++r) {
+        std::vector<Cost> costs;
+        for (size_t j = 0; j < nj; ++j) {
+            const int64_t n0 = r * round_steps, nc = std::min<int64_t>(round_steps, run_cfgs[j].n_steps - n0);
+            SimArgs a = plans[j].a;
+            a.n0 = n0;
+            a.n_chunk = (int32_t)std::max<int64_t>(nc, 0);
+            a.ou_table = ou_off[j] >= 0 ? b->d_ou.as<float>() + ou_off[j] + n0 * b->jobs[j]->N : nullptr;
+            if (run_cfgs[j].series_mode == TVBX_SERIES_STREAM)
+                a.series = series_at(b->jobs[j]->d_series.ptr, n0 / run_cfgs[j].tavg_steps, b->jobs[j]->N,
+                                     b->jobs[j]->P);
+            jobs[(size_t)r * nj + j] = BatchJob{a, pbs[j], dirs[j]};
+            if (nc <= 0) continue;
+            const int N = b->jobs[j]->N;
+            for (int32_t t = 0; t < plans[j].n_tiles; ++t) {
+                const double per_step = (double)N * 40.0 + (double)plans[j].tile_nnz[t];   // TF work + gathers
+                costs.push_back(Cost{per_step * (double)nc * plans[j].tiles[t].nq, (int32_t)(r * nj + j), t});
+            }
         }
+        std::stable_sort(costs.begin(), costs.end(), [](const Cost& x, const Cost& y) { return x.c > y.c; });
+        for (const Cost& c : costs) items.push_back(BatchItem{c.job, c.tile});
+        item_off[(size_t)r + 1] = (int64_t)items.size();
     }
-    std::stable_sort(costs.begin(), costs.end(), [](const Cost& x, const Cost& y) { return x.c > y.c; });
-    std::vector<BatchItem> items(costs.size());
-    for (size_t i = 0; i < costs.size(); ++i) items[i] = BatchItem{costs[i].job, costs[i].tile};
     b->n_items = (int32_t)items.size();
-    CK(b->d_jobs.ensure(sizeof(BatchJob) * nj), "batch jobs");
+    CK(b->d_jobs.ensure(sizeof(BatchJob) * jobs.size()), "batch jobs");
     CK(b->d_items.ensure(sizeof(BatchItem) * std::max<size_t>(items.size(), 1)), "batch items");
-    CK(b->d_head.ensure(sizeof(int32_t)), "batch queue");
-    CK(cudaMemcpyAsync(b->d_jobs.ptr, jobs.data(), sizeof(BatchJob) * nj, cudaMemcpyHostToDevice, b->stream), "upload");
+    CK(b->d_head.ensure(sizeof(int32_t) * (size_t)R), "batch queue");
+    CK(cudaMemcpyAsync(b->d_jobs.ptr, jobs.data(), sizeof(BatchJob) * jobs.size(), cudaMemcpyHostToDevice, b->stream),
+       "upload");
     if (!items.empty())
         CK(cudaMemcpyAsync(b->d_items.ptr, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
                            b->stream),
@@ -1555,10 +1685,11 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
     // capture the device work of one run
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
     cudaError_t ce = cudaSuccess;
+    tvbx_status fst = TVBX_OK;
     int64_t kernels = 0;
     for (size_t j = 0; j < nj && ce == cudaSuccess; ++j) {
         tvbx_sweep* h = b->jobs[j];
-        const SimArgs& a = jobs[j].a;
+        const SimArgs& a = jobs[j].a;   // round 0
         if ((ce = cudaMemsetAsync(h->d_error.ptr, 0, sizeof(uint32_t), b->stream)) != cudaSuccess) break;
         if ((ce = launch_init_state(a, b->stream)) != cudaSuccess) break;
         ++kernels;
@@ -1567,25 +1698,43 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
             ++kernels;
         }
         if (ce != cudaSuccess) break;
-        if (a.ou_table) {
+        if (ou_off[j] >= 0) {   // the job's whole OU table
             if ((ce = cudaMemsetAsync(h->d_ou_state.ptr, 0, sizeof(float) * h->N, b->stream)) != cudaSuccess) break;
-            if ((ce = launch_ou_table(a.m, const_cast<float*>(a.ou_table), h->d_ou_state.as<float>(), h->N, 0,
-                                      a.n_chunk, a.seed, b->stream)) != cudaSuccess)
+            if ((ce = launch_ou_table(a.m, b->d_ou.as<float>() + ou_off[j], h->d_ou_state.as<float>(), h->N, 0,
+                                      (int32_t)run_cfgs[j].n_steps, a.seed, b->stream)) != cudaSuccess)
                 break;
             ++kernels;
         }
+        if (run_cfgs[j].series_mode == TVBX_SERIES_STREAM)
+            ce = cudaMemsetAsync(h->d_fcacc.ptr, 0, sizeof(float) * (size_t)h->P * ((size_t)h->N * h->N + h->N),
+                                 b->stream);
     }
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_head.ptr, 0, sizeof(int32_t), b->stream);
-    if (ce == cudaSuccess && b->n_items > 0) {
-        ce = launch_sim_batch(b->d_jobs.as<BatchJob>(), b->d_items.as<BatchItem>(), b->n_items,
-                              b->d_head.as<int32_t>(), b->grid, threads, smem, b->only_direct, b->stream);
-        ++kernels;
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_head.ptr, 0, sizeof(int32_t) * (size_t)R, b->stream);
+    std::vector<char> shift_set(nj, 0);
+    for (int64_t r = 0; r < R && ce == cudaSuccess && fst == TVBX_OK; ++r) {
+        const int64_t n_r = item_off[(size_t)r + 1] - item_off[(size_t)r];
+        if (n_r > 0) {
+            const int32_t grid_r = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, n_r));
+            ce = launch_sim_batch(b->d_jobs.as<BatchJob>(), b->d_items.as<BatchItem>() + item_off[(size_t)r],
+                                  (int32_t)n_r, b->d_head.as<int32_t>() + r, grid_r, threads, smem, b->only_direct,
+                                  b->stream);
+            ++kernels;
+        }
+        for (size_t j = 0; j < nj && ce == cudaSuccess && fst == TVBX_OK; ++j) {
+            const SimArgs& a = jobs[(size_t)r * nj + j].a;
+            if (run_cfgs[j].series_mode != TVBX_SERIES_STREAM || a.n_chunk <= 0) continue;
+            bool ss = shift_set[j] != 0;
+            kernels += ss ? 2 : 3;   // (shift,) moments, accumulation
+            fst = stream_fc_chunk(b->jobs[j], a, a.n0, a.n_chunk, ss, b->stream);
+            shift_set[j] = ss ? 1 : 0;
+        }
     }
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
-    if (ce != cudaSuccess || ee != cudaSuccess) {
+    if (ce != cudaSuccess || ee != cudaSuccess || fst != TVBX_OK) {
         if (g) cudaGraphDestroy(g);
         (void)cudaGetLastError();
+        if (fst != TVBX_OK && ce == cudaSuccess && ee == cudaSuccess) return fst;
         return cuda_fail(ce != cudaSuccess ? ce : ee, "batch graph capture");
     }
     b->graph = g;

@@ -13,6 +13,8 @@
 // (G_b + G_b^T) / 2 for each pair (k, j), which also makes the FC exactly
 // symmetric.
 
+#include <algorithm>
+
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -288,6 +290,23 @@ __global__ void fc_shift_kernel(const float* __restrict__ series, int32_t N, int
         s += series[t * N * P + i];
     }
     shift[i] = n > 0 ? s / (float)n : 0.0f;
+}
+
+// acc += add over n floats: the block moments of one chunk of a streamed
+// series folded into the moments of the run (the blocks of all chunks share
+// one shift, so their sums add).
+__global__ void fc_accumulate_kernel(const float* __restrict__ add, float* __restrict__ acc, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc[i] += add[i];
+}
+
+cudaError_t launch_fc_accumulate(const float* add, float* acc, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    note_launch();
+    fc_accumulate_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(add, acc, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fc_shift(const float* series, int32_t N, int64_t P, int64_t t_begin, int64_t t_end,

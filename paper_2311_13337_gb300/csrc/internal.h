@@ -180,6 +180,7 @@ bool fc_tc_supported(int N, int prec);
 // Pearson FC, chi and mean FC from the block moments.
 cudaError_t launch_fc_finalize(const FcArgs& a, cudaStream_t s);
 // Shift m_k = mean of up to 64 evenly spaced samples (standalone series).
+cudaError_t launch_fc_accumulate(const float* add, float* acc, int64_t n, cudaStream_t s);
 cudaError_t launch_fc_shift(const float* series, int32_t N, int64_t P, int64_t t_begin, int64_t t_end,
                             float* shift, cudaStream_t s);
 cudaError_t launch_fcd(const float* blocks, int32_t P, int32_t N, int32_t n_blocks,

@@ -68,7 +68,7 @@ class RunCfg(ctypes.Structure):
     _fields_ = [("dt_ms", ctypes.c_double), ("n_steps", ctypes.c_int64), ("tavg_steps", ctypes.c_int32),
                 ("noise_per_set", ctypes.c_int32), ("seed", ctypes.c_uint64), ("p_offset", ctypes.c_int64),
                 ("transient_samples", ctypes.c_int32), ("chunk_steps", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("withhold_step", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("withhold_step", ctypes.c_int32), ("series_mode", ctypes.c_int32)]
 
 
 class FcCfg(ctypes.Structure):
@@ -281,22 +281,27 @@ def sweep_info(h) -> tuple[int, int, int]:
 
 
 KERNEL_AUTO, KERNEL_GENERAL, KERNEL_PREFETCH, KERNEL_DIRECT = 0, 1, 2, 100
+SERIES_KEEP, SERIES_STREAM = 0, 1   # tvbx_run_cfg.series_mode
 N_PREFETCH_VARIANTS = 17
 PACKED_VARIANTS = (8, 9, 10, 11)   # FP32x2 kernels: need tau_e == tau_i
 
 
 def _run_cfg(dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
-             transient_samples=0, chunk_steps=0, kernel=KERNEL_AUTO, withhold_step=0) -> RunCfg:
+             transient_samples=0, chunk_steps=0, kernel=KERNEL_AUTO, withhold_step=0,
+             series_mode=SERIES_KEEP) -> RunCfg:
     return RunCfg(float(dt_ms), int(n_steps), int(tavg_steps), int(bool(noise_per_set)), int(seed),
-                  int(p_offset), int(transient_samples), int(chunk_steps), int(kernel), int(withhold_step))
+                  int(p_offset), int(transient_samples), int(chunk_steps), int(kernel), int(withhold_step),
+                  int(series_mode))
 
 
 def run(h, dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
-        transient_samples=0, chunk_steps=0, stream=None, kernel=KERNEL_AUTO, withhold_step=0):
+        transient_samples=0, chunk_steps=0, stream=None, kernel=KERNEL_AUTO, withhold_step=0,
+        series_mode=SERIES_KEEP):
     """Enqueue the integration on `stream` (a torch.cuda.Stream, a raw handle
-    or None for the default stream)."""
+    or None for the default stream). series_mode SERIES_STREAM keeps one
+    chunk of samples and folds it into the FC moments (no series export)."""
     cfg = _run_cfg(dt_ms, n_steps, tavg_steps, seed, noise_per_set, p_offset, transient_samples, chunk_steps,
-                   kernel, withhold_step)
+                   kernel, withhold_step, series_mode)
     sp = None
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))

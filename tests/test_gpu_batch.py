@@ -57,10 +57,14 @@ def test_batch_equals_jobs_run_alone(tvbx, oracle):
         assert np.array_equal(st, st1, equal_nan=True)
         for key in ("mean_e_hz", "mean_i_hz", "status"):
             assert np.array_equal(summ[key], s1[key], equal_nan=True), key
-    # a second graph launch starts from the initial state again
+    # a second graph launch starts from the initial state again, and the FC
+    # pass behind the summary runs again (its status bits included)
     b.run()
-    for sw, (X, _, _) in zip(sweeps, first):
+    for sw, (X, summ, _) in zip(sweeps, first):
         assert np.array_equal(sw.series(), X, equal_nan=True)
+        s2 = sw.summary()
+        for key in ("status", "chi", "mean_fc"):
+            assert np.array_equal(s2[key], summ[key], equal_nan=True), key
     # autotuned tiling: same results
     threads, smem_kb, trials = b.tune(trial_steps=100)
     assert threads in (128, 256, 512) and smem_kb in (64, 100, 200)
