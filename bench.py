@@ -1008,12 +1008,14 @@ def run_batch_engine(args):
     from paper_2311_13337_gb300 import synth, tvbx
     m = tvbx.make_model()
     specs = batch_jobs(args.batch_scale)
+    mode = tvbx.SERIES_STREAM if args.batch_series == "stream" else tvbx.SERIES_KEEP
     sweeps, kws = [], []
     total_rs = 0.0
-    alg_bytes = 0.0   # coupling gather + ring write + series write of every job
+    alg_bytes = 0.0   # coupling gather + ring write + sample write of every job
     for sp in specs:
         W, L = synth.connectome(sp["N"])
-        alg_bytes += float(sp["side"] ** 2) * sp["N"] * sp["steps"] * algorithmic_bytes_per_region_step(W, 10)
+        sp["alg_bytes_per_region_step"] = algorithmic_bytes_per_region_step(W, 10)
+        alg_bytes += float(sp["side"] ** 2) * sp["N"] * sp["steps"] * sp["alg_bytes_per_region_step"]
         g = np.linspace(0.0, 0.9, sp["side"])
         be = np.linspace(0.0, 120.0, sp["side"])
         pts = np.tile(np.array([m.defaults[i] for i in range(tvbx.N_AXES)]), (sp["side"] ** 2, 1))
@@ -1021,22 +1023,23 @@ def run_batch_engine(args):
         pts[:, tvbx.AXES.index("b_e")] = np.tile(be, sp["side"])
         pts[:, tvbx.AXES.index("speed")] = sp["v"]
         sweeps.append(tvbx.Sweep(W, L, points=pts))
-        kws.append(dict(dt_ms=0.1, n_steps=sp["steps"], tavg_steps=10, seed=1))
+        kws.append(dict(dt_ms=0.1, n_steps=sp["steps"], tavg_steps=10, seed=1, transient_samples=100,
+                        series_mode=mode))
         total_rs += float(sp["side"] ** 2) * sp["N"] * sp["steps"]
 
-    def plain(kernel):
-        for sw, kw in zip(sweeps, kws):
-            tvbx.run(sw.h, kernel=kernel, **kw)
-        torch.cuda.synchronize()
-
-    def timed(fn, reps):
-        fn()   # warm-up
+    def timed(fn, reps, warm=True):
+        if warm:
+            fn()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):
             fn()
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) / reps
+
+    def results():
+        """Per job: final state, summary and FC (the outputs a streamed run keeps)."""
+        return [(sw.state(), sw.summary(), sw.fc(precision=tvbx.FC_FP32)) for sw in sweeps]
 
     b = tvbx.Batch(list(zip(sweeps, kws)))
     t0 = time.perf_counter()
@@ -1049,13 +1052,29 @@ def run_batch_engine(args):
     t_batch = timed(b.run, args.steps)
     clocks = stop_clock_sampler(sampler)
     launches = (tvbx.launch_count() - launches0) / (args.steps + 1)
-    fc_batch = sweeps[3].fc(precision=tvbx.FC_FP32)          # the 64 x 64, 68-region job
-    X_batch = sweeps[3].series()
-    t_general = timed(lambda: plain(tvbx.KERNEL_GENERAL), 1)
-    X_general = sweeps[3].series()
-    t_auto = timed(lambda: plain(tvbx.KERNEL_AUTO), 1)
-    fc_auto = sweeps[3].fc(precision=tvbx.FC_FP32)
-    fin = np.all(np.isfinite(fc_auto), axis=(1, 2)) & np.all(np.isfinite(fc_batch), axis=(1, 2))
+    res_batch = results()
+    # the plain method: every job alone with the automatic kernel choice, timed per job
+    t_jobs = []
+    for sw, kw in zip(sweeps, kws):
+        t_jobs.append(timed(lambda: tvbx.run(sw.h, kernel=tvbx.KERNEL_AUTO, **kw), 1, warm=False))
+    t_auto = float(sum(t_jobs))
+    res_auto = results()
+    per_job = []
+    for sp, sw, tj, rb, ra in zip(specs, sweeps, t_jobs, res_batch, res_auto):
+        same_state = np.all(np.equal(rb[0], ra[0]) | (np.isnan(rb[0]) & np.isnan(ra[0])), axis=(1, 2))
+        fin = np.all(np.isfinite(ra[2]), axis=(1, 2)) & np.all(np.isfinite(rb[2]), axis=(1, 2))
+        rs = float(sp["side"] ** 2) * sp["N"] * sp["steps"]
+        per_job.append({"N": sp["N"], "v": sp["v"], "sets": sp["side"] ** 2, "steps": sp["steps"],
+                        "plain_auto_s": tj, "plain_kernel": list(tvbx.last_kernel(sw.h)),
+                        "plain_region_steps_per_s": rs / tj,
+                        "plain_alg_gbs": rs * sp["alg_bytes_per_region_step"] / tj / 1e9,
+                        "sets_state_bit_equal": int(same_state.sum()),
+                        "fc_bit_equal_sets": int(np.all(rb[2] == ra[2], axis=(1, 2)).sum()),
+                        "fc_max_abs_diff_finite": float(np.abs(rb[2][fin] - ra[2][fin]).max()) if fin.any() else None})
+    t_general = None
+    if args.batch_general:
+        t_general = timed(lambda: [tvbx.run(sw.h, kernel=tvbx.KERNEL_GENERAL, **kw) for sw, kw in zip(sweeps, kws)],
+                          1, warm=False)
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs") if peaks else 6800.0
     achieved = alg_bytes / t_batch / 1e9
@@ -1070,16 +1089,16 @@ def run_batch_engine(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "uneven batch: 20 sweeps, N in {68,84,192,360} x v in {1,2,4,8,16} m/s, "
                                    "g x b_e grids side (8,16,32,64)[j mod 4], durations (1,2,5,10,20)[j mod 5] s x "
-                                   f"{args.batch_scale}", "duration_scale": args.batch_scale,
-                       "region_steps_per_step": total_rs, "jobs": specs},
+                                   f"{args.batch_scale}; series {args.batch_series}", "duration_scale": args.batch_scale,
+                       "series_mode": args.batch_series, "region_steps_per_step": total_rs,
+                       "jobs": [{k: v for k, v in sp.items() if k != "alg_bytes_per_region_step"} for sp in specs]},
             "clocks": clocks, "gpu_launches": launches,
             "batched": {"s": t_batch, "region_steps_per_s": total_rs / t_batch, "threads": threads, "smem_kb": smem_kb,
                         "tune_s": tune_s, "trial_ms": [float(x) for x in trials], **b.info()},
-            "plain_general": {"s": t_general, "region_steps_per_s": total_rs / t_general,
-                              "series_equal_to_batched": bool(np.array_equal(X_general, X_batch, equal_nan=True))},
-            "plain_auto": {"s": t_auto, "region_steps_per_s": total_rs / t_auto},
-            "speedup_vs_plain_general": t_general / t_batch, "speedup_vs_plain_auto": t_auto / t_batch,
-            "fc_max_abs_diff_batched_vs_plain_auto_68_regions": float(np.abs(fc_batch[fin] - fc_auto[fin]).max()),
+            "plain_auto": {"s": t_auto, "region_steps_per_s": total_rs / t_auto, "jobs": per_job},
+            "speedup_vs_plain_auto": t_auto / t_batch,
+            "plain_general": ({"s": t_general, "region_steps_per_s": total_rs / t_general,
+                               "speedup": t_general / t_batch} if t_general else None),
             "roofline": roofline, "cpu_baseline": base}
     print(json.dumps(line), flush=True)
     b.close()
@@ -1381,7 +1400,10 @@ def main():
                     help="sweep: the paper-scale sweep (default); fc: the FC stage alone on 32,768 "
                          "series of 68 regions x 5,000 samples")
     ap.add_argument("--fc-precision", choices=["fp32", "bf16", "bf16x3", "tf32", "tf32x3"], default="bf16x3")
-    ap.add_argument("--batch-scale", type=float, default=0.25, help="duration scale of the uneven batch")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="duration scale of the uneven batch")
+    ap.add_argument("--batch-series", choices=["stream", "keep"], default="stream",
+                    help="batch jobs keep one chunk of samples and fold it into the FC (stream) or keep the series")
+    ap.add_argument("--batch-general", action="store_true", help="also time the jobs alone on the general kernel")
     ap.add_argument("--t4-seconds", type=float, default=1.0, help="biological seconds per set of the Table 4 grid")
     ap.add_argument("--sur-epochs", type=int, default=60)
     ap.add_argument("--sur-rounds", type=int, default=8)
