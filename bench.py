@@ -290,6 +290,9 @@ def run_engine(args):
             fcsc_dev.copy_(tvbx.fc_fitness(fc_src, sc_dev, stream=stream))
         if world > 1:
             idx, val = gridsearch.gather_fittest(idx, val, 10)
+            # the per-set results of every rank, in global set order
+            best["sets"] = gridsearch.gather_sets({"mean_e": summ["e"], "mean_i": summ["i"], "chi": summ["chi"],
+                                                   "mean_fc": summ["mfc"], "status": status, "fcsc": fcsc_dev})
         best["idx"], best["val"] = idx, val
 
     def step():
@@ -328,6 +331,15 @@ def run_engine(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     el_max = float(t.item())
     value = args.steps * region_steps * world / el_max
+    gathered = None
+    if world > 1:
+        # after the timed region: every set's FC upper triangle, in global set order
+        iu = torch.triu_indices(N, N, 1, device=dev)
+        tri = gridsearch.gather_sets({"fc_triangle": fc_dev[:, iu[0], iu[1]]})["fc_triangle"]
+        gathered = {"sets": int(best["sets"]["chi"].shape[0]), "per_step_floats_per_set": 6,
+                    "fc_triangle_floats": int(tri.numel()),
+                    "fc_triangle_finite_sets": int(torch.isfinite(tri).all(dim=1).sum().item())}
+        del tri
 
     # end to end through the public API with host buffers: inputs from pinned
     # host memory, results read back to host every step
@@ -406,14 +418,16 @@ def run_engine(args):
                                        "per GPU, 68-region synthetic connectome (seed 1), 50000 steps "
                                        "(5 s, dt 0.1 ms), v 4 m/s, FC + FCD (1000/500) + summary",
                            "n_sets_per_gpu": P, "n_regions": N, "n_steps": S, "tavg_steps": ts,
-                           "parallelism": f"dp{world} (set slices, no collective)",
+                           "parallelism": f"dp{world} (set slices; the gathers of the ten fittest and of "
+                                          "the per-set summaries are the only collectives)",
                            "l2": "inputs larger than L2 (ring 4.3 GB, series 44.6 GB per GPU)"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
                 "fc": fc_err, "cpu_baseline": base,
                 "grid_search": {"fittest_sets": [int(i) for i in best["idx"]],
                                 "fitness": [float(v) for v in best["val"]],
                                 "target": "synthetic reference FC of the connectome (seed 11)",
-                                "fcsc_mean": float(torch.nanmean(fcsc_dev).item())}}
+                                "fcsc_mean": float(torch.nanmean(fcsc_dev).item())},
+                "gathered": gathered}
         print(json.dumps(line), flush=True)
     sw.close()
     if world > 1:

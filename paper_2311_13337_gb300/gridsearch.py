@@ -6,8 +6,10 @@ correlation of the simulated FC with a reference FC).
 
 A rank's share is a contiguous range of the global set indices (the one
 bench.py and the sweep partition give), so the ten fittest of the whole sweep
-are among the union of every rank's ten fittest. The gather is the only
-exchange: k (index, fitness) pairs per rank.
+are among the union of every rank's ten fittest. The exchanges are the
+gathers: k (index, fitness) pairs per rank for the selection, and the
+per-set results of every rank (summaries, fitness, FC triangles) in
+global set order.
 """
 from __future__ import annotations
 
@@ -66,3 +68,31 @@ def gather_fittest(idx, val, k: int = 10, select=None, group=None):
     dist.all_gather(parts, pair, group=group)
     parts = [(p[0].cpu().numpy().astype(np.int64), p[1].cpu().numpy().astype(np.float32)) for p in parts]
     return merge(parts, k, select=select)
+
+
+def gather_sets(arrays: dict, group=None) -> dict:
+    """All-gather per-set results over ranks: `arrays` maps a name to a
+    tensor whose first axis is this rank's sets (any count per rank, the
+    same trailing shape and dtype on every rank); returns, on every rank,
+    each name's tensor of all sets in rank order (= global set order for the
+    contiguous slices of the partition)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else torch.device("cpu")
+    any_t = next(iter(arrays.values()))
+    n = torch.tensor([int(any_t.shape[0])], dtype=torch.int64, device=dev)
+    counts = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(counts, n, group=group)
+    counts = [int(c.item()) for c in counts]
+    top = max(counts)
+    out = {}
+    for name, t in arrays.items():
+        if int(t.shape[0]) != counts[dist.get_rank(group)]:
+            raise ValueError(f"{name}: every array needs this rank's set count as its first axis")
+        pad = torch.zeros((top,) + tuple(t.shape[1:]), dtype=t.dtype, device=dev)
+        pad[:t.shape[0]] = t.to(dev)
+        parts = [torch.empty_like(pad) for _ in range(world)]
+        dist.all_gather(parts, pad, group=group)
+        out[name] = torch.cat([p[:c] for p, c in zip(parts, counts)])
+    return out

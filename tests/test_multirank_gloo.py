@@ -123,3 +123,36 @@ def test_grid_search_gathers_the_global_ten_fittest(tmp_path):
     assert np.array_equal(got[1].astype(np.float32), wv.astype(np.float32))
     assert 3 not in wi.tolist()
     assert wi[:2].tolist() == [9, 40]
+
+
+def _sets_rank_main(rank, world, port, out_path):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2311_13337_gb300 import gridsearch
+    n = 3 if rank == 0 else 5                                   # uneven slices
+    base = 0 if rank == 0 else 3
+    ids = torch.arange(base, base + n, dtype=torch.int64)
+    arrays = {"mean_e": ids.to(torch.float32) * 0.5, "status": ids.to(torch.int32) * 2,
+              "fc_triangle": ids.to(torch.float32)[:, None] + torch.arange(6, dtype=torch.float32)[None, :] / 10}
+    got = gridsearch.gather_sets(arrays)
+    torch.save({k: v for k, v in got.items()}, out_path + f".{rank}")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_per_set_results_gather_in_global_order(tmp_path):
+    """Summaries, status words and FC triangles of uneven rank slices arrive
+    on every rank concatenated in global set order."""
+    out = str(tmp_path / "sets")
+    mp.start_processes(_sets_rank_main, args=(WORLD, _free_port(), out), nprocs=WORLD, start_method="spawn")
+    ids = np.arange(8)
+    for rank in range(WORLD):
+        got = torch.load(out + f".{rank}")
+        assert np.array_equal(got["mean_e"].numpy(), ids * 0.5)
+        assert got["status"].dtype == torch.int32 and np.array_equal(got["status"].numpy(), ids * 2)
+        want = ids[:, None] + np.arange(6)[None, :] / 10
+        assert np.allclose(got["fc_triangle"].numpy(), want) and got["fc_triangle"].shape == (8, 6)
