@@ -855,16 +855,32 @@ def run_tffit_engine(args):
     import __graft_entry__ as ge
     ge.build()
     from paper_2311_13337_gb300 import tvbx
-    cell = tvbx.cell_defaults(0)
-    g = np.linspace(0.001, 0.03, 16)
-    nu_e, nu_i, W = np.meshgrid(g, g, [0.0, 50.0, 100.0], indexing="ij")
-    nu_e, nu_i, W = nu_e.ravel(), nu_i.ravel(), W.ravel()
+    m = tvbx.make_model()
     n_cells, T_ms, tr_ms, dt = 128, 5000.0, 200.0, 0.05
-    EL = np.full(nu_e.size, cell["EL"])
+    # input grids: 1,024 points per cell type; the adaptation current only for
+    # the regular-spiking (excitatory) cells, as in the mean field (b_i = 0)
+    g = np.geomspace(0.0005, 0.04, 16)
+    grids = {}
+    e, i, w = np.meshgrid(g, g, [0.0, 25.0, 50.0, 100.0], indexing="ij")
+    grids["RS"] = (e.ravel(), i.ravel(), w.ravel())
+    g2 = np.geomspace(0.0005, 0.04, 32)
+    e, i = np.meshgrid(g2, g2, indexing="ij")
+    grids["FS"] = (e.ravel(), i.ravel(), np.zeros(e.size))
+    cells = {"RS": tvbx.cell_defaults(0), "FS": tvbx.cell_defaults(1)}
+    table1 = {"RS": np.array(list(m.P_e)), "FS": np.array(list(m.P_i))}
+    printed = {"RS": table1["RS"] * np.array([1.0] * 9 + [-1.0]), "FS": table1["FS"]}   # RS P_sigmaV.tauN as printed
 
     def step():
-        r = tvbx.cell_rates(cell, nu_e, nu_i, W, n_cells=n_cells, T_ms=T_ms, transient_ms=tr_ms, dt_ms=dt, seed=1)
-        return r, tvbx.tf_fit(nu_e, nu_i, W, EL, r)
+        out = {}
+        for name in ("RS", "FS"):
+            ne, ni, W = grids[name]
+            EL = np.full(ne.size, cells[name]["EL"])
+            r = tvbx.cell_rates(cells[name], ne, ni, W, n_cells=n_cells, T_ms=T_ms, transient_ms=tr_ms, dt_ms=dt,
+                                seed=1)
+            P1, used1 = tvbx.tf_fit(ne, ni, W, EL, r)
+            P2, rms2, used2 = tvbx.tf_refit(ne, ni, W, EL, r, P1)
+            out[name] = (r, P1, used1, P2, rms2, used2)
+        return out
 
     for _ in range(args.warmup):
         step()
@@ -872,29 +888,45 @@ def run_tffit_engine(args):
     sampler = start_clock_sampler(0)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        rates, (P, used) = step()
+        res = step()
     el = (time.perf_counter() - t0) / args.steps
     clocks = stop_clock_sampler(sampler)
-    units = float(nu_e.size) * n_cells * (T_ms / dt)
-    m = tvbx.make_model()
+    units = float(sum(grids[k][0].size for k in grids)) * n_cells * (T_ms / dt)
+    fits = {}
+    for name in ("RS", "FS"):
+        ne, ni, W = grids[name]
+        EL = np.full(ne.size, cells[name]["EL"])
+        r, P1, used1, P2, rms2, used2 = res[name]
+
+        def rate_rms(P):
+            # the rate error of fixed coefficients (a refit of zero steps)
+            return tvbx.tf_refit(ne, ni, W, EL, r, P, max_iter=0)[1]
+        fits[name] = {"points": int(ne.size), "silent_points": int((r <= 0).sum()),
+                      "stage1_points_in_range": int(used1), "stage1_P_mV": [float(x) for x in P1],
+                      "stage2_points": int(used2), "stage2_P_mV": [float(x) for x in P2],
+                      "table1_P_mV": [float(x) for x in printed[name]],
+                      "rms_rate_hz": {"table1_printed": 1e3 * rate_rms(printed[name]),
+                                      "engine_reading": 1e3 * rate_rms(table1[name]),
+                                      "stage1": 1e3 * rate_rms(P1), "stage2": 1e3 * rms2}}
+    fits["RS"]["P_sigmaV_tauN_sign_of_stage2"] = int(np.sign(fits["RS"]["stage2_P_mV"][9]))
     base = None
     if not args.no_cpu_baseline:
         from oracle import adex_cell as A
+        ne, ni, W = grids["RS"]
         t0 = time.time()
-        A.simulate_cells(A.CELL_RS, nu_e[:32], nu_i[:32], W[:32], 8, 500.0, 0.0, dt, 1)
+        A.simulate_cells(A.CELL_RS, ne[:32], ni[:32], W[:32], 8, 500.0, 0.0, dt, 1)
         cel = time.time() - t0
         base = {"value": 32 * 8 * (500.0 / dt) / cel, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                 "sample": f"32 points x 8 cells x 0.5 s (FP64 numpy); {cel:.1f} s"}
     line = {"metric": TF_METRIC, "value": units / el, "unit": "cell-steps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * el, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "768 points (nu_e 16 x nu_i 16 in 1-30 Hz, W in {0, 50, 100} pA) x 128 "
-                                   "regular-spiking AdEx cells x 5 s at dt 0.05 ms, then the Table 1 least-squares "
-                                   "fit", "n_points": int(nu_e.size), "n_cells": n_cells},
+            "config": {"workload": "1,024 points per cell type (RS: nu_e 16 x nu_i 16 in 0.5-40 Hz, log-spaced, x W "
+                                   "in {0, 25, 50, 100} pA; FS: 32 x 32, W 0) x 128 AdEx cells x 5 s at dt 0.05 "
+                                   "ms, then both stages of the Table 1 fit (inverted thresholds by linear least "
+                                   "squares, then Levenberg-Marquardt on the rates)", "n_cells": n_cells},
             "clocks": clocks, "gpu_launches": (tvbx.launch_count() - launches0) / args.steps,
-            "fit": {"points_used": used, "P_fitted_mV": [float(x) for x in P],
-                    "P_table1_RS_mV": [float(x) for x in m.P_e]},
-            "roofline": None, "cpu_baseline": base,
+            "fit": fits, "roofline": None, "cpu_baseline": base,
             "note": "compute-bound cell integration (an exponential per step); see DESIGN for the roofline reading"}
     print(json.dumps(line), flush=True)
     return 0

@@ -686,6 +686,22 @@ tvbx_status tvbx_tf_fit(const tvbx_model* m, int64_t n_points, const double* nu_
                         const double* W_pA, const double* E_L, const double* rate_khz, double P_out[10],
                         int32_t* n_used);
 
+/* tvbx_tf_refit: host computation (no device use), the fit's second stage
+ * (Sec. "Transfer Function": the polynomial is fitted to single-cell rates;
+ * Zerlaut's procedure refines the threshold fit on the rates themselves).
+ * Starting from P_init[10] (e.g. tvbx_tf_fit's result), the coefficients
+ * that minimise sum_p (F_p(P) - rate_p)^2, F_p(P) the template's rate
+ * erfc((V_thre(P) - mu_V) / (sqrt(2) sigma_V)) / (2 tau_V), over every point
+ * with a finite rate >= 0 (silent and saturated points included), by
+ * Levenberg-Marquardt with the analytic Jacobian, at most max_iter steps
+ * (0: P_out = P_init, i.e. the rate error of given coefficients).
+ * P_out[10] (mV, Table 1 column order); *rms_out = root-mean-square rate
+ * error (kHz) at P_out and *n_used = points used (both nullable). Fewer than
+ * 10 usable points or non-finite rates at P_init: TVBX_E_NUMERIC. */
+tvbx_status tvbx_tf_refit(const tvbx_model* m, int64_t n_points, const double* nu_e_khz, const double* nu_i_khz,
+                          const double* W_pA, const double* E_L, const double* rate_khz, const double P_init[10],
+                          int32_t max_iter, double P_out[10], double* rms_out, int32_t* n_used);
+
 /* ---- Surrogate network ---------------------------------------------------
  * The paper has no surrogate model; it motivates guided exploration of the
  * parameter space (Sec. "Discussion"). This is the learned form of the

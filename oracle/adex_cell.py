@@ -159,3 +159,35 @@ def fit_polynomial(muV, sigV, tauVN, vthre, norm):
     A = basis((np.asarray(muV) - mu0) / dmu0, (np.asarray(sigV) - sig0) / dsig0, (np.asarray(tauVN) - tau0) / dtau0)
     P, *_ = np.linalg.lstsq(A, np.asarray(vthre, dtype=np.float64), rcond=None)
     return P
+
+
+def template_rate(P, muV, sigV, tauV, tauVN, norm):
+    """The template's rate erfc((V_thre - mu_V) / (sqrt(2) sigma_V)) / (2 tau_V)
+    with V_thre the Table 1 polynomial of coefficients P (kHz for tau_V in ms)."""
+    from scipy.special import erfc
+    mu0, dmu0, sig0, dsig0, tau0, dtau0 = norm
+    B = basis((np.asarray(muV) - mu0) / dmu0, (np.asarray(sigV) - sig0) / dsig0, (np.asarray(tauVN) - tau0) / dtau0)
+    vth = B @ np.asarray(P, dtype=np.float64)
+    return erfc((vth - muV) / (np.sqrt(2.0) * sigV)) / (2.0 * tauV), B
+
+
+def refit_polynomial(muV, sigV, tauV, tauVN, F, P_init, norm):
+    """Second stage of the fit: the coefficients minimising the squared error
+    of the template's rate against the measured rates F over all the given
+    points, from P_init (scipy's Levenberg-Marquardt least squares with the
+    analytic Jacobian). Returns (P, rms rate error)."""
+    from scipy.optimize import least_squares
+    muV, sigV, tauV, tauVN, F = (np.asarray(a, dtype=np.float64) for a in (muV, sigV, tauV, tauVN, F))
+
+    def res(P):
+        return template_rate(P, muV, sigV, tauV, tauVN, norm)[0] - F
+
+    def jac(P):
+        Fp, B = template_rate(P, muV, sigV, tauV, tauVN, norm)
+        z = (B @ P - muV) / (np.sqrt(2.0) * sigV)
+        g = -np.exp(-z * z) / (np.sqrt(2.0 * np.pi) * sigV * tauV)
+        return g[:, None] * B
+
+    out = least_squares(res, np.asarray(P_init, dtype=np.float64), jac=jac, method="lm", xtol=1e-15, ftol=1e-15,
+                        gtol=1e-15, max_nfev=20000)
+    return out.x, float(np.sqrt(np.mean(out.fun ** 2)))

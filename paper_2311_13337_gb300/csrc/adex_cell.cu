@@ -232,6 +232,39 @@ extern "C" tvbx_status tvbx_cell_rates(const tvbx_cell_params* cell, int64_t n_p
     return TVBX_OK;
 }
 
+// Template moments of one point (the same template as the engine's transfer
+// function, FP64): mu_V, sigma_V, tau_V and the normalised tau_V^N; false if
+// sigma_V is not finite.
+static bool tf_moments(const tvbx_model* m, double nu_e, double nu_i, double W, double EL, double* muV_o,
+                       double* sigV_o,
+                       double* tauV_o, double* tauVN_o)
+{
+    const double fe = m->K_e * std::max(nu_e, 0.0) + m->rate_floor;
+    const double fi = m->K_i * std::max(nu_i, 0.0) + m->rate_floor;
+    const double mGe = m->Q_e * m->tau_e * fe, mGi = m->Q_i * m->tau_i * fi;
+    const double muG = m->g_L + mGe + mGi;
+    const double muV = (mGe * m->E_e + mGi * m->E_i + m->g_L * EL - W) / muG;
+    const double Tm = m->C_m / muG;
+    const double Ue = m->Q_e * (m->E_e - muV) / muG, Ui = m->Q_i * (m->E_i - muV) / muG;
+    const double Ae = fe * (Ue * m->tau_e) * (Ue * m->tau_e), Ai = fi * (Ui * m->tau_i) * (Ui * m->tau_i);
+    const double s2 = Ae / (m->tau_e + Tm) + Ai / (m->tau_i + Tm);   // 2 sigma_V^2
+    const double sigV = std::sqrt(0.5 * s2);
+    const double tauV = (Ae + Ai) / s2;
+    *muV_o = muV;
+    *sigV_o = sigV;
+    *tauV_o = tauV;
+    *tauVN_o = tauV * m->g_L / m->C_m;
+    return std::isfinite(sigV) && sigV > 0.0 && std::isfinite(tauV) && tauV > 0.0;
+}
+
+// The ten Table 1 basis functions of a point's normalised moments.
+static void tf_basis(const tvbx_model* m, double muV, double sigV, double tauVN, double row[10])
+{
+    const double V = (muV - m->mu0) / m->dmu0, S = (sigV - m->sig0) / m->dsig0, Z = (tauVN - m->tau0) / m->dtau0;
+    const double r[10] = {1.0, V, S, Z, V * V, S * S, Z * Z, V * S, V * Z, S * Z};
+    for (int i = 0; i < 10; ++i) row[i] = r[i];
+}
+
 extern "C" tvbx_status tvbx_tf_fit(const tvbx_model* m, int64_t n_points, const double* nu_e_khz,
                                    const double* nu_i_khz, const double* W_pA, const double* E_L,
                                    const double* rate_khz, double P_out[10], int32_t* n_used)
@@ -242,24 +275,13 @@ extern "C" tvbx_status tvbx_tf_fit(const tvbx_model* m, int64_t n_points, const 
     std::vector<double> A, b;
     int rows = 0;
     for (int64_t p = 0; p < n_points; ++p) {
-        // template moments (the same template as the engine's transfer function)
-        const double fe = m->K_e * std::max(nu_e_khz[p], 0.0) + m->rate_floor;
-        const double fi = m->K_i * std::max(nu_i_khz[p], 0.0) + m->rate_floor;
-        const double mGe = m->Q_e * m->tau_e * fe, mGi = m->Q_i * m->tau_i * fi;
-        const double muG = m->g_L + mGe + mGi;
-        const double muV = (mGe * m->E_e + mGi * m->E_i + m->g_L * E_L[p] - W_pA[p]) / muG;
-        const double Tm = m->C_m / muG;
-        const double Ue = m->Q_e * (m->E_e - muV) / muG, Ui = m->Q_i * (m->E_i - muV) / muG;
-        const double Ae = fe * (Ue * m->tau_e) * (Ue * m->tau_e), Ai = fi * (Ui * m->tau_i) * (Ui * m->tau_i);
-        const double s2 = Ae / (m->tau_e + Tm) + Ai / (m->tau_i + Tm);   // 2 sigma_V^2
-        const double sigV = std::sqrt(0.5 * s2);
-        const double tauV = (Ae + Ai) / s2;
-        const double tauVN = tauV * m->g_L / m->C_m;
+        double muV, sigV, tauV, tauVN;
+        const bool ok = tf_moments(m, nu_e_khz[p], nu_i_khz[p], W_pA[p], E_L[p], &muV, &sigV, &tauV, &tauVN);
         const double F = rate_khz[p];
-        if (!(F > 0.0) || !(2.0 * tauV * F < 1.0) || !std::isfinite(sigV)) continue;
+        if (!(F > 0.0) || !(2.0 * tauV * F < 1.0) || !ok) continue;
         const double vth = muV + std::sqrt(2.0) * sigV * inv_erfc(2.0 * tauV * F);
-        const double V = (muV - m->mu0) / m->dmu0, S = (sigV - m->sig0) / m->dsig0, Z = (tauVN - m->tau0) / m->dtau0;
-        const double row[10] = {1.0, V, S, Z, V * V, S * S, Z * Z, V * S, V * Z, S * Z};
+        double row[10];
+        tf_basis(m, muV, sigV, tauVN, row);
         A.insert(A.end(), row, row + 10);
         b.push_back(vth);
         ++rows;
@@ -267,5 +289,95 @@ extern "C" tvbx_status tvbx_tf_fit(const tvbx_model* m, int64_t n_points, const 
     if (n_used) *n_used = rows;
     if (rows < 10) return report_error(TVBX_E_NUMERIC, "only %d points with a rate in (0, 1 / (2 tau_V))", rows);
     if (!least_squares(A, b, rows, 10, P_out)) return report_error(TVBX_E_NUMERIC, "rank-deficient fit");
+    return TVBX_OK;
+}
+
+// Second stage of the fit: the coefficients that minimise the squared error
+// of the template's rate F(P) = erfc((V_thre(P) - mu_V) / (sqrt(2) sigma_V)) /
+// (2 tau_V), V_thre(P) = sum_i P_i B_i, over every point with a finite rate
+// (silent and saturated points included). Levenberg-Marquardt from P_init
+// with the analytic Jacobian dF/dP_i = -exp(-z^2) B_i / (sqrt(2 pi) sigma_V
+// tau_V); each step solves the damped system [J; sqrt(lambda) D] d = [-r; 0]
+// (D = the column norms of J) by Householder QR.
+extern "C" tvbx_status tvbx_tf_refit(const tvbx_model* m, int64_t n_points, const double* nu_e_khz,
+                                     const double* nu_i_khz, const double* W_pA, const double* E_L,
+                                     const double* rate_khz, const double P_init[10], int32_t max_iter,
+                                     double P_out[10], double* rms_out, int32_t* n_used)
+{
+    if (!m || !nu_e_khz || !nu_i_khz || !W_pA || !E_L || !rate_khz || !P_init || !P_out)
+        return report_error(TVBX_E_INVALID_ARG, "NULL argument");
+    if (n_points < 1 || max_iter < 0) return report_error(TVBX_E_INVALID_ARG, "need n_points >= 1 and max_iter >= 0");
+    struct Pt { double muV, sigV, tauV, B[10], F; };
+    std::vector<Pt> pts;
+    for (int64_t p = 0; p < n_points; ++p) {
+        Pt q;
+        double tauVN;
+        if (!std::isfinite(rate_khz[p]) || rate_khz[p] < 0.0) continue;
+        if (!tf_moments(m, nu_e_khz[p], nu_i_khz[p], W_pA[p], E_L[p], &q.muV, &q.sigV, &q.tauV, &tauVN)) continue;
+        tf_basis(m, q.muV, q.sigV, tauVN, q.B);
+        q.F = rate_khz[p];
+        pts.push_back(q);
+    }
+    const int n = (int)pts.size();
+    if (n_used) *n_used = n;
+    if (n < 10) return report_error(TVBX_E_NUMERIC, "only %d points with a finite rate", n);
+    const double c_erf = 1.0 / std::sqrt(2.0 * M_PI);
+    auto residuals = [&](const double* P, std::vector<double>& r, std::vector<double>* J) {
+        double cost = 0.0;
+        for (int p = 0; p < n; ++p) {
+            const Pt& q = pts[p];
+            double vth = 0.0;
+            for (int i = 0; i < 10; ++i) vth += P[i] * q.B[i];
+            const double z = (vth - q.muV) / (std::sqrt(2.0) * q.sigV);
+            r[p] = std::erfc(z) / (2.0 * q.tauV) - q.F;
+            cost += r[p] * r[p];
+            if (J) {
+                const double g = -c_erf * std::exp(-z * z) / (q.sigV * q.tauV);
+                for (int i = 0; i < 10; ++i) (*J)[(size_t)p * 10 + i] = g * q.B[i];
+            }
+        }
+        return cost;
+    };
+    double P[10], Pn[10];
+    for (int i = 0; i < 10; ++i) P[i] = P_init[i];
+    std::vector<double> r(n), rn(n), J((size_t)n * 10);
+    double cost = residuals(P, r, &J);
+    if (!std::isfinite(cost)) return report_error(TVBX_E_NUMERIC, "the rates at P_init are not finite");
+    double lambda = 1e-3;
+    std::vector<double> Aug((size_t)(n + 10) * 10), rhs(n + 10);
+    for (int it = 0; it < max_iter; ++it) {
+        double D[10];
+        for (int i = 0; i < 10; ++i) {
+            double s = 0.0;
+            for (int p = 0; p < n; ++p) s += J[(size_t)p * 10 + i] * J[(size_t)p * 10 + i];
+            D[i] = std::sqrt(s) > 0.0 ? std::sqrt(s) : 1.0;
+        }
+        bool accepted = false;
+        while (!accepted && lambda < 1e16) {
+            std::copy(J.begin(), J.end(), Aug.begin());
+            for (int p = 0; p < n; ++p) rhs[p] = -r[p];
+            for (int i = 0; i < 10; ++i) {
+                for (int j = 0; j < 10; ++j) Aug[(size_t)(n + i) * 10 + j] = i == j ? std::sqrt(lambda) * D[i] : 0.0;
+                rhs[n + i] = 0.0;
+            }
+            double d[10];
+            if (!least_squares(Aug, rhs, n + 10, 10, d)) return report_error(TVBX_E_NUMERIC, "singular step");
+            for (int i = 0; i < 10; ++i) Pn[i] = P[i] + d[i];
+            const double cn = residuals(Pn, rn, nullptr);
+            if (std::isfinite(cn) && cn < cost) {
+                const double gain = cost - cn;
+                for (int i = 0; i < 10; ++i) P[i] = Pn[i];
+                cost = residuals(P, r, &J);
+                lambda = std::max(lambda * 0.3, 1e-12);
+                accepted = true;
+                if (gain <= 1e-15 * cost) it = max_iter;   // converged
+            } else {
+                lambda *= 10.0;
+            }
+        }
+        if (!accepted) break;   // no descent at any damping: a minimum
+    }
+    for (int i = 0; i < 10; ++i) P_out[i] = P[i];
+    if (rms_out) *rms_out = std::sqrt(cost / n);
     return TVBX_OK;
 }

@@ -92,7 +92,7 @@ EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep
            "tvbx_surrogate_destroy", "tvbx_fc_pca", "tvbx_fc_pca_project", "tvbx_batch_create", "tvbx_batch_tune",
            "tvbx_batch_run", "tvbx_batch_info", "tvbx_batch_destroy", "tvbx_fc_fitness", "tvbx_top_k",
            "tvbx_series_analysis", "tvbx_bold_defaults", "tvbx_bold", "tvbx_phfcd",
-           "tvbx_cell_defaults", "tvbx_cell_rates", "tvbx_tf_fit", "tvbx_run_continue", "tvbx_checkpoint_size",
+           "tvbx_cell_defaults", "tvbx_cell_rates", "tvbx_tf_fit", "tvbx_tf_refit", "tvbx_run_continue", "tvbx_checkpoint_size",
            "tvbx_checkpoint", "tvbx_restore", "tvbx_set_allocator")
 
 
@@ -168,6 +168,8 @@ def load(build_if_missing: bool = False):
     L.tvbx_cell_rates.argtypes = [ctypes.POINTER(CellParams), i64, dp, dp, dp, i32, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_uint64, dp]
     L.tvbx_tf_fit.argtypes = [ctypes.POINTER(Model), i64, dp, dp, dp, dp, dp, dp, ctypes.POINTER(i32)]
+    L.tvbx_tf_refit.argtypes = [ctypes.POINTER(Model), i64, dp, dp, dp, dp, dp, dp, i32, dp,
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
     L.tvbx_bold.argtypes = [fp, i32, i64, i64, ctypes.c_double, i32, ctypes.POINTER(BoldParams), fp, i32, fp, vp]
     L.tvbx_phfcd.argtypes = [fp, i32, i64, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, fp,
                              ctypes.POINTER(i32), vp]
@@ -773,6 +775,23 @@ def cell_rates(cell: dict, nu_e_khz, nu_i_khz, W_pA, n_cells=16, T_ms=5000.0, tr
                                   _dptr(arrs[2]), int(n_cells), float(T_ms), float(transient_ms), float(dt_ms),
                                   int(seed), _dptr(out)), "tvbx_cell_rates")
     return out
+
+
+def tf_refit(nu_e_khz, nu_i_khz, W_pA, E_L, rate_khz, P_init, max_iter=200, model: Model | None = None):
+    """Second stage of the Table 1 fit (tvbx_tf_refit): least squares on the
+    rates from P_init: (P[10], rms rate error in kHz, points used)."""
+    m = model if model is not None else make_model()
+    arrs = [np.ascontiguousarray(np.atleast_1d(a), dtype=np.float64) for a in (nu_e_khz, nu_i_khz, W_pA, E_L,
+                                                                               rate_khz)]
+    P0 = np.ascontiguousarray(P_init, dtype=np.float64)
+    if P0.shape != (10,):
+        raise ValueError("P_init must have 10 coefficients")
+    P = np.zeros(10)
+    rms = ctypes.c_double(0.0)
+    used = ctypes.c_int32(0)
+    _check(load().tvbx_tf_refit(ctypes.byref(m), arrs[0].size, *[_dptr(a) for a in arrs], _dptr(P0), int(max_iter),
+                                _dptr(P), ctypes.byref(rms), ctypes.byref(used)), "tvbx_tf_refit")
+    return P, rms.value, used.value
 
 
 def tf_fit(nu_e_khz, nu_i_khz, W_pA, E_L, rate_khz, model: Model | None = None):

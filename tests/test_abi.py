@@ -190,6 +190,34 @@ def test_tf_fit_on_the_host_equals_the_oracle_fit(lib, oracle):
     assert used2 == keep.sum() and np.allclose(P2, Po, rtol=1e-8, atol=1e-8)
 
 
+def test_tf_refit_on_the_host_equals_the_oracle_refit(lib, oracle):
+    """tvbx_tf_refit is host arithmetic: on template rates it returns Table 1
+    from a perturbed start, and on perturbed rates (silent points included)
+    it reaches the oracle's least-squares minimum."""
+    from oracle import adex_cell as A
+    m_e = lib.make_model()
+    om = oracle.make_model()
+    norm = (om.mu0, om.dmu0, om.sig0, om.dsig0, om.tau0, om.dtau0)
+    rng = np.random.default_rng(21)
+    rows = []
+    for _ in range(300):
+        x_e, x_i, w = rng.uniform(0.0005, 0.04), rng.uniform(0.0005, 0.04), rng.uniform(0, 150)
+        jet, aux = oracle.tf_eval(om, "e", -64.0, x_e, x_i, w)
+        rows.append((x_e, x_i, w, aux[1], aux[3], aux[4], aux[5], jet[0]))
+    R = np.array(rows)
+    EL = np.full(len(R), -64.0)
+    P_true = np.array(list(om.P_e))
+    P0 = P_true * (1 + 0.05 * rng.standard_normal(10)) + rng.uniform(-1, 1, 10)
+    P, rms, used = lib.tf_refit(R[:, 0], R[:, 1], R[:, 2], EL, R[:, 7], P0, model=m_e)
+    assert used == len(R) and np.allclose(P, P_true, atol=1e-6) and rms < 1e-10
+    F = R[:, 7] * rng.uniform(0.8, 1.25, len(R))
+    P2, rms2, _ = lib.tf_refit(R[:, 0], R[:, 1], R[:, 2], EL, F, P_true, model=m_e)
+    Po, rms_o = A.refit_polynomial(R[:, 3], R[:, 4], R[:, 5], R[:, 6], F, P_true, norm)
+    assert np.allclose(P2, Po, rtol=1e-6, atol=1e-5) and rms2 == pytest.approx(rms_o, rel=1e-8)
+    with pytest.raises(lib.TvbxError):
+        lib.tf_refit(R[:5, 0], R[:5, 1], R[:5, 2], EL[:5], F[:5], P_true, model=m_e)   # fewer than 10 points
+
+
 def test_cell_defaults_match_the_oracle(lib):
     from oracle import adex_cell as A
     assert lib.cell_defaults(0) == A.CELL_RS and lib.cell_defaults(1) == A.CELL_FS

@@ -92,3 +92,60 @@ def test_fit_recovers_table1_from_template_rates(oracle):
     assert len(vth) >= 40
     P = A.fit_polynomial(muV, sigV, tauVN, vth, norm)
     assert np.allclose(P, P_true, atol=1e-5)
+
+
+def _template_points(oracle, m, rng, n):
+    """Moments and template rates of n random input points (silent and
+    near-saturated ones included)."""
+    rows = []
+    for _ in range(n):
+        x_e, x_i, W = rng.uniform(0.0005, 0.04), rng.uniform(0.0005, 0.04), rng.uniform(0, 150)
+        jet, aux = oracle.tf_eval(m, "e", -64.0, x_e, x_i, W)
+        rows.append((x_e, x_i, W, aux[1], aux[3], aux[4], aux[5], jet[0]))
+    return np.array(rows)
+
+
+def test_refit_rate_model_is_the_oracle_transfer_function(oracle):
+    """The refit's rate of Table 1's coefficients is the oracle's transfer
+    function at every point, zero and near-saturated rates included."""
+    m = oracle.make_model()
+    norm = (m.mu0, m.dmu0, m.sig0, m.dsig0, m.tau0, m.dtau0)
+    R = _template_points(oracle, m, np.random.default_rng(11), 200)
+    F, _ = A.template_rate(np.array(list(m.P_e)), R[:, 3], R[:, 4], R[:, 5], R[:, 6], norm)
+    assert np.allclose(F, R[:, 7], rtol=1e-10, atol=1e-14)
+    assert (R[:, 7] < 1e-6).sum() >= 10   # silent points are part of the data
+
+
+def test_refit_recovers_table1_from_template_rates(oracle):
+    """From coefficients perturbed by 5% and 1 mV, the second stage returns
+    Table 1 on rates the template itself produced (zero residual there)."""
+    m = oracle.make_model()
+    norm = (m.mu0, m.dmu0, m.sig0, m.dsig0, m.tau0, m.dtau0)
+    P_true = np.array(list(m.P_e))
+    rng = np.random.default_rng(12)
+    R = _template_points(oracle, m, rng, 300)
+    P0 = P_true * (1 + 0.05 * rng.standard_normal(10)) + rng.uniform(-1, 1, 10)
+    P, rms = A.refit_polynomial(R[:, 3], R[:, 4], R[:, 5], R[:, 6], R[:, 7], P0, norm)
+    assert np.allclose(P, P_true, atol=1e-6) and rms < 1e-12
+
+
+def test_refit_is_a_stationary_point_no_worse_than_its_start(oracle):
+    """On perturbed rates the refit lowers the rate error of its start and the
+    gradient of the squared error vanishes there."""
+    m = oracle.make_model()
+    norm = (m.mu0, m.dmu0, m.sig0, m.dsig0, m.tau0, m.dtau0)
+    rng = np.random.default_rng(13)
+    R = _template_points(oracle, m, rng, 300)
+    F = R[:, 7] * rng.uniform(0.8, 1.25, len(R))
+    P0 = np.array(list(m.P_e))
+    P, rms = A.refit_polynomial(R[:, 3], R[:, 4], R[:, 5], R[:, 6], F, P0, norm)
+    F0, _ = A.template_rate(P0, R[:, 3], R[:, 4], R[:, 5], R[:, 6], norm)
+    assert rms < np.sqrt(np.mean((F0 - F) ** 2))
+    Fp, B = A.template_rate(P, R[:, 3], R[:, 4], R[:, 5], R[:, 6], norm)
+    z = (B @ P - R[:, 3]) / (np.sqrt(2.0) * R[:, 4])
+    J = (-np.exp(-z * z) / (np.sqrt(2 * np.pi) * R[:, 4] * R[:, 5]))[:, None] * B
+    g = J.T @ (Fp - F)
+    assert np.linalg.norm(g) <= 1e-7 * np.linalg.norm(J) * np.linalg.norm(Fp - F)
+    z0 = (B @ P0 - R[:, 3]) / (np.sqrt(2.0) * R[:, 4])
+    J0 = (-np.exp(-z0 * z0) / (np.sqrt(2 * np.pi) * R[:, 4] * R[:, 5]))[:, None] * B
+    assert np.linalg.norm(J0.T @ (F0 - F)) >= 1e4 * np.linalg.norm(g)   # far from stationary at the start
