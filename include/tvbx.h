@@ -139,6 +139,12 @@ typedef struct {
                                  run reports TVBX_E_TIMEOUT (no fault, the context
                                  stays usable). Other kernels ignore it. */
     int32_t series_mode;      /* TVBX_SERIES_KEEP (0) or TVBX_SERIES_STREAM */
+    int32_t keep_i_series;    /* 1: also keep the inhibitory rate series
+                                 [T][N][P] (block means like E; read with
+                                 tvbx_series_pop_range, pop 1), e.g. for the
+                                 PLI of the I rates (Table 2 PLI_i) through
+                                 tvbx_series_analysis; needs TVBX_SERIES_KEEP
+                                 and doubles the series memory. 0: E only. */
 } tvbx_run_cfg;
 
 /* Series modes of tvbx_run_cfg.
@@ -316,6 +322,12 @@ tvbx_status tvbx_restore(tvbx_sweep* h, const void* host_buf, uint64_t bytes);
  * run since the last tvbx_run. Errors: TVBX_E_BAD_STATE before tvbx_run. */
 tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* mean_i_hz,
                          float* chi, float* mean_fc, uint32_t* status);
+
+/* Copy a window of the E (pop 0) or I (pop 1) series, as tvbx_series_range;
+ * the I series exists when the last run set keep_i_series (else
+ * TVBX_E_BAD_STATE). */
+tvbx_status tvbx_series_pop_range(const tvbx_sweep* h, int32_t pop, int64_t set_begin, int64_t set_count,
+                                  int64_t t_begin, int64_t t_count, int32_t mem, float* out);
 
 /* Copy the E series [n_sets][n_regions][n_samples] (kHz) of the last run. */
 tvbx_status tvbx_series(const tvbx_sweep* h, int32_t mem, float* out);

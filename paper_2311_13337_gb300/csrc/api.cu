@@ -249,13 +249,14 @@ struct tvbx_sweep {
     DevBuf d_csr_row, d_csr_cd, d_csr_w, d_groups, d_tiles;
     DevBuf d_blocks, d_fc, d_chi, d_meanfc, d_vec, d_fcd, d_tmp, d_perm, d_inv, d_mean_e, d_mean_i, d_error;
     DevBuf d_fcacc, d_shift;        // streamed series: FC moments over the run, fixed shift [N][P]
+    DevBuf d_series_i;              // I series [T][N][P] when the run keeps it
 
     ~tvbx_sweep()
     {
         DevBuf* all[] = {&d_prm, &d_ext, &d_state, &d_status, &d_ring, &d_series, &d_ou_table,
                          &d_ou_state, &d_csr_row, &d_csr_cd, &d_csr_w, &d_groups, &d_tiles,
                          &d_blocks, &d_fc, &d_chi, &d_meanfc, &d_vec, &d_fcd, &d_tmp, &d_perm,
-                         &d_inv, &d_mean_e, &d_mean_i, &d_error, &d_fcacc, &d_shift};
+                         &d_inv, &d_mean_e, &d_mean_i, &d_error, &d_fcacc, &d_shift, &d_series_i};
         for (DevBuf* b : all) b->release();
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
@@ -560,6 +561,10 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
         return fail(TVBX_E_INVALID_ARG, "unknown series_mode %d", c.series_mode);
     if (c.series_mode == TVBX_SERIES_STREAM && h->N > 384)
         return fail(TVBX_E_UNSUPPORTED, "a streamed series needs n_regions <= 384 (have %d)", h->N);
+    if (c.keep_i_series != 0 && c.keep_i_series != 1)
+        return fail(TVBX_E_INVALID_ARG, "keep_i_series must be 0 or 1");
+    if (c.keep_i_series && c.series_mode != TVBX_SERIES_KEEP)
+        return fail(TVBX_E_INVALID_ARG, "keep_i_series needs series_mode TVBX_SERIES_KEEP");
     h->stream = s;
     h->ran = false;
     h->fc_valid = false;
@@ -681,6 +686,7 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     CK(h->d_status.ensure(sizeof(uint32_t) * P), "status");
     CK(h->d_ring.ensure(sizeof(float) * (size_t)std::max<int64_t>(ring_floats, 1)), "ring buffers");
     CK(h->d_series.ensure(sizeof(float) * (size_t)std::max<int64_t>(series_T * N * P, 1)), "series");
+    if (c.keep_i_series) CK(h->d_series_i.ensure(sizeof(float) * (size_t)std::max<int64_t>(T * N * P, 1)), "I series");
     if (c.series_mode == TVBX_SERIES_STREAM) {
         CK(h->d_fcacc.ensure(sizeof(float) * (size_t)P * ((size_t)N * N + N)), "streamed FC moments");
         CK(h->d_blocks.ensure(sizeof(float) * (size_t)P * ((size_t)N * N + N)), "FC block moments");
@@ -738,6 +744,7 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     a.ext_index = h->d_ext.as<int64_t>();
     a.state = h->d_state.as<float>();
     a.series = h->d_series.as<float>();
+    a.series_i = c.keep_i_series ? h->d_series_i.as<float>() : nullptr;
     a.ou_table = c.noise_per_set ? nullptr : h->d_ou_table.as<float>();
     a.status = h->d_status.as<uint32_t>();
     a.error = h->d_error.as<uint32_t>();
@@ -758,6 +765,9 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
         const int64_t t_base = n_base / c.tavg_steps;
         a.series = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(h->d_series.ptr) -
                                             (uintptr_t)(sizeof(float) * (size_t)t_base * N * P));
+        if (c.keep_i_series)
+            a.series_i = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(h->d_series_i.ptr) -
+                                                  (uintptr_t)(sizeof(float) * (size_t)t_base * N * P));
         a.T = t_base + T;
         a.transient = t_base + c.transient_samples;
         // running sums (means, FC shift) cover the new samples only
@@ -937,6 +947,7 @@ struct CkptHeader {
     int64_t chunk_steps;
     int64_t kernel;
     int64_t series_mode;
+    int64_t keep_i_series;
 };
 
 // FNV-1a over the bytes of the definition of a sweep (all fields are doubles
@@ -999,6 +1010,7 @@ tvbx_status tvbx_checkpoint(tvbx_sweep* h, void* host_buf, uint64_t bytes)
     hd.chunk_steps = h->cfg.chunk_steps;
     hd.kernel = h->cfg.kernel;
     hd.series_mode = h->cfg.series_mode;
+    hd.keep_i_series = h->cfg.keep_i_series;
     unsigned char* out = static_cast<unsigned char*>(host_buf);
     memcpy(out, &hd, sizeof hd);
     size_t off = sizeof hd;
@@ -1039,6 +1051,7 @@ tvbx_status tvbx_restore(tvbx_sweep* h, const void* host_buf, uint64_t bytes)
     c.chunk_steps = (int32_t)hd.chunk_steps;
     c.kernel = (int32_t)hd.kernel;
     c.series_mode = (int32_t)hd.series_mode;
+    c.keep_i_series = (int32_t)hd.keep_i_series;
     // lay out the buffers as the checkpointed run did, then fill them; the
     // handle's earlier stream may no longer exist, so the device is drained
     // and the default stream used
@@ -1356,15 +1369,18 @@ tvbx_status tvbx_summary(tvbx_sweep* h, int32_t mem, float* mean_e_hz, float* me
     return TVBX_OK;
 }
 
-tvbx_status tvbx_series_range(const tvbx_sweep* hc, int64_t set_begin, int64_t set_count, int64_t t_begin,
-                              int64_t t_count, int32_t mem, float* out)
+tvbx_status tvbx_series_pop_range(const tvbx_sweep* hc, int32_t pop, int64_t set_begin, int64_t set_count,
+                                  int64_t t_begin, int64_t t_count, int32_t mem, float* out)
 {
     tvbx_sweep* h = const_cast<tvbx_sweep*>(hc);
     if (!h || !out) return fail(TVBX_E_INVALID_ARG, "NULL handle or out");
+    if (pop != 0 && pop != 1) return fail(TVBX_E_INVALID_ARG, "pop must be 0 (E) or 1 (I)");
     if (check_mem(mem)) return TVBX_E_INVALID_ARG;
     if (!h->ran) return fail(TVBX_E_BAD_STATE, "series export before tvbx_run");
     if (h->cfg.series_mode == TVBX_SERIES_STREAM)
         return fail(TVBX_E_BAD_STATE, "the last run streamed its series (series_mode): there is none to export");
+    if (pop == 1 && !h->cfg.keep_i_series)
+        return fail(TVBX_E_BAD_STATE, "the last run kept no I series (keep_i_series)");
     if (tvbx_status e = check_device_error(h)) return e;
     if (set_begin < 0 || set_count < 0 || set_begin + set_count > h->P || t_begin < 0 || t_count < 0 ||
         t_begin + t_count > h->T)
@@ -1379,11 +1395,17 @@ tvbx_status tvbx_series_range(const tvbx_sweep* hc, int64_t set_begin, int64_t s
     }
     note_launch();
     series_export_kernel<<<grid_for((int64_t)total), 256, 0, h->stream>>>(
-        h->d_series.as<float>(), target, h->d_inv.as<int64_t>(), h->N, h->P, set_begin, set_count, t_begin,
-        t_count);
+        (pop ? h->d_series_i : h->d_series).as<float>(), target, h->d_inv.as<int64_t>(), h->N, h->P, set_begin,
+        set_count, t_begin, t_count);
     CK(cudaGetLastError(), "series export");
     if (mem == TVBX_MEM_HOST) return copy_out(out, target, sizeof(float) * total, mem, h->stream, &h->d2h);
     return TVBX_OK;
+}
+
+tvbx_status tvbx_series_range(const tvbx_sweep* h, int64_t set_begin, int64_t set_count, int64_t t_begin,
+                              int64_t t_count, int32_t mem, float* out)
+{
+    return tvbx_series_pop_range(h, 0, set_begin, set_count, t_begin, t_count, mem, out);
 }
 
 tvbx_status tvbx_series(const tvbx_sweep* h, int32_t mem, float* out)

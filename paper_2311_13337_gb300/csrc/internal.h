@@ -110,6 +110,7 @@ struct SimArgs {
     int32_t noise_per_set;
     uint64_t seed;
     int64_t p_offset;
+    float* series_i;           // [T][N][P] I samples (sets fastest), or null
 };
 
 // Kernels / launchers (sim.cu).

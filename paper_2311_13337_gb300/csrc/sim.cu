@@ -159,6 +159,7 @@ static __device__ __forceinline__ void chunk_body(const SimArgs& a, const TileDe
                     const float xE = accE * inv_ts, xI = accI * inv_ts;
                     if (t < a.T) {
                         a.series[t * (int64_t)N * P + (int64_t)k * P + p] = xE;
+                        if (a.series_i) a.series_i[t * (int64_t)N * P + (int64_t)k * P + p] = xI;
                         if (t >= a.transient) {
                             kahan_add(sk[SV_SUM_E * npairs], sk[SV_CMP_E * npairs], xE);
                             kahan_add(sk[SV_SUM_I * npairs], sk[SV_CMP_I * npairs], xI);

@@ -68,7 +68,8 @@ class RunCfg(ctypes.Structure):
     _fields_ = [("dt_ms", ctypes.c_double), ("n_steps", ctypes.c_int64), ("tavg_steps", ctypes.c_int32),
                 ("noise_per_set", ctypes.c_int32), ("seed", ctypes.c_uint64), ("p_offset", ctypes.c_int64),
                 ("transient_samples", ctypes.c_int32), ("chunk_steps", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("withhold_step", ctypes.c_int32), ("series_mode", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("withhold_step", ctypes.c_int32), ("series_mode", ctypes.c_int32),
+                ("keep_i_series", ctypes.c_int32)]
 
 
 class FcCfg(ctypes.Structure):
@@ -84,7 +85,7 @@ class SurrogateCfg(ctypes.Structure):
 _lib = None
 EXPORTS = ("tvbx_version", "tvbx_last_error", "tvbx_model_defaults", "tvbx_sweep_create",
            "tvbx_sweep_create_points", "tvbx_sweep_info", "tvbx_run", "tvbx_summary", "tvbx_series",
-           "tvbx_series_range", "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_last_kernel",
+           "tvbx_series_range", "tvbx_series_pop_range", "tvbx_state", "tvbx_fc", "tvbx_transfer_function", "tvbx_last_kernel",
            "tvbx_launch_count",
            "tvbx_transfer_bytes", "tvbx_profile_enable", "tvbx_profile_read", "tvbx_fc_noalloc", "tvbx_fc_series",
            "tvbx_sweep_destroy", "tvbx_surrogate_create", "tvbx_surrogate_info", "tvbx_surrogate_train",
@@ -133,6 +134,7 @@ def load(build_if_missing: bool = False):
     L.tvbx_summary.argtypes = [vp, i32, fp, fp, fp, fp, fp]
     L.tvbx_series.argtypes = [vp, i32, fp]
     L.tvbx_series_range.argtypes = [vp, i64, i64, i64, i64, i32, fp]
+    L.tvbx_series_pop_range.argtypes = [vp, i32, i64, i64, i64, i64, i32, fp]
     L.tvbx_state.argtypes = [vp, i32, fp]
     L.tvbx_fc.argtypes = [vp, ctypes.POINTER(FcCfg), i32, fp, fp, ctypes.POINTER(i32)]
     L.tvbx_transfer_function.argtypes = [ctypes.POINTER(Model), i32, i64, i32, fp, fp, fp, fp, fp, fp]
@@ -290,20 +292,20 @@ PACKED_VARIANTS = (8, 9, 10, 11)   # FP32x2 kernels: need tau_e == tau_i
 
 def _run_cfg(dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
              transient_samples=0, chunk_steps=0, kernel=KERNEL_AUTO, withhold_step=0,
-             series_mode=SERIES_KEEP) -> RunCfg:
+             series_mode=SERIES_KEEP, keep_i_series=False) -> RunCfg:
     return RunCfg(float(dt_ms), int(n_steps), int(tavg_steps), int(bool(noise_per_set)), int(seed),
                   int(p_offset), int(transient_samples), int(chunk_steps), int(kernel), int(withhold_step),
-                  int(series_mode))
+                  int(series_mode), int(bool(keep_i_series)))
 
 
 def run(h, dt_ms=0.1, n_steps=10_000, tavg_steps=10, seed=1, noise_per_set=False, p_offset=0,
         transient_samples=0, chunk_steps=0, stream=None, kernel=KERNEL_AUTO, withhold_step=0,
-        series_mode=SERIES_KEEP):
+        series_mode=SERIES_KEEP, keep_i_series=False):
     """Enqueue the integration on `stream` (a torch.cuda.Stream, a raw handle
     or None for the default stream). series_mode SERIES_STREAM keeps one
     chunk of samples and folds it into the FC moments (no series export)."""
     cfg = _run_cfg(dt_ms, n_steps, tavg_steps, seed, noise_per_set, p_offset, transient_samples, chunk_steps,
-                   kernel, withhold_step, series_mode)
+                   kernel, withhold_step, series_mode, keep_i_series)
     sp = None
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -381,10 +383,11 @@ def series(h, out):
     _check(load().tvbx_series(h, mem, ptr), "tvbx_series")
 
 
-def series_range(h, set_begin, set_count, t_begin, t_count, out):
+def series_range(h, set_begin, set_count, t_begin, t_count, out, pop=0):
+    """Window of the E (pop 0) or I (pop 1, runs with keep_i_series) series."""
     ptr, mem = _out_ptr(out)
-    _check(load().tvbx_series_range(h, int(set_begin), int(set_count), int(t_begin), int(t_count), mem, ptr),
-           "tvbx_series_range")
+    _check(load().tvbx_series_pop_range(h, int(pop), int(set_begin), int(set_count), int(t_begin), int(t_count),
+                                        mem, ptr), "tvbx_series_pop_range")
 
 
 def state(h, out):
@@ -557,9 +560,13 @@ class Sweep:
         out["status"] = st
         return out
 
-    def series(self) -> np.ndarray:
+    def series(self, pop=0) -> np.ndarray:
+        """E (pop 0) or I (pop 1, runs with keep_i_series) series [P][N][T]."""
         x = np.zeros((self.n_sets, self.n_regions, self.n_samples), dtype=np.float32)
-        series(self.h, x)
+        if pop == 0:
+            series(self.h, x)
+        else:
+            series_range(self.h, 0, self.n_sets, 0, self.n_samples, x, pop=pop)
         return x
 
     def series_window(self, set_begin, set_count, t_begin=0, t_count=None) -> np.ndarray:
