@@ -5,6 +5,7 @@
   python profile_case.py --analysis --sets 4096 --samples 5000
   python profile_case.py --bold --sets 8192 --samples 10000
   python profile_case.py --surrogate --sets 36864 --epochs 5
+  python profile_case.py --fc-noalloc --sets 1787 --samples 5000
 
 Takes the first `--sets` sets of the 32,768-set grid (68 regions, v 4 m/s),
 integrates `--n-steps` steps in launches of `--chunk` steps and optionally
@@ -14,7 +15,9 @@ synthetic rate-like series of `--sets` x 68 regions x `--samples`. With
 --analysis, runs only the Table 2 metrics (tvbx_series_analysis) on such
 series in the [sets][regions][samples] layout. With --bold, runs the
 Balloon-Windkessel kernel on such rates (TR 1 s) and the phFCD of 300 TRs.
-With --surrogate, trains the 4-member 5 -> 256 x 3 -> 24 surrogate for
+With --fc-noalloc, times the allocation-free FC entry point (tvbx_fc_noalloc)
+against tvbx_fc_series (FP32, no FCD) on the same synthetic series, with CUDA
+events. With --surrogate, trains the 4-member 5 -> 256 x 3 -> 24 surrogate for
 `--epochs` passes (batch 1024) on `--sets` synthetic rows and predicts a
 65,536-point map.
 Sized so
@@ -48,10 +51,13 @@ def main():
     ap.add_argument("--analysis", action="store_true")
     ap.add_argument("--bold", action="store_true")
     ap.add_argument("--surrogate", action="store_true")
+    ap.add_argument("--fc-noalloc", action="store_true")
     ap.add_argument("--epochs", type=int, default=5)
     args = ap.parse_args()
     if args.surrogate:
         return surrogate_case(args)
+    if args.fc_noalloc:
+        return fc_noalloc_case(args)
     if args.bold:
         return bold_case(args)
     if args.fc_series:
@@ -169,6 +175,34 @@ def surrogate_case(args):
         print(f"surrogate {args.sets} rows x {args.epochs} epochs: {t1 - t0:.4f} s; predict 65,536: "
               f"{time.time() - t1:.4f} s")
     sur.close()
+
+
+def fc_noalloc_case(args):
+    import torch
+
+    from paper_2311_13337_gb300 import build, synth, tvbx
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    P, N, T = args.sets, 68, args.samples
+    X = synth.rate_series_device(torch, dev, P, N, T, seed=1000)
+    fc = torch.empty((P, N, N), dtype=torch.float32, device=dev)
+    chi = torch.empty(P, dtype=torch.float32, device=dev)
+    mfc = torch.empty(P, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, fn in (("tvbx_fc_noalloc", lambda: tvbx.fc_noalloc(X, N, P, T, fc, chi, mfc)),
+                     ("tvbx_fc_series fp32", lambda: tvbx.fc_series(X, N, P, T, precision=tvbx.FC_FP32, fc_out=fc)),
+                     ("tvbx_fc_series bf16x3", lambda: tvbx.fc_series(X, N, P, T, precision=tvbx.FC_BF16X3,
+                                                                       fc_out=fc))):
+        for i in range(args.repeat + 1):
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            if i > 0:
+                ms = e0.elapsed_time(e1)
+                print(f"{name} {P} x {N} x {T}: {ms:.3f} ms = {4.0 * P * N * T / ms / 1e6:.0f} GB/s of series read")
 
 
 if __name__ == "__main__":
