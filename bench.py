@@ -527,10 +527,16 @@ def run_fc_engine(args):
     st = torch.zeros(P, dtype=torch.int32, device=dev)
     stream = torch.cuda.Stream(device=dev)
     prec = getattr(tvbx, "FC_" + args.fc_precision.upper())
+    # the series as the engine keeps its own (groups of 4 sets) or sets fastest
+    layout = tvbx.LAYOUT_SET4 if args.fc_layout == "set4" else tvbx.LAYOUT_TNP
+    sample = np.linspace(0, P - 1, 32).astype(int)
+    xs = X[:, :, torch.as_tensor(sample, device=dev)].permute(2, 1, 0).double().cpu().numpy()
+    if layout == tvbx.LAYOUT_SET4:
+        X = X.view(T, N, P // 4, 4).permute(2, 0, 1, 3).contiguous()
 
     def step(pr=prec):
         tvbx.fc_series(X, N, P, T, precision=pr, fc_out=fc, fcd_out=fcd, fcd_window=FCD_WINDOW,
-                       fcd_step=FCD_STEP, chi=chi, mean_fc=mfc, set_status=st, stream=stream)
+                       fcd_step=FCD_STEP, chi=chi, mean_fc=mfc, set_status=st, stream=stream, layout=layout)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -539,8 +545,6 @@ def run_fc_engine(args):
         torch.cuda.synchronize(dev)
 
     # error of every precision form against FP64 on 32 sampled sets
-    sample = np.linspace(0, P - 1, 32).astype(int)
-    xs = X[:, :, torch.as_tensor(sample, device=dev)].permute(2, 1, 0).double().cpu().numpy()
     ref_fc = [fp64_pearson(x) for x in xs]
     ref_fcd = [fp64_fcd(x, FCD_WINDOW, FCD_STEP) for x in xs]
     forms = {}
@@ -583,7 +587,7 @@ def run_fc_engine(args):
     value = args.steps * units * world / el_max
 
     # end to end: series from pinned host memory, FC / chi / mean FC back to host
-    pin_X = torch.empty((T, N, P), dtype=torch.float32).pin_memory()
+    pin_X = torch.empty(X.shape, dtype=torch.float32).pin_memory()
     pin_X.copy_(X)
     host_fc = torch.empty((P, N, N), dtype=torch.float32).pin_memory()
     host_s = [torch.empty(P, dtype=torch.float32).pin_memory() for _ in range(2)]
@@ -625,6 +629,7 @@ def run_fc_engine(args):
                 "config": {"workload": "FC stage: 32768 series of 68 regions x 5000 samples per GPU, Pearson FC "
                                        "+ FCD (1000/500) + chi + mean FC",
                            "n_sets_per_gpu": P, "n_regions": N, "n_samples": T, "fc_precision": args.fc_precision,
+                           "series_layout": args.fc_layout,
                            "parallelism": f"dp{world} (set slices, no collective)",
                            "l2": "inputs larger than L2 (series 44.6 GB per GPU)"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
@@ -1453,6 +1458,8 @@ def main():
                     help="sweep: the paper-scale sweep (default); fc: the FC stage alone on 32,768 "
                          "series of 68 regions x 5,000 samples")
     ap.add_argument("--fc-precision", choices=["fp32", "bf16", "bf16x3", "tf32", "tf32x3"], default="bf16x3")
+    ap.add_argument("--fc-layout", choices=["set4", "tnp"], default="set4",
+                    help="series layout of the FC workload: groups of 4 sets (the engine's own) or sets fastest")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="duration scale of the uneven batch")
     ap.add_argument("--batch-series", choices=["stream", "keep"], default="stream",
                     help="batch jobs keep one chunk of samples and fold it into the FC (stream) or keep the series")

@@ -194,7 +194,20 @@ typedef struct {
     int32_t fcd_window;       /* samples per FCD window; 0 = no FCD */
     int32_t fcd_step;         /* samples between window starts; fcd_window must
                                  be a multiple of fcd_step */
+    int32_t series_layout;    /* tvbx_fc_series only: TVBX_LAYOUT_TNP (0) or
+                                 TVBX_LAYOUT_SET4 (below); tvbx_fc reads the
+                                 sweep's own series and ignores it */
 } tvbx_fc_cfg;
+
+/* Layouts of a series given to tvbx_fc_series.
+ * TVBX_LAYOUT_TNP: [n_samples][n_regions][n_sets], sets fastest.
+ * TVBX_LAYOUT_SET4: groups of 4 sets, [ceil(n_sets / 4)][n_samples][n_regions][4]
+ *   (element (t, k, p) at ((p / 4) n_samples + t) n_regions 4 + 4 k + p % 4;
+ *   the last group padded to 4 sets, padding never read). The engine keeps its
+ *   own series this way: the FC readers then load whole lines along the
+ *   regions. */
+#define TVBX_LAYOUT_TNP 0
+#define TVBX_LAYOUT_SET4 1
 /* The Gram matrix G = Z Z^T of the shifted series Z (the contraction behind
  * the covariance of Eq. 6) is formed
  *   FP32:    with FP32 CUDA-core FMAs;
@@ -356,9 +369,9 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
 
 /* Pearson FC (Eq. 6), FCD, synchrony index chi and mean off-diagonal FC of
  * series that are not the output of a sweep (the FC stage on its own).
- * series: DEVICE pointer, [n_samples][n_regions][n_sets] FP32 (sets
- * fastest, the layout tvbx_series exports with mem = TVBX_MEM_DEVICE),
- * read-only. Outputs are DEVICE pointers owned by the caller, each nullable:
+ * series: DEVICE pointer, FP32, read-only, in cfg->series_layout:
+ * [n_samples][n_regions][n_sets] (TVBX_LAYOUT_TNP, sets fastest) or the
+ * set-blocked TVBX_LAYOUT_SET4. Outputs are DEVICE pointers owned by the caller, each nullable:
  * fc_out [n_sets][n_regions][n_regions], fcd_out [n_sets][W][W] with
  * W = (n_samples - fcd_window) / fcd_step + 1 (written to *n_windows when
  * non-NULL), chi and mean_fc [n_sets], set_status [n_sets] (OR-ed with

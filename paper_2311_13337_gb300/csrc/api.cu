@@ -249,7 +249,8 @@ struct tvbx_sweep {
     DevBuf d_csr_row, d_csr_cd, d_csr_w, d_groups, d_tiles;
     DevBuf d_blocks, d_fc, d_chi, d_meanfc, d_vec, d_fcd, d_tmp, d_perm, d_inv, d_mean_e, d_mean_i, d_error;
     DevBuf d_fcacc, d_shift;        // streamed series: FC moments over the run, fixed shift [N][P]
-    DevBuf d_series_i;              // I series [T][N][P] when the run keeps it
+    DevBuf d_series_i;              // I series (layout sl) when the run keeps it
+    SeriesLayout sl{4, 0, 0};      // layout of d_series and d_series_i: set-blocked
 
     ~tvbx_sweep()
     {
@@ -283,15 +284,15 @@ __global__ void gather_u32_kernel(const uint32_t* __restrict__ in, uint32_t* __r
 }
 // series [T][N][P] (internal order) -> out [np][N][nt] for external sets
 // [p0, p0 + np) and samples [t0, t0 + nt); inv maps external -> internal.
-__global__ void series_export_kernel(const float* __restrict__ X, float* __restrict__ out,
-                                     const int64_t* __restrict__ inv, int32_t N, int64_t P, int64_t p0,
-                                     int64_t np, int64_t t0, int64_t nt)
+__global__ void series_export_kernel(const float* __restrict__ X, const SeriesLayout sl, float* __restrict__ out,
+                                     const int64_t* __restrict__ inv, int32_t N, int64_t p0, int64_t np, int64_t t0,
+                                     int64_t nt)
 {
     const int64_t total = np * N * nt;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = i % nt, rest = i / nt, k = rest % N, q = rest / N;
-        out[i] = X[((t0 + t) * N + k) * P + inv[p0 + q]];
+        out[i] = X[series_index(sl, t0 + t, k, inv[p0 + q])];
     }
 }
 // state [SV][N][P] -> out [P][8][N]; shared OU from ou_state[k]
@@ -685,8 +686,12 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     CK(h->d_state.ensure(sizeof(float) * (size_t)SV_COUNT * N * P), "state");
     CK(h->d_status.ensure(sizeof(uint32_t) * P), "status");
     CK(h->d_ring.ensure(sizeof(float) * (size_t)std::max<int64_t>(ring_floats, 1)), "ring buffers");
-    CK(h->d_series.ensure(sizeof(float) * (size_t)std::max<int64_t>(series_T * N * P, 1)), "series");
-    if (c.keep_i_series) CK(h->d_series_i.ensure(sizeof(float) * (size_t)std::max<int64_t>(T * N * P, 1)), "I series");
+    // set-blocked series: groups of 4 sets, [ceil(P / 4)][series_T][N][4]
+    const int64_t P4 = (P + 3) / 4 * 4;
+    h->sl = layout_blocked(N, std::max<int64_t>(series_T, 1));
+    CK(h->d_series.ensure(sizeof(float) * (size_t)std::max<int64_t>(series_T * N * P4, 1)), "series");
+    if (c.keep_i_series)
+        CK(h->d_series_i.ensure(sizeof(float) * (size_t)std::max<int64_t>(T * N * P4, 1)), "I series");
     if (c.series_mode == TVBX_SERIES_STREAM) {
         CK(h->d_fcacc.ensure(sizeof(float) * (size_t)P * ((size_t)N * N + N)), "streamed FC moments");
         CK(h->d_blocks.ensure(sizeof(float) * (size_t)P * ((size_t)N * N + N)), "FC block moments");
@@ -744,6 +749,7 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
     a.ext_index = h->d_ext.as<int64_t>();
     a.state = h->d_state.as<float>();
     a.series = h->d_series.as<float>();
+    a.sl = h->sl;
     a.series_i = c.keep_i_series ? h->d_series_i.as<float>() : nullptr;
     a.ou_table = c.noise_per_set ? nullptr : h->d_ou_table.as<float>();
     a.status = h->d_status.as<uint32_t>();
@@ -764,10 +770,10 @@ static tvbx_status prepare_run(tvbx_sweep* h, const tvbx_run_cfg& c, cudaStream_
         // address is formed in integers; every write lands inside the buffer)
         const int64_t t_base = n_base / c.tavg_steps;
         a.series = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(h->d_series.ptr) -
-                                            (uintptr_t)(sizeof(float) * (size_t)t_base * N * P));
+                                            (uintptr_t)(sizeof(float) * (size_t)t_base * h->sl.st));
         if (c.keep_i_series)
             a.series_i = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(h->d_series_i.ptr) -
-                                                  (uintptr_t)(sizeof(float) * (size_t)t_base * N * P));
+                                                  (uintptr_t)(sizeof(float) * (size_t)t_base * h->sl.st));
         a.T = t_base + T;
         a.transient = t_base + c.transient_samples;
         // running sums (means, FC shift) cover the new samples only
@@ -816,12 +822,13 @@ static tvbx_status stream_fc_chunk(tvbx_sweep* h, const SimArgs& a, int64_t n0, 
     if (u0 >= tc1) return TVBX_OK;
     const float* buf = h->d_series.as<float>();
     if (!shift_set) {
-        CK(launch_fc_shift(buf, a.N, a.P, u0 - tc0, tc1 - tc0, h->d_shift.as<float>(), s), "FC shift");
+        CK(launch_fc_shift(buf, h->sl, a.N, a.P, u0 - tc0, tc1 - tc0, h->d_shift.as<float>(), s), "FC shift");
         shift_set = true;
     }
     FcArgs f;
     memset(&f, 0, sizeof f);
     f.series = buf;
+    f.sl = h->sl;
     f.shift = h->d_shift.as<float>();
     f.N = a.N;
     f.P = a.P;
@@ -841,9 +848,9 @@ static tvbx_status stream_fc_chunk(tvbx_sweep* h, const SimArgs& a, int64_t n0, 
 // The series pointer of a chunk whose first sample t0 goes to row 0 of the
 // buffer (the kernels index samples by the global step; the address is
 // formed in integers and every write lands inside the buffer).
-static float* series_at(void* buf, int64_t t0, int N, int64_t P)
+static float* series_at(void* buf, int64_t t0, const SeriesLayout& sl)
 {
-    return reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(buf) - (uintptr_t)(sizeof(float) * (size_t)t0 * N * P));
+    return reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(buf) - (uintptr_t)(sizeof(float) * (size_t)t0 * sl.st));
 }
 
 // Enqueue the chunked launches of a prepared run over global steps
@@ -864,7 +871,7 @@ static tvbx_status run_chunks(tvbx_sweep* h, const tvbx_run_cfg& c, const RunPla
     for (int64_t n0 = n_base; n0 < n_base + c.n_steps; n0 += chunk) {
         a.n0 = n0;
         a.n_chunk = (int32_t)std::min<int64_t>(chunk, n_base + c.n_steps - n0);
-        if (streamed) a.series = series_at(h->d_series.ptr, n0 / c.tavg_steps, N, P);
+        if (streamed) a.series = series_at(h->d_series.ptr, n0 / c.tavg_steps, h->sl);
         if (!c.noise_per_set)
             CK(launch_ou_table(a.m, h->d_ou_table.as<float>(), h->d_ou_state.as<float>(), N, n0, a.n_chunk, c.seed, s),
                "OU table");
@@ -1135,6 +1142,7 @@ static tvbx_status run_fc(tvbx_sweep* h, int32_t precision, int32_t fcd_window, 
     FcArgs f;
     memset(&f, 0, sizeof f);
     f.series = h->d_series.as<float>();
+    f.sl = h->sl;
     f.state = h->d_state.as<float>();
     f.N = N;
     f.P = (int32_t)P;
@@ -1247,6 +1255,9 @@ tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_set
         return fail(TVBX_E_INVALID_ARG, "tensor-core FC needs n_regions <= 128 (have %d)", N);
     if (cfg->precision == TVBX_FC_FP32 && N > 384) return fail(TVBX_E_INVALID_ARG, "FC needs n_regions <= 384");
     int32_t blk = 0, n_blocks = 1, m = 0, nw = 0;
+    if (cfg->series_layout != TVBX_LAYOUT_TNP && cfg->series_layout != TVBX_LAYOUT_SET4)
+        return fail(TVBX_E_INVALID_ARG, "unknown series_layout %d", cfg->series_layout);
+    const SeriesLayout sl = cfg->series_layout == TVBX_LAYOUT_SET4 ? layout_blocked(N, Tn) : layout_tnp(N, P);
     if (cfg->fcd_window < 0) return fail(TVBX_E_INVALID_ARG, "fcd_window must be >= 0");
     if (cfg->fcd_window > 0) {
         if (cfg->fcd_step < 1 || cfg->fcd_window % cfg->fcd_step != 0)
@@ -1290,10 +1301,11 @@ tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_set
     cudaError_t e = cudaSuccess;
     do {
         if ((e = cudaMemsetAsync(small, 0, sz_small, s)) != cudaSuccess) break;
-        if ((e = launch_fc_shift(series, N, P, 0, Tn, d_shift, s)) != cudaSuccess) break;
+        if ((e = launch_fc_shift(series, sl, N, P, 0, Tn, d_shift, s)) != cudaSuccess) break;
         FcArgs f;
         memset(&f, 0, sizeof f);
         f.series = series;
+        f.sl = sl;
         f.state = nullptr;
         f.shift = d_shift;
         f.N = N;
@@ -1395,7 +1407,7 @@ tvbx_status tvbx_series_pop_range(const tvbx_sweep* hc, int32_t pop, int64_t set
     }
     note_launch();
     series_export_kernel<<<grid_for((int64_t)total), 256, 0, h->stream>>>(
-        (pop ? h->d_series_i : h->d_series).as<float>(), target, h->d_inv.as<int64_t>(), h->N, h->P, set_begin,
+        (pop ? h->d_series_i : h->d_series).as<float>(), h->sl, target, h->d_inv.as<int64_t>(), h->N, set_begin,
         set_count, t_begin, t_count);
     CK(cudaGetLastError(), "series export");
     if (mem == TVBX_MEM_HOST) return copy_out(out, target, sizeof(float) * total, mem, h->stream, &h->d2h);
@@ -1668,8 +1680,7 @@ tvbx_status batch_build(tvbx_batch* b, int32_t threads, size_t budget, int64_t t
             a.n_chunk = (int32_t)std::max<int64_t>(nc, 0);
             a.ou_table = ou_off[j] >= 0 ? b->d_ou.as<float>() + ou_off[j] + n0 * b->jobs[j]->N : nullptr;
             if (run_cfgs[j].series_mode == TVBX_SERIES_STREAM)
-                a.series = series_at(b->jobs[j]->d_series.ptr, n0 / run_cfgs[j].tavg_steps, b->jobs[j]->N,
-                                     b->jobs[j]->P);
+                a.series = series_at(b->jobs[j]->d_series.ptr, n0 / run_cfgs[j].tavg_steps, b->jobs[j]->sl);
             jobs[(size_t)r * nj + j] = BatchJob{a, pbs[j], dirs[j]};
             if (nc <= 0) continue;
             const int N = b->jobs[j]->N;

@@ -77,7 +77,6 @@ fc_moments_kernel(const __grid_constant__ FcArgs a, int32_t Npad, int32_t Tt, in
         for (int c = 0; c < 4; ++c) rs[i][c] = 0.0f;
     }
     const int64_t blk = a.blk > 0 ? a.blk : Tn;
-    const int64_t NP = (int64_t)N * a.P;
     const int64_t stride_b = (int64_t)N * N + N;
     __syncthreads();
 
@@ -91,7 +90,7 @@ fc_moments_kernel(const __grid_constant__ FcArgs a, int32_t Npad, int32_t Tt, in
             const int tt = rem / Npad;
             float v = 0.0f;
             if (k < N && q < nsets)
-                v = a.series[(a.t_begin + t0 + tt) * NP + (int64_t)k * a.P + p0 + q] - shift[q * N + k];
+                v = a.series[series_index(a.sl, a.t_begin + t0 + tt, k, p0 + q)] - shift[q * N + k];
             xs[((int64_t)q * Tt + tt) * Npad + k] = v;
         }
         __syncthreads();
@@ -277,17 +276,18 @@ cudaError_t launch_fc_moments(const FcArgs& a, cudaStream_t s)
 // [t_begin, t_end). Any shift gives the same moments in exact arithmetic; one
 // within a few standard deviations of the mean keeps the low-precision
 // operands of the tensor-core path small relative to the fluctuations.
-__global__ void fc_shift_kernel(const float* __restrict__ series, int32_t N, int64_t P, int64_t t_begin,
-                                int64_t t_end, float* __restrict__ shift)
+__global__ void fc_shift_kernel(const float* __restrict__ series, const SeriesLayout sl, int32_t N, int64_t P,
+                                int64_t t_begin, int64_t t_end, float* __restrict__ shift)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // shift[k][p], i = k P + p
     if (i >= (int64_t)N * P) return;
+    const int64_t k = i / P, p = i - k * P;
     const int64_t Tn = t_end - t_begin;
     const int64_t n = Tn < 64 ? Tn : 64;
     float s = 0.0f;
     for (int64_t q = 0; q < n; ++q) {
         const int64_t t = t_begin + (q * Tn) / n;
-        s += series[t * N * P + i];
+        s += series[series_index(sl, t, k, p)];
     }
     shift[i] = n > 0 ? s / (float)n : 0.0f;
 }
@@ -309,12 +309,12 @@ cudaError_t launch_fc_accumulate(const float* add, float* acc, int64_t n, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_fc_shift(const float* series, int32_t N, int64_t P, int64_t t_begin, int64_t t_end,
-                            float* shift, cudaStream_t s)
+cudaError_t launch_fc_shift(const float* series, const SeriesLayout& sl, int32_t N, int64_t P, int64_t t_begin,
+                            int64_t t_end, float* shift, cudaStream_t s)
 {
     const int64_t n = (int64_t)N * P;
     note_launch();
-    fc_shift_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(series, N, P, t_begin, t_end, shift);
+    fc_shift_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(series, sl, N, P, t_begin, t_end, shift);
     return cudaGetLastError();
 }
 

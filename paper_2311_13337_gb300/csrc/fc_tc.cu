@@ -17,7 +17,10 @@
 // finalize (Pearson, chi, mean FC) and FCD kernels are shared.
 //
 // Layout. A CTA owns SC consecutive sets (one 16- or 8-byte piece of every
-// (t, k) row of the [T][N][P] series) and all their samples. Per chunk of 128
+// (t, k) row of the series: in the set-blocked layout the pieces of
+// neighbouring regions are adjacent, so a warp's 4 regions x 8 sample groups
+// read 8 segments of 64 bytes; in [T][N][P], 32 separate pieces) and all
+// their samples. Per chunk of 128
 // bytes of K (64 BF16 or 32 TF32 samples) each loader thread (k, j) copies
 // samples j*SPC .. j*SPC+SPC-1 of region k for the SC sets into one of its two
 // raw slots in shared memory (cp.async, one chunk ahead), then subtracts the
@@ -224,7 +227,9 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
             }
             sh[s] = m;
         }
-        const float* src0 = a.series + (a.t_begin + (int64_t)j * SPC) * NP + (int64_t)k * P + p0;
+        // sample t of region k for sets p0 ..: series_index(t, k, p0), consecutive samples st apart
+        const float* src0 = a.series + series_index(a.sl, a.t_begin + (int64_t)j * SPC, k, p0);
+        const int64_t st = a.sl.st;
         const bool fast_sets = loader && all_sets && vec_ok;
         // this thread's raw slots (two, alternating by chunk): SPC pieces of SC
         // floats, piece i of slot q at raw_base + ((q * SPC + i) * NLT + tid) * 4 SC
@@ -235,18 +240,18 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
         // copy samples [ts, te) of this thread's piece into raw slot q; samples
         // outside and sets >= P are zero-filled
         auto issue_chunk = [&](int64_t ts, int64_t te, int q) {
-            const float* src = src0 + ts * NP;
+            const float* src = src0 + ts * st;
             if (fast_sets && te - ts == KC) {
                 const uint32_t dst0 = raw_base + (uint32_t)(q * SPC * NLT + tid) * PBYTES;
 #pragma unroll
                 for (int i = 0; i < SPC; ++i)
-                    cp_async_zfill<PBYTES>(dst0 + (uint32_t)(i * NLT * PBYTES), src + i * NP, PBYTES);
+                    cp_async_zfill<PBYTES>(dst0 + (uint32_t)(i * NLT * PBYTES), src + i * st, PBYTES);
             } else if (all_sets && vec_ok) {
 #pragma unroll
                 for (int i = 0; i < SPC; ++i) {
                     const uint32_t dst = raw_base + (uint32_t)((q * SPC + i) * NLT + tid) * PBYTES;
                     const bool tv = loader && ts + j * SPC + i < te;
-                    cp_async_zfill<PBYTES>(dst, tv ? (const void*)(src + i * NP) : (const void*)a.series,
+                    cp_async_zfill<PBYTES>(dst, tv ? (const void*)(src + i * st) : (const void*)a.series,
                                            tv ? PBYTES : 0u);
                 }
             } else {   // sets not a multiple of SC or an unaligned series: 4-byte copies
@@ -257,7 +262,7 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
 #pragma unroll 1
                     for (int s = 0; s < SC; ++s) {
                         const bool ok_s = tv && p0 + s < P;
-                        cp_async_zfill<4>(dst + 4 * s, ok_s ? (const void*)(src + i * NP + s) : (const void*)a.series,
+                        cp_async_zfill<4>(dst + 4 * s, ok_s ? (const void*)(src + i * st + s) : (const void*)a.series,
                                           ok_s ? 4u : 0u);
                     }
                 }
@@ -468,7 +473,8 @@ static cudaError_t launch_one(const FcArgs& a, const FcTcGeom& g, int vec_ok, cu
 template <int PREC>
 static cudaError_t launch_prec(const FcArgs& a, const FcTcGeom& g, cudaStream_t s)
 {
-    const int vec_ok = (a.P % g.SC == 0) && ((uintptr_t)a.series % 16 == 0) ? 1 : 0;
+    // whole 16- (8-) byte pieces: every group of sets is aligned in the set-blocked layout
+    const int vec_ok = (a.sl.sk == 4 || a.P % g.SC == 0) && ((uintptr_t)a.series % 16 == 0) ? 1 : 0;
     if (g.SC == 4) return launch_one<PREC, 4, 576>(a, g, vec_ok, s);
     return launch_one<PREC, 2, 1024>(a, g, vec_ok, s);
 }

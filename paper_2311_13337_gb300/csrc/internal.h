@@ -87,6 +87,23 @@ struct TileDev {
 };
 
 // Arguments of one simulation chunk launch.
+// Layout of a rate series: element (sample t, region k, set p) at
+//   (p / 4) sg + t st + k sk + p % 4.
+// [T][N][P] (sets fastest; the external layout): sg = 4, st = N P, sk = P.
+// Set-blocked [ceil(P / 4)][T_buf][N][4] (the engine's own series): sg = 4 N
+// T_buf, st = 4 N, sk = 4 -- the 16 bytes of a group of 4 sets for all
+// regions of a sample are contiguous, so readers that own a group of sets
+// read whole lines along the regions.
+struct SeriesLayout {
+    int64_t sg, st, sk;
+};
+__host__ __device__ __forceinline__ int64_t series_index(const SeriesLayout& l, int64_t t, int64_t k, int64_t p)
+{
+    return (p >> 2) * l.sg + t * l.st + k * l.sk + (p & 3);
+}
+inline SeriesLayout layout_tnp(int64_t N, int64_t P) { return SeriesLayout{4, N * P, P}; }
+inline SeriesLayout layout_blocked(int64_t N, int64_t T_buf) { return SeriesLayout{4 * N * T_buf, 4 * N, 4}; }
+
 struct SimArgs {
     DevModel m;
     const GroupDev* groups;
@@ -94,7 +111,8 @@ struct SimArgs {
     const float* prm;          // [TVBX_N_AXES][P] per-set parameters (internal order)
     const int64_t* ext_index;  // [P] external set index (keys per-set noise)
     float* state;              // [SV_COUNT][N][P]
-    float* series;             // [T][N][P] E samples (sets fastest)
+    float* series;             // E samples, layout sl
+    SeriesLayout sl;           // of series and series_i
     const float* ou_table;     // [n_chunk][N] shared OU values, or null
     uint32_t* status;          // [P]
     uint32_t* error;           // device error word (TVBX_DEVERR_*)
@@ -110,7 +128,7 @@ struct SimArgs {
     int32_t noise_per_set;
     uint64_t seed;
     int64_t p_offset;
-    float* series_i;           // [T][N][P] I samples (sets fastest), or null
+    float* series_i;           // I samples (layout sl), or null
 };
 
 // Kernels / launchers (sim.cu).
@@ -151,7 +169,8 @@ cudaError_t launch_sim_batch(const BatchJob* jobs, const BatchItem* items, int32
 int sim_batch_ctas_per_sm(int32_t threads, size_t smem, bool only_direct);
 
 struct FcArgs {
-    const float* series;       // [T][N][P]
+    const float* series;       // samples, layout sl
+    SeriesLayout sl;
     const float* state;        // [SV_COUNT][N][P] (running sums give the shift)
     int32_t N, P;
     int64_t t_begin, t_end;    // samples used: [t_begin, t_end)
@@ -182,8 +201,8 @@ bool fc_tc_supported(int N, int prec);
 cudaError_t launch_fc_finalize(const FcArgs& a, cudaStream_t s);
 // Shift m_k = mean of up to 64 evenly spaced samples (standalone series).
 cudaError_t launch_fc_accumulate(const float* add, float* acc, int64_t n, cudaStream_t s);
-cudaError_t launch_fc_shift(const float* series, int32_t N, int64_t P, int64_t t_begin, int64_t t_end,
-                            float* shift, cudaStream_t s);
+cudaError_t launch_fc_shift(const float* series, const SeriesLayout& sl, int32_t N, int64_t P, int64_t t_begin,
+                            int64_t t_end, float* shift, cudaStream_t s);
 cudaError_t launch_fcd(const float* blocks, int32_t P, int32_t N, int32_t n_blocks,
                        int32_t blocks_per_window, int32_t n_windows, int64_t window_samples,
                        float* vec_scratch, float* fcd, cudaStream_t s);

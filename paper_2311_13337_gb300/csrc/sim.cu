@@ -158,8 +158,9 @@ static __device__ __forceinline__ void chunk_body(const SimArgs& a, const TileDe
                 if (sample_now) {
                     const float xE = accE * inv_ts, xI = accI * inv_ts;
                     if (t < a.T) {
-                        a.series[t * (int64_t)N * P + (int64_t)k * P + p] = xE;
-                        if (a.series_i) a.series_i[t * (int64_t)N * P + (int64_t)k * P + p] = xI;
+                        const int64_t so = series_index(a.sl, t, k, p);
+                        a.series[so] = xE;
+                        if (a.series_i) a.series_i[so] = xI;
                         if (t >= a.transient) {
                             kahan_add(sk[SV_SUM_E * npairs], sk[SV_CMP_E * npairs], xE);
                             kahan_add(sk[SV_SUM_I * npairs], sk[SV_CMP_I * npairs], xI);

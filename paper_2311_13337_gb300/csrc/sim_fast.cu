@@ -471,8 +471,9 @@ sim_pack_kernel(const __grid_constant__ SimArgs a)
 #pragma unroll
                     for (int l = 0; l < 2; ++l) {
                         if (!(l ? act1 : act0)) continue;
-                        a.series[t * NP + o + l] = lane(xE, l);
-                        if (a.series_i) a.series_i[t * NP + o + l] = lane(xI, l);
+                        const int64_t so = series_index(a.sl, t, k, col0 + qt + l);
+                        a.series[so] = lane(xE, l);
+                        if (a.series_i) a.series_i[so] = lane(xI, l);
                         if (t >= a.transient) {
                             float* st = a.state + o + l;
                             float sE = st[SV_SUM_E * NP], cE = st[SV_CMP_E * NP];

@@ -211,8 +211,9 @@ static __device__ __forceinline__ void advance_pairs(const SimArgs& a, const Thr
                 if (t < a.T) {
                     const float xE = tp.accE[i] * inv_ts, xI = tp.accI[i] * inv_ts;
                     const int64_t o = (int64_t)k * a.P + ts.col0 + ts.qt + s;
-                    a.series[t * NP + o] = xE;
-                    if (a.series_i) a.series_i[t * NP + o] = xI;
+                    const int64_t so = series_index(a.sl, t, k, ts.col0 + ts.qt + s);
+                    a.series[so] = xE;
+                    if (a.series_i) a.series_i[so] = xI;
                     if (t >= a.transient) {
                         float sE = a.state[SV_SUM_E * NP + o], cE = a.state[SV_CMP_E * NP + o];
                         float sI = a.state[SV_SUM_I * NP + o], cI = a.state[SV_CMP_I * NP + o];

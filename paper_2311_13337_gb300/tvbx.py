@@ -73,7 +73,8 @@ class RunCfg(ctypes.Structure):
 
 
 class FcCfg(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int32), ("fcd_window", ctypes.c_int32), ("fcd_step", ctypes.c_int32)]
+    _fields_ = [("precision", ctypes.c_int32), ("fcd_window", ctypes.c_int32), ("fcd_step", ctypes.c_int32),
+                ("series_layout", ctypes.c_int32)]
 
 
 class SurrogateCfg(ctypes.Structure):
@@ -286,6 +287,7 @@ def sweep_info(h) -> tuple[int, int, int]:
 
 KERNEL_AUTO, KERNEL_GENERAL, KERNEL_PREFETCH, KERNEL_DIRECT = 0, 1, 2, 100
 SERIES_KEEP, SERIES_STREAM = 0, 1   # tvbx_run_cfg.series_mode
+LAYOUT_TNP, LAYOUT_SET4 = 0, 1      # tvbx_fc_cfg.series_layout (tvbx_fc_series)
 N_PREFETCH_VARIANTS = 17
 PACKED_VARIANTS = (8, 9, 10, 11)   # FP32x2 kernels: need tau_e == tau_i
 
@@ -446,10 +448,11 @@ def fc_noalloc(series, n_regions: int, n_sets: int, n_samples: int, fc_out, chi=
 
 
 def fc_series(series, n_regions: int, n_sets: int, n_samples: int, precision=FC_FP32, fc_out=None, fcd_out=None,
-              fcd_window=0, fcd_step=0, chi=None, mean_fc=None, set_status=None, stream=None) -> int:
-    """FC / FCD / chi / mean FC of device series [n_samples][n_regions][n_sets]
-    (tvbx_fc_series). Every buffer is a CUDA tensor; returns the number of FCD
-    windows. Synchronises the stream."""
+              fcd_window=0, fcd_step=0, chi=None, mean_fc=None, set_status=None, stream=None, layout=LAYOUT_TNP) -> int:
+    """FC / FCD / chi / mean FC of device series (tvbx_fc_series):
+    [n_samples][n_regions][n_sets] (layout LAYOUT_TNP) or set-blocked
+    [ceil(n_sets / 4)][n_samples][n_regions][4] (LAYOUT_SET4). Every buffer is a
+    CUDA tensor; returns the number of FCD windows. Synchronises the stream."""
     sp = None
     if stream is not None:
         sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -462,7 +465,7 @@ def fc_series(series, n_regions: int, n_sets: int, n_samples: int, precision=FC_
             if mem != MEM_DEVICE:
                 raise ValueError("tvbx_fc_series takes device buffers only")
             args.append(ptr)
-    cfg = FcCfg(int(precision), int(fcd_window), int(fcd_step))
+    cfg = FcCfg(int(precision), int(fcd_window), int(fcd_step), int(layout))
     nw = ctypes.c_int32(0)
     _check(load().tvbx_fc_series(args[0], int(n_regions), int(n_sets), int(n_samples), ctypes.byref(cfg), args[1],
                                  args[2], ctypes.byref(nw), args[3], args[4], args[5], sp), "tvbx_fc_series")

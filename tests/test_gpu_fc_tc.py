@@ -164,3 +164,33 @@ def test_invalid_fc_arguments(tvbx, torch):
     with pytest.raises(tvbx.TvbxError) as e:
         tvbx.fc_series(x, 129, 4, 50, precision=0, fc_out=fc, fcd_window=30, fcd_step=20)
     assert e.value.code == -1
+
+def _to_set4(torch, x):
+    """[P][N][T] -> the set-blocked layout [ceil(P / 4)][T][N][4] (padding sets NaN:
+    never read)."""
+    P, N, T = x.shape
+    G = (P + 3) // 4
+    y = np.full((G * 4, N, T), np.nan)
+    y[:P] = x
+    return torch.from_numpy(np.ascontiguousarray(y.reshape(G, 4, N, T).transpose(0, 3, 2, 1)).astype(np.float32)).cuda()
+
+
+@pytest.mark.parametrize("N,P,T", [(68, 12, 1300), (68, 10, 777), (84, 6, 1000), (5, 3, 100), (90, 9, 700)])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
+def test_set_blocked_layout_gives_the_same_results(tvbx, torch, N, P, T, prec):
+    """The FC stage reads a series in groups of 4 sets exactly as it reads the
+    sets-fastest layout: every output bit-equal, FCD included."""
+    if prec != 0 and N > 128:
+        pytest.skip("tensor cores up to 128 regions")
+    x = _series(P, N, T, 40 + N + P, "rates")
+    outs = []
+    for layout, d in ((tvbx.LAYOUT_TNP, _to_device(torch, x)), (tvbx.LAYOUT_SET4, _to_set4(torch, x))):
+        fc = torch.empty((P, N, N), dtype=torch.float32, device="cuda")
+        chi = torch.empty(P, dtype=torch.float32, device="cuda")
+        nw = (T - 50) // 25 + 1
+        fcd = torch.empty((P, nw, nw), dtype=torch.float32, device="cuda")
+        tvbx.fc_series(d, N, P, T, precision=prec, fc_out=fc, fcd_out=fcd, fcd_window=50, fcd_step=25, chi=chi,
+                       layout=layout)
+        outs.append((fc.cpu().numpy(), fcd.cpu().numpy(), chi.cpu().numpy()))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b, equal_nan=True)
