@@ -175,7 +175,7 @@ __global__ void fcd_kernel(const float* __restrict__ blocks, int32_t N, int32_t 
             const int j = k + 1 + r;
             float g = 0.0f, sk = 0.0f, sj = 0.0f;
             for (int b = w; b < w + m; ++b) {
-                g += 0.5f * (B[b * stride_b + (int64_t)k * N + j] + B[b * stride_b + (int64_t)j * N + k]);
+                g += B[b * stride_b + (int64_t)k * N + j];   // upper triangle (the matrices are symmetric)
                 sk += B[b * stride_b + (int64_t)N * N + k];
                 sj += B[b * stride_b + (int64_t)N * N + j];
             }
@@ -324,6 +324,11 @@ cudaError_t launch_fc_shift(const float* series, const SeriesLayout& sl, int32_t
 // window FC vectors (upper triangles) stay in shared memory. MW > 0: m == MW
 // and n_blocks <= FCR_MAXB, block values in registers with compile-time
 // indices; MW == 0: any m and n_blocks, block values re-read.
+//
+// Every producer writes a Gram matrix that is symmetric up to FP32 rounding
+// (the SIMT kernel exactly, the tensor-core forms as H H^T or
+// H H^T + H L^T + L H^T), so only the upper triangle is read: row r from
+// column r + 1 on, along the row (coalesced).
 constexpr int RED_THREADS = 512;
 constexpr int FCR_MAXB = 12;
 
@@ -381,21 +386,20 @@ fc_reduce_kernel(const __grid_constant__ FcArgs a, int32_t m, int32_t nw, int64_
         const float sr = sSf[r], ir = isd[r];
         const int e0 = r * N - r * (r + 1) / 2 - r - 1;   // triangle index of (r, jj) is e0 + jj
         const float* Br = B + (int64_t)r * N;              // row r of block 0
-        const float* Bc = B + r;                           // column r of block 0
         for (int jj = r + 1 + lane; jj < N; jj += 32) {
-            // symmetric part of the stored block matrices at (r, jj)
+            // the block matrices at (r, jj)
             float g = 0.0f;
             float pre[FCR_MAXB + 1];
             if constexpr (MW > 0) {
                 pre[0] = 0.0f;
 #pragma unroll
                 for (int b = 0; b < FCR_MAXB; ++b) {
-                    const float gb = b < nb ? 0.5f * (Br[b * stride_b + jj] + Bc[b * stride_b + (int64_t)jj * N]) : 0.0f;
+                    const float gb = b < nb ? Br[b * stride_b + jj] : 0.0f;
                     pre[b + 1] = pre[b] + gb;
                 }
                 g = pre[FCR_MAXB];
             } else {
-                for (int b = 0; b < nb; ++b) g += 0.5f * (Br[b * stride_b + jj] + Bc[b * stride_b + (int64_t)jj * N]);
+                for (int b = 0; b < nb; ++b) g += Br[b * stride_b + jj];
             }
             const float c = g - sr * sSf[jj] * invT;
             const float f = c * ir * isd[jj];
@@ -418,7 +422,7 @@ fc_reduce_kernel(const __grid_constant__ FcArgs a, int32_t m, int32_t nw, int64_
                 for (int w = 0; w < nw; ++w) {
                     float gw = 0.0f;
                     for (int b = w; b < w + m; ++b)
-                        gw += 0.5f * (Br[b * stride_b + jj] + Bc[b * stride_b + (int64_t)jj * N]);
+                        gw += Br[b * stride_b + jj];
                     const float cw = gw - sSw[w * N + r] * sSw[w * N + jj] * invL;
                     V[(size_t)w * M + e0 + jj] = cw * isdw[w * N + r] * isdw[w * N + jj];
                 }

@@ -5,10 +5,12 @@
 // Z[k][t] = x_k(t) - m_k, is a dense contraction over time, so it runs on the
 // fifth-generation tensor cores (tcgen05) with the accumulator in tensor
 // memory. Z is split into a high part H and a low part L (Z = H + L up to the
-// rounding of L) in BF16 or TF32; the "x3" modes form
-//   D = H H^T + H (2L)^T,   G = (D + D^T) / 2 = H H^T + H L^T + L H^T,
-// i.e. the three-product split-precision form with two MMAs (the L L^T term
-// is below the FP32 rounding of G). The single modes use D = H H^T.
+// rounding of L) in BF16 or TF32; the "x3" modes form the three-product
+// split-precision Gram matrix
+//   G = H H^T + H L^T + L H^T
+// with three MMAs per K step (the L L^T term is below the FP32 rounding of
+// G). The single modes use G = H H^T. Both are symmetric up to the rounding
+// of the accumulation, so readers take the upper triangle.
 // Accumulation is FP32 throughout. The row sums s[k] = sum_t Z[k][t] use
 // compensated (Kahan) FP32 summation in the loading threads.
 //
@@ -22,19 +24,21 @@
 // read 8 segments of 64 bytes; in [T][N][P], 32 separate pieces) and all
 // their samples. Per chunk of 128
 // bytes of K (64 BF16 or 32 TF32 samples) each loader thread (k, j) copies
-// samples j*SPC .. j*SPC+SPC-1 of region k for the SC sets into one of its two
-// raw slots in shared memory (cp.async, one chunk ahead), then subtracts the
-// shift, splits into registers, and only then waits for the MMAs of the
-// previous chunk to release the single operand stage, so the conversion of
-// chunk c+1 overlaps the MMAs of chunk c; it writes one 16-byte piece of row k
+// samples j*SPC .. j*SPC+SPC-1 of region k for the SC sets into its raw slot
+// in shared memory (cp.async). Once chunk c has landed the thread reads its
+// slot into registers and subtracts the shift, copies chunk c+1 into the same
+// slot (in flight during the conversion), splits into registers, and waits
+// only for the MMAs of chunk c-2 to release the operand stage it writes (two
+// stages, alternating by chunk), so the conversion of chunk c overlaps the
+// MMAs of chunk c-1; it writes one 16-byte piece of row k
 // of each operand buffer in the 128-byte swizzled K-major layout the MMA
 // reads. One lane of the MMA warp issues the MMAs (M = 128 rows, of which the
 // first N are regions; N_mma = N rounded up to 16) and commits them to the
-// stage's mbarrier. At the end of a block loader warps 0-3 read the
+// stage's mbarrier. Shared memory: the two operand stages, (128 - R) rows of
+// 128 bytes (the A rows read beyond the last buffer), the raw slots. At the end of a block loader warps 0-3 read the
 // accumulator rows out of tensor memory (lane = region) and write them to
 // global memory as they are, while the other loader warps already stage the
-// next block's first chunk; the x3 forms leave D unsymmetric and every reader
-// of the block moments takes (D + D^T) / 2.
+// next block's first chunk.
 //
 // Rows N .. 127 of the A operand and N .. N_mma - 1 of the B operand are
 // whatever follows the buffer in shared memory (in bounds by construction);
@@ -62,15 +66,6 @@ static __device__ __forceinline__ float lv(const float4& v, int s)
     return s == 0 ? v.x : (s == 1 ? v.y : (s == 2 ? v.z : v.w));
 }
 static __device__ __forceinline__ float lv(const float2& v, int s) { return s == 0 ? v.x : v.y; }
-static __device__ __forceinline__ void lset(float4& v, int s, float x)
-{
-    if (s == 0) v.x = x; else if (s == 1) v.y = x; else if (s == 2) v.z = x; else v.w = x;
-}
-static __device__ __forceinline__ void lset(float2& v, int s, float x)
-{
-    if (s == 0) v.x = x; else v.y = x;
-}
-
 static __device__ __forceinline__ void kahan(float& sum, float& comp, float x)
 {
     const float y = x - comp;
@@ -102,6 +97,41 @@ static __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, u
 {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
                  : "memory");
+}
+
+// Two FP32 values in one 64-bit register pair, for the packed f32x2
+// arithmetic of sm_100-class SMs (each lane rounds exactly like the scalar
+// instruction, so packed and scalar forms give the same bits).
+static __device__ __forceinline__ uint64_t pk2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};\n" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+static __device__ __forceinline__ float2 un2(uint64_t v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;\n" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+static __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;\n" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+static __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;\n" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// BF16 pair (lo, hi) rounded to nearest even, lo in the low half
+static __device__ __forceinline__ uint32_t bf2(float lo, float hi)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;\n" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 }  // namespace
@@ -159,7 +189,7 @@ static __device__ __forceinline__ void drain_quarter(const FcArgs& a, uint32_t t
 // region k, 16-byte piece j of each 128-byte row); warp NLW issues the MMAs
 // (one lane); loader warps 0 .. 3 also drain the accumulator of each finished
 // block from tensor memory (warp w reads lanes 32 w ..). Hand-offs are
-// mbarriers: full (one arrival per loader warp), empty (MMA commit), accf
+// mbarriers: full[stage] (one arrival per loader warp), empty[stage] (MMA commit), accf
 // (MMA commit after a block's last chunk), drained (one arrival per draining
 // warp) -- no CTA-wide barrier inside the loop.
 template <int PREC, int SC, int MAXT>
@@ -175,7 +205,7 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
     using V = typename LoadVec<SC>::T;
 
     extern __shared__ uint8_t dyn_smem[];
-    __shared__ uint64_t s_full, s_empty, s_accf, s_drained;
+    __shared__ uint64_t s_full[2], s_empty[2], s_accf, s_drained;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
 
@@ -198,8 +228,10 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
 
     if (warp == NLW) tmem_alloc(&s_tmem, tmem_cols);
     if (tid == 0) {
-        mbar_init(&s_full, NLW);
-        mbar_init(&s_empty, 1);
+        mbar_init(&s_full[0], NLW);
+        mbar_init(&s_full[1], NLW);
+        mbar_init(&s_empty[0], 1);
+        mbar_init(&s_empty[1], 1);
         mbar_init(&s_accf, 1);
         mbar_init(&s_drained, 4);
         s_abort = 0;
@@ -210,7 +242,9 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    auto block_len = [&](int64_t b) { return ((b * blk + blk < Tn) ? b * blk + blk : Tn) - b * blk; };
+    // sample indices within the window fit in 32 bits (the launcher checks)
+    const int T32 = (int)Tn, blk32 = (int)blk, nb32 = (int)n_blocks;
+    auto block_len = [&](int b) { return ((b * blk32 + blk32 < T32) ? b * blk32 + blk32 : T32) - b * blk32; };
 
     if (warp < NLW) {
         // ------------------------------------------------------------ loaders
@@ -231,16 +265,16 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
         const float* src0 = a.series + series_index(a.sl, a.t_begin + (int64_t)j * SPC, k, p0);
         const int64_t st = a.sl.st;
         const bool fast_sets = loader && all_sets && vec_ok;
-        // this thread's raw slots (two, alternating by chunk): SPC pieces of SC
-        // floats, piece i of slot q at raw_base + ((q * SPC + i) * NLT + tid) * 4 SC
+        // this thread's raw slot (q = 0): SPC pieces of SC floats, piece i at
+        // raw_base + ((q * SPC + i) * NLT + tid) * 4 SC
         // (a warp's pieces are contiguous)
         constexpr int PBYTES = 4 * SC;
         const int NLT = 32 * NLW;
-        const uint32_t raw_base = base + stage_bytes + (uint32_t)(128 - R) * 128u;
+        const uint32_t raw_base = base + 2u * stage_bytes + (uint32_t)(128 - R) * 128u;
         // copy samples [ts, te) of this thread's piece into raw slot q; samples
         // outside and sets >= P are zero-filled
-        auto issue_chunk = [&](int64_t ts, int64_t te, int q) {
-            const float* src = src0 + ts * st;
+        auto issue_chunk = [&](int ts, int te, int q) {
+            const float* src = src0 + (int64_t)ts * st;
             if (fast_sets && te - ts == KC) {
                 const uint32_t dst0 = raw_base + (uint32_t)(q * SPC * NLT + tid) * PBYTES;
 #pragma unroll
@@ -270,98 +304,162 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
         };
         const uint32_t row_off = (uint32_t)(k >> 3) * 1024u + (uint32_t)(k & 7) * 128u +
                                  (uint32_t)((j ^ (k & 7)) << 4);
-        float S[SC], C[SC];
+        float S[SC], C[SC];   // TF32 forms: row sums and their compensation
 #pragma unroll
         for (int s = 0; s < SC; ++s) S[s] = C[s] = 0.0f;
-        issue_chunk(0, block_len(0) < KC ? block_len(0) : KC, 0);
-        cp_async_commit();
-        int64_t gc = 0;
-        for (int64_t b = 0; b < n_blocks; ++b) {
-            const int64_t b0 = b * blk, blen = block_len(b);
-            const int64_t nck = (blen + KC - 1) / KC;
-            for (int64_t c = 0; c < nck; ++c) {
-                const int64_t ts = b0 + c * KC;
-                const int64_t te = (ts + KC < b0 + blen) ? ts + KC : b0 + blen;
-                const int q = (int)(gc & 1);
-                // copy the next chunk (in this block or the next one) into the
-                // other slot, whose contents were consumed by the previous chunk
-                if (c + 1 < nck) {
-                    const int64_t nts = ts + KC;
-                    issue_chunk(nts, (nts + KC < b0 + blen) ? nts + KC : b0 + blen, q ^ 1);
-                } else if (b + 1 < n_blocks) {
-                    const int64_t nts = b0 + blk, nl = block_len(b + 1);
-                    issue_chunk(nts, nts + (nl < KC ? nl : KC), q ^ 1);
-                }
-                cp_async_commit();
-                asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this chunk has landed
-                // shift and split into registers while the previous chunk's MMAs run
-                uint32_t hw[SC][4], lw[SC][4];
+        constexpr int NH = SC / 2;
+        uint64_t S2[NH], C2[NH], shp[NH];   // BF16 forms: the same per set pair
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            S2[h] = C2[h] = pk2(0.0f, 0.0f);
+            shp[h] = pk2(sh[2 * h], sh[2 * h + 1]);
+        }
+        // chunks are issued two ahead of the one being converted: the cursor
+        // (ib, ic) is the next chunk to copy; an empty group keeps the count
+        int ib = 0, ic = 0;
+        auto issue_next = [&](int q) {
+            if (ib < nb32) {
+                const int b0 = ib * blk32, blen = block_len(ib);
+                const int ts = b0 + ic * KC;
+                issue_chunk(ts, (ts + KC < b0 + blen) ? ts + KC : b0 + blen, q);
+                if (++ic * KC >= blen) { ic = 0; ++ib; }
+            }
+            cp_async_commit();
+        };
+        issue_next(0);
+        int gc = 0;
+        for (int b = 0; b < nb32; ++b) {
+            const int b0 = b * blk32, blen = block_len(b);
+            const int nck = (blen + KC - 1) / KC;
+            for (int c = 0; c < nck; ++c) {
+                const int ts = b0 + c * KC;
+                const int te = (ts + KC < b0 + blen) ? ts + KC : b0 + blen;
+                const int q = 0;                                          // the single raw slot
+                const uint32_t st_q = (uint32_t)(gc & 1);                 // operand stage of this chunk
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this chunk has landed
+                // the chunk's samples to registers, shifted; padding samples and
+                // missing sets are 0
                 const bool full_chunk = fast_sets && te - ts == KC;
                 const uint8_t* slot = dyn_smem + (raw_base - raw) + (size_t)(q * SPC * NLT + tid) * PBYTES;
-                float2 raw2[SPC];   // two sets of every sample per 8-byte load
+                uint32_t hw[SC][4], lw[SC][4];
+                if constexpr (KIND == 0) {
+                    // sets 2h and 2h + 1 of every sample in one register pair
+                    uint64_t zp[SPC][NH];
 #pragma unroll
-                for (int s = 0; s < SC; ++s) {
-                    if ((s & 1) == 0) {
+                    for (int i = 0; i < SPC; ++i) {
+                        const V x = *reinterpret_cast<const V*>(slot + (size_t)i * NLT * PBYTES);
 #pragma unroll
-                        for (int i = 0; i < SPC; ++i)
-                            raw2[i] = *reinterpret_cast<const float2*>(slot + (size_t)i * NLT * PBYTES + 4 * s);
+                        for (int h = 0; h < NH; ++h) zp[i][h] = sub2(pk2(lv(x, 2 * h), lv(x, 2 * h + 1)), shp[h]);
                     }
-                    float z[SPC];
-#pragma unroll
-                    for (int i = 0; i < SPC; ++i) z[i] = ((s & 1) ? raw2[i].y : raw2[i].x) - sh[s];
                     if (!full_chunk) {   // padding samples and missing sets are 0
 #pragma unroll
                         for (int i = 0; i < SPC; ++i)
-                            if (!(loader && ts + j * SPC + i < te && p0 + s < P)) z[i] = 0.0f;
+#pragma unroll
+                            for (int h = 0; h < NH; ++h) {
+                                float2 v = un2(zp[i][h]);
+                                const bool tv = loader && ts + j * SPC + i < te;
+                                if (!(tv && p0 + 2 * h < P)) v.x = 0.0f;
+                                if (!(tv && p0 + 2 * h + 1 < P)) v.y = 0.0f;
+                                zp[i][h] = pk2(v.x, v.y);
+                            }
                     }
-                    float part[SPC];
+                    // the slot has been read (the values above depend on it): copy
+                    // the next chunk into it while this one is split and the
+                    // previous chunk's MMAs run
+                    issue_next(q);
 #pragma unroll
-                    for (int i = 0; i < SPC; ++i) part[i] = z[i];
+                    for (int h = 0; h < NH; ++h) {
+                        uint64_t part[SPC];
 #pragma unroll
-                    for (int w = SPC / 2; w > 0; w >>= 1)
+                        for (int i = 0; i < SPC; ++i) part[i] = zp[i][h];
 #pragma unroll
-                        for (int i = 0; i < w; ++i) part[i] += part[i + w];
-                    kahan(S[s], C[s], part[0]);
-                    if constexpr (KIND == 0) {
+                        for (int w = SPC / 2; w > 0; w >>= 1)
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const __nv_bfloat162 h = __floats2bfloat162_rn(z[2 * u], z[2 * u + 1]);
-                            hw[s][u] = *reinterpret_cast<const uint32_t*>(&h);
+                            for (int i = 0; i < w; ++i) part[i] = add2(part[i], part[i + w]);
+                        const uint64_t y = sub2(part[0], C2[h]);   // compensated sum, both sets
+                        const uint64_t t = add2(S2[h], y);
+                        C2[h] = sub2(sub2(t, S2[h]), y);
+                        S2[h] = t;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                        for (int h = 0; h < NH; ++h) {
+                            const float2 z0 = un2(zp[2 * u][h]), z1 = un2(zp[2 * u + 1][h]);
+                            const uint32_t ha = bf2(z0.x, z1.x);   // set 2h, samples 2u and 2u + 1
+                            const uint32_t hb = bf2(z0.y, z1.y);   // set 2h + 1
+                            hw[2 * h][u] = ha;
+                            hw[2 * h + 1][u] = hb;
                             if constexpr (SPLIT) {
-                                const float2 hf = __bfloat1622float2(h);
-                                const __nv_bfloat162 l = __floats2bfloat162_rn(2.0f * (z[2 * u] - hf.x),
-                                                                               2.0f * (z[2 * u + 1] - hf.y));
-                                lw[s][u] = *reinterpret_cast<const uint32_t*>(&l);
+                                // the high parts back in FP32 (exact), then the low parts
+                                const uint64_t h0 = pk2(__uint_as_float(ha << 16), __uint_as_float(hb << 16));
+                                const uint64_t h1 = pk2(__uint_as_float(ha & 0xffff0000u), __uint_as_float(hb & 0xffff0000u));
+                                const float2 l0 = un2(sub2(zp[2 * u][h], h0)), l1 = un2(sub2(zp[2 * u + 1][h], h1));
+                                lw[2 * h][u] = bf2(l0.x, l1.x);
+                                lw[2 * h + 1][u] = bf2(l0.y, l1.y);
                             }
                         }
-                    } else {
+                    }
+                } else {
+                    float zz[SC][SPC];
+#pragma unroll
+                    for (int i = 0; i < SPC; ++i) {
+                        const V x = *reinterpret_cast<const V*>(slot + (size_t)i * NLT * PBYTES);
+#pragma unroll
+                        for (int s = 0; s < SC; ++s) zz[s][i] = lv(x, s) - sh[s];
+                    }
+                    if (!full_chunk) {
+#pragma unroll
+                        for (int s = 0; s < SC; ++s)
+#pragma unroll
+                            for (int i = 0; i < SPC; ++i)
+                                if (!(loader && ts + j * SPC + i < te && p0 + s < P)) zz[s][i] = 0.0f;
+                    }
+                    issue_next(q);
+#pragma unroll
+                    for (int s = 0; s < SC; ++s) {
+                        const float* z = zz[s];
+                        float part[SPC];
+#pragma unroll
+                        for (int i = 0; i < SPC; ++i) part[i] = z[i];
+#pragma unroll
+                        for (int w = SPC / 2; w > 0; w >>= 1)
+#pragma unroll
+                            for (int i = 0; i < w; ++i) part[i] += part[i + w];
+                        kahan(S[s], C[s], part[0]);
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             hw[s][u] = tf32_rna(z[u]);
-                            if constexpr (SPLIT) lw[s][u] = __float_as_uint(2.0f * (z[u] - __uint_as_float(hw[s][u])));
+                            if constexpr (SPLIT) lw[s][u] = __float_as_uint(z[u] - __uint_as_float(hw[s][u]));
                         }
                     }
                 }
                 // the operand stage is free once the previous chunk's MMAs completed
-                if (gc >= 1) warp_wait(&s_empty, (uint32_t)((gc - 1) & 1), a.wait_limit, abort, a.error, 20);
+                if (gc >= 2) warp_wait(&s_empty[st_q], (uint32_t)(((gc >> 1) - 1) & 1), a.wait_limit, abort, a.error, 20);
                 if (loader) {
 #pragma unroll
                     for (int s = 0; s < SC; ++s) {
-                        const uint32_t hb = base + (uint32_t)s * NBUF * buf_bytes;
+                        const uint32_t hb = base + st_q * stage_bytes + (uint32_t)s * NBUF * buf_bytes;
                         st_shared_v4(hb + row_off, hw[s][0], hw[s][1], hw[s][2], hw[s][3]);
                         if constexpr (SPLIT) st_shared_v4(hb + buf_bytes + row_off, lw[s][0], lw[s][1], lw[s][2], lw[s][3]);
                     }
                 }
                 fence_proxy_async_shared();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&s_full);
+                if (lane == 0) mbar_arrive(&s_full[st_q]);
                 ++gc;
             }
             // this block's row sums
             const int64_t stride_b = (int64_t)N * N + N;
 #pragma unroll
             for (int s = 0; s < SC; ++s) {
-                float v = S[s] - C[s];
+                float v;
+                if constexpr (KIND == 0) {
+                    const float2 d = un2(sub2(S2[s >> 1], C2[s >> 1]));
+                    v = (s & 1) ? d.y : d.x;
+                } else {
+                    v = S[s] - C[s];
+                }
                 v += __shfl_xor_sync(0xffffffffu, v, 1);
                 v += __shfl_xor_sync(0xffffffffu, v, 2);
                 v += __shfl_xor_sync(0xffffffffu, v, 4);
@@ -369,6 +467,8 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
                     a.blocks[((p0 + s) * n_blocks + b) * stride_b + (int64_t)N * N + k] = v;
                 S[s] = C[s] = 0.0f;
             }
+#pragma unroll
+            for (int h = 0; h < NH; ++h) S2[h] = C2[h] = pk2(0.0f, 0.0f);
             // warps 0-3: drain block b (accumulator rows, lane = region) to global
             if (warp < 4) {
                 warp_wait(&s_accf, (uint32_t)(b & 1), a.wait_limit, abort, a.error, 64);
@@ -382,28 +482,32 @@ fc_tc_kernel(const __grid_constant__ FcArgs a, int32_t R, int32_t Ncols, uint32_
     } else {
         // ------------------------------------------------------- MMA issue
         const uint32_t idesc = tc_idesc(KIND == 0 ? 1u : 2u, 128u, (uint32_t)Ncols);
-        int64_t gc = 0;
-        for (int64_t b = 0; b < n_blocks; ++b) {
-            const int64_t nck = (block_len(b) + KC - 1) / KC;
-            for (int64_t c = 0; c < nck; ++c) {
-                warp_wait(&s_full, (uint32_t)(gc & 1), a.wait_limit, abort, a.error, 32);
+        int gc = 0;
+        for (int b = 0; b < nb32; ++b) {
+            const int nck = (block_len(b) + KC - 1) / KC;
+            for (int c = 0; c < nck; ++c) {
+                const uint32_t st_q = (uint32_t)(gc & 1);
+                warp_wait(&s_full[st_q], (uint32_t)((gc >> 1) & 1), a.wait_limit, abort, a.error, 32);
                 if (c == 0 && b > 0)   // the accumulator of block b-1 must have been read
                     warp_wait(&s_drained, (uint32_t)((b - 1) & 1), a.wait_limit, abort, a.error, 32);
                 tc_fence_after();
                 if (lane == 0) {
 #pragma unroll 1
                     for (int s = 0; s < SC; ++s) {
-                        const uint32_t hb = base + (uint32_t)s * NBUF * buf_bytes;
+                        const uint32_t hb = base + st_q * stage_bytes + (uint32_t)s * NBUF * buf_bytes;
                         const uint32_t d = tmem + (uint32_t)(s * Ncols);
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
                             const uint64_t ad = sw128_desc(hb + 32u * ks);
                             tc_mma<KIND>(d, ad, ad, idesc, (c == 0 && ks == 0) ? 0u : 1u);
-                            if constexpr (SPLIT)
-                                tc_mma<KIND>(d, ad, sw128_desc(hb + buf_bytes + 32u * ks), idesc, 1u);
+                            if constexpr (SPLIT) {
+                                const uint64_t ld = sw128_desc(hb + buf_bytes + 32u * ks);
+                                tc_mma<KIND>(d, ad, ld, idesc, 1u);   // H L^T
+                                tc_mma<KIND>(d, ld, ad, idesc, 1u);   // L H^T
+                            }
                         }
                     }
-                    tc_commit(&s_empty);
+                    tc_commit(&s_empty[st_q]);
                     if (c + 1 == nck) tc_commit(&s_accf);
                 }
                 __syncwarp();
@@ -442,7 +546,7 @@ static bool fc_tc_geom(int N, int prec, FcTcGeom& g)
     const size_t buf = (size_t)g.R * 128;
     const size_t stage = (size_t)g.SC * nbuf * buf;
     const int spc = (prec == TVBX_FC_BF16 || prec == TVBX_FC_BF16X3) ? 8 : 4;
-    g.smem = 1024 + stage + (size_t)(128 - g.R) * 128 + (size_t)2 * 32 * g.loader_warps * spc * 4 * g.SC;
+    g.smem = 1024 + 2 * stage + (size_t)(128 - g.R) * 128 + (size_t)32 * g.loader_warps * spc * 4 * g.SC;
     uint32_t need = (uint32_t)(g.SC * g.Ncols), cols = 32;
     while (cols < need) cols <<= 1;
     g.tmem_cols = cols;
@@ -483,6 +587,7 @@ cudaError_t launch_fc_tc_moments(const FcArgs& a, int prec, cudaStream_t s)
 {
     FcTcGeom g;
     if (!fc_tc_geom(a.N, prec, g) || !a.error) return cudaErrorInvalidValue;
+    if (a.t_end - a.t_begin > (int64_t)INT32_MAX - 4096) return cudaErrorInvalidValue;   // 32-bit sample indices
     switch (prec) {
     case TVBX_FC_BF16: return launch_prec<TVBX_FC_BF16>(a, g, s);
     case TVBX_FC_BF16X3: return launch_prec<TVBX_FC_BF16X3>(a, g, s);

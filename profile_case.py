@@ -11,7 +11,8 @@ Takes the first `--sets` sets of the 32,768-set grid (68 regions, v 4 m/s),
 integrates `--n-steps` steps in launches of `--chunk` steps and optionally
 runs the FC/FCD pass, then prints the wall time. With --fc-series, runs
 only the FC stage (tvbx_fc_series, FCD 1000/500 unless --no-fcd) on
-synthetic rate-like series of `--sets` x 68 regions x `--samples`. With
+synthetic rate-like series of `--sets` x 68 regions x `--samples`, in groups
+of 4 sets (the engine's own layout) or, with --fc-layout tnp, sets fastest. With
 --analysis, runs only the Table 2 metrics (tvbx_series_analysis) on such
 series in the [sets][regions][samples] layout. With --bold, runs the
 Balloon-Windkessel kernel on such rates (TR 1 s) and the phFCD of 300 TRs.
@@ -47,6 +48,7 @@ def main():
     ap.add_argument("--samples", type=int, default=5000)
     ap.add_argument("--fc-precision", default="bf16x3", choices=["fp32", "bf16", "bf16x3", "tf32", "tf32x3"])
     ap.add_argument("--no-fcd", action="store_true")
+    ap.add_argument("--fc-layout", default="set4", choices=["set4", "tnp"])
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--analysis", action="store_true")
     ap.add_argument("--bold", action="store_true")
@@ -103,6 +105,9 @@ def fc_series_case(args):
     dev = torch.device("cuda", 0)
     P, N, T = args.sets, 68, args.samples
     X = synth.rate_series_device(torch, dev, P, N, T, seed=1000)
+    layout = tvbx.LAYOUT_SET4 if args.fc_layout == "set4" else tvbx.LAYOUT_TNP
+    if layout == tvbx.LAYOUT_SET4:
+        X = X.view(T, N, P // 4, 4).permute(2, 0, 1, 3).contiguous()
     fc = torch.empty((P, N, N), dtype=torch.float32, device=dev)
     w, s = (0, 0) if args.no_fcd else (min(1000, T), min(500, T))
     nw = (T - w) // s + 1 if w else 0
@@ -110,7 +115,7 @@ def fc_series_case(args):
     prec = getattr(tvbx, "FC_" + args.fc_precision.upper())
     for i in range(args.repeat):
         t0 = time.time()
-        tvbx.fc_series(X, N, P, T, precision=prec, fc_out=fc, fcd_out=fcd if w else None, fcd_window=w,
+        tvbx.fc_series(X, N, P, T, precision=prec, fc_out=fc, fcd_out=fcd if w else None, layout=layout, fcd_window=w,
                        fcd_step=s)
         print(f"fc series {P} x {N} x {T} {args.fc_precision}: {time.time() - t0:.4f} s")
 
