@@ -276,12 +276,25 @@ cudaError_t launch_fc_moments(const FcArgs& a, cudaStream_t s)
 // [t_begin, t_end). Any shift gives the same moments in exact arithmetic; one
 // within a few standard deviations of the mean keeps the low-precision
 // operands of the tensor-core path small relative to the fluctuations.
+// Consecutive threads take consecutive elements of a sample: sets fastest in
+// the [T][N][P] layout, (region, set within the group of 4) in the
+// set-blocked one.
 __global__ void fc_shift_kernel(const float* __restrict__ series, const SeriesLayout sl, int32_t N, int64_t P,
                                 int64_t t_begin, int64_t t_end, float* __restrict__ shift)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // shift[k][p], i = k P + p
-    if (i >= (int64_t)N * P) return;
-    const int64_t k = i / P, p = i - k * P;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t k, p;
+    if (sl.sk == 4) {   // i = (group, region, set within the group)
+        const int64_t g = i / (4 * (int64_t)N), q = i - g * 4 * (int64_t)N;
+        k = q >> 2;
+        p = 4 * g + (q & 3);
+        if (p >= P) return;
+    } else {            // i = (region, set)
+        if (i >= (int64_t)N * P) return;
+        k = i / P;
+        p = i - k * P;
+    }
+    const int64_t o = k * P + p;   // shift[k][p]
     const int64_t Tn = t_end - t_begin;
     const int64_t n = Tn < 64 ? Tn : 64;
     float s = 0.0f;
@@ -289,7 +302,7 @@ __global__ void fc_shift_kernel(const float* __restrict__ series, const SeriesLa
         const int64_t t = t_begin + (q * Tn) / n;
         s += series[series_index(sl, t, k, p)];
     }
-    shift[i] = n > 0 ? s / (float)n : 0.0f;
+    shift[o] = n > 0 ? s / (float)n : 0.0f;
 }
 
 // acc += add over n floats: the block moments of one chunk of a streamed
@@ -312,7 +325,8 @@ cudaError_t launch_fc_accumulate(const float* add, float* acc, int64_t n, cudaSt
 cudaError_t launch_fc_shift(const float* series, const SeriesLayout& sl, int32_t N, int64_t P, int64_t t_begin,
                             int64_t t_end, float* shift, cudaStream_t s)
 {
-    const int64_t n = (int64_t)N * P;
+    // threads: N P, or N x (P rounded up to 4) in the set-blocked layout
+    const int64_t n = (int64_t)N * (sl.sk == 4 ? (P + 3) / 4 * 4 : P);
     note_launch();
     fc_shift_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(series, sl, N, P, t_begin, t_end, shift);
     return cudaGetLastError();

@@ -152,7 +152,10 @@ static __device__ __forceinline__ void warp_wait(uint64_t* bar, uint32_t parity,
 
 // Accumulator rows of one lane quarter (the calling warp's) of every set
 // to the block-moment rows in global memory (16-byte stores where the rows
-// are 16-byte aligned, i.e. N a multiple of 4).
+// are 16-byte aligned, i.e. N a multiple of 4). Readers take the diagonal and
+// the upper triangle only, so a row is written from the 16-column block that
+// holds its diagonal on, and blocks below every row of the quarter are not
+// read out of tensor memory.
 template <int SC>
 static __device__ __forceinline__ void drain_quarter(const FcArgs& a, uint32_t tmem, int quarter, int Ncols, int64_t p0,
                                                      int64_t b)
@@ -165,10 +168,10 @@ static __device__ __forceinline__ void drain_quarter(const FcArgs& a, uint32_t t
     for (int s = 0; s < SC; ++s) {
         float* out = a.blocks + ((p0 + s) * a.n_blocks + b) * stride_b + (int64_t)row * N;
         const bool w_ok = row < N && p0 + s < P;
-        for (int cb = 0; cb * 16 < N; ++cb) {
+        for (int cb = quarter * 2; cb * 16 < N; ++cb) {   // columns from 32 * quarter on
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * Ncols + cb * 16), v);
-            if (w_ok) {
+            if (w_ok && cb * 16 + 16 > row) {
                 if (vec && cb * 16 + 16 <= N) {
 #pragma unroll
                     for (int q = 0; q < 16; q += 4)
