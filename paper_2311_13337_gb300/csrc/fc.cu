@@ -344,7 +344,23 @@ cudaError_t launch_fc_shift(const float* series, const SeriesLayout& sl, int32_t
 // H H^T + H L^T + L H^T), so only the upper triangle is read: row r from
 // column r + 1 on, along the row (coalesced).
 constexpr int RED_THREADS = 512;
+constexpr int RED_WARPS = RED_THREADS / 32;
 constexpr int FCR_MAXB = 12;
+
+// Work items of the row pass: (row r, first column of a 32-column chunk right
+// of the diagonal), row by row; their number is sum over L = 1 .. N-1 of
+// ceil(L / 32).
+static __host__ __device__ inline int fc_reduce_items(int N)
+{
+    const int Q = (N - 1) / 32, R = (N - 1) % 32;
+    return N > 1 ? 16 * Q * (Q + 1) + R * (Q + 1) : 0;
+}
+
+static __device__ __forceinline__ float warp_sum(float x)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
 
 template <int MW>
 __global__ void __launch_bounds__(RED_THREADS)
@@ -364,10 +380,17 @@ fc_reduce_kernel(const __grid_constant__ FcArgs a, int32_t m, int32_t nw, int64_
     float* sSw = cdg + N;                   // [nw][N] window row sums
     float* isdw = sSw + nw * N;             // [nw][N] window 1 / sd
     float* V = isdw + nw * N;               // [nw][M] window FC upper triangles
-    float* red = V + (size_t)nw * M;        // [48] + [nw]
+    float* red = V + (size_t)nw * M;        // [48] sums, [nw] inverse norms
+    int* items = reinterpret_cast<int*>(red + 48 + nw);   // row-pass items
+    const int n_items = fc_reduce_items(N);
     const float invT = Tn > 0 ? 1.0f / (float)Tn : 0.0f;
     const float invL = Lw > 0 ? 1.0f / (float)Lw : 0.0f;
 
+    if (tid == RED_THREADS - 1) {
+        int q = 0;
+        for (int r = 0; r + 1 < N; ++r)
+            for (int c = r + 1; c < N; c += 32) items[q++] = (r << 16) | c;
+    }
     for (int k = tid; k < N; k += blockDim.x) {
         const float* sk_b = B + (int64_t)N * N + k;
         const float* dk_b = B + (int64_t)k * N + k;
@@ -396,11 +419,14 @@ fc_reduce_kernel(const __grid_constant__ FcArgs a, int32_t m, int32_t nw, int64_
         if (!(isd[k] > 0.0f)) zero = true;
         if (fc) fc[(int64_t)k * N + k] = 1.0f;
     }
-    for (int r = warp; r < N; r += nwarps) {
+    // the row pass: items (row, 32-column chunk) dealt to the warps in turn,
+    // so every warp gets the same number of chunks up to one
+    for (int it = warp; it < n_items; it += RED_WARPS) {
+        const int r = items[it] >> 16, jj = (items[it] & 0xffff) + lane;
         const float sr = sSf[r], ir = isd[r];
         const int e0 = r * N - r * (r + 1) / 2 - r - 1;   // triangle index of (r, jj) is e0 + jj
         const float* Br = B + (int64_t)r * N;              // row r of block 0
-        for (int jj = r + 1 + lane; jj < N; jj += 32) {
+        if (jj < N) {
             // the block matrices at (r, jj)
             float g = 0.0f;
             float pre[FCR_MAXB + 1];
@@ -460,40 +486,54 @@ fc_reduce_kernel(const __grid_constant__ FcArgs a, int32_t m, int32_t nw, int64_
     }
     if (nw == 0) return;
 
-    // FCD: centre and normalise each window vector, then all pairwise products
+    // FCD: centre and normalise each window vector (a warp per window), then
+    // the products of window u with up to four windows v > u per warp item
+    // (window u read once for all four)
     float* mom = red + 48;   // [nw] inverse norms
-    for (int w = warp; w < nw; w += nwarps) {
+    for (int w = warp; w < nw; w += RED_WARPS) {
         float* v = V + (size_t)w * M;
         float sum = 0.0f;
         for (int i = lane; i < M; i += 32) sum += v[i];
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        const float mu = sum / (float)M;
+        const float mean = warp_sum(sum) / (float)M;
         float ss = 0.0f;
         for (int i = lane; i < M; i += 32) {
-            const float x = v[i] - mu;
+            const float x = v[i] - mean;
             v[i] = x;
             ss += x * x;
         }
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        if (lane == 0) mom[w] = ss > 0.0f ? rsqrtf(ss) : 0.0f;
+        ss = warp_sum(ss);
+        if (lane == 0) {
+            mom[w] = ss > 0.0f ? rsqrtf(ss) : 0.0f;
+            fcd[(p * nw + w) * nw + w] = 1.0f;
+        }
     }
     __syncthreads();
-    const int npair = nw * (nw + 1) / 2;
-    for (int q = warp; q < npair; q += nwarps) {
-        int u = 0, rem = q;
-        while (rem >= nw - u) { rem -= nw - u; ++u; }
-        const int v2 = u + rem;
-        float dot = 0.0f;
-        if (u != v2) {
-            const float* x = V + (size_t)u * M;
-            const float* y = V + (size_t)v2 * M;
-            for (int i = lane; i < M; i += 32) dot += x[i] * y[i];
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    int n_pitems = 0;   // items (u, first v) with v = u + 1, u + 5, ...
+    for (int u = 0; u < nw; ++u) n_pitems += (nw - 1 - u + 3) / 4;
+    for (int it = warp; it < n_pitems; it += RED_WARPS) {
+        int u = 0, rem = it;
+        while (rem >= (nw - 1 - u + 3) / 4) { rem -= (nw - 1 - u + 3) / 4; ++u; }
+        const int v0 = u + 1 + 4 * rem, nv = nw - v0 < 4 ? nw - v0 : 4;
+        const float* x = V + (size_t)u * M;
+        const float* y0 = V + (size_t)v0 * M;
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int i = lane; i < M; i += 32) {
+            const float xi = x[i];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < nv) acc[c] += xi * y0[(size_t)c * M + i];
         }
-        if (lane == 0) {
-            const float r = u == v2 ? 1.0f : dot * mom[u] * mom[v2];
-            fcd[(p * nw + u) * nw + v2] = r;
-            fcd[(p * nw + v2) * nw + u] = r;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (c < nv) {
+                const float dot = warp_sum(acc[c]);
+                if (lane == 0) {
+                    const int v2 = v0 + c;
+                    const float r = dot * mom[u] * mom[v2];
+                    fcd[(p * nw + u) * nw + v2] = r;
+                    fcd[(p * nw + v2) * nw + u] = r;
+                }
+            }
         }
     }
 }
@@ -502,7 +542,8 @@ static size_t fc_reduce_smem(int N, int nb, int nw)
 {
     (void)nb;
     const size_t M = (size_t)N * (N - 1) / 2;
-    return sizeof(float) * (3 * (size_t)N + 2 * (size_t)nw * N + (size_t)nw * M + 48 + nw);
+    return sizeof(float) * (3 * (size_t)N + 2 * (size_t)nw * N + (size_t)nw * M + 48 + (size_t)nw) +
+           sizeof(int) * (size_t)fc_reduce_items(N);
 }
 
 template <int MW>
