@@ -11,14 +11,14 @@
 //   y = V0 (k1 (1 - q) + k2 (1 - q/v) + k3 (1 - v)).
 // One thread per (region, set) integrates forward Euler with the step of the
 // rate samples. The state is kept as deviations from rest (f - 1, v - 1,
-// q - 1) and the powers are written with log1p / expm1, so FP32 resolves the
+// q - 1) and the powers are written as functions of those deviations
+// (series for small arguments, log1p / expm1 beyond), so FP32 resolves the
 // small excursions a drive of a few Hz causes (about 1e-3 of the resting
 // values) instead of rounding them against 1, and a zero drive keeps the
 // resting state exactly.
 //
-// Layouts: series [T][N][P] (the engine's layout: consecutive threads read
-// consecutive sets), BOLD [T / decim][N][P], state [4][N][P] = s, f - 1,
-// v - 1, q - 1.
+// Layouts: series [T][N][P] (consecutive threads read consecutive sets), BOLD
+// [T / decim][N][P], state [4][N][P] = s, f - 1, v - 1, q - 1.
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -34,7 +34,42 @@ namespace {
 
 struct BoldDev {
     float kappa, gamma, inv_tau, inv_alpha, r_E0, lnE, V0, k1, k2, k3, dt;   // r_E0 = (1 - E0) / E0
+    float ca[8];   // binomial coefficients C(1/alpha, k), k = 1 .. 8
+    float v_series;   // |v - 1| up to which the binomial series is used (0: never)
 };
+
+// (1 + v)^a - 1 for |v| <= v_series: the binomial series sum_k C(a, k) v^k to
+// degree 8 (Horner); v_series is chosen on the host so that the rest of the
+// series stays below 1e-8 of the first term (exact for integer a <= 8).
+// Beyond it, expm1(a log1p(v)).
+static __device__ __forceinline__ float pow1p_m1(float v, const BoldDev& c)
+{
+    if (fabsf(v) <= c.v_series) {
+        float h = c.ca[7];
+#pragma unroll
+        for (int k = 6; k >= 0; --k) h = fmaf(h, v, c.ca[k]);
+        return h * v;
+    }
+    return expm1f(log1pf(v) * c.inv_alpha);
+}
+
+// e^x - 1 for |x| <= 1/4 by its Taylor series to degree 8 (the rest is below
+// 1.1e-11 of the first term), else expm1f
+static __device__ __forceinline__ float expm1_small(float x)
+{
+    if (fabsf(x) <= 0.25f) {
+        float h = 1.0f / 40320.0f;                 // 1/8!
+        h = fmaf(h, x, 1.0f / 5040.0f);            // 1/7!
+        h = fmaf(h, x, 1.0f / 720.0f);             // 1/6!
+        h = fmaf(h, x, 1.0f / 120.0f);             // 1/5!
+        h = fmaf(h, x, 1.0f / 24.0f);              // 1/4!
+        h = fmaf(h, x, 1.0f / 6.0f);               // 1/3!
+        h = fmaf(h, x, 0.5f);                      // 1/2!
+        h = fmaf(h, x, 1.0f);
+        return h * x;
+    }
+    return expm1f(x);
+}
 
 __global__ void bold_kernel(const float* __restrict__ series, int64_t NP, int64_t T, int decim, BoldDev c,
                             float* __restrict__ state, int reset, float* __restrict__ out)
@@ -53,11 +88,11 @@ __global__ void bold_kernel(const float* __restrict__ series, int64_t NP, int64_
     for (int64_t t = 0; t < T; ++t) {
         const float z = __ldg(series + t * NP + i);
         const float f = 1.0f + ft;
-        const float vpa_m1 = expm1f(log1pf(vt) * c.inv_alpha);                // v^(1/alpha) - 1
+        const float vpa_m1 = pow1p_m1(vt, c);                                 // v^(1/alpha) - 1
         // f E(f) / E0 - 1 = ft - (1 + ft) r_E0 expm1(-ln(1 - E0) ft / f), since
         // (1 - E0)^(1/f) = (1 - E0) exp(-ln(1 - E0) ft / f): exactly 0 at rest
         // (the argument of expm1 to 2 ulp)
-        const float fE_m1 = fmaf(-f * c.r_E0, expm1f(__fdividef(-c.lnE * ft, f)), ft);
+        const float fE_m1 = fmaf(-f * c.r_E0, expm1_small(__fdividef(-c.lnE * ft, f)), ft);
         // v^(1/alpha - 1) q - 1, with v^(1/alpha - 1) - 1 = (v^(1/alpha) - v) / v
         // = (vpa_m1 - vt) / (1 + vt) (no cancellation: vpa_m1 is about vt / alpha)
         const float vq_m1 = fmaf((vpa_m1 - vt) * __frcp_rn(1.0f + vt), 1.0f + qt, qt);
@@ -130,6 +165,25 @@ extern "C" tvbx_status tvbx_bold(const float* series, int32_t n_regions, int64_t
     c.k2 = (float)(p.eps * p.r0 * p.E0 * p.TE);
     c.k3 = (float)(1.0 - p.eps);
     c.dt = (float)(dt_ms * 1e-3);
+    // binomial coefficients of (1 + v)^a, a = 1 / alpha, and the largest
+    // |v| (a power of 2 from 1/4 down) at which the series beyond degree 8
+    // stays below 1e-8 of its first term a |v|
+    {
+        const double a = 1.0 / p.alpha;
+        double C[41];
+        C[0] = 1.0;
+        for (int k = 1; k <= 40; ++k) C[k] = C[k - 1] * (a - (k - 1)) / k;
+        for (int k = 0; k < 8; ++k) c.ca[k] = (float)C[k + 1];
+        c.v_series = 0.0f;
+        for (double vm = 0.25; vm >= 1.0 / 1024.0; vm *= 0.5) {
+            double tail = 0.0, pw = std::pow(vm, 9);
+            for (int k = 9; k <= 40; ++k, pw *= vm) tail += std::fabs(C[k]) * pw;
+            if (tail <= 1e-8 * std::fabs(a) * vm) {
+                c.v_series = (float)vm;
+                break;
+            }
+        }
+    }
     const int64_t NP = (int64_t)n_regions * n_sets;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     note_launch();
