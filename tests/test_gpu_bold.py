@@ -102,3 +102,26 @@ def test_phfcd_of_phase_locked_regions_and_bold_of_a_sweep(tvbx, oracle):
             continue
         ref, _ = B.bold(X[p].astype(np.float64), 1.0, 100)
         assert np.abs(Yb[:, :, p].T - ref).max() <= 1e-4 * max(np.abs(ref).max(), 1e-12)
+
+
+@pytest.mark.parametrize("alpha", [0.32, 0.2, 0.1])
+def test_bold_series_and_fallback_against_oracle(tvbx, alpha):
+    """The kernel takes v^(1/alpha) - 1 and the oxygen-extraction e^x - 1 by
+    series below bounds that depend on alpha (1/4 for alpha 0.32 and 0.2 --
+    an exact polynomial there --, 1/16 for alpha 0.1) and by log1p/expm1
+    above them. A drive ramp from rest to 1 kHz crosses both bounds; the BOLD
+    must follow the FP64 oracle within 1e-4 of its range throughout."""
+    import torch
+    T, N, P, decim = 12000, 3, 4, 20
+    t = np.arange(T, dtype=np.float64) / T
+    X = np.empty((T, N, P), np.float32)
+    for k in range(N):
+        for p in range(P):
+            X[:, k, p] = (1.0 * t ** (1 + k + p) * (1.0 + 0.1 * np.sin(40 * t + p))).astype(np.float32)
+    params = dict(B.BW_PARAMS, alpha=alpha)
+    Y = tvbx.bold(torch.from_numpy(X).cuda(), 1.0, decim, params=params).cpu().numpy()
+    for k in range(N):
+        for p in range(P):
+            ref, _ = B.bold(X[:, k, p][None, :].astype(np.float64), 1.0, decim, p=params)
+            scale = np.abs(ref).max()
+            assert np.abs(Y[:, k, p] - ref[0]).max() <= 1e-4 * scale, (alpha, k, p)
