@@ -136,14 +136,33 @@ static __device__ __forceinline__ uint32_t bf2(float lo, float hi)
 
 }  // namespace
 
+// Bounded wait that lets the hardware suspend the thread for up to ns
+// nanoseconds per attempt (the suspend-time hint of try_wait: the thread
+// resumes when the phase completes), instead of polling with sleeps in
+// between. Returns false after limit attempts.
+static __device__ __forceinline__ bool mbar_wait_hint(uint64_t* bar, uint32_t parity, uint32_t limit, uint32_t ns)
+{
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // Bounded wait by lane 0 of a warp, then the whole warp proceeds. After an
 // expiry (or once any wait of the CTA has expired) the wait is skipped: the
 // kernel then runs to its end without blocking and reports the error.
+// sleep_ns != 0 marks a wait that may be long: its attempts are
+// hardware-suspended for up to 1 us each (2^22 attempts bound it to seconds).
 static __device__ __forceinline__ void warp_wait(uint64_t* bar, uint32_t parity, uint32_t limit,
                                                  volatile int* abort, uint32_t* error, uint32_t sleep_ns = 0)
 {
     if ((threadIdx.x & 31) == 0 && !*abort &&
-        !(sleep_ns ? mbar_wait_sleep(bar, parity, limit, sleep_ns) : mbar_wait_bounded(bar, parity, limit))) {
+        !(sleep_ns ? mbar_wait_hint(bar, parity, limit, 1000u) : mbar_wait_bounded(bar, parity, limit))) {
         atomicOr(error, TVBX_DEVERR_TIMEOUT);
         *abort = 1;
     }
