@@ -298,9 +298,12 @@ __global__ void fc_shift_kernel(const float* __restrict__ series, const SeriesLa
     const int64_t Tn = t_end - t_begin;
     const int64_t n = Tn < 64 ? Tn : 64;
     float s = 0.0f;
-    for (int64_t q = 0; q < n; ++q) {
-        const int64_t t = t_begin + (q * Tn) / n;
-        s += series[series_index(sl, t, k, p)];
+    if (Tn <= (int64_t)(UINT32_MAX / 64)) {   // the same sample indices in 32-bit arithmetic
+        const uint32_t tn = (uint32_t)Tn, nn = (uint32_t)n;
+#pragma unroll 8
+        for (uint32_t q = 0; q < nn; ++q) s += series[series_index(sl, t_begin + (q * tn) / nn, k, p)];
+    } else {
+        for (int64_t q = 0; q < n; ++q) s += series[series_index(sl, t_begin + (q * Tn) / n, k, p)];
     }
     shift[o] = n > 0 ? s / (float)n : 0.0f;
 }
