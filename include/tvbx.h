@@ -213,9 +213,10 @@ typedef struct {
  *   FP32:    with FP32 CUDA-core FMAs;
  *   BF16:    on the tensor cores from Z rounded to BF16, FP32 accumulation;
  *   BF16X3:  split precision, Z = H + L with H, L in BF16, G = H H^T + H L^T
- *            + L H^T (two MMAs and a symmetrisation), FP32 accumulation;
+ *            + L H^T (three MMAs per K step; symmetric up to the FP32
+ *            accumulation), FP32 accumulation;
  *   TF32, TF32X3: the same with TF32 operands.
- * The tensor-core forms need n_regions <= 128; the row sums of Z use
+ * The tensor-core forms need n_regions <= 112; the row sums of Z use
  * compensated FP32 summation in every form. */
 #define TVBX_FC_FP32   0
 #define TVBX_FC_BF16   1
@@ -383,7 +384,7 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
  * into it before return; the pool keeps that memory for later calls until the
  * process exits. The call synchronises cuda_stream before it returns.
  * Errors: TVBX_E_INVALID_ARG (NULL series, sizes < 1, bad window, a
- * tensor-core precision with n_regions > 128), TVBX_E_OOM, TVBX_E_CUDA,
+ * tensor-core precision with n_regions > 112), TVBX_E_OOM, TVBX_E_CUDA,
  * TVBX_E_TIMEOUT (a bounded wait of the tensor-core kernel expired; the
  * outputs are then invalid), TVBX_E_UNSUPPORTED (unknown precision). */
 tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_sets, int64_t n_samples,

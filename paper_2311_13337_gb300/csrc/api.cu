@@ -1187,7 +1187,7 @@ tvbx_status tvbx_fc(tvbx_sweep* h, const tvbx_fc_cfg* cfg, int32_t mem, float* f
         return fail(TVBX_E_UNSUPPORTED, "FC precision %d", cfg->precision);
     if (cfg->precision != TVBX_FC_FP32 && h->cfg.series_mode != TVBX_SERIES_STREAM &&
         !fc_tc_supported(h->N, cfg->precision))
-        return fail(TVBX_E_INVALID_ARG, "tensor-core FC needs n_regions <= 128 (have %d)", h->N);
+        return fail(TVBX_E_INVALID_ARG, "tensor-core FC needs n_regions <= 112 (have %d)", h->N);
     if (cfg->fcd_window < 0) return fail(TVBX_E_INVALID_ARG, "fcd_window must be >= 0");
     int32_t nw = 0;
     tvbx_status st = run_fc(h, cfg->precision, cfg->fcd_window, cfg->fcd_step, &nw);
@@ -1252,7 +1252,7 @@ tvbx_status tvbx_fc_series(const float* series, int32_t n_regions, int64_t n_set
     if (cfg->precision < TVBX_FC_FP32 || cfg->precision > TVBX_FC_TF32X3)
         return fail(TVBX_E_UNSUPPORTED, "FC precision %d", cfg->precision);
     if (cfg->precision != TVBX_FC_FP32 && !fc_tc_supported(N, cfg->precision))
-        return fail(TVBX_E_INVALID_ARG, "tensor-core FC needs n_regions <= 128 (have %d)", N);
+        return fail(TVBX_E_INVALID_ARG, "tensor-core FC needs n_regions <= 112 (have %d)", N);
     if (cfg->precision == TVBX_FC_FP32 && N > 384) return fail(TVBX_E_INVALID_ARG, "FC needs n_regions <= 384");
     int32_t blk = 0, n_blocks = 1, m = 0, nw = 0;
     if (cfg->series_layout != TVBX_LAYOUT_TNP && cfg->series_layout != TVBX_LAYOUT_SET4)

@@ -180,8 +180,8 @@ def _to_set4(torch, x):
 def test_set_blocked_layout_gives_the_same_results(tvbx, torch, N, P, T, prec):
     """The FC stage reads a series in groups of 4 sets exactly as it reads the
     sets-fastest layout: every output bit-equal, FCD included."""
-    if prec != 0 and N > 128:
-        pytest.skip("tensor cores up to 128 regions")
+    if prec != 0 and N > 112:
+        pytest.skip("tensor cores up to 112 regions")
     x = _series(P, N, T, 40 + N + P, "rates")
     outs = []
     for layout, d in ((tvbx.LAYOUT_TNP, _to_device(torch, x)), (tvbx.LAYOUT_SET4, _to_set4(torch, x))):
@@ -194,3 +194,18 @@ def test_set_blocked_layout_gives_the_same_results(tvbx, torch, N, P, T, prec):
         outs.append((fc.cpu().numpy(), fcd.cpu().numpy(), chi.cpu().numpy()))
     for a, b in zip(*outs):
         assert np.array_equal(a, b, equal_nan=True)
+
+
+def test_tensor_core_region_limit(tvbx, torch, oracle):
+    """112 regions is the largest tensor-core shape (2 sets per CTA, 28 loader
+    warps): it matches the FP64 Pearson FC; 113 regions is refused before any
+    launch with the stated limit, and the FP32 form still takes it."""
+    x = _series(3, 112, 400, seed=23, kind="rates")
+    g = _run(tvbx, torch, x, 2)
+    assert np.abs(g["fc"] - oracle.fc_pearson(x)).max() <= TOL[2]
+    x = _series(3, 113, 200, seed=24, kind="rates")
+    with pytest.raises(tvbx.TvbxError) as e:
+        _run(tvbx, torch, x, 2)
+    assert "112" in str(e.value)
+    g = _run(tvbx, torch, x, 0)
+    assert np.abs(g["fc"] - oracle.fc_pearson(x)).max() <= TOL[0]
