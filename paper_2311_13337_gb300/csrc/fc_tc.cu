@@ -22,23 +22,25 @@
 // (t, k) row of the series: in the set-blocked layout the pieces of
 // neighbouring regions are adjacent, so a warp's 4 regions x 8 sample groups
 // read 8 segments of 64 bytes; in [T][N][P], 32 separate pieces) and all
-// their samples. Per chunk of 128
-// bytes of K (64 BF16 or 32 TF32 samples) each loader thread (k, j) copies
+// their samples. Per chunk of 128 bytes of K (64 BF16 or 32 TF32 samples)
+// each loader thread (k, j) copies
 // samples j*SPC .. j*SPC+SPC-1 of region k for the SC sets into its raw slot
 // in shared memory (cp.async). Once chunk c has landed the thread reads its
 // slot into registers and subtracts the shift, copies chunk c+1 into the same
-// slot (in flight during the conversion), splits into registers, and waits
-// only for the MMAs of chunk c-2 to release the operand stage it writes (two
-// stages, alternating by chunk), so the conversion of chunk c overlaps the
-// MMAs of chunk c-1; it writes one 16-byte piece of row k
-// of each operand buffer in the 128-byte swizzled K-major layout the MMA
-// reads. One lane of the MMA warp issues the MMAs (M = 128 rows, of which the
+// slot (in flight during the conversion), splits into registers (packed
+// f32x2 arithmetic for the BF16 forms), and waits only for the MMAs of chunk
+// c-2 to release the operand stage it writes (two stages, alternating by
+// chunk), so the conversion of chunk c overlaps the MMAs of chunk c-1; it
+// writes one 16-byte piece of row k of each operand buffer in the 128-byte
+// swizzled K-major layout the MMA reads. One lane of the MMA warp issues the MMAs (M = 128 rows, of which the
 // first N are regions; N_mma = N rounded up to 16) and commits them to the
 // stage's mbarrier. Shared memory: the two operand stages, (128 - R) rows of
-// 128 bytes (the A rows read beyond the last buffer), the raw slots. At the end of a block loader warps 0-3 read the
-// accumulator rows out of tensor memory (lane = region) and write them to
-// global memory as they are, while the other loader warps already stage the
-// next block's first chunk.
+// 128 bytes (the A rows read beyond the last buffer), the raw slots. At the
+// end of a block loader warps 0-3 read the accumulator rows out of tensor
+// memory (lane = region) and write their diagonal and upper triangle to
+// global memory, while the other loader warps already stage the next block's
+// first chunk. Waits that may be long suspend in hardware (try_wait with a
+// time hint) rather than poll.
 //
 // Rows N .. 127 of the A operand and N .. N_mma - 1 of the B operand are
 // whatever follows the buffer in shared memory (in bounds by construction);
