@@ -119,6 +119,132 @@ __global__ void bold_kernel(const float* __restrict__ series, int64_t NP, int64_
     }
 }
 
+// Two FP32 values in a 64-bit register pair and the packed f32x2 operations
+// of sm_100-class SMs (each lane rounds like the scalar instruction).
+static __device__ __forceinline__ uint64_t p2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+static __device__ __forceinline__ float2 u2(uint64_t v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+static __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+static __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+static __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+static __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// The same integration for two neighbouring (region, set) elements per
+// thread, i and i + 1 (i even; NP even, so every sample row starts 8-byte
+// aligned), in packed f32x2 arithmetic: the series of both powers run packed
+// when both lanes are inside their bounds, else lane by lane; the divisions
+// and the output are lane by lane.
+__global__ void bold_kernel2(const float* __restrict__ series, int64_t NP, int64_t T, int decim, BoldDev c,
+                             float* __restrict__ state, int reset, float* __restrict__ out)
+{
+    const int64_t i = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    if (i >= NP) return;
+    float2 s0 = make_float2(0.0f, 0.0f), f0 = s0, v0 = s0, q0 = s0;
+    if (state && !reset) {
+        s0 = *reinterpret_cast<const float2*>(state + i);
+        f0 = *reinterpret_cast<const float2*>(state + NP + i);
+        v0 = *reinterpret_cast<const float2*>(state + 2 * NP + i);
+        q0 = *reinterpret_cast<const float2*>(state + 3 * NP + i);
+    }
+    uint64_t s = p2(s0.x, s0.y), ft = p2(f0.x, f0.y), vt = p2(v0.x, v0.y), qt = p2(q0.x, q0.y);
+    const uint64_t one = p2(1.0f, 1.0f), m_kappa = p2(-c.kappa, -c.kappa), m_gamma = p2(-c.gamma, -c.gamma);
+    const uint64_t dt = p2(c.dt, c.dt), dtt = p2(c.dt * c.inv_tau, c.dt * c.inv_tau);
+    const uint64_t m_rE0 = p2(-c.r_E0, -c.r_E0);
+    uint64_t ca[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ca[k] = p2(c.ca[k], c.ca[k]);
+    int phase = 0;
+    int64_t o = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        const float2 zf = __ldg(reinterpret_cast<const float2*>(series + t * NP + i));
+        const uint64_t z = p2(zf.x, zf.y);
+        const uint64_t f = add2(one, ft);
+        const float2 vtf = u2(vt), ftf = u2(ft), ff = u2(f);
+        // v^(1/alpha) - 1
+        uint64_t vpa_m1;
+        if (fabsf(vtf.x) <= c.v_series && fabsf(vtf.y) <= c.v_series) {
+            uint64_t h = ca[7];
+#pragma unroll
+            for (int k = 6; k >= 0; --k) h = fma2(h, vt, ca[k]);
+            vpa_m1 = mul2(h, vt);
+        } else {
+            vpa_m1 = p2(pow1p_m1(vtf.x, c), pow1p_m1(vtf.y, c));
+        }
+        // e^x - 1 of the oxygen extraction, x = -ln(1 - E0) ft / f
+        const float x0 = __fdividef(-c.lnE * ftf.x, ff.x), x1 = __fdividef(-c.lnE * ftf.y, ff.y);
+        uint64_t em1;
+        if (fabsf(x0) <= 0.25f && fabsf(x1) <= 0.25f) {
+            const uint64_t x = p2(x0, x1);
+            uint64_t h = p2(1.0f / 40320.0f, 1.0f / 40320.0f);
+            h = fma2(h, x, p2(1.0f / 5040.0f, 1.0f / 5040.0f));
+            h = fma2(h, x, p2(1.0f / 720.0f, 1.0f / 720.0f));
+            h = fma2(h, x, p2(1.0f / 120.0f, 1.0f / 120.0f));
+            h = fma2(h, x, p2(1.0f / 24.0f, 1.0f / 24.0f));
+            h = fma2(h, x, p2(1.0f / 6.0f, 1.0f / 6.0f));
+            h = fma2(h, x, p2(0.5f, 0.5f));
+            h = fma2(h, x, one);
+            em1 = mul2(h, x);
+        } else {
+            em1 = p2(expm1_small(x0), expm1_small(x1));
+        }
+        const uint64_t fE_m1 = fma2(mul2(f, m_rE0), em1, ft);
+        const float2 w = u2(add2(one, vt));
+        const uint64_t rv = p2(__frcp_rn(w.x), __frcp_rn(w.y));
+        const uint64_t vq_m1 = fma2(mul2(sub2(vpa_m1, vt), rv), add2(one, qt), qt);
+        const uint64_t ds = fma2(m_gamma, ft, fma2(m_kappa, s, z));
+        const uint64_t nft = fma2(dt, s, ft);
+        const uint64_t nvt = fma2(dtt, sub2(ft, vpa_m1), vt);
+        const uint64_t nqt = fma2(dtt, sub2(fE_m1, vq_m1), qt);
+        s = fma2(dt, ds, s);
+        ft = nft;
+        vt = nvt;
+        qt = nqt;
+        if (++phase == decim) {
+            phase = 0;
+            const float2 a = u2(vt), b = u2(qt);
+            const float y0 = c.V0 * (c.k3 * -a.x + fmaf(c.k1, -b.x, c.k2 * (a.x - b.x) / (1.0f + a.x)));
+            const float y1 = c.V0 * (c.k3 * -a.y + fmaf(c.k1, -b.y, c.k2 * (a.y - b.y) / (1.0f + a.y)));
+            *reinterpret_cast<float2*>(out + o * NP + i) = make_float2(y0, y1);
+            ++o;
+        }
+    }
+    if (state) {
+        *reinterpret_cast<float2*>(state + i) = u2(s);
+        *reinterpret_cast<float2*>(state + NP + i) = u2(ft);
+        *reinterpret_cast<float2*>(state + 2 * NP + i) = u2(vt);
+        *reinterpret_cast<float2*>(state + 3 * NP + i) = u2(qt);
+    }
+}
+
 }  // namespace
 }  // namespace tvbx
 
@@ -187,8 +313,16 @@ extern "C" tvbx_status tvbx_bold(const float* series, int32_t n_regions, int64_t
     const int64_t NP = (int64_t)n_regions * n_sets;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     note_launch();
-    bold_kernel<<<(unsigned)((NP + 255) / 256), 256, 0, s>>>(series, NP, n_samples, decim, c, state, reset_state,
-                                                            bold_out);
+    // two elements per thread when every row of series, BOLD and state starts
+    // 8-byte aligned (NP even, 8-byte aligned buffers), else one
+    const bool pair = NP % 2 == 0 && (uintptr_t)series % 8 == 0 && (uintptr_t)bold_out % 8 == 0 &&
+                      (!state || (uintptr_t)state % 8 == 0);
+    if (pair)
+        bold_kernel2<<<(unsigned)((NP / 2 + 255) / 256), 256, 0, s>>>(series, NP, n_samples, decim, c, state,
+                                                                      reset_state, bold_out);
+    else
+        bold_kernel<<<(unsigned)((NP + 255) / 256), 256, 0, s>>>(series, NP, n_samples, decim, c, state, reset_state,
+                                                                bold_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return report_error(TVBX_E_CUDA, "BOLD: %s", cudaGetErrorString(e));
     return TVBX_OK;

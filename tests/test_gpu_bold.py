@@ -125,3 +125,22 @@ def test_bold_series_and_fallback_against_oracle(tvbx, alpha):
             ref, _ = B.bold(X[:, k, p][None, :].astype(np.float64), 1.0, decim, p=params)
             scale = np.abs(ref).max()
             assert np.abs(Y[:, k, p] - ref[0]).max() <= 1e-4 * scale, (alpha, k, p)
+
+
+def test_bold_odd_element_count_against_oracle(tvbx):
+    """n_regions x n_sets odd: the kernel of one element per thread (the
+    packed kernel takes two neighbouring elements and needs an even count);
+    against the oracle, and two halves with the state carried equal one
+    pass."""
+    import torch
+    T, N, P, decim = 8000, 3, 5, 40
+    X = _rates(T, N, P, seed=4)
+    Xd = torch.from_numpy(X).cuda()
+    Y = tvbx.bold(Xd, 1.0, decim).cpu().numpy()
+    for p in range(P):
+        ref, _ = B.bold(X[:, :, p].T.astype(np.float64), 1.0, decim)
+        assert np.abs(Y[:, :, p].T - ref).max() <= 1e-4 * np.abs(ref).max(), p
+    st = torch.zeros((4, N, P), dtype=torch.float32, device="cuda")
+    a = tvbx.bold(Xd[:T // 2], 1.0, decim, state=st, reset_state=True)
+    b = tvbx.bold(Xd[T // 2:], 1.0, decim, state=st, reset_state=False)
+    assert np.array_equal(torch.cat([a, b]).cpu().numpy(), Y)
