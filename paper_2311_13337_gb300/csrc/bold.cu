@@ -71,6 +71,15 @@ static __device__ __forceinline__ float expm1_small(float x)
     return expm1f(x);
 }
 
+// 1 / x by the SM's approximate reciprocal (about 1 ulp; x is the blood
+// volume 1 + (v - 1), near 1, so no denormals arise)
+static __device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __global__ void bold_kernel(const float* __restrict__ series, int64_t NP, int64_t T, int decim, BoldDev c,
                             float* __restrict__ state, int reset, float* __restrict__ out)
 {
@@ -95,7 +104,7 @@ __global__ void bold_kernel(const float* __restrict__ series, int64_t NP, int64_
         const float fE_m1 = fmaf(-f * c.r_E0, expm1_small(__fdividef(-c.lnE * ft, f)), ft);
         // v^(1/alpha - 1) q - 1, with v^(1/alpha - 1) - 1 = (v^(1/alpha) - v) / v
         // = (vpa_m1 - vt) / (1 + vt) (no cancellation: vpa_m1 is about vt / alpha)
-        const float vq_m1 = fmaf((vpa_m1 - vt) * __frcp_rn(1.0f + vt), 1.0f + qt, qt);
+        const float vq_m1 = fmaf((vpa_m1 - vt) * rcp_approx(1.0f + vt), 1.0f + qt, qt);
         const float ds = z - c.kappa * s - c.gamma * ft;
         const float nft = fmaf(c.dt, s, ft);
         const float nvt = fmaf(c.dt * c.inv_tau, ft - vpa_m1, vt);
@@ -218,7 +227,7 @@ __global__ void bold_kernel2(const float* __restrict__ series, int64_t NP, int64
         }
         const uint64_t fE_m1 = fma2(mul2(f, m_rE0), em1, ft);
         const float2 w = u2(add2(one, vt));
-        const uint64_t rv = p2(__frcp_rn(w.x), __frcp_rn(w.y));
+        const uint64_t rv = p2(rcp_approx(w.x), rcp_approx(w.y));
         const uint64_t vq_m1 = fma2(mul2(sub2(vpa_m1, vt), rv), add2(one, qt), qt);
         const uint64_t ds = fma2(m_gamma, ft, fma2(m_kappa, s, z));
         const uint64_t nft = fma2(dt, s, ft);
