@@ -54,7 +54,7 @@ static __device__ __forceinline__ float pow1p_m1(float v, const BoldDev& c)
 }
 
 // e^x - 1 for |x| <= 1/4 by its Taylor series to degree 8 (the rest is below
-// 1.1e-11 of the first term), else expm1f
+// 4.4e-11 of the first term: about x^8 / 9!), else expm1f
 static __device__ __forceinline__ float expm1_small(float x)
 {
     if (fabsf(x) <= 0.25f) {
