@@ -8,8 +8,10 @@
 // rounding of L) in BF16 or TF32; the "x3" modes form the three-product
 // split-precision Gram matrix
 //   G = H H^T + H L^T + L H^T
-// with three MMAs per K step (the L L^T term is below the FP32 rounding of
-// G). The single modes use G = H H^T. Both are symmetric up to the rounding
+// with three MMAs per K step. The L L^T term left out, like the rounding of L
+// itself, is about 2^-16 of G in the BF16 forms (2^-22 in TF32), so the x3
+// forms reach a few 1e-6 in the FC, not FP32 rounding. The single modes use
+// G = H H^T. Both are symmetric up to the rounding
 // of the accumulation, so readers take the upper triangle.
 // Accumulation is FP32 throughout. The row sums s[k] = sum_t Z[k][t] use
 // compensated (Kahan) FP32 summation in the loading threads.
