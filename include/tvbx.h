@@ -216,8 +216,10 @@ typedef struct {
  *            + L H^T (three MMAs per K step; symmetric up to the FP32
  *            accumulation), FP32 accumulation;
  *   TF32, TF32X3: the same with TF32 operands.
- * The tensor-core forms need n_regions <= 112; the row sums of Z use
- * compensated FP32 summation in every form. */
+ * The tensor-core forms need n_regions <= 112. The row sums of Z use
+ * compensated FP32 summation in the tensor-core forms and plain FP32 sums in
+ * the FP32 form (the shifted rows sum to near zero, so either error is far
+ * below that of the Gram matrix). */
 #define TVBX_FC_FP32   0
 #define TVBX_FC_BF16   1
 #define TVBX_FC_BF16X3 2
