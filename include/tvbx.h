@@ -638,8 +638,8 @@ tvbx_status tvbx_series_analysis(const float* series, int32_t n_regions, int64_t
  *   y = V0 (k1 (1 - q) + k2 (1 - q/v) + k3 (1 - v)),
  *   k1 = 4.3 theta0 E0 TE, k2 = eps r0 E0 TE, k3 = 1 - eps;
  * one step per rate sample (dt_ms), one BOLD value after every `decim`
- * steps. series: DEVICE [n_samples][n_regions][n_sets] (the engine's layout,
- * e.g. a stretch of rates the caller keeps); bold_out: DEVICE
+ * steps. series: DEVICE [n_samples][n_regions][n_sets] (sets fastest, as
+ * TVBX_LAYOUT_TNP, e.g. a stretch of rates the caller keeps); bold_out: DEVICE
  * [n_samples / decim][n_regions][n_sets]; state: DEVICE [4][n_regions]
  * [n_sets] = (s, f - 1, v - 1, q - 1), nullable; with reset_state = 1 (or no
  * state) the integration starts at rest, otherwise from *state, and the final

@@ -88,7 +88,7 @@ def test_phfcd_of_phase_locked_regions_and_bold_of_a_sweep(tvbx, oracle):
     Y = np.stack([np.cos(2 * np.pi * 0.03 * t + ph) for ph in (0.0, 0.4, 1.1)], axis=1)[:, :, None]
     out, Tp = tvbx.phfcd(torch.from_numpy(Y.astype(np.float32)).cuda(), tr, 0.008, 0.08, 4)
     assert np.abs(out.cpu().numpy() - 1.0).max() <= 1e-5
-    # a sweep's rates through BOLD (the engine's layout) equal the oracle's BOLD of the same rates
+    # a sweep's rates through BOLD ([T][N][P], sets fastest) equal the oracle's BOLD of the same rates
     W, L = synth.connectome(68)
     pts = oracle.expand_grid([("g", [0.1, 0.5]), ("b_e", [0.0, 60.0])])
     sw = tvbx.Sweep(W, L, points=pts)

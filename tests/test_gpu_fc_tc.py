@@ -42,7 +42,7 @@ def _series(P, N, T, seed, kind):
 
 
 def _to_device(torch, x):
-    # engine layout [T][N][P], FP32
+    # [T][N][P] (sets fastest, TVBX_LAYOUT_TNP), FP32
     return torch.from_numpy(np.ascontiguousarray(np.transpose(x, (2, 1, 0))).astype(np.float32)).cuda()
 
 
