@@ -282,7 +282,7 @@ __global__ void gather_u32_kernel(const uint32_t* __restrict__ in, uint32_t* __r
          i += (int64_t)gridDim.x * blockDim.x)
         out[perm[i]] = in[i];
 }
-// series [T][N][P] (internal order) -> out [np][N][nt] for external sets
+// series in layout sl (internal set order) -> out [np][N][nt] for external sets
 // [p0, p0 + np) and samples [t0, t0 + nt); inv maps external -> internal.
 __global__ void series_export_kernel(const float* __restrict__ X, const SeriesLayout sl, float* __restrict__ out,
                                      const int64_t* __restrict__ inv, int32_t N, int64_t p0, int64_t np, int64_t t0,

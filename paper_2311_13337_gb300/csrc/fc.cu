@@ -2,16 +2,16 @@
 // Sec. "Output": the FC is obtained from the covariance of the simulated
 // series; Eq. 6: Pearson correlation; Table 2 "mean_FC").
 //
-// The E series is stored [T][N][P] (sets fastest). For each set the kernels
+// The E series is read through a SeriesLayout: the engine's set-blocked
+// [P/4][T][N][4] or the sets-fastest [T][N][P]. For each set the kernels
 // form block moments over the samples [t_begin, t_end):
 //   G_b[k][j] = sum_{t in block b} (x_k(t) - m_k)(x_j(t) - m_j),
 //   s_b[k]    = sum_{t in block b} (x_k(t) - m_k),
 // with the shift m_k = the running mean kept by the simulation, or a given
 // shift (any shift is exact; a close one avoids cancellation). The covariance over a union of
-// blocks of length L is sum G_b - (sum s_b)(sum s_b)^T / L. The tensor-core
-// producer leaves G_b unsymmetric in its split forms, so the readers take
-// (G_b + G_b^T) / 2 for each pair (k, j), which also makes the FC exactly
-// symmetric.
+// blocks of length L is sum G_b - (sum s_b)(sum s_b)^T / L. Every producer's
+// G_b is symmetric up to FP32 rounding, so the readers take the diagonal and
+// the upper triangle (k < j) and write the FC symmetric.
 
 #include <algorithm>
 
